@@ -1,0 +1,130 @@
+"""Oracle: the discrete Stokes system on one level (test infrastructure).
+
+Builds the block system of Sec. 3 (the linear system with matrix
+K = [A B^T; B -C] and right-hand side (f, g)) from the assembled operators of
+oracle.fem, with the Dirichlet velocity nodes eliminated (Sec. 2.1: the
+velocity space carries the boundary condition, the pressure is free at every
+node).  Vectors are kept as u: (3, n_u) over the free velocity nodes and
+p: (n_p,) over all nodes of the level.
+
+Readings where the paper is silent:
+  * right-hand side: the body force enters through its nodal interpolant,
+    f_h = M I_h f and g_h = sum_d G_d (I_h f)_d, integrated exactly;
+  * inhomogeneous Dirichlet data u_D is lifted: f <- f - A_{I,D} u_D,
+    g <- g - B_{.,D} u_D;
+  * pure-Dirichlet problems: g is projected onto the range of K by removing
+    its Euclidean mean (the null vector of K is (0, 1)), and the pressure is
+    normalised by sum_i m_i p_i = 0 (the discrete L^2_0 condition, Sec. 2).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import fem
+from .mesh import RefinedMesh, refine
+
+
+@dataclass
+class StokesLevel:
+    mesh: RefinedMesh
+    ops: fem.Operators
+    free: np.ndarray        # indices of free velocity nodes
+    dir: np.ndarray         # indices of Dirichlet velocity nodes
+    A: sp.csr_matrix        # A restricted to free x free
+    A_diag: np.ndarray
+    B: list                 # B_d restricted to (all pressure) x free
+    BT: list                # transposes
+    C: sp.csr_matrix
+    C_diag: np.ndarray
+    m: np.ndarray           # lumped pressure mass
+    pure_dirichlet: bool
+
+    @property
+    def n_u(self) -> int:
+        return len(self.free)
+
+    @property
+    def n_p(self) -> int:
+        return self.mesh.n_nodes
+
+    @property
+    def n_dofs(self) -> int:
+        return 3 * self.n_u + self.n_p
+
+    # --- the operator K and the residual (Sec. 3) --------------------------
+    def apply(self, u: np.ndarray, p: np.ndarray):
+        """K (u, p) = (A u_d + B_d^T p,  sum_d B_d u_d - C p)."""
+        ru = np.stack([self.A @ u[d] + self.BT[d] @ p for d in range(3)])
+        rp = sum(self.B[d] @ u[d] for d in range(3)) - self.C @ p
+        return ru, rp
+
+    def residual(self, u, p, f, g):
+        """(f, g) - K (u, p)."""
+        ku, kp = self.apply(u, p)
+        return f - ku, g - kp
+
+    @staticmethod
+    def norm(ru, rp) -> float:
+        """Euclidean norm over all free DoFs (Sec. 3.6)."""
+        return float(np.sqrt(np.sum(ru * ru) + np.sum(rp * rp)))
+
+    def project_pressure(self, p: np.ndarray) -> np.ndarray:
+        """Remove the m-weighted mean so that sum_i m_i p_i = 0."""
+        if not self.pure_dirichlet:
+            return p
+        return p - np.dot(self.m, p) / self.m.sum()
+
+    # --- right-hand side ----------------------------------------------------
+    def rhs(self, f_nodal=None, u_dirichlet=None):
+        """(f, g) for nodal body force f_nodal (n, 3) and boundary data u_dirichlet (n, 3)."""
+        n = self.mesh.n_nodes
+        fn = np.zeros((n, 3)) if f_nodal is None else np.asarray(f_nodal, float)
+        fu = np.stack([(self.ops.M @ fn[:, d])[self.free] for d in range(3)])
+        g = sum(self.ops.G[d] @ fn[:, d] for d in range(3))
+        if u_dirichlet is not None:
+            uD = np.asarray(u_dirichlet, float)
+            for d in range(3):
+                vd = uD[self.dir, d]
+                fu[d] -= self.ops.A[self.free][:, self.dir] @ vd
+                g = g - self.ops.B[d][:, self.dir] @ vd
+        if self.pure_dirichlet:
+            g = g - g.mean()
+        return fu, g
+
+    def scatter(self, u: np.ndarray, u_dirichlet=None) -> np.ndarray:
+        """Full nodal velocity (n, 3) from free values (3, n_u) and boundary data."""
+        out = np.zeros((self.mesh.n_nodes, 3))
+        if u_dirichlet is not None:
+            out[self.dir] = np.asarray(u_dirichlet)[self.dir]
+        out[self.free] = u.T
+        return out
+
+
+def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0) -> StokesLevel:
+    ops = fem.assemble(mesh, nu=nu, delta=delta)
+    free = np.where(mesh.free_velocity)[0]
+    dirn = np.where(~mesh.free_velocity)[0]
+    A = ops.A[free][:, free].tocsr()
+    B = [ops.B[d][:, free].tocsr() for d in range(3)]
+    return StokesLevel(mesh=mesh, ops=ops, free=free, dir=dirn, A=A, A_diag=A.diagonal().copy(),
+                       B=B, BT=[b.T.tocsr() for b in B], C=ops.C, C_diag=ops.C.diagonal().copy(),
+                       m=ops.m, pure_dirichlet=not mesh.has_outflow)
+
+
+def build_from_macro(macro, level: int, nu: float = 1.0, delta: float = 1.0 / 12.0) -> StokesLevel:
+    mesh = refine(macro.vertices, macro.tets, macro.bc_flags, level, spacing=macro.spacing)
+    return build_level(mesh, nu=nu, delta=delta)
+
+
+def full_matrix(L: StokesLevel) -> sp.csr_matrix:
+    """K as one sparse matrix, unknown order (u_0, u_1, u_2, p)."""
+    Z = [[None] * 4 for _ in range(4)]
+    for d in range(3):
+        Z[d][d] = L.A
+        Z[d][3] = L.BT[d]
+        Z[3][d] = L.B[d]
+    Z[3][3] = -L.C
+    return sp.bmat(Z, format="csr")

@@ -1,0 +1,118 @@
+"""Pins of the oracle mesh (uniform refinement, Sec. 2.1 and Sec. 4).
+
+The refinement is checked against facts that do not come from its own code:
+node and element counts of a regular refinement, positive equal volumes,
+conformity (every interior face shared by exactly two elements), the surface
+area of the domain, the Kuhn-lattice structure of the refined cube, and the
+free-DoF counts the paper prints.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import analysis, mesh as M
+from oracle.fem import element_geometry
+
+
+def _faces(tets):
+    f = np.concatenate([np.sort(tets[:, [a, b, c]], axis=1) for a, b, c in itertools.combinations(range(4), 3)])
+    uniq, counts = np.unique(f, axis=0, return_counts=True)
+    return uniq, counts
+
+
+@pytest.mark.parametrize("level", [0, 1, 2, 3, 4])
+def test_cube_counts_and_volumes(level):
+    cube = W.unit_cube()
+    m = M.refine(cube.vertices, cube.tets, cube.bc_flags, level)
+    n = 1 << level
+    assert m.n_nodes == (n + 1) ** 3
+    assert len(m.tets) == 6 * n ** 3
+    vol, _ = element_geometry(m.xyz, m.tets)
+    assert np.allclose(vol, (1.0 / n) ** 3 / 6.0, rtol=1e-12)
+    assert abs(vol.sum() - 1.0) < 1e-12
+    # Dirichlet nodes = boundary of the cube
+    on_bnd = np.any((m.xyz == 0.0) | (m.xyz == 1.0), axis=1)
+    assert np.array_equal(on_bnd, m.on_dirichlet)
+
+
+@pytest.mark.parametrize("macro_name,level", [("cube", 3), ("channel", 1)])
+def test_conformity_and_surface(macro_name, level):
+    macro = W.unit_cube() if macro_name == "cube" else W.obstacle_channel()
+    m = M.refine(macro.vertices, macro.tets, macro.bc_flags, level)
+    faces, counts = _faces(m.tets)
+    assert set(np.unique(counts)) <= {1, 2}
+    bf = faces[counts == 1]
+    P = m.xyz[bf]
+    area = 0.5 * np.linalg.norm(np.cross(P[:, 1] - P[:, 0], P[:, 2] - P[:, 0]), axis=1).sum()
+    if macro_name == "cube":
+        expect = 6.0
+    else:
+        # box surface plus the exposed faces of the obstacle cubes
+        nx, ny, nz = macro.cells
+        expect = 2 * (nx * ny + ny * nz + nx * nz)
+        rem = set(macro.removed)
+        for c in rem:
+            for d in range(3):
+                for s in (-1, 1):
+                    nb = list(c)
+                    nb[d] += s
+                    if tuple(nb) not in rem:
+                        expect += 1
+    assert abs(area - expect) < 1e-9
+
+
+def test_cube_is_kuhn_lattice():
+    """Every fine tet of the refined 6-tet cube is a Kuhn tetrahedron of a lattice
+    cell: sorted by coordinate sum, its edge steps are h times a permutation of e1, e2, e3."""
+    cube = W.unit_cube()
+    m = M.refine(cube.vertices, cube.tets, cube.bc_flags, 3)
+    ijk = m.ijk[m.tets]                       # (nT, 4, 3)
+    order = np.argsort(ijk.sum(axis=2), axis=1)
+    s = np.take_along_axis(ijk, order[:, :, None], axis=1)
+    steps = np.diff(s, axis=1)                # (nT, 3, 3)
+    assert np.all(np.sort(steps.reshape(-1, 9), axis=1) == np.array([0] * 6 + [1] * 3))
+    assert np.all(np.abs(np.linalg.det(steps.astype(float))) == 1.0)
+
+
+def test_free_dofs_match_paper(golden):
+    """Free DoF counts (3 x interior velocity nodes + all pressure nodes) of the
+    refined mesh equal the closed form and round to the paper's printed values."""
+    cube = W.unit_cube()
+    for level in (2, 3, 4):
+        m = M.refine(cube.vertices, cube.tets, cube.bc_flags, level)
+        assert 3 * m.free_velocity.sum() + m.n_nodes == analysis.cube_free_dofs(level)
+    for row in golden["itertime1_umg"]["rows"]:
+        ours = analysis.cube_free_dofs(row["L"] + 2)
+        printed = row["dofs"]
+        # printed with two significant digits; the table truncates some rows
+        # (8.29e6 -> 8.2e6) and rounds others (1.25e5 -> 1.3e5)
+        scale = 10 ** np.floor(np.log10(ours))
+        mant = ours / scale
+        candidates = {np.floor(mant * 10) / 10 * scale, np.round(mant * 10) / 10 * scale}
+        assert any(c == pytest.approx(printed, rel=1e-12) for c in candidates)
+    cg = golden["coarse_grid_dofs"]
+    m = M.refine(cube.vertices, cube.tets, cube.bc_flags, 2)
+    assert 3 * m.free_velocity.sum() == cg["velocity"]
+    assert 3 * m.free_velocity.sum() + m.n_nodes == cg["coupled"]
+
+
+def test_channel_obstacles():
+    ch = W.obstacle_channel(seed=0)
+    assert len(ch.removed) == 6
+    for i, j, k in ch.removed:
+        assert 1 <= i <= 14 and 1 <= j <= 2 and 1 <= k <= 2
+    assert len(ch.tets) == 6 * (16 * 4 * 4 - 6)
+    m = M.refine(ch.vertices, ch.tets, ch.bc_flags, 2)
+    # no node strictly inside a removed cube
+    for c in ch.removed:
+        inside = np.all((m.xyz > np.array(c)) & (m.xyz < np.array(c) + 1), axis=1)
+        assert not inside.any()
+    # outflow face x = 16 is natural except for its no-slip rim
+    on_x16 = np.isclose(m.xyz[:, 0], 16.0)
+    rim = on_x16 & (np.isclose(m.xyz[:, 1], 0) | np.isclose(m.xyz[:, 1], 4) |
+                    np.isclose(m.xyz[:, 2], 0) | np.isclose(m.xyz[:, 2], 4))
+    assert np.array_equal(m.on_outflow, on_x16 & ~rim)
+    assert np.all(m.on_dirichlet[rim])
+    assert m.on_outflow.sum() == 15 * 15

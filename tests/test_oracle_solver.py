@@ -1,0 +1,217 @@
+"""Pins of the oracle's solver: smoother, transfers, coarse solver, cycle, stop rule.
+
+Each pin ties the oracle to something outside itself:
+  * the colouring has no same-colour coupling in A, C or the mesh graph;
+  * the colour sweep equals a brute-force node-by-node Gauss-Seidel loop;
+  * CG and MINRES equal scipy's on fixed linear preconditioners;
+  * the Uzawa smoother alone converges to the direct solution (fixed point);
+  * the V_var cycle converges to the direct solution and contracts by about
+    0.1 per cycle (paper: 8-9 cycles to 1e-8, Tab. "itertime1");
+  * the manufactured solution of Sec. 5 is approximated with O(h^2) velocity
+    error;
+  * converged solutions satisfy sum m_i p_i = 0 and exact discrete mass
+    conservation through the outflow (b(u_h, 1) = 0 with c(1, .) = g(1) = 0);
+  * instrumented operator counts reproduce the paper's weighted counts
+    (Sec. 4.2) and the memory model reproduces its 13.63 GB (Sec. 4.1);
+  * the adjoint gradient equals finite differences of the direct solution.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as sla
+
+import workloads as W
+from oracle import adjoint, analysis, direct, krylov, multigrid as MG, stokes as S
+
+
+@pytest.fixture(scope="module")
+def cube3():
+    H = MG.build_hierarchy(W.unit_cube(), 3)
+    L = H.levels[3]
+    x = L.mesh.xyz
+    f, g = L.rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    return H, f, g
+
+
+@pytest.mark.parametrize("macro_name,levels", [("cube", (2, 3, 4)), ("channel", (0, 1, 2))])
+def test_colouring_valid(macro_name, levels):
+    macro = W.unit_cube() if macro_name == "cube" else W.obstacle_channel()
+    for l in levels:
+        assert MG.colouring_is_valid(S.build_from_macro(macro, l))
+
+
+def test_colour_sweep_equals_sequential_gs():
+    H = MG.build_hierarchy(W.unit_cube(), 2)
+    L = H.levels[2]
+    rng = np.random.default_rng(5)
+    x0 = rng.standard_normal(L.n_u)
+    rhs = rng.standard_normal(L.n_u)
+    x = MG._gs_sweep(L.A, L.A_diag, x0.copy(), rhs, H.colours_u[2], (0, 1, 2, 3))
+    # brute force: visit nodes one by one in colour order, then by index
+    Ad = L.A.toarray()
+    y = x0.copy()
+    col = MG.colour_of(L)[L.free]
+    for c in (0, 1, 2, 3):
+        for i in np.where(col == c)[0]:
+            y[i] += (rhs[i] - Ad[i] @ y) / Ad[i, i]
+    np.testing.assert_allclose(x, y, rtol=1e-13, atol=1e-13)
+
+
+def test_cg_and_minres_match_scipy():
+    rng = np.random.default_rng(0)
+    L = S.build_from_macro(W.unit_cube(), 2)
+    K = S.full_matrix(L)
+    # regularise the pressure null space so the system is non-singular
+    K = K - sp.diags(np.r_[np.zeros(3 * L.n_u), 1e-3 * L.m])
+    dvec = np.r_[np.tile(L.A_diag, 3), L.m]
+    b = rng.standard_normal(K.shape[0])
+    for k in (1, 2, 5, 17):
+        x = krylov.pminres(lambda v: K @ v, b, lambda v: v / dvec, k, 0.0)
+        xs, _ = sla.minres(K, b, M=sp.diags(1 / dvec), maxiter=k, rtol=0.0)
+        np.testing.assert_allclose(x, xs, rtol=1e-10, atol=1e-12 * np.abs(xs).max())
+        y = krylov.cg(lambda v: L.A @ v, b[:L.n_u], k, 0.0)
+        ys, _ = sla.cg(L.A, b[:L.n_u], maxiter=k, rtol=0.0)
+        np.testing.assert_allclose(y, ys, rtol=1e-10, atol=1e-12 * np.abs(ys).max())
+
+
+def test_uzawa_smoother_fixed_point():
+    H = MG.build_hierarchy(W.unit_cube(), 2)
+    L = H.levels[2]
+    x = L.mesh.xyz
+    f, g = L.rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    ud, pd = direct.solve_direct(L, f, g)
+    u = np.zeros((3, L.n_u))
+    p = np.zeros(L.n_p)
+    for _ in range(3000):
+        MG.uzawa_step(H, 2, u, p, f, g)
+    p = L.project_pressure(p)
+    assert np.abs(u - ud).max() <= 1e-8 * np.abs(ud).max()
+    assert np.abs(p - pd).max() <= 1e-8 * np.abs(pd).max()
+
+
+def test_vcycle_converges_to_direct(cube3):
+    H, f, g = cube3
+    L = H.levels[3]
+    res = MG.solve(H, f, g, tol=1e-14, max_cycles=40)
+    ud, pd = direct.solve_direct(L, f, g)
+    assert np.abs(res.u - ud).max() <= 1e-10 * np.abs(ud).max()
+    assert np.abs(res.p - pd).max() <= 1e-10 * np.abs(pd).max()
+    assert abs(np.dot(L.m, res.p)) <= 1e-12 * np.abs(res.p).max()
+    # discrete divergence equation holds to the tolerance level
+    rp = L.residual(res.u, res.p, f, g)[1]
+    assert np.linalg.norm(rp) <= 1e-12 * np.linalg.norm(g)
+
+
+def test_cycle_count_and_contraction(golden):
+    """Paper protocol at level 4 (paper L = 2): f = 0, random initial guess;
+    the paper needs 9 cycles (Tab. 'itertime1').  The ordering differs, so the
+    pin is soft: 7..11 cycles and average contraction below 0.15."""
+    H = MG.build_hierarchy(W.unit_cube(), 4)
+    L = H.levels[4]
+    h_min = (L.mesh.h ** 3 / 6.0) ** (1.0 / 3.0)
+    u0, p0 = W.random_initial_guess(L.mesh.n_nodes, h_min, seed=0)
+    f, g = L.rhs(None, None)
+    res = MG.solve(H, f, g, u0=u0[L.free].T, p0=p0, tol=1e-8, max_cycles=30)
+    paper = golden["itertime1_umg"]["rows"][0]
+    assert paper["L"] == 2
+    assert abs(res.cycles - paper["iter"]) <= 2
+    rho = res.history[-1] ** (1.0 / res.cycles)
+    assert rho < 0.15
+
+
+@pytest.mark.slow
+def test_manufactured_solution_order():
+    errs_u, errs_p = [], []
+    for l in (3, 4, 5):
+        H = MG.build_hierarchy(W.unit_cube(), l)
+        L = H.levels[l]
+        x = L.mesh.xyz
+        f, g = L.rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+        res = MG.solve(H, f, g, tol=1e-10, max_cycles=30)
+        h3 = L.mesh.h ** 3
+        errs_u.append(np.sqrt(h3 * np.sum((res.u - W.manufactured_velocity(x)[L.free].T) ** 2)))
+        errs_p.append(np.sqrt(h3 * np.sum((res.p - W.manufactured_pressure(x)) ** 2)))
+    ru = np.array(errs_u[:-1]) / np.array(errs_u[1:])
+    rp = np.array(errs_p[:-1]) / np.array(errs_p[1:])
+    assert np.all(ru > 3.5), ru          # O(h^2): ratio -> 4
+    assert np.all(rp > 2.0), rp          # O(h) or better
+
+
+def test_channel_mass_conservation():
+    """With an outflow, q = 1 is a pressure test function; c(1, p) = 0 and
+    g(1) = 0 for f = 0, so the discrete flux out equals the flux of the
+    interpolated inflow exactly (up to the solver tolerance)."""
+    ch = W.obstacle_channel()
+    H = MG.build_hierarchy(ch, 2, coarsest=1, opt=MG.Options(coarse_minres_max=300))
+    L = H.levels[2]
+    uD = W.channel_inflow(L.mesh.xyz)
+    f, g = L.rhs(None, uD)
+    res = MG.solve(H, f, g, tol=1e-12, max_cycles=60)
+    assert res.history[-1] <= 1e-12
+    flux_out = adjoint.functional(L, res.u, uD)
+    # flux in of the interpolated inflow: sum_i (B_0 u_D)_i = -int d_x u_D
+    # = -int_{x=0} u_D . n = +int_{x=0} u_D,x  (u_D vanishes on every other face)
+    full = np.zeros(L.mesh.n_nodes)
+    full[L.dir] = uD[L.dir, 0]
+    flux_in = float(np.sum(L.ops.B[0] @ full))
+    # sum_i (B u_h)_i = -int div u_h = b(u_h, 1) = 0
+    u_full = L.scatter(res.u, uD)
+    total = sum(float(np.sum(L.ops.B[d] @ u_full[:, d])) for d in range(3))
+    assert abs(total) <= 1e-10 * abs(flux_out)
+    assert flux_out == pytest.approx(flux_in, rel=1e-9)
+
+
+def test_operator_counts_match_paper(golden):
+    ref = golden["operator_counts_L6"]
+    L = ref["L"]
+    H = MG.build_hierarchy(W.unit_cube(), L, coarsest=0)
+    H.counts = {}
+    Lf = H.levels[L]
+    u = np.zeros((3, Lf.n_u))
+    p = np.zeros(Lf.n_p)
+    f = np.ones((3, Lf.n_u))
+    g = np.zeros(Lf.n_p)
+    MG.vcycle(H, L, u, p, f, g)
+    for op in ("A", "B", "C"):
+        n = analysis.weighted_count({l: c[op] for l, c in H.counts.items()}, L, ref["n_I"])
+        assert round(n, 2) == pytest.approx(ref[op], abs=0.011), (op, n)
+
+
+def test_memory_model_matches_paper(golden):
+    ref = golden["memory_L7"]
+    n = analysis.cube_free_dofs(ref["L"] + 2)
+    m = analysis.memory_bytes(n, ref["L"] + 1)
+    # the paper's 13.63 GB is reproduced to 0.5 % (GiB reading; see the design notes)
+    assert m / 2 ** 30 == pytest.approx(ref["theory_GB"], rel=5e-3)
+
+
+def test_plain_outflow_flux_has_zero_gradient():
+    """The unweighted outflow flux is fixed by the inflow data (mass conservation)."""
+    ch = W.obstacle_channel()
+    L = S.build_from_macro(ch, 1)
+    n = L.mesh.n_nodes
+    uD = W.channel_inflow(L.mesh.xyz)
+    f0 = W.random_body_force(n, seed=1)
+    j0 = adjoint.functional_direct(L, None, uD)
+    j1 = adjoint.functional_direct(L, f0, uD)
+    assert j1 == pytest.approx(j0, rel=1e-10)
+    grad = adjoint.gradient_direct(L)
+    ref = np.abs(adjoint.gradient_direct(L, W.outflow_flux_weight(L.mesh.xyz))).max()
+    assert np.abs(grad).max() <= 1e-9 * ref
+
+
+def test_adjoint_gradient_matches_finite_differences():
+    ch = W.obstacle_channel()
+    L = S.build_from_macro(ch, 1)
+    n = L.mesh.n_nodes
+    uD = W.channel_inflow(L.mesh.xyz)
+    psi = W.outflow_flux_weight(L.mesh.xyz)
+    f0 = W.random_body_force(n, seed=1)
+    grad = adjoint.gradient_direct(L, psi)
+    dirs = W.random_directions(n, count=4, seed=2)
+    eps = 1.0   # J is affine in f: any step is exact up to roundoff, a large one damps it
+    for d in dirs:
+        jp = adjoint.functional_direct(L, f0 + eps * d, uD, psi)
+        jm = adjoint.functional_direct(L, f0 - eps * d, uD, psi)
+        fd = (jp - jm) / (2 * eps)
+        assert fd == pytest.approx(float(np.sum(grad * d)), rel=1e-8)
