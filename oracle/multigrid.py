@@ -222,7 +222,9 @@ def coarse_solve(H: Hierarchy, f, g, history=None):
 def vcycle(H: Hierarchy, l: int, u, p, f, g):
     """One V_var cycle on level l, in place on (u, p)."""
     if l == H.coarsest:
-        cu, cp = coarse_solve(H, f, g)
+        # correction from the residual equation (inside a cycle u = p = 0 here)
+        ru, rp = H.levels[l].residual(u, p, f, g)
+        cu, cp = coarse_solve(H, ru, rp)
         u += cu
         p += cp
         return u, p
