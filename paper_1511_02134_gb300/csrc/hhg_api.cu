@@ -1,0 +1,1020 @@
+// C ABI of the solver (include/hhg_stokes.h): hierarchy set-up, the V_var
+// cycle driver (Sec. 3.3-3.6), FP64 and FP32-in-FP64-refinement solves, the
+// adjoint gradient, and step-level hooks for parity tests.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hhg_stokes.h"
+#include "hhg_kernels.h"
+#include "hhg_lattice.h"
+
+using namespace hhg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct LevelHost {
+  int level = 0;
+  LevelShape sh{};
+  int64_t px = 0, py = 0, pz = 0, nalloc = 0;
+  double h = 0, hT2 = 0;
+  std::vector<uint8_t> flags;  // lattice order
+  uint8_t* d_flags = nullptr;
+  int64_t n_vel = 0, n_pres = 0;
+  double* mem64 = nullptr;
+  float* mem32 = nullptr;
+  LevelDev<double> d64{};
+  LevelDev<float> d32{};
+};
+
+template <class T>
+void bind_fields(LevelDev<T>& L, T* base, int64_t nalloc) {
+  for (int d = 0; d < 3; ++d) {
+    L.u[d] = base + (int64_t)d * nalloc;
+    L.f[d] = base + (int64_t)(4 + d) * nalloc;
+    L.r[d] = base + (int64_t)(8 + d) * nalloc;
+  }
+  L.p = base + 3 * nalloc;
+  L.g = base + 7 * nalloc;
+  L.rp = base + 11 * nalloc;
+}
+
+}  // namespace
+
+struct hhg_mesh {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  hhg_options opt{};
+  MacroLattice macro;
+  int finest = 0, coarsest = 0;
+  std::vector<LevelHost> lv;
+  uint8_t* d_mmask = nullptr;
+  int64_t ndir = 0;
+  int64_t* d_dir_lat = nullptr;
+  int64_t* d_dir_pad = nullptr;
+  double* d_dir_val = nullptr;
+  double* d_stage = nullptr;  // 3 n doubles (finest)
+  double* d_partial = nullptr;
+  double* d_scalars = nullptr;  // [0] norm2, [1..2] moments, [3..4] g-mean, [5..7] coarse info
+  double* h_scalars = nullptr;  // pinned mirror
+  double* d_coarse = nullptr;
+  double* d_backup = nullptr;  // 8 finest FP64 fields (adjoint)
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t graph_launches[2] = {0, 0};
+  bool rhs_set = false;
+  int64_t launches = 0;
+  int64_t device_bytes = 0;
+  std::string err;
+};
+
+namespace {
+
+int fail(hhg_mesh* M, int code, const std::string& msg) {
+  if (M) M->err = msg;
+  return code;
+}
+
+int cuda_fail(hhg_mesh* M, cudaError_t e, const char* where) {
+  return fail(M, HHG_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                      \
+  do {                                                \
+    cudaError_t e_ = (call);                          \
+    if (e_ != cudaSuccess) return cuda_fail(M, e_, #call); \
+  } while (0)
+
+int dalloc(hhg_mesh* M, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(M, HHG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
+  }
+  M->device_bytes += (int64_t)bytes;
+  return HHG_OK;
+}
+
+void fill_coefs(hhg_mesh* M, LevelHost& H) {
+  auto set = [&](auto& L) {
+    using T = std::remove_reference_t<decltype(L.nuh)>;
+    L.nx = H.sh.nx;
+    L.ny = H.sh.ny;
+    L.nz = H.sh.nz;
+    L.level = H.level;
+    L.mx = M->macro.mx;
+    L.my = M->macro.my;
+    L.mz = M->macro.mz;
+    L.px = H.px;
+    L.pxy = H.px * H.py;
+    L.nalloc = H.nalloc;
+    L.flags = H.d_flags;
+    L.mmask = M->d_mmask;
+    L.nuh = (T)(M->opt.nu * H.h);
+    L.c = (T)(M->opt.delta * H.hT2 * H.h);
+    L.h2 = (T)(H.h * H.h);
+    L.h3 = (T)(H.h * H.h * H.h);
+    L.dh2 = (T)(M->opt.delta * H.hT2);
+    L.omega = (T)M->opt.omega;
+  };
+  set(H.d64);
+  set(H.d32);
+}
+
+int ensure32(hhg_mesh* M) {
+  for (int l = M->coarsest; l <= M->finest; ++l) {
+    LevelHost& H = M->lv[l];
+    if (H.mem32) continue;
+    int rc = dalloc(M, (void**)&H.mem32, sizeof(float) * 12 * (size_t)H.nalloc);
+    if (rc) return rc;
+    CK(cudaMemsetAsync(H.mem32, 0, sizeof(float) * 12 * (size_t)H.nalloc, M->stream));
+    bind_fields(H.d32, H.mem32, H.nalloc);
+  }
+  return HHG_OK;
+}
+
+// ---- enqueue helpers (no synchronisation; graph-capturable) -------------------
+
+template <class T>
+LevelDev<T>& view(hhg_mesh* M, int l);
+template <>
+LevelDev<double>& view<double>(hhg_mesh* M, int l) { return M->lv[l].d64; }
+template <>
+LevelDev<float>& view<float>(hhg_mesh* M, int l) { return M->lv[l].d32; }
+
+template <class T>
+void enq_vel_sweep(hhg_mesh* M, int l, bool forward) {
+  for (int q = 0; q < 4; ++q) launch_vel_colour<T>(view<T>(M, l), forward ? q : 3 - q, M->stream);
+  M->launches += 4;
+}
+
+template <class T>
+void enq_pres_sweep(hhg_mesh* M, int l) {
+  for (int q = 0; q < 4; ++q) launch_pres_colour<T>(view<T>(M, l), q, M->stream);
+  M->launches += 4;
+}
+
+// One inexact Uzawa step (Sec. 3.3): velocity SHGS on f - B^T p, then the
+// pressure sweep on B u - g.
+template <class T>
+void enq_uzawa(hhg_mesh* M, int l) {
+  launch_vel_rhs<T>(view<T>(M, l), M->stream);
+  M->launches += 1;
+  enq_vel_sweep<T>(M, l, true);
+  enq_vel_sweep<T>(M, l, false);
+  launch_pres_rhs<T>(view<T>(M, l), M->stream);
+  M->launches += 1;
+  enq_pres_sweep<T>(M, l);
+}
+
+template <class T>
+void enq_coarse(hhg_mesh* M);
+template <>
+void enq_coarse<double>(hhg_mesh* M) {
+  CoarseParams prm{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max, M->opt.coarse_cg_rtol};
+  launch_coarse_solve(M->lv[M->coarsest].d64, M->d_coarse, prm, M->d_scalars + 5, M->stream);
+  M->launches += 1;
+}
+template <>
+void enq_coarse<float>(hhg_mesh* M) {
+  LevelHost& H = M->lv[M->coarsest];
+  launch_coarse_in(H.d32, H.d64, M->stream);
+  enq_coarse<double>(M);
+  launch_coarse_out(H.d32, H.d64, M->stream);
+  M->launches += 2;
+}
+
+template <class T>
+int nu_steps(hhg_mesh* M, int l, bool pre) {
+  return (pre ? M->opt.nu_pre : M->opt.nu_post) + M->opt.var_increment * (M->finest - l);
+}
+
+// One V_var cycle rooted at level l (Sec. 3.5).
+template <class T>
+void enq_vcycle(hhg_mesh* M, int l) {
+  if (l == M->coarsest) {
+    enq_coarse<T>(M);
+    return;
+  }
+  for (int s = 0; s < nu_steps<T>(M, l, true); ++s) enq_uzawa<T>(M, l);
+  launch_residual<T>(view<T>(M, l), M->stream);
+  launch_restrict<T>(view<T>(M, l), view<T>(M, l - 1), M->stream);
+  M->launches += 2;
+  enq_vcycle<T>(M, l - 1);
+  launch_prolong_add<T>(view<T>(M, l), view<T>(M, l - 1), M->stream);
+  M->launches += 1;
+  for (int s = 0; s < nu_steps<T>(M, l, false); ++s) enq_uzawa<T>(M, l);
+}
+
+template <class T>
+void enq_project(hhg_mesh* M, int l) {
+  launch_mass_moments<T>(view<T>(M, l), M->d_partial, M->d_scalars + 1, M->stream);
+  launch_project<T>(view<T>(M, l), M->d_scalars + 1, M->stream);
+  M->launches += 3;
+}
+
+// FP64 cycle body: V-cycle, mean projection, residual and its norm.
+void enq_cycle64(hhg_mesh* M) {
+  enq_vcycle<double>(M, M->finest);
+  if (!M->macro.has_outflow) enq_project<double>(M, M->finest);
+  launch_residual<double>(M->lv[M->finest].d64, M->stream);
+  launch_residual_norm2<double>(M->lv[M->finest].d64, M->d_partial, M->d_scalars, M->stream);
+  M->launches += 3;
+}
+
+// FP32+IR cycle body: correction V-cycle in FP32 from zero on the FP32
+// residual, x += e in FP64, projection in FP64, FP64 residual -> FP32 rhs.
+void enq_cycle32(hhg_mesh* M) {
+  LevelHost& H = M->lv[M->finest];
+  launch_zero<float>(H.d32, 0, M->stream);
+  enq_vcycle<float>(M, M->finest);
+  launch_ir_update(H.d64, H.d32, M->stream);
+  M->launches += 1;
+  if (!M->macro.has_outflow) enq_project<double>(M, M->finest);
+  launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
+  M->launches += 2;
+}
+
+int run_cycle(hhg_mesh* M, int mode, double* norm2) {
+  if (M->opt.use_graphs) {
+    if (!M->graph[mode]) {
+      cudaGraph_t g;
+      const int64_t before = M->launches;
+      CK(cudaStreamBeginCapture(M->stream, cudaStreamCaptureModeThreadLocal));
+      if (mode == 0)
+        enq_cycle64(M);
+      else
+        enq_cycle32(M);
+      cudaError_t e = cudaStreamEndCapture(M->stream, &g);
+      if (e != cudaSuccess) return cuda_fail(M, e, "graph capture");
+      M->graph_launches[mode] = M->launches - before;
+      M->launches = before;
+      e = cudaGraphInstantiate(&M->graph[mode], g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return cuda_fail(M, e, "graph instantiate");
+    }
+    CK(cudaGraphLaunch(M->graph[mode], M->stream));
+    M->launches += M->graph_launches[mode];
+  } else {
+    if (mode == 0)
+      enq_cycle64(M);
+    else
+      enq_cycle32(M);
+    CK(cudaGetLastError());
+  }
+  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  *norm2 = M->h_scalars[0];
+  return HHG_OK;
+}
+
+int residual_norm2(hhg_mesh* M, int mode, double* norm2) {
+  LevelHost& H = M->lv[M->finest];
+  if (mode == 0) {
+    launch_residual<double>(H.d64, M->stream);
+    launch_residual_norm2<double>(H.d64, M->d_partial, M->d_scalars, M->stream);
+    M->launches += 3;
+  } else {
+    launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
+    M->launches += 2;
+  }
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  *norm2 = M->h_scalars[0];
+  return HHG_OK;
+}
+
+int check_level(hhg_mesh* M, int level) {
+  if (!M) return HHG_EINVAL;
+  if (level < M->coarsest || level > M->finest) return fail(M, HHG_EINVAL, "level outside the hierarchy");
+  return HHG_OK;
+}
+
+// host/device pointer -> staging buffer (n * ncomp doubles)
+int stage_in(hhg_mesh* M, const double* src, int64_t count) {
+  CK(cudaMemcpyAsync(M->d_stage, src, sizeof(double) * (size_t)count, cudaMemcpyDefault, M->stream));
+  return HHG_OK;
+}
+int stage_out(hhg_mesh* M, double* dst, int64_t count) {
+  CK(cudaMemcpyAsync(dst, M->d_stage, sizeof(double) * (size_t)count, cudaMemcpyDefault, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  return HHG_OK;
+}
+
+int do_solve(hhg_mesh* M, double tol, int max_cycles, int mode, hhg_stats* st) {
+  auto t0 = std::chrono::steady_clock::now();
+  if (mode == HHG_MODE_FP32_IR) {
+    int rc = ensure32(M);
+    if (rc) return rc;
+  }
+  const int64_t l0 = M->launches;
+  double r2;
+  int rc = residual_norm2(M, mode, &r2);
+  if (rc) return rc;
+  const double r0 = std::sqrt(r2);
+  hhg_stats s{};
+  s.r0 = r0;
+  s.history[0] = 1.0;
+  s.status = HHG_OK;
+  double rel = 1.0;
+  int cycles = 0;
+  if (r0 > 0.0 && std::isfinite(r0)) {
+    while (cycles < max_cycles) {
+      rc = run_cycle(M, mode, &r2);
+      if (rc) return rc;
+      ++cycles;
+      rel = std::sqrt(r2) / r0;
+      if (cycles < 64) s.history[cycles] = rel;
+      if (!std::isfinite(rel) || rel > 1e3) {
+        s.status = HHG_EDIVERGED;
+        break;
+      }
+      if (rel <= tol) break;
+    }
+    if (s.status == HHG_OK && rel > tol) s.status = HHG_EMAXIT;
+  } else if (!std::isfinite(r0)) {
+    s.status = HHG_EDIVERGED;
+  }
+  s.cycles = cycles;
+  s.rel_residual = rel;
+  s.kernel_launches = M->launches - l0;
+  s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (st) *st = s;
+  if (s.status == HHG_EDIVERGED) return fail(M, HHG_EDIVERGED, "residual diverged");
+  return s.status;
+}
+
+int gather_solution(hhg_mesh* M, double* u_out, double* p_out) {
+  LevelHost& H = M->lv[M->finest];
+  const int64_t n = H.sh.n();
+  if (u_out) {
+    const double* src[3] = {H.d64.u[0], H.d64.u[1], H.d64.u[2]};
+    launch_gather<double>(H.d64, src, 3, M->d_stage, M->stream);
+    launch_dirichlet_fill(M->d_dir_lat, M->d_dir_val, M->ndir, H.d64, M->d_stage, M->stream);
+    CK(cudaGetLastError());
+    int rc = stage_out(M, u_out, 3 * n);
+    if (rc) return rc;
+  }
+  if (p_out) {
+    const double* src[1] = {H.d64.p};
+    launch_gather<double>(H.d64, src, 1, M->d_stage, M->stream);
+    CK(cudaGetLastError());
+    int rc = stage_out(M, p_out, n);
+    if (rc) return rc;
+  }
+  return HHG_OK;
+}
+
+void release(hhg_mesh* M) {
+  if (!M) return;
+  cudaSetDevice(M->device);
+  for (auto& g : M->graph)
+    if (g) cudaGraphExecDestroy(g);
+  for (auto& H : M->lv) {
+    cudaFree(H.d_flags);
+    cudaFree(H.mem64);
+    cudaFree(H.mem32);
+  }
+  cudaFree(M->d_mmask);
+  cudaFree(M->d_dir_lat);
+  cudaFree(M->d_dir_pad);
+  cudaFree(M->d_dir_val);
+  cudaFree(M->d_stage);
+  cudaFree(M->d_partial);
+  cudaFree(M->d_scalars);
+  cudaFree(M->d_coarse);
+  cudaFree(M->d_backup);
+  if (M->h_scalars) cudaFreeHost(M->h_scalars);
+  if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
+}
+
+}  // namespace
+
+// =============================== C ABI ==========================================
+
+extern "C" {
+
+void hhg_default_options(hhg_options* opt) {
+  if (!opt) return;
+  std::memset(opt, 0, sizeof(*opt));
+  opt->nu = 1.0;
+  opt->delta = 1.0 / 12.0;
+  opt->omega = 0.3;
+  opt->nu_pre = 3;
+  opt->nu_post = 3;
+  opt->var_increment = 2;
+  opt->coarsest_level = 2;
+  opt->coarse_minres_max = 5;
+  opt->coarse_minres_rtol = 5e-3;
+  opt->coarse_cg_max = 50;
+  opt->coarse_cg_rtol = 1e-3;
+  opt->use_graphs = 1;
+}
+
+const char* hhg_strerror(int code) {
+  switch (code) {
+    case HHG_OK: return "ok";
+    case HHG_EINVAL: return "invalid argument";
+    case HHG_EMESH: return "macro mesh not supported";
+    case HHG_ENOMEM: return "out of device memory";
+    case HHG_EDIVERGED: return "solver diverged";
+    case HHG_EMAXIT: return "tolerance not reached within max_cycles";
+    case HHG_ECUDA: return "CUDA error";
+    case HHG_ESTATE: return "call out of order";
+    default: return "unknown error";
+  }
+}
+
+const char* hhg_last_error(const hhg_mesh* mesh) {
+  return mesh ? mesh->err.c_str() : g_create_error.c_str();
+}
+
+int hhg_lattice_classify(const double* V, int64_t nv, const int32_t* T, int64_t nt, const uint8_t* bc,
+                         int32_t level, int64_t dims[3], uint8_t* flags) {
+  if (!dims || level < 0 || level > 12) return HHG_EINVAL;
+  MacroLattice m;
+  int rc = build_macro_lattice(V, nv, T, nt, bc, m, g_create_error);
+  if (rc) return rc;
+  LevelShape sh = level_shape(m, level);
+  dims[0] = sh.nx;
+  dims[1] = sh.ny;
+  dims[2] = sh.nz;
+  if (flags) classify_nodes(m, level, flags);
+  return HHG_OK;
+}
+
+int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, const uint8_t* bc,
+                    int32_t finest, const hhg_options* opt, void* stream, hhg_mesh** out) {
+  if (!out) return HHG_EINVAL;
+  *out = nullptr;
+  hhg_options o;
+  if (opt)
+    o = *opt;
+  else
+    hhg_default_options(&o);
+  if (finest < 0 || finest > 12 || o.coarsest_level < 0 || o.coarsest_level > finest || o.nu <= 0 ||
+      o.delta <= 0 || o.omega <= 0 || o.nu_pre < 0 || o.nu_post < 0 || o.var_increment < 0 ||
+      o.coarse_minres_max < 0 || o.coarse_cg_max < 0) {
+    g_create_error = "invalid level or option";
+    return HHG_EINVAL;
+  }
+  hhg_mesh* M = new hhg_mesh();
+  M->opt = o;
+  M->finest = finest;
+  M->coarsest = o.coarsest_level;
+  int rc = build_macro_lattice(V, nv, T, nt, bc, M->macro, g_create_error);
+  if (rc) {
+    delete M;
+    return rc;
+  }
+  auto bail = [&](int code) {
+    g_create_error = M->err;
+    release(M);
+    delete M;
+    return code;
+  };
+  cudaError_t e = cudaGetDevice(&M->device);
+  if (e != cudaSuccess) {
+    M->err = std::string("no CUDA device: ") + cudaGetErrorString(e);
+    return bail(HHG_ECUDA);
+  }
+  if (stream) {
+    M->stream = (cudaStream_t)stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      M->err = std::string("stream: ") + cudaGetErrorString(e);
+      return bail(HHG_ECUDA);
+    }
+    M->own_stream = true;
+  }
+  if ((rc = dalloc(M, (void**)&M->d_mmask, M->macro.mask.size()))) return bail(rc);
+  if ((e = cudaMemcpy(M->d_mmask, M->macro.mask.data(), M->macro.mask.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    M->err = cudaGetErrorString(e);
+    return bail(HHG_ECUDA);
+  }
+  M->lv.resize(finest + 1);
+  for (int l = M->coarsest; l <= finest; ++l) {
+    LevelHost& H = M->lv[l];
+    H.level = l;
+    H.sh = level_shape(M->macro, l);
+    H.px = ((H.sh.nx + 2 + 3) / 4) * 4;
+    H.py = H.sh.ny + 2;
+    H.pz = H.sh.nz + 2;
+    H.nalloc = H.px * H.py * H.pz;
+    H.h = M->macro.H / (double)(1 << l);
+    H.hT2 = std::pow(H.h * H.h * H.h / 6.0, 2.0 / 3.0);
+    H.flags.resize(H.sh.n());
+    classify_nodes(M->macro, l, H.flags.data());
+    std::vector<uint8_t> padded(H.nalloc, 0);
+    for (int k = 0; k < H.sh.nz; ++k)
+      for (int j = 0; j < H.sh.ny; ++j)
+        for (int i = 0; i < H.sh.nx; ++i) {
+          const uint8_t f = H.flags[i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k)];
+          padded[(i + 1) + H.px * (j + 1) + H.px * H.py * (k + 1)] = f;
+          if (f & F_VFREE) H.n_vel++;
+          if (f & F_ACT) H.n_pres++;
+        }
+    if ((rc = dalloc(M, (void**)&H.d_flags, H.nalloc))) return bail(rc);
+    if ((e = cudaMemcpy(H.d_flags, padded.data(), H.nalloc, cudaMemcpyHostToDevice)) != cudaSuccess) {
+      M->err = cudaGetErrorString(e);
+      return bail(HHG_ECUDA);
+    }
+    if ((rc = dalloc(M, (void**)&H.mem64, sizeof(double) * 12 * (size_t)H.nalloc))) return bail(rc);
+    if ((e = cudaMemset(H.mem64, 0, sizeof(double) * 12 * (size_t)H.nalloc)) != cudaSuccess) {
+      M->err = cudaGetErrorString(e);
+      return bail(HHG_ECUDA);
+    }
+    bind_fields(H.d64, H.mem64, H.nalloc);
+    fill_coefs(M, H);
+  }
+  // Dirichlet nodes of the finest level (compact list)
+  {
+    LevelHost& H = M->lv[finest];
+    std::vector<int64_t> lat, pad;
+    for (int k = 0; k < H.sh.nz; ++k)
+      for (int j = 0; j < H.sh.ny; ++j)
+        for (int i = 0; i < H.sh.nx; ++i) {
+          const int64_t q = i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k);
+          if ((H.flags[q] & F_DIR) && (H.flags[q] & F_ACT)) {
+            lat.push_back(q);
+            pad.push_back((i + 1) + H.px * (j + 1) + H.px * H.py * (k + 1));
+          }
+        }
+    M->ndir = (int64_t)lat.size();
+    if (M->ndir) {
+      if ((rc = dalloc(M, (void**)&M->d_dir_lat, sizeof(int64_t) * lat.size()))) return bail(rc);
+      if ((rc = dalloc(M, (void**)&M->d_dir_pad, sizeof(int64_t) * pad.size()))) return bail(rc);
+      if ((rc = dalloc(M, (void**)&M->d_dir_val, sizeof(double) * 3 * lat.size()))) return bail(rc);
+      cudaMemcpy(M->d_dir_lat, lat.data(), sizeof(int64_t) * lat.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(M->d_dir_pad, pad.data(), sizeof(int64_t) * pad.size(), cudaMemcpyHostToDevice);
+      cudaMemset(M->d_dir_val, 0, sizeof(double) * 3 * lat.size());
+    }
+    if ((rc = dalloc(M, (void**)&M->d_stage, sizeof(double) * 3 * (size_t)H.sh.n()))) return bail(rc);
+  }
+  if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * REDUCE_BLOCKS))) return bail(rc);
+  if ((rc = dalloc(M, (void**)&M->d_scalars, sizeof(double) * 16))) return bail(rc);
+  cudaMemset(M->d_scalars, 0, sizeof(double) * 16);
+  if ((e = cudaMallocHost((void**)&M->h_scalars, sizeof(double) * 16)) != cudaSuccess) {
+    M->err = cudaGetErrorString(e);
+    return bail(HHG_ENOMEM);
+  }
+  if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * COARSE_FIELDS * (size_t)M->lv[M->coarsest].nalloc)))
+    return bail(rc);
+  if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
+    M->err = std::string("set-up: ") + cudaGetErrorString(e);
+    return bail(HHG_ECUDA);
+  }
+  *out = M;
+  return HHG_OK;
+}
+
+void hhg_destroy(hhg_mesh* mesh) {
+  if (!mesh) return;
+  release(mesh);
+  delete mesh;
+}
+
+int hhg_lattice_dims(const hhg_mesh* mesh, int32_t level, int64_t dims[3]) {
+  hhg_mesh* M = const_cast<hhg_mesh*>(mesh);
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (!dims) return HHG_EINVAL;
+  dims[0] = M->lv[level].sh.nx;
+  dims[1] = M->lv[level].sh.ny;
+  dims[2] = M->lv[level].sh.nz;
+  return HHG_OK;
+}
+
+int hhg_num_nodes(const hhg_mesh* mesh, int32_t level, int64_t* n) {
+  hhg_mesh* M = const_cast<hhg_mesh*>(mesh);
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (!n) return HHG_EINVAL;
+  *n = M->lv[level].sh.n();
+  return HHG_OK;
+}
+
+int hhg_num_dofs(const hhg_mesh* mesh, int32_t level, int64_t* nv, int64_t* np) {
+  hhg_mesh* M = const_cast<hhg_mesh*>(mesh);
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (nv) *nv = M->lv[level].n_vel;
+  if (np) *np = M->lv[level].n_pres;
+  return HHG_OK;
+}
+
+int hhg_node_coords(const hhg_mesh* mesh, int32_t level, double* xyz) {
+  hhg_mesh* M = const_cast<hhg_mesh*>(mesh);
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (!xyz) return HHG_EINVAL;
+  const LevelHost& H = M->lv[level];
+  std::vector<double> tmp(3 * (size_t)H.sh.n());
+  for (int k = 0; k < H.sh.nz; ++k)
+    for (int j = 0; j < H.sh.ny; ++j)
+      for (int i = 0; i < H.sh.nx; ++i) {
+        const int64_t q = i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k);
+        tmp[3 * q + 0] = M->macro.origin[0] + i * H.h;
+        tmp[3 * q + 1] = M->macro.origin[1] + j * H.h;
+        tmp[3 * q + 2] = M->macro.origin[2] + k * H.h;
+      }
+  CK(cudaMemcpy(xyz, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyDefault));
+  return HHG_OK;
+}
+
+int hhg_node_flags(const hhg_mesh* mesh, int32_t level, uint8_t* flags) {
+  hhg_mesh* M = const_cast<hhg_mesh*>(mesh);
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (!flags) return HHG_EINVAL;
+  CK(cudaMemcpy(flags, M->lv[level].flags.data(), M->lv[level].flags.size(), cudaMemcpyDefault));
+  return HHG_OK;
+}
+
+int hhg_outflow_weights(const hhg_mesh* mesh, int32_t level, double* w) {
+  hhg_mesh* M = const_cast<hhg_mesh*>(mesh);
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (!w) return HHG_EINVAL;
+  std::vector<double> tmp(3 * (size_t)M->lv[level].sh.n());
+  outflow_weights(M->macro, level, tmp.data());
+  CK(cudaMemcpy(w, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyDefault));
+  return HHG_OK;
+}
+
+int hhg_device_bytes(const hhg_mesh* mesh, int64_t* bytes) {
+  if (!mesh || !bytes) return HHG_EINVAL;
+  *bytes = mesh->device_bytes;
+  return HHG_OK;
+}
+
+int hhg_set_rhs(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet) {
+  if (!M) return HHG_EINVAL;
+  CK(cudaSetDevice(M->device));
+  LevelHost& H = M->lv[M->finest];
+  LevelDev<double>& L = H.d64;
+  const int64_t n = H.sh.n();
+  launch_zero<double>(L, 0, M->stream);
+  launch_zero<double>(L, 2, M->stream);
+  // staged body force in RU (active nodes), Dirichlet data in U (Dirichlet nodes)
+  if (f_nodal) {
+    int rc = stage_in(M, f_nodal, 3 * n);
+    if (rc) return rc;
+    launch_scatter(L, M->d_stage, 3, L.r, F_ACT, M->stream);
+  }
+  if (u_dirichlet) {
+    int rc = stage_in(M, u_dirichlet, 3 * n);
+    if (rc) return rc;
+    launch_scatter(L, M->d_stage, 3, L.u, F_DIR, M->stream);
+  }
+  launch_set_rhs(L, L.r, L.u, M->stream);
+  if (!M->macro.has_outflow) launch_remove_mean_g(L, M->d_partial, M->d_scalars + 3, M->stream);
+  launch_dirichlet_gather(M->d_dir_pad, M->ndir, L, M->d_dir_val, M->stream);
+  M->launches += (f_nodal ? 1 : 0) + (u_dirichlet ? 1 : 0) + 1 + (M->macro.has_outflow ? 0 : 3) + (M->ndir ? 1 : 0);
+  launch_zero<double>(L, 0, M->stream);
+  launch_zero<double>(L, 2, M->stream);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(M->stream));
+  M->rhs_set = true;
+  return HHG_OK;
+}
+
+int hhg_set_initial(hhg_mesh* M, const double* u, const double* p) {
+  if (!M) return HHG_EINVAL;
+  if (!M->rhs_set) return fail(M, HHG_ESTATE, "hhg_set_initial before hhg_set_rhs");
+  CK(cudaSetDevice(M->device));
+  LevelHost& H = M->lv[M->finest];
+  LevelDev<double>& L = H.d64;
+  const int64_t n = H.sh.n();
+  launch_zero<double>(L, 0, M->stream);
+  if (u) {
+    int rc = stage_in(M, u, 3 * n);
+    if (rc) return rc;
+    launch_scatter(L, M->d_stage, 3, L.u, F_VFREE, M->stream);
+  }
+  if (p) {
+    int rc = stage_in(M, p, n);
+    if (rc) return rc;
+    double* dst[1] = {L.p};
+    launch_scatter(L, M->d_stage, 1, dst, F_ACT, M->stream);
+  }
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(M->stream));
+  return HHG_OK;
+}
+
+int hhg_vcycle(hhg_mesh* M, int32_t count, double* rel) {
+  if (!M || count < 0) return HHG_EINVAL;
+  if (!M->rhs_set) return fail(M, HHG_ESTATE, "hhg_vcycle before hhg_set_rhs");
+  CK(cudaSetDevice(M->device));
+  double r2;
+  int rc = residual_norm2(M, 0, &r2);
+  if (rc) return rc;
+  const double r0 = std::sqrt(r2);
+  double cur = r2;
+  for (int c = 0; c < count; ++c) {
+    rc = run_cycle(M, 0, &cur);
+    if (rc) return rc;
+  }
+  if (rel) *rel = r0 > 0 ? std::sqrt(cur) / r0 : 0.0;
+  return HHG_OK;
+}
+
+int hhg_solve(hhg_mesh* M, double tol, int32_t max_cycles, int32_t mode, double* u_out, double* p_out,
+              hhg_stats* stats) {
+  if (!M || max_cycles < 0 || !(tol >= 0) || (mode != HHG_MODE_FP64 && mode != HHG_MODE_FP32_IR))
+    return HHG_EINVAL;
+  if (!M->rhs_set) return fail(M, HHG_ESTATE, "hhg_solve before hhg_set_rhs");
+  CK(cudaSetDevice(M->device));
+  int rc = do_solve(M, tol, max_cycles, mode, stats);
+  if (rc != HHG_OK && rc != HHG_EMAXIT) return rc;
+  int rc2 = gather_solution(M, u_out, p_out);
+  return rc2 ? rc2 : rc;
+}
+
+int hhg_get_solution(hhg_mesh* M, double* u_out, double* p_out) {
+  if (!M) return HHG_EINVAL;
+  CK(cudaSetDevice(M->device));
+  return gather_solution(M, u_out, p_out);
+}
+
+int hhg_apply_operator(hhg_mesh* M, int32_t level, const double* u, const double* p, double* ku, double* kp) {
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  CK(cudaSetDevice(M->device));
+  LevelHost& H = M->lv[level];
+  const int64_t n = H.sh.n();
+  double* tmp = nullptr;
+  if ((rc = dalloc(M, (void**)&tmp, sizeof(double) * 12 * (size_t)H.nalloc))) return rc;
+  M->device_bytes -= (int64_t)(sizeof(double) * 12 * (size_t)H.nalloc);
+  cudaMemsetAsync(tmp, 0, sizeof(double) * 12 * (size_t)H.nalloc, M->stream);
+  LevelDev<double> L = H.d64;
+  bind_fields(L, tmp, H.nalloc);
+  double* stage = nullptr;
+  if ((rc = dalloc(M, (void**)&stage, sizeof(double) * 3 * (size_t)n))) {
+    cudaFree(tmp);
+    return rc;
+  }
+  M->device_bytes -= (int64_t)(sizeof(double) * 3 * (size_t)n);
+  auto done = [&](int code) {
+    cudaStreamSynchronize(M->stream);
+    cudaFree(tmp);
+    cudaFree(stage);
+    return code;
+  };
+  if (u) {
+    if (cudaMemcpyAsync(stage, u, sizeof(double) * 3 * n, cudaMemcpyDefault, M->stream) != cudaSuccess)
+      return done(fail(M, HHG_ECUDA, "copy u"));
+    launch_scatter(L, stage, 3, L.u, F_VFREE, M->stream);
+  }
+  if (p) {
+    if (cudaMemcpyAsync(stage, p, sizeof(double) * n, cudaMemcpyDefault, M->stream) != cudaSuccess)
+      return done(fail(M, HHG_ECUDA, "copy p"));
+    double* dst[1] = {L.p};
+    launch_scatter(L, stage, 1, dst, F_ACT, M->stream);
+  }
+  launch_residual<double>(L, M->stream);  // (RU, RP) = -K (U, P) since F = G = 0
+  if (ku) {
+    const double* src[3] = {L.r[0], L.r[1], L.r[2]};
+    launch_gather<double>(L, src, 3, stage, M->stream);
+    launch_scale(stage, 3 * n, -1.0, M->stream);
+    if (cudaMemcpyAsync(ku, stage, sizeof(double) * 3 * n, cudaMemcpyDefault, M->stream) != cudaSuccess)
+      return done(fail(M, HHG_ECUDA, "copy ku"));
+    cudaStreamSynchronize(M->stream);
+  }
+  if (kp) {
+    const double* src[1] = {L.rp};
+    launch_gather<double>(L, src, 1, stage, M->stream);
+    launch_scale(stage, n, -1.0, M->stream);
+    if (cudaMemcpyAsync(kp, stage, sizeof(double) * n, cudaMemcpyDefault, M->stream) != cudaSuccess)
+      return done(fail(M, HHG_ECUDA, "copy kp"));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return done(cuda_fail(M, e, "apply_operator"));
+  return done(HHG_OK);
+}
+
+int hhg_adjoint_gradient(hhg_mesh* M, const double* ju, const double* jp, double tol, int32_t max_cycles,
+                         int32_t mode, double* grad_f, hhg_stats* stats) {
+  if (!M || !grad_f || (mode != HHG_MODE_FP64 && mode != HHG_MODE_FP32_IR)) return HHG_EINVAL;
+  if (!M->macro.has_outflow) return fail(M, HHG_EINVAL, "adjoint needs a mesh with an outflow face");
+  CK(cudaSetDevice(M->device));
+  LevelHost& H = M->lv[M->finest];
+  LevelDev<double>& L = H.d64;
+  const int64_t n = H.sh.n();
+  const size_t fb = sizeof(double) * 8 * (size_t)H.nalloc;
+  int rc;
+  if (!M->d_backup && (rc = dalloc(M, (void**)&M->d_backup, fb))) return rc;
+  CK(cudaMemcpyAsync(M->d_backup, L.u[0], fb, cudaMemcpyDeviceToDevice, M->stream));  // U, P, F, G
+  const bool had_rhs = M->rhs_set;
+  launch_zero<double>(L, 0, M->stream);
+  launch_zero<double>(L, 1, M->stream);
+  if (ju) {
+    if ((rc = stage_in(M, ju, 3 * n))) return rc;
+    launch_scatter(L, M->d_stage, 3, L.f, F_VFREE, M->stream);
+  }
+  if (jp) {
+    if ((rc = stage_in(M, jp, n))) return rc;
+    double* dst[1] = {L.g};
+    launch_scatter(L, M->d_stage, 1, dst, F_ACT, M->stream);
+  }
+  M->rhs_set = true;
+  rc = do_solve(M, tol, max_cycles, mode, stats);
+  if (rc == HHG_OK || rc == HHG_EMAXIT) {
+    launch_rhs_transpose(L, L.r, M->stream);
+    const double* src[3] = {L.r[0], L.r[1], L.r[2]};
+    launch_gather<double>(L, src, 3, M->d_stage, M->stream);
+    int rc2 = stage_out(M, grad_f, 3 * n);
+    if (rc2) rc = rc2;
+  }
+  cudaMemcpyAsync(L.u[0], M->d_backup, fb, cudaMemcpyDeviceToDevice, M->stream);
+  cudaStreamSynchronize(M->stream);
+  M->rhs_set = had_rhs;
+  return rc;
+}
+
+int hhg_level_field(hhg_mesh* M, int32_t level, int32_t precision, int32_t field, int32_t write, double* buf) {
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if (!buf || field < 0 || field > 5 || (precision != 0 && precision != 1)) return fail(M, HHG_EINVAL, "bad field");
+  CK(cudaSetDevice(M->device));
+  if (precision == 1 && (rc = ensure32(M))) return rc;
+  LevelHost& H = M->lv[level];
+  const int64_t n = H.sh.n();
+  const int ncomp = (field == HHG_FIELD_U || field == HHG_FIELD_F || field == HHG_FIELD_RU) ? 3 : 1;
+  const uint8_t mask = (field == HHG_FIELD_U || field == HHG_FIELD_F || field == HHG_FIELD_RU) ? F_VFREE : F_ACT;
+  auto ptrs64 = [&](LevelDev<double>& L, double** out) {
+    switch (field) {
+      case HHG_FIELD_U: out[0] = L.u[0]; out[1] = L.u[1]; out[2] = L.u[2]; break;
+      case HHG_FIELD_P: out[0] = L.p; break;
+      case HHG_FIELD_F: out[0] = L.f[0]; out[1] = L.f[1]; out[2] = L.f[2]; break;
+      case HHG_FIELD_G: out[0] = L.g; break;
+      case HHG_FIELD_RU: out[0] = L.r[0]; out[1] = L.r[1]; out[2] = L.r[2]; break;
+      default: out[0] = L.rp; break;
+    }
+  };
+  auto ptrs32 = [&](LevelDev<float>& L, float** out) {
+    switch (field) {
+      case HHG_FIELD_U: out[0] = L.u[0]; out[1] = L.u[1]; out[2] = L.u[2]; break;
+      case HHG_FIELD_P: out[0] = L.p; break;
+      case HHG_FIELD_F: out[0] = L.f[0]; out[1] = L.f[1]; out[2] = L.f[2]; break;
+      case HHG_FIELD_G: out[0] = L.g; break;
+      case HHG_FIELD_RU: out[0] = L.r[0]; out[1] = L.r[1]; out[2] = L.r[2]; break;
+      default: out[0] = L.rp; break;
+    }
+  };
+  double* stage = nullptr;
+  if ((rc = dalloc(M, (void**)&stage, sizeof(double) * 3 * (size_t)n))) return rc;
+  M->device_bytes -= (int64_t)(sizeof(double) * 3 * (size_t)n);
+  double* tmp = nullptr;
+  auto done = [&](int code) {
+    cudaStreamSynchronize(M->stream);
+    cudaFree(stage);
+    cudaFree(tmp);
+    return code;
+  };
+  if (write) {
+    if (cudaMemcpyAsync(stage, buf, sizeof(double) * ncomp * n, cudaMemcpyDefault, M->stream) != cudaSuccess)
+      return done(fail(M, HHG_ECUDA, "copy in"));
+    if (precision == 0) {
+      double* dst[3];
+      ptrs64(H.d64, dst);
+      launch_scatter(H.d64, stage, ncomp, dst, mask, M->stream);
+    } else {
+      if ((rc = dalloc(M, (void**)&tmp, sizeof(double) * 3 * (size_t)H.nalloc))) return done(rc);
+      M->device_bytes -= (int64_t)(sizeof(double) * 3 * (size_t)H.nalloc);
+      double* dst[3] = {tmp, tmp + H.nalloc, tmp + 2 * H.nalloc};
+      launch_scatter(H.d64, stage, ncomp, dst, mask, M->stream);
+      float* d32[3];
+      ptrs32(H.d32, d32);
+      for (int c = 0; c < ncomp; ++c) launch_cast_field(dst[c], d32[c], H.nalloc, M->stream);
+    }
+  } else {
+    if (precision == 0) {
+      double* src[3];
+      ptrs64(H.d64, src);
+      const double* cs[3] = {src[0], ncomp > 1 ? src[1] : src[0], ncomp > 2 ? src[2] : src[0]};
+      launch_gather<double>(H.d64, cs, ncomp, stage, M->stream);
+    } else {
+      float* src[3];
+      ptrs32(H.d32, src);
+      const float* cs[3] = {src[0], ncomp > 1 ? src[1] : src[0], ncomp > 2 ? src[2] : src[0]};
+      launch_gather<float>(H.d32, cs, ncomp, stage, M->stream);
+    }
+    if (cudaMemcpyAsync(buf, stage, sizeof(double) * ncomp * n, cudaMemcpyDefault, M->stream) != cudaSuccess)
+      return done(fail(M, HHG_ECUDA, "copy out"));
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return done(cuda_fail(M, e, "level_field"));
+  return done(HHG_OK);
+}
+
+static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op);
+
+int hhg_level_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32_t count) {
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if ((precision != 0 && precision != 1) || count < 0) return fail(M, HHG_EINVAL, "bad precision or count");
+  CK(cudaSetDevice(M->device));
+  if (precision == 1 && (rc = ensure32(M))) return rc;
+  for (int it = 0; it < count; ++it) {
+    if ((rc = enqueue_op(M, level, precision, op))) return rc;
+    CK(cudaGetLastError());
+  }
+  CK(cudaStreamSynchronize(M->stream));
+  return HHG_OK;
+}
+
+int hhg_time_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32_t reps, double* ms) {
+  int rc = check_level(M, level);
+  if (rc) return rc;
+  if ((precision != 0 && precision != 1) || reps < 1 || !ms) return fail(M, HHG_EINVAL, "bad arguments");
+  CK(cudaSetDevice(M->device));
+  if (precision == 1 && (rc = ensure32(M))) return rc;
+  if ((rc = enqueue_op(M, level, precision, op))) return rc;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaStreamSynchronize(M->stream));
+  cudaEventRecord(e0, M->stream);
+  for (int it = 0; it < reps && rc == 0; ++it) rc = enqueue_op(M, level, precision, op);
+  cudaEventRecord(e1, M->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float t = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc) return rc;
+  if (e != cudaSuccess) return cuda_fail(M, e, "time_op");
+  *ms = (double)t / reps;
+  return HHG_OK;
+}
+
+int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count) {
+  if (!mesh || !count) return HHG_EINVAL;
+  *count = mesh->launches;
+  return HHG_OK;
+}
+
+static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op) {
+  {
+    switch (op) {
+      case HHG_OP_UZAWA_STEP:
+        precision ? enq_uzawa<float>(M, level) : enq_uzawa<double>(M, level);
+        break;
+      case HHG_OP_VEL_FORWARD:
+        precision ? enq_vel_sweep<float>(M, level, true) : enq_vel_sweep<double>(M, level, true);
+        break;
+      case HHG_OP_VEL_BACKWARD:
+        precision ? enq_vel_sweep<float>(M, level, false) : enq_vel_sweep<double>(M, level, false);
+        break;
+      case HHG_OP_VEL_RHS:
+        precision ? launch_vel_rhs<float>(M->lv[level].d32, M->stream) : launch_vel_rhs<double>(M->lv[level].d64, M->stream);
+        break;
+      case HHG_OP_PRES_RHS:
+        precision ? launch_pres_rhs<float>(M->lv[level].d32, M->stream) : launch_pres_rhs<double>(M->lv[level].d64, M->stream);
+        break;
+      case HHG_OP_PRES_SWEEP:
+        precision ? enq_pres_sweep<float>(M, level) : enq_pres_sweep<double>(M, level);
+        break;
+      case HHG_OP_RESIDUAL:
+        precision ? launch_residual<float>(M->lv[level].d32, M->stream) : launch_residual<double>(M->lv[level].d64, M->stream);
+        break;
+      case HHG_OP_RESTRICT:
+        if (level == M->coarsest) return fail(M, HHG_EINVAL, "no coarser level");
+        precision ? launch_restrict<float>(M->lv[level].d32, M->lv[level - 1].d32, M->stream)
+                  : launch_restrict<double>(M->lv[level].d64, M->lv[level - 1].d64, M->stream);
+        break;
+      case HHG_OP_PROLONG_ADD:
+        if (level == M->coarsest) return fail(M, HHG_EINVAL, "no coarser level");
+        precision ? launch_prolong_add<float>(M->lv[level].d32, M->lv[level - 1].d32, M->stream)
+                  : launch_prolong_add<double>(M->lv[level].d64, M->lv[level - 1].d64, M->stream);
+        break;
+      case HHG_OP_COARSE_SOLVE:
+        if (level != M->coarsest) return fail(M, HHG_EINVAL, "coarse solve runs on the coarsest level");
+        precision ? enq_coarse<float>(M) : enq_coarse<double>(M);
+        break;
+      case HHG_OP_VCYCLE:
+        precision ? enq_vcycle<float>(M, level) : enq_vcycle<double>(M, level);
+        break;
+      case HHG_OP_PROJECT:
+        precision ? enq_project<float>(M, level) : enq_project<double>(M, level);
+        break;
+      default:
+        return fail(M, HHG_EINVAL, "unknown op");
+    }
+  }
+  return HHG_OK;
+}
+
+}  // extern "C"

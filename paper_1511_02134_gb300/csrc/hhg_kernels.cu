@@ -1,0 +1,626 @@
+// Level kernels of the all-at-once Uzawa multigrid (Sec. 3.3-3.6).
+//
+// Every kernel works on one level of the padded lattice (hhg_device.cuh).
+// Colour kernels update the nodes with (i + j + k) mod 4 == colour; these
+// are not coupled by the 15-point pattern of the operator, so one launch per
+// colour performs the Gauss-Seidel sweep in colour order.
+#include "hhg_kernels.h"
+
+namespace hhg {
+
+namespace {
+
+constexpr int CX = 32, CY = 4;  // colour kernels: quarter-rows x rows
+constexpr int FX = 64, FY = 4;  // full kernels
+
+template <class T>
+dim3 colour_grid(const LevelDev<T>& L) {
+  const int nq = (L.nx + 3) / 4;
+  return dim3((nq + CX - 1) / CX, (L.ny + CY - 1) / CY, L.nz);
+}
+template <class T>
+dim3 full_grid(const LevelDev<T>& L) {
+  return dim3((L.nx + FX - 1) / FX, (L.ny + FY - 1) / FY, L.nz);
+}
+
+// Colour-kernel node: returns false if outside the lattice.
+template <class T>
+__device__ __forceinline__ bool colour_node(const LevelDev<T>& L, int colour, int& i, int& j, int& k) {
+  const int t = blockIdx.x * CX + threadIdx.x;
+  j = blockIdx.y * CY + threadIdx.y;
+  k = blockIdx.z;
+  i = ((colour - j - k) & 3) + 4 * t;
+  return i < L.nx && j < L.ny;
+}
+
+template <class T>
+__device__ __forceinline__ bool full_node(const LevelDev<T>& L, int& i, int& j, int& k) {
+  i = blockIdx.x * FX + threadIdx.x;
+  j = blockIdx.y * FY + threadIdx.y;
+  k = blockIdx.z;
+  return i < L.nx && j < L.ny;
+}
+
+// ---- smoother ----------------------------------------------------------------
+
+// RU = F - B^T P on velocity nodes (the right-hand side of both velocity
+// sweeps of one Uzawa step, Sec. 3.3).
+template <class T>
+__global__ void k_vel_rhs(LevelDev<T> L) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_VFREE)) return;
+  T bt[3];
+  row_BT(L, L.p, i, j, k, c, fl, bt);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - bt[d];
+}
+
+// Gauss-Seidel update of the velocity nodes of one colour:
+// u_d <- u_d + (RU_d - (A u_d)) / A_ii.
+template <class T>
+__global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
+  int i, j, k;
+  if (!colour_node(L, colour, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_VFREE)) return;
+  if (!(fl & F_IRR)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.u[d][c] = (L.r[d][c] + L.nuh * nb6(L.u[d], c, L.px, L.pxy)) * inv6nuh;
+  } else {
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      T dg, of;
+      irr_lap_row(L, L.u[d], i, j, k, dg, of);
+      L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
+    }
+  }
+}
+
+// RP = B U - G on pressure nodes.
+template <class T>
+__global__ void k_pres_rhs(LevelDev<T> L) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_ACT)) return;
+  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};  // no address of kernel-parameter members
+  L.rp[c] = row_B(L, uu, i, j, k, c, fl) - L.g[c];
+}
+
+// Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour:
+// p <- p + omega (RP - C p) / C_ii  (forward SOR sweep from zero, Sec. 3.5).
+template <class T>
+__global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
+  int i, j, k;
+  if (!colour_node(L, colour, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_ACT)) return;
+  const T pc = L.p[c];
+  if (!(fl & F_IRR)) {
+    const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
+    L.p[c] = pc + omega_over_6c * (L.rp[c] - cp);
+  } else {
+    T dg, of;
+    irr_lap_row(L, L.p, i, j, k, dg, of);
+    const T cp = L.c * (dg * pc + of);
+    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
+  }
+}
+
+// ---- residual and transfers ---------------------------------------------------
+
+template <class T>
+__global__ void k_residual(LevelDev<T> L) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};  // no address of kernel-parameter members
+  if (fl & F_VFREE) {
+    T au[3], bt[3];
+    row_A(L, uu, i, j, k, c, fl, au);
+    row_BT(L, L.p, i, j, k, c, fl, bt);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - au[d] - bt[d];
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.r[d][c] = (T)0;
+  }
+  if (fl & F_ACT) {
+    L.rp[c] = L.g[c] - row_B(L, uu, i, j, k, c, fl) + row_C(L, L.p, i, j, k, c, fl);
+  } else {
+    L.rp[c] = (T)0;
+  }
+}
+
+// Coarse (F, G) = P^T (RU, RP): P1 interpolation is the identity on coarse
+// nodes and the mean of the two ends on coarse-edge midpoints, which on the
+// Kuhn lattice are the 14 neighbours along the Kuhn directions.  Coarse
+// (U, P) start from zero.
+template <class T>
+__global__ void k_restrict(LevelDev<T> Lf, LevelDev<T> Lc) {
+  int i, j, k;
+  if (!full_node(Lc, i, j, k)) return;
+  const int64_t cc = pidx(Lc.px, Lc.pxy, i, j, k);
+  const uint8_t fl = Lc.flags[cc];
+  const int64_t cf = pidx(Lf.px, Lf.pxy, 2 * i, 2 * j, 2 * k);
+  const int64_t a = 1, b = Lf.px, e = Lf.pxy;
+  const int64_t off[7] = {a, b, e, a + b, b + e, a + e, a + b + e};
+  T s[4];
+  const T* src[4] = {Lf.r[0], Lf.r[1], Lf.r[2], Lf.rp};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T* x = src[q];
+    T acc = 0;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) acc += x[cf + off[o]] + x[cf - off[o]];
+    s[q] = x[cf] + (T)0.5 * acc;
+  }
+  const bool vf = fl & F_VFREE, ac = fl & F_ACT;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Lc.f[d][cc] = vf ? s[d] : (T)0;
+    Lc.u[d][cc] = (T)0;
+  }
+  Lc.g[cc] = ac ? s[3] : (T)0;
+  Lc.p[cc] = (T)0;
+}
+
+// Fine (U, P) += P (coarse U, P) on fine unknowns.
+template <class T>
+__global__ void k_prolong_add(LevelDev<T> Lf, LevelDev<T> Lc) {
+  int i, j, k;
+  if (!full_node(Lf, i, j, k)) return;
+  const int64_t cf = pidx(Lf.px, Lf.pxy, i, j, k);
+  const uint8_t fl = Lf.flags[cf];
+  if (!(fl & F_ACT)) return;
+  const int a = i & 1, b = j & 1, e = k & 1;
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int64_t c0 = pidx(Lc.px, Lc.pxy, I, J, K);
+  const bool mid = (a | b | e) != 0;
+  const int64_t c1 = pidx(Lc.px, Lc.pxy, I + a, J + b, K + e);
+  if (fl & F_VFREE) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* x = Lc.u[d];
+      const T v = mid ? (T)0.5 * (x[c0] + x[c1]) : x[c0];
+      Lf.u[d][cf] += v;
+    }
+  }
+  const T v = mid ? (T)0.5 * (Lc.p[c0] + Lc.p[c1]) : Lc.p[c0];
+  Lf.p[cf] += v;
+}
+
+// ---- reductions ---------------------------------------------------------------
+
+template <int W>
+__device__ __forceinline__ void block_reduce_store(double (&v)[W], double* out) {
+  __shared__ double sh[W][REDUCE_THREADS / 32];
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    double x = v[w];
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) sh[w][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      double acc = 0;
+      for (int q = 0; q < REDUCE_THREADS / 32; ++q) acc += sh[w][q];
+      out[w * gridDim.x + blockIdx.x] = acc;
+    }
+  }
+}
+
+template <int W>
+__global__ void k_final_sum(const double* partial, int nblocks, double* out) {
+  __shared__ double sh[W][32];
+  const int lane = threadIdx.x;  // 32 threads
+#pragma unroll
+  for (int w = 0; w < W; ++w) {
+    double acc = 0;
+    for (int b = lane; b < nblocks; b += 32) acc += partial[w * nblocks + b];
+    sh[w][lane] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) {
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      double acc = 0;
+      for (int q = 0; q < 32; ++q) acc += sh[w][q];
+      out[w] = acc;
+    }
+  }
+}
+
+template <class T>
+__global__ void k_residual_norm2(LevelDev<T> L, double* partial) {
+  double v[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L.nalloc; q += stride) {
+    const double a = (double)L.r[0][q], b = (double)L.r[1][q], c = (double)L.r[2][q], d = (double)L.rp[q];
+    v[0] += (a * a + b * b) + (c * c + d * d);
+  }
+  block_reduce_store<1>(v, partial);
+}
+
+template <class T>
+__global__ void k_mass_moments(LevelDev<T> L, double* partial) {
+  double v[2] = {0.0, 0.0};
+  const int64_t n = (int64_t)L.nx * L.ny * L.nz;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int i = (int)(q % L.nx);
+    const int j = (int)((q / L.nx) % L.ny);
+    const int k = (int)(q / ((int64_t)L.nx * L.ny));
+    const int64_t c = pidx(L.px, L.pxy, i, j, k);
+    const uint8_t fl = L.flags[c];
+    if (!(fl & F_ACT)) continue;
+    const double m = (double)lumped_mass(L, i, j, k, fl);
+    v[0] += m * (double)L.p[c];
+    v[1] += m;
+  }
+  block_reduce_store<2>(v, partial);
+}
+
+template <class T>
+__global__ void k_project(LevelDev<T> L, const double* mom) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  if (!(L.flags[c] & F_ACT)) return;
+  L.p[c] -= (T)(mom[0] / mom[1]);
+}
+
+// ---- right-hand side and its transpose (FP64) ------------------------------------
+
+// (M x)_node on a regular node: h^3 [2/5 x_c + 1/20 (axis and body neighbours) + 1/30 (face diagonals)].
+__device__ __forceinline__ double mass_reg(const double* x, int64_t c, int64_t px, int64_t pxy, double h3) {
+  const double ax = nb6(x, c, px, pxy) + (x[c + 1 + px + pxy] + x[c - 1 - px - pxy]);
+  const double fc = (x[c + 1 + px] + x[c - 1 - px]) + (x[c + px + pxy] + x[c - px - pxy]) +
+                    (x[c + 1 + pxy] + x[c - 1 - pxy]);
+  return h3 * (0.4 * x[c] + 0.05 * ax + fc * (1.0 / 30.0));
+}
+
+__global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1, const double* f2,
+                          const double* d0, const double* d1, const double* d2) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  const double* fn[3] = {f0, f1, f2};
+  const double* ud[3] = {d0, d1, d2};
+  const bool irr = fl & F_IRR;
+  if (fl & F_VFREE) {
+    double au[3];
+    row_A(L, ud, i, j, k, c, fl, au);
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      const double mf = irr ? L.h3 * (1.0 / 120.0) * irr_mass(L, fn[d], i, j, k) : mass_reg(fn[d], c, L.px, L.pxy, L.h3);
+      L.f[d][c] = mf - au[d];
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.f[d][c] = 0.0;
+  }
+  if (fl & F_ACT) {
+    // g = delta h_T^2 sum_d B_d^T f_d - sum_d B_d u_D,d
+    double gs = 0.0;
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      double bt[3];
+      row_BT(L, fn[d], i, j, k, c, fl, bt);
+      gs += bt[d];
+    }
+    L.g[c] = L.dh2 * gs - row_B(L, ud, i, j, k, c, fl);
+  } else {
+    L.g[c] = 0.0;
+  }
+}
+
+__global__ void k_sum_g(LevelDev<double> L, double* partial) {
+  double v[2] = {0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L.nalloc; q += stride) {
+    if (L.flags[q] & F_ACT) {
+      v[0] += L.g[q];
+      v[1] += 1.0;
+    }
+  }
+  block_reduce_store<2>(v, partial);
+}
+
+__global__ void k_sub_mean_g(LevelDev<double> L, const double* s) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const double mean = s[0] / s[1];
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L.nalloc; q += stride)
+    if (L.flags[q] & F_ACT) L.g[q] -= mean;
+}
+
+// grad_f_d = M lam_u,d + delta h_T^2 B_d lam_p on active nodes (transpose of
+// the right-hand side map f -> (M f, sum_d G_d f_d), with G_d = delta h_T^2 B_d^T).
+__global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, double* o2) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[c];
+  double* out[3] = {o0, o1, o2};
+  if (!(fl & F_ACT)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[d][c] = 0.0;
+    return;
+  }
+  const bool irr = fl & F_IRR;
+  double bl[3];
+  if (!irr) {
+    const Diff7<double> dl = diff7(L.p, c, L.px, L.pxy);
+    div12_all(dl, bl);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) bl[d] *= L.h2 * (1.0 / 12.0);
+  } else {
+    irr_grad_scalar(L, L.p, i, j, k, bl);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) bl[d] *= -L.h2 * (1.0 / 24.0);
+  }
+#pragma unroll 1
+  for (int d = 0; d < 3; ++d) {
+    const double mu = irr ? L.h3 * (1.0 / 120.0) * irr_mass(L, L.u[d], i, j, k) : mass_reg(L.u[d], c, L.px, L.pxy, L.h3);
+    out[d][c] = mu + L.dh2 * bl[d];
+  }
+}
+
+// ---- mixed precision -------------------------------------------------------------------
+
+__global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* partial) {
+  double v[1] = {0.0};
+  const int64_t n = (int64_t)X.nx * X.ny * X.nz;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int i = (int)(q % X.nx);
+    const int j = (int)((q / X.nx) % X.ny);
+    const int k = (int)(q / ((int64_t)X.nx * X.ny));
+    const int64_t c = pidx(X.px, X.pxy, i, j, k);
+    const uint8_t fl = X.flags[c];
+    const double* uu[3] = {X.u[0], X.u[1], X.u[2]};  // no address of kernel-parameter members
+    if (fl & F_VFREE) {
+      double au[3], bt[3];
+      row_A(X, uu, i, j, k, c, fl, au);
+      row_BT(X, X.p, i, j, k, c, fl, bt);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double r = X.f[d][c] - au[d] - bt[d];
+        E.f[d][c] = (float)r;
+        v[0] += r * r;
+      }
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) E.f[d][c] = 0.f;
+    }
+    if (fl & F_ACT) {
+      const double r = X.g[c] - row_B(X, uu, i, j, k, c, fl) + row_C(X, X.p, i, j, k, c, fl);
+      E.g[c] = (float)r;
+      v[0] += r * r;
+    } else {
+      E.g[c] = 0.f;
+    }
+  }
+  block_reduce_store<1>(v, partial);
+}
+
+__global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
+    X.u[0][q] += (double)E.u[0][q];
+    X.u[1][q] += (double)E.u[1][q];
+    X.u[2][q] += (double)E.u[2][q];
+    X.p[q] += (double)E.p[q];
+  }
+}
+
+__global__ void k_coarse_in(LevelDev<float> S, LevelDev<double> D) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D.nalloc; q += stride) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      D.f[d][q] = (double)S.f[d][q];
+      D.u[d][q] = (double)S.u[d][q];
+    }
+    D.g[q] = (double)S.g[q];
+    D.p[q] = (double)S.p[q];
+  }
+}
+
+__global__ void k_coarse_out(LevelDev<float> S, LevelDev<double> D) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D.nalloc; q += stride) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) S.u[d][q] = (float)D.u[d][q];
+    S.p[q] = (float)D.p[q];
+  }
+}
+
+// ---- layout conversion ---------------------------------------------------------------------
+
+__global__ void k_scatter(LevelDev<double> L, const double* src, int ncomp, double* d0, double* d1, double* d2,
+                          uint8_t mask) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const int64_t q = i + (int64_t)L.nx * (j + (int64_t)L.ny * k);
+  const bool keep = mask == 0 || (L.flags[c] & mask);
+  double* dst[3] = {d0, d1, d2};
+  for (int d = 0; d < ncomp; ++d) dst[d][c] = keep ? src[ncomp * q + d] : 0.0;
+}
+
+template <class T>
+__global__ void k_gather(LevelDev<T> L, const T* s0, const T* s1, const T* s2, int ncomp, double* dst) {
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const int64_t q = i + (int64_t)L.nx * (j + (int64_t)L.ny * k);
+  const T* src[3] = {s0, s1, s2};
+  for (int d = 0; d < ncomp; ++d) dst[ncomp * q + d] = (double)src[d][c];
+}
+
+__global__ void k_dirichlet_fill(const int64_t* idx, const double* val, int64_t ndir, double* dst) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= ndir) return;
+  const int64_t n = idx[q];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) dst[3 * n + d] = val[3 * q + d];
+}
+
+__global__ void k_dirichlet_gather(const int64_t* pad, int64_t ndir, const double* u0, const double* u1,
+                                   const double* u2, double* val) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= ndir) return;
+  const int64_t c = pad[q];
+  val[3 * q + 0] = u0[c];
+  val[3 * q + 1] = u1[c];
+  val[3 * q + 2] = u2[c];
+}
+
+__global__ void k_scale(double* x, int64_t n, double a) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) x[q] *= a;
+}
+
+__global__ void k_cast(const double* src, float* dst, int64_t n) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) dst[q] = (float)src[q];
+}
+
+int flat_blocks(int64_t n) {
+  const int64_t b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b < 1 ? 1 : b) : 152 * 16);
+}
+
+}  // namespace
+
+// ---- launchers -------------------------------------------------------------------------
+
+template <class T>
+void launch_vel_rhs(const LevelDev<T>& L, cudaStream_t s) {
+  k_vel_rhs<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
+}
+template <class T>
+void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
+  const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
+  k_vel_colour<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, inv);
+}
+template <class T>
+void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s) {
+  k_pres_rhs<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
+}
+template <class T>
+void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
+  const T w = (T)((double)L.omega / (6.0 * (double)L.c));
+  k_pres_colour<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, w);
+}
+template <class T>
+void launch_residual(const LevelDev<T>& L, cudaStream_t s) {
+  k_residual<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
+}
+template <class T>
+void launch_restrict(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s) {
+  k_restrict<T><<<full_grid(coarse), dim3(FX, FY), 0, s>>>(fine, coarse);
+}
+template <class T>
+void launch_prolong_add(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s) {
+  k_prolong_add<T><<<full_grid(fine), dim3(FX, FY), 0, s>>>(fine, coarse);
+}
+template <class T>
+void launch_residual_norm2(const LevelDev<T>& L, double* partial, double* out, cudaStream_t s) {
+  k_residual_norm2<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(L, partial);
+  k_final_sum<1><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+}
+template <class T>
+void launch_mass_moments(const LevelDev<T>& L, double* partial, double* out, cudaStream_t s) {
+  k_mass_moments<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(L, partial);
+  k_final_sum<2><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+}
+template <class T>
+void launch_project(const LevelDev<T>& L, const double* moments, cudaStream_t s) {
+  k_project<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L, moments);
+}
+template <class T>
+void launch_zero(const LevelDev<T>& L, int what, cudaStream_t s) {
+  T* base = what == 0 ? L.u[0] : (what == 1 ? L.f[0] : L.r[0]);
+  cudaMemsetAsync(base, 0, sizeof(T) * 4 * (size_t)L.nalloc, s);
+}
+
+void launch_set_rhs(const LevelDev<double>& L, const double* const* fnod, const double* const* uD, cudaStream_t s) {
+  k_set_rhs<<<full_grid(L), dim3(FX, FY), 0, s>>>(L, fnod[0], fnod[1], fnod[2], uD[0], uD[1], uD[2]);
+}
+void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s) {
+  k_sum_g<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(L, partial);
+  k_final_sum<2><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+  k_sub_mean_g<<<flat_blocks(L.nalloc), 256, 0, s>>>(L, out);
+}
+void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStream_t s) {
+  k_rhs_transpose<<<full_grid(L), dim3(FX, FY), 0, s>>>(L, out[0], out[1], out[2]);
+}
+void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
+                        cudaStream_t s) {
+  k_ir_residual<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(x, e, partial);
+  k_final_sum<1><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+}
+void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
+  k_ir_update<<<flat_blocks(x.nalloc), 256, 0, s>>>(x, e);
+}
+void launch_coarse_in(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s) {
+  k_coarse_in<<<flat_blocks(l64.nalloc), 256, 0, s>>>(l32, l64);
+}
+void launch_coarse_out(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s) {
+  k_coarse_out<<<flat_blocks(l64.nalloc), 256, 0, s>>>(l32, l64);
+}
+void launch_scatter(const LevelDev<double>& L, const double* src, int ncomp, double* const* dst, uint8_t mask,
+                    cudaStream_t s) {
+  k_scatter<<<full_grid(L), dim3(FX, FY), 0, s>>>(L, src, ncomp, dst[0], ncomp > 1 ? dst[1] : dst[0],
+                                                   ncomp > 2 ? dst[2] : dst[0], mask);
+}
+template <class T>
+void launch_gather(const LevelDev<T>& L, const T* const* src, int ncomp, double* dst, cudaStream_t s) {
+  k_gather<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L, src[0], ncomp > 1 ? src[1] : src[0],
+                                                     ncomp > 2 ? src[2] : src[0], ncomp, dst);
+}
+void launch_dirichlet_fill(const int64_t* idx, const double* val, int64_t ndir, const LevelDev<double>&, double* dst,
+                           cudaStream_t s) {
+  if (ndir == 0) return;
+  k_dirichlet_fill<<<(unsigned)((ndir + 255) / 256), 256, 0, s>>>(idx, val, ndir, dst);
+}
+void launch_dirichlet_gather(const int64_t* pad, int64_t ndir, const LevelDev<double>& L, double* val,
+                             cudaStream_t s) {
+  if (ndir == 0) return;
+  k_dirichlet_gather<<<(unsigned)((ndir + 255) / 256), 256, 0, s>>>(pad, ndir, L.u[0], L.u[1], L.u[2], val);
+}
+void launch_scale(double* x, int64_t n, double a, cudaStream_t s) { k_scale<<<flat_blocks(n), 256, 0, s>>>(x, n, a); }
+void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s) {
+  k_cast<<<flat_blocks(n), 256, 0, s>>>(src, dst, n);
+}
+
+#define HHG_INST(T)                                                                                    \
+  template void launch_vel_rhs<T>(const LevelDev<T>&, cudaStream_t);                                    \
+  template void launch_vel_colour<T>(const LevelDev<T>&, int, cudaStream_t);                            \
+  template void launch_pres_rhs<T>(const LevelDev<T>&, cudaStream_t);                                   \
+  template void launch_pres_colour<T>(const LevelDev<T>&, int, cudaStream_t);                           \
+  template void launch_residual<T>(const LevelDev<T>&, cudaStream_t);                                   \
+  template void launch_restrict<T>(const LevelDev<T>&, const LevelDev<T>&, cudaStream_t);               \
+  template void launch_prolong_add<T>(const LevelDev<T>&, const LevelDev<T>&, cudaStream_t);            \
+  template void launch_residual_norm2<T>(const LevelDev<T>&, double*, double*, cudaStream_t);           \
+  template void launch_mass_moments<T>(const LevelDev<T>&, double*, double*, cudaStream_t);             \
+  template void launch_project<T>(const LevelDev<T>&, const double*, cudaStream_t);                     \
+  template void launch_zero<T>(const LevelDev<T>&, int, cudaStream_t);                                  \
+  template void launch_gather<T>(const LevelDev<T>&, const T* const*, int, double*, cudaStream_t);
+
+HHG_INST(double)
+HHG_INST(float)
+
+}  // namespace hhg

@@ -1,0 +1,80 @@
+// Host-side launchers of the level kernels (hhg_kernels.cu, hhg_coarse.cu).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "hhg_device.cuh"
+
+namespace hhg {
+
+// Smoother pieces (Sec. 3.3 inexact Uzawa step, Sec. 3.5 smoothers)
+template <class T> void launch_vel_rhs(const LevelDev<T>& L, cudaStream_t s);
+template <class T> void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s);
+template <class T> void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s);
+template <class T> void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s);
+
+// Residual (RU, RP) = (F, G) - K (U, P); zero on nodes without unknowns.
+template <class T> void launch_residual(const LevelDev<T>& L, cudaStream_t s);
+
+// Transfers between level l (fine) and l-1 (coarse).
+template <class T> void launch_restrict(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s);
+template <class T> void launch_prolong_add(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s);
+
+// Reductions: partial sums per block (REDUCE_BLOCKS of them, `width` values
+// each) followed by a fixed-order final sum into out[0..width).
+constexpr int REDUCE_BLOCKS = 304;
+constexpr int REDUCE_THREADS = 256;
+template <class T> void launch_residual_norm2(const LevelDev<T>& L, double* partial, double* out, cudaStream_t s);
+template <class T> void launch_mass_moments(const LevelDev<T>& L, double* partial, double* out, cudaStream_t s);
+// P -= moments[0] / moments[1] on active nodes.
+template <class T> void launch_project(const LevelDev<T>& L, const double* moments, cudaStream_t s);
+
+// Zero every field of the set {U, P} (what = 0), {F, G} (1), {RU, RP} (2).
+template <class T> void launch_zero(const LevelDev<T>& L, int what, cudaStream_t s);
+
+// Right-hand side of the finest level from staged nodal arrays (padded
+// layout, component planes): fnod[3], uD[3] (uD zero off Dirichlet nodes).
+void launch_set_rhs(const LevelDev<double>& L, const double* const* fnod, const double* const* uD, cudaStream_t s);
+// G -= mean(G) over active nodes (two passes through partial/out).
+void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s);
+
+// Gradient of the right-hand side map: grad_f[d] = M lam_u[d] + G_d^T lam_p
+// with lam fields in L.u / L.p of an FP64 level, written to out[3] (padded).
+void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStream_t s);
+
+// Mixed precision: FP64 residual of (x, b) written as FP32 into e.f/e.g,
+// squared norm partials; and x += e.
+void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
+                        cudaStream_t s);
+void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s);
+// Coarsest level of the FP32 hierarchy through the FP64 coarse solver.
+void launch_coarse_in(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s);
+void launch_coarse_out(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s);
+
+// Layout conversion between contiguous (n, 3)/(n,) arrays and padded fields.
+// mask: nodes whose value is kept (others get 0); 0 = keep all.
+void launch_scatter(const LevelDev<double>& L, const double* src, int ncomp, double* const* dst, uint8_t mask,
+                    cudaStream_t s);
+template <class T>
+void launch_gather(const LevelDev<T>& L, const T* const* src, int ncomp, double* dst, cudaStream_t s);
+// u_out[dir] = values of the compact Dirichlet list
+void launch_dirichlet_fill(const int64_t* idx, const double* val, int64_t ndir, const LevelDev<double>& L, double* dst,
+                           cudaStream_t s);
+// val (3 per entry) = U at the padded indices pad (compact Dirichlet data)
+void launch_dirichlet_gather(const int64_t* pad, int64_t ndir, const LevelDev<double>& L, double* val,
+                             cudaStream_t s);
+void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s);
+void launch_scale(double* x, int64_t n, double a, cudaStream_t s);
+
+// Coarse-grid solver (hhg_coarse.cu): (U, P) += PMINRES correction of the
+// residual equation, FP64, one thread block.  scratch: COARSE_VECTORS fields.
+constexpr int COARSE_FIELDS = 48;
+struct CoarseParams {
+  int minres_max;
+  double minres_rtol;
+  int cg_max;
+  double cg_rtol;
+};
+void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s);
+
+}  // namespace hhg

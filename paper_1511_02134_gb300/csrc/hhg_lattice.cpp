@@ -1,0 +1,315 @@
+// Host-side lattice logic: macro mesh validation, node classification,
+// boundary rasterisation and outflow weights.  Pure C++ (no CUDA), so the
+// classification can be checked on machines without a GPU.
+#include "hhg_lattice.h"
+
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <map>
+#include <thread>
+
+#include "../../include/hhg_stokes.h"
+#include "hhg_common.h"
+
+namespace hhg {
+
+namespace {
+
+using Key3 = std::array<int64_t, 3>;
+
+int axis_step(const Key3& d, int* sign) {
+  // returns the axis if d is +-e_axis, else -1
+  int nz = 0, ax = -1;
+  for (int a = 0; a < 3; ++a) {
+    if (d[a] != 0) {
+      ++nz;
+      ax = a;
+    }
+  }
+  if (nz != 1 || (d[ax] != 1 && d[ax] != -1)) return -1;
+  *sign = (int)d[ax];
+  return ax;
+}
+
+}  // namespace
+
+int build_macro_lattice(const double* V, int64_t nv, const int32_t* T, int64_t nt,
+                        const uint8_t* bc, MacroLattice& out, std::string& err) {
+  if (!V || !T || nv < 4 || nt < 1) {
+    err = "macro mesh needs at least 4 vertices and 1 tetrahedron";
+    return HHG_EINVAL;
+  }
+  for (int64_t t = 0; t < nt * 4; ++t) {
+    if (T[t] < 0 || T[t] >= nv) {
+      err = "tetrahedron vertex id out of range";
+      return HHG_EINVAL;
+    }
+  }
+  // spacing from the first edge of the first tetrahedron
+  double e[3];
+  for (int a = 0; a < 3; ++a) e[a] = V[3 * T[1] + a] - V[3 * T[0] + a];
+  const double H = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+  if (!(H > 0) || !std::isfinite(H)) {
+    err = "degenerate first edge";
+    return HHG_EMESH;
+  }
+  double lo[3] = {INFINITY, INFINITY, INFINITY};
+  for (int64_t t = 0; t < nt * 4; ++t)
+    for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], V[3 * T[t] + a]);
+  std::vector<Key3> L(nv, Key3{0, 0, 0});
+  std::vector<char> used(nv, 0);
+  for (int64_t t = 0; t < nt * 4; ++t) used[T[t]] = 1;
+  for (int64_t v = 0; v < nv; ++v) {
+    if (!used[v]) continue;
+    for (int a = 0; a < 3; ++a) {
+      const double x = (V[3 * v + a] - lo[a]) / H;
+      const double r = std::nearbyint(x);
+      if (!std::isfinite(x) || std::fabs(x - r) > 1e-9 * std::max(1.0, std::fabs(x))) {
+        err = "macro vertex not on the lattice of the first edge's spacing";
+        return HHG_EMESH;
+      }
+      L[v][a] = (int64_t)r;
+    }
+  }
+  int64_t hi[3] = {0, 0, 0};
+  for (int64_t v = 0; v < nv; ++v)
+    if (used[v])
+      for (int a = 0; a < 3; ++a) hi[a] = std::max(hi[a], L[v][a]);
+  if (hi[0] < 1 || hi[1] < 1 || hi[2] < 1 || hi[0] > 4096 || hi[1] > 4096 || hi[2] > 4096) {
+    err = "macro lattice extent out of range";
+    return HHG_EMESH;
+  }
+  out.H = H;
+  for (int a = 0; a < 3; ++a) out.origin[a] = lo[a];
+  out.mx = (int)hi[0];
+  out.my = (int)hi[1];
+  out.mz = (int)hi[2];
+  out.mask.assign((size_t)out.mx * out.my * out.mz, 0);
+  out.bfaces.clear();
+  out.has_outflow = false;
+
+  // cell and path of every tetrahedron
+  for (int64_t t = 0; t < nt; ++t) {
+    const Key3& p0 = L[T[4 * t + 0]];
+    const Key3& p1 = L[T[4 * t + 1]];
+    const Key3& p2 = L[T[4 * t + 2]];
+    const Key3& p3 = L[T[4 * t + 3]];
+    Key3 d1, d2, d3;
+    for (int a = 0; a < 3; ++a) {
+      d1[a] = p1[a] - p0[a];
+      d2[a] = p2[a] - p1[a];
+      d3[a] = p3[a] - p2[a];
+    }
+    int s1 = 0, s2 = 0, s3 = 0;
+    const int a1 = axis_step(d1, &s1), a2 = axis_step(d2, &s2), a3 = axis_step(d3, &s3);
+    if (a1 < 0 || a2 < 0 || a3 < 0 || a1 == a2 || a2 == a3 || a1 == a3 || s1 != s2 || s2 != s3) {
+      err = "tetrahedron " + std::to_string(t) +
+            " is not a lattice Kuhn tetrahedron listed along its path";
+      return HHG_EMESH;
+    }
+    Key3 cell;
+    int path;
+    if (s1 > 0) {
+      cell = p0;
+      path = path_index(a1, a2, a3);
+    } else {
+      cell = p3;
+      path = path_index(a3, a2, a1);
+    }
+    const size_t ci = (size_t)cell[0] + (size_t)out.mx * ((size_t)cell[1] + (size_t)out.my * cell[2]);
+    if (out.mask[ci] & (1u << path)) {
+      err = "duplicate tetrahedron " + std::to_string(t);
+      return HHG_EMESH;
+    }
+    out.mask[ci] |= (uint8_t)(1u << path);
+  }
+
+  // boundary faces: faces that belong to exactly one tetrahedron
+  std::map<std::array<int64_t, 9>, std::pair<int, int64_t>> faces;  // key -> (count, t*4+f)
+  for (int64_t t = 0; t < nt; ++t) {
+    for (int f = 0; f < 4; ++f) {
+      std::array<Key3, 3> fv;
+      int k = 0;
+      for (int m = 0; m < 4; ++m)
+        if (m != f) fv[k++] = L[T[4 * t + m]];
+      std::sort(fv.begin(), fv.end());
+      std::array<int64_t, 9> key;
+      for (int i = 0; i < 3; ++i)
+        for (int a = 0; a < 3; ++a) key[3 * i + a] = fv[i][a];
+      auto it = faces.find(key);
+      if (it == faces.end())
+        faces.emplace(key, std::make_pair(1, 4 * t + f));
+      else
+        it->second.first += 1;
+    }
+  }
+  for (auto& kv : faces) {
+    if (kv.second.first > 2) {
+      err = "non-manifold macro face";
+      return HHG_EMESH;
+    }
+    if (kv.second.first != 1) continue;
+    const int64_t tf = kv.second.second;
+    const int64_t t = tf / 4;
+    const int f = (int)(tf % 4);
+    const uint8_t code = bc ? bc[tf] : (uint8_t)HHG_BC_AUTO;
+    if (code > HHG_BC_OUTFLOW) {
+      err = "unknown boundary flag";
+      return HHG_EINVAL;
+    }
+    BoundaryFace bf;
+    int k = 0;
+    for (int m = 0; m < 4; ++m)
+      if (m != f) {
+        for (int a = 0; a < 3; ++a) bf.v[k][a] = L[T[4 * t + m]][a];
+        ++k;
+      }
+    bf.flag = code == HHG_BC_OUTFLOW ? 2 : 1;
+    if (bf.flag == 2) out.has_outflow = true;
+    double u[3], w[3], n[3];
+    for (int a = 0; a < 3; ++a) {
+      u[a] = (double)(bf.v[1][a] - bf.v[0][a]);
+      w[a] = (double)(bf.v[2][a] - bf.v[0][a]);
+    }
+    n[0] = u[1] * w[2] - u[2] * w[1];
+    n[1] = u[2] * w[0] - u[0] * w[2];
+    n[2] = u[0] * w[1] - u[1] * w[0];
+    const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double to_opp = 0;
+    for (int a = 0; a < 3; ++a) to_opp += n[a] * (double)(L[T[4 * t + f]][a] - bf.v[0][a]);
+    const double sgn = to_opp > 0 ? -1.0 : 1.0;
+    for (int a = 0; a < 3; ++a) bf.normal[a] = sgn * n[a] / nn;
+    bf.area = 0.5 * nn * H * H;
+    out.bfaces.push_back(bf);
+  }
+  return HHG_OK;
+}
+
+LevelShape level_shape(const MacroLattice& m, int level) {
+  LevelShape s;
+  s.level = level;
+  const int N = 1 << level;
+  s.nx = m.mx * N + 1;
+  s.ny = m.my * N + 1;
+  s.nz = m.mz * N + 1;
+  return s;
+}
+
+int active_incident(const MacroLattice& m, int level, int i, int j, int k) {
+  int count = 0;
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+    for (int s = 0; s < 6; ++s) {
+      if (corner_local(s, qx, qy, qz) < 0) continue;
+      if (tet_active(m.mask.data(), m.mx, m.my, m.mz, level, i - qx, j - qy, k - qz, s)) ++count;
+    }
+  }
+  return count;
+}
+
+namespace {
+
+// Visit every fine node of a boundary face at `level`.
+template <class F>
+void for_face_nodes(const BoundaryFace& bf, int level, F&& fn) {
+  const int64_t N = 1ll << level;
+  int64_t A[3], U[3], W[3];
+  for (int a = 0; a < 3; ++a) {
+    A[a] = bf.v[0][a] * N;
+    U[a] = bf.v[1][a] - bf.v[0][a];  // one fine step along each macro edge
+    W[a] = bf.v[2][a] - bf.v[0][a];
+  }
+  for (int64_t s = 0; s <= N; ++s)
+    for (int64_t t = 0; s + t <= N; ++t)
+      fn(A[0] + s * U[0] + t * W[0], A[1] + s * U[1] + t * W[1], A[2] + s * U[2] + t * W[2]);
+}
+
+}  // namespace
+
+void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
+  const LevelShape sh = level_shape(m, level);
+  const int N = 1 << level;
+  const int64_t nxy = (int64_t)sh.nx * sh.ny;
+  auto work = [&](int k0, int k1) {
+    for (int k = k0; k < k1; ++k) {
+      for (int j = 0; j < sh.ny; ++j) {
+        for (int i = 0; i < sh.nx; ++i) {
+          int count;
+          // fast path: strictly inside one macro cell
+          if ((i % N) && (j % N) && (k % N)) {
+            const uint8_t mm = m.mask[(size_t)(i / N) + (size_t)m.mx * ((size_t)(j / N) + (size_t)m.my * (k / N))];
+            count = mm == 63 ? 24 : (mm == 0 ? 0 : active_incident(m, level, i, j, k));
+          } else {
+            count = active_incident(m, level, i, j, k);
+          }
+          uint8_t f = 0;
+          if (count > 0) f |= F_ACT;
+          if (count > 0 && count < 24) f |= F_IRR;
+          flags[i + sh.nx * j + nxy * k] = f;
+        }
+      }
+    }
+  };
+  unsigned nth = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if ((int64_t)sh.nx * sh.ny * sh.nz < (1 << 16)) nth = 1;
+  std::vector<std::thread> th;
+  const int chunk = (sh.nz + (int)nth - 1) / (int)nth;
+  for (unsigned t = 0; t < nth; ++t) {
+    const int k0 = (int)t * chunk, k1 = std::min(sh.nz, k0 + chunk);
+    if (k0 < k1) th.emplace_back(work, k0, k1);
+  }
+  for (auto& x : th) x.join();
+  // boundary faces: Dirichlet first, then outflow
+  for (const BoundaryFace& bf : m.bfaces) {
+    const uint8_t bit = bf.flag == 1 ? F_DIR : F_OUT;
+    for_face_nodes(bf, level, [&](int64_t x, int64_t y, int64_t z) {
+      flags[x + sh.nx * y + nxy * z] |= bit;
+    });
+  }
+  const int64_t n = sh.n();
+  for (int64_t i = 0; i < n; ++i) {
+    uint8_t f = flags[i];
+    if (f & F_DIR) f &= (uint8_t)~F_OUT;
+    if ((f & F_ACT) && !(f & F_DIR)) f |= F_VFREE;
+    flags[i] = f;
+  }
+}
+
+void outflow_weights(const MacroLattice& m, int level, double* w) {
+  const LevelShape sh = level_shape(m, level);
+  const int64_t nxy = (int64_t)sh.nx * sh.ny;
+  std::fill(w, w + 3 * sh.n(), 0.0);
+  const int64_t N = 1ll << level;
+  for (const BoundaryFace& bf : m.bfaces) {
+    if (bf.flag != 2) continue;
+    // uniform subdivision of the macro triangle into N^2 triangles of equal area
+    const double third = bf.area / (double)(N * N) / 3.0;
+    int64_t A[3], U[3], W[3];
+    for (int a = 0; a < 3; ++a) {
+      A[a] = bf.v[0][a] * N;
+      U[a] = bf.v[1][a] - bf.v[0][a];
+      W[a] = bf.v[2][a] - bf.v[0][a];
+    }
+    auto node = [&](int64_t s, int64_t t) {
+      return (A[0] + s * U[0] + t * W[0]) + sh.nx * (A[1] + s * U[1] + t * W[1]) + nxy * (A[2] + s * U[2] + t * W[2]);
+    };
+    auto add = [&](int64_t id) {
+      for (int a = 0; a < 3; ++a) w[3 * id + a] += third * bf.normal[a];
+    };
+    for (int64_t s = 0; s < N; ++s) {
+      for (int64_t t = 0; s + t < N; ++t) {
+        add(node(s, t));
+        add(node(s + 1, t));
+        add(node(s, t + 1));
+        if (s + t + 1 < N) {
+          add(node(s + 1, t));
+          add(node(s, t + 1));
+          add(node(s + 1, t + 1));
+        }
+      }
+    }
+  }
+}
+
+}  // namespace hhg

@@ -1,0 +1,344 @@
+"""GPU parity: every step of the CUDA path against the CPU oracle, element by
+element, on the same seeded inputs, through the C ABI.
+
+Tolerances: FP64 single operations agree to 1e-12 relative to the field's
+maximum (rounding order differs: factored stencils vs assembled rows);
+whole cycles to 1e-10 (1e-9 where the coarse MINRES runs 30+ iterations:
+its recurrence amplifies the rounding-order differences of dot products);
+converged solutions to 1e-10.  FP32 steps agree with
+the FP64 oracle to 1e-5 relative (single-precision rounding of ~30
+dependent operations), and FP32+IR solutions reach the FP64 residual
+tolerance.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint, direct, multigrid as MG
+from tests.helpers import (lattice_index, macro_by_name, nodal_to_lattice, p_from_lattice, p_to_lattice,
+                           rel_err, u_from_lattice, u_to_lattice)
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1511_02134_gb300 as p
+    return p
+
+
+def _pair(pkg, name, finest, coarsest=2, **opt):
+    macro = macro_by_name(name)
+    mesh = pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, finest, coarsest_level=coarsest, **opt)
+    oo = MG.Options(**{k: v for k, v in opt.items() if k in MG.Options.__dataclass_fields__})
+    H = MG.build_hierarchy(macro, finest, coarsest=coarsest, opt=oo)
+    return macro, mesh, H
+
+
+def _random_state(H, l, seed):
+    L = H.levels[l]
+    rng = np.random.default_rng(seed)
+    return (rng.standard_normal((3, L.n_u)), rng.standard_normal(L.n_p),
+            rng.standard_normal((3, L.n_u)), rng.standard_normal(L.n_p))
+
+
+def _load(mesh, H, l, state, precision=0):
+    L = H.levels[l]
+    dims = mesh.dims(l)
+    u, p, f, g = state
+    mesh.level_field(l, "U", precision, u_to_lattice(L, dims, u))
+    mesh.level_field(l, "P", precision, p_to_lattice(L, dims, p))
+    mesh.level_field(l, "F", precision, u_to_lattice(L, dims, f))
+    mesh.level_field(l, "G", precision, p_to_lattice(L, dims, g))
+
+
+def _read_up(mesh, H, l, precision=0):
+    L = H.levels[l]
+    dims = mesh.dims(l)
+    return (u_from_lattice(L, dims, mesh.level_field(l, "U", precision)),
+            p_from_lattice(L, dims, mesh.level_field(l, "P", precision)))
+
+
+# ---- operator and right-hand side ---------------------------------------------------
+
+@pytest.mark.parametrize("name,level", [("cube", 2), ("cube", 4), ("cube", 5), ("channel", 1), ("channel", 2),
+                                        ("partial", 3)])
+def test_apply_operator(pkg, name, level):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level))
+    L = H.levels[level]
+    dims = mesh.dims()
+    u, p, _, _ = _random_state(H, level, 1)
+    ku, kp = mesh.apply_operator(u_to_lattice(L, dims, u), p_to_lattice(L, dims, p))
+    ou, op = L.apply(u, p)
+    assert rel_err(u_from_lattice(L, dims, ku), ou) < TOL64
+    assert rel_err(p_from_lattice(L, dims, kp), op) < TOL64
+    # nothing written off the unknowns
+    lat = lattice_index(L, dims)
+    mask = np.ones(len(kp), bool)
+    mask[lat] = False
+    assert np.all(kp[mask] == 0) and np.all(ku[mask] == 0)
+
+
+@pytest.mark.parametrize("name,level", [("cube", 3), ("cube", 5), ("channel", 2), ("partial", 3)])
+def test_set_rhs(pkg, name, level):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level))
+    L = H.levels[level]
+    dims = mesh.dims()
+    x = mesh.node_coords()
+    rng = np.random.default_rng(3)
+    fn = rng.standard_normal(x.shape)
+    ud = W.manufactured_velocity(x) if name != "channel" else W.channel_inflow(x)
+    mesh.set_rhs(fn, ud)
+    lat = lattice_index(L, dims)
+    f, g = L.rhs(fn[lat], ud[lat])
+    assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "F")), f) < TOL64
+    assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "G")), g) < TOL64
+
+
+# ---- smoother pieces, transfers, coarse solve ---------------------------------------------
+
+@pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3)])
+def test_smoother_pieces(pkg, name, level):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level))
+    L = H.levels[level]
+    dims = mesh.dims()
+    st = _random_state(H, level, 7)
+    u, p, f, g = (a.copy() for a in st)
+    _load(mesh, H, level, st)
+    # RU = F - B^T P
+    mesh.level_op(level, "vel_rhs")
+    ru = np.stack([f[d] - L.BT[d] @ p for d in range(3)])
+    assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU")), ru) < TOL64
+    # forward and backward velocity sweeps with RU as right-hand side
+    mesh.level_op(level, "vel_forward")
+    for d in range(3):
+        MG._gs_sweep(L.A, L.A_diag, u[d], ru[d], H.colours_u[level], (0, 1, 2, 3))
+    gu, _ = _read_up(mesh, H, level)
+    assert rel_err(gu, u) < TOL64
+    mesh.level_op(level, "vel_backward")
+    for d in range(3):
+        MG._gs_sweep(L.A, L.A_diag, u[d], ru[d], H.colours_u[level], (3, 2, 1, 0))
+    gu, _ = _read_up(mesh, H, level)
+    assert rel_err(gu, u) < TOL64
+    # RP = B U - G, then the relaxed pressure sweep
+    mesh.level_op(level, "pres_rhs")
+    rp = sum(L.B[d] @ u[d] for d in range(3)) - g
+    assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP")), rp) < TOL64
+    mesh.level_op(level, "pres_sweep")
+    MG._gs_sweep(L.C, L.C_diag, p, rp, H.colours_p[level], (0, 1, 2, 3), relax=H.opt.omega)
+    _, gp = _read_up(mesh, H, level)
+    assert rel_err(gp, p) < TOL64
+    # whole Uzawa steps
+    _load(mesh, H, level, st)
+    mesh.level_op(level, "uzawa_step", count=3)
+    u, p, f, g = (a.copy() for a in st)
+    for _ in range(3):
+        MG.uzawa_step(H, level, u, p, f, g)
+    gu, gp = _read_up(mesh, H, level)
+    assert rel_err(gu, u) < 1e-11 and rel_err(gp, p) < 1e-11
+    # residual
+    mesh.level_op(level, "residual")
+    ru, rp = L.residual(u, p, f, g)
+    assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU")), ru) < 1e-11
+    assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP")), rp) < 1e-11
+
+
+@pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
+def test_transfers(pkg, name, level):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=level - 1)
+    Lf, Lc = H.levels[level], H.levels[level - 1]
+    df, dc = mesh.dims(level), mesh.dims(level - 1)
+    rng = np.random.default_rng(11)
+    ru = rng.standard_normal((3, Lf.n_u))
+    rp = rng.standard_normal(Lf.n_p)
+    mesh.level_field(level, "RU", 0, u_to_lattice(Lf, df, ru))
+    mesh.level_field(level, "RP", 0, p_to_lattice(Lf, df, rp))
+    mesh.level_op(level, "restrict")
+    fc = np.stack([H.Pu[level].T @ ru[d] for d in range(3)])
+    gc = H.P[level].T @ rp
+    assert rel_err(u_from_lattice(Lc, dc, mesh.level_field(level - 1, "F")), fc) < TOL64
+    assert rel_err(p_from_lattice(Lc, dc, mesh.level_field(level - 1, "G")), gc) < TOL64
+    assert np.all(mesh.level_field(level - 1, "U") == 0)
+    # prolongate a random coarse correction onto a random fine iterate
+    uc = rng.standard_normal((3, Lc.n_u))
+    pc = rng.standard_normal(Lc.n_p)
+    uf = rng.standard_normal((3, Lf.n_u))
+    pf = rng.standard_normal(Lf.n_p)
+    mesh.level_field(level - 1, "U", 0, u_to_lattice(Lc, dc, uc))
+    mesh.level_field(level - 1, "P", 0, p_to_lattice(Lc, dc, pc))
+    mesh.level_field(level, "U", 0, u_to_lattice(Lf, df, uf))
+    mesh.level_field(level, "P", 0, p_to_lattice(Lf, df, pf))
+    mesh.level_op(level, "prolong_add")
+    gu, gp = _read_up(mesh, H, level)
+    assert rel_err(gu, uf + np.stack([H.Pu[level] @ uc[d] for d in range(3)])) < TOL64
+    assert rel_err(gp, pf + H.P[level] @ pc) < TOL64
+
+
+@pytest.mark.parametrize("name,level,mx", [("cube", 2, 5), ("cube", 3, 30), ("channel", 0, 40), ("partial", 2, 30)])
+def test_coarse_solve(pkg, name, level, mx):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=level, coarse_minres_max=mx)
+    L = H.levels[level]
+    st = _random_state(H, level, 5)
+    _load(mesh, H, level, st)
+    mesh.level_op(level, "coarse_solve")
+    u, p, f, g = (a.copy() for a in st)
+    MG.vcycle(H, level, u, p, f, g)   # on the coarsest level: the MINRES correction
+    gu, gp = _read_up(mesh, H, level)
+    # rounding differences are amplified by the Krylov recurrence; 1e-9 is
+    # far below the 5e-3 tolerance the solver is asked for
+    assert rel_err(gu, u) < 1e-9 and rel_err(gp, p) < 1e-9
+
+
+# ---- cycles and solves ------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 3, 2, 5), ("cube", 5, 2, 5), ("channel", 2, 1, 200),
+                                                    ("partial", 3, 1, 30)])
+def test_vcycle_iterates(pkg, name, level, coarsest, mx):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx)
+    L = H.levels[level]
+    st = _random_state(H, level, 9)
+    _load(mesh, H, level, st)
+    u, p, f, g = (a.copy() for a in st)
+    tol = 1e-10 if mx <= 5 else 1e-9
+    for cyc in range(2):
+        mesh.level_op(level, "vcycle")
+        MG.vcycle(H, level, u, p, f, g)
+        gu, gp = _read_up(mesh, H, level)
+        print(name, level, "cycle", cyc, "u err", rel_err(gu, u), "p err", rel_err(gp, p))
+        assert rel_err(gu, u) < tol, cyc
+        assert rel_err(gp, p) < tol, cyc
+
+
+@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 4, 2, 5), ("cube", 5, 2, 5), ("channel", 3, 1, 200)])
+def test_fp64_solve_matches_oracle(pkg, name, level, coarsest, mx):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx)
+    L = H.levels[level]
+    dims = mesh.dims()
+    x = mesh.node_coords()
+    lat = lattice_index(L, dims)
+    if name == "cube":
+        fn, ud = W.manufactured_forcing(x), W.manufactured_velocity(x)
+    else:
+        fn, ud = np.zeros_like(x), W.channel_inflow(x)
+    mesh.set_rhs(fn, ud)
+    u, p, st = mesh.solve(tol=1e-10, max_cycles=40, mode=pkg.MODE_FP64)
+    f, g = L.rhs(fn[lat], ud[lat])
+    ref = MG.solve(H, f, g, tol=1e-10, max_cycles=40, keep_iterates=False)
+    assert st.status == 0 and st.cycles == ref.cycles
+    # relative residuals near 1e-10 sit at the rounding floor of a residual
+    # assembled from O(1) terms: compare with an absolute floor
+    np.testing.assert_allclose(st.history, ref.history, rtol=1e-7, atol=1e-14)
+    uo = L.scatter(ref.u, ud[lat])
+    assert rel_err(u[lat], uo) < 1e-10
+    assert rel_err(p[lat], ref.p) < 1e-10
+    if name == "cube":
+        m = L.m
+        assert abs(np.dot(m, p[lat])) < 1e-12 * np.abs(p).max()
+
+
+@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 5, 2, 5), ("channel", 3, 1, 200)])
+def test_fp32_ir_solve(pkg, name, level, coarsest, mx):
+    """FP32 V-cycles inside FP64 refinement reach the FP64 tolerance; the
+    solution differs from the FP64 solution by far less than it differs from
+    the exact discrete solution at that tolerance."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx)
+    L = H.levels[level]
+    dims = mesh.dims()
+    x = mesh.node_coords()
+    lat = lattice_index(L, dims)
+    if name == "cube":
+        fn, ud = W.manufactured_forcing(x), W.manufactured_velocity(x)
+    else:
+        fn, ud = np.zeros_like(x), W.channel_inflow(x)
+    mesh.set_rhs(fn, ud)
+    u32, p32, s32 = mesh.solve(tol=1e-8, max_cycles=40, mode=pkg.MODE_FP32_IR)
+    assert s32.status == 0 and s32.rel_residual <= 1e-8
+    mesh.set_rhs(fn, ud)
+    u64, p64, s64 = mesh.solve(tol=1e-12, max_cycles=60, mode=pkg.MODE_FP64)
+    assert s64.rel_residual <= 1e-12
+    # error of the FP32+IR solution w.r.t. the (nearly) exact discrete solution
+    eu = rel_err(u32[lat], u64[lat])
+    ep = rel_err(p32[lat], p64[lat])
+    assert eu < 1e-6 and ep < 1e-4, (eu, ep)
+
+
+def test_edge_cases(pkg):
+    cube = W.unit_cube()
+    # finest == coarsest: the solve is the coarse MINRES alone
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 2, coarsest_level=2, coarse_minres_max=200,
+                    coarse_minres_rtol=1e-12, coarse_cg_rtol=1e-14, coarse_cg_max=100)
+    x = mesh.node_coords()
+    mesh.set_rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    u, p, st = mesh.solve(tol=1e-9, max_cycles=20)
+    assert st.status == 0
+    H = MG.build_hierarchy(cube, 2)
+    L = H.levels[2]
+    lat = lattice_index(L, mesh.dims())
+    f, g = L.rhs(W.manufactured_forcing(L.mesh.xyz), W.manufactured_velocity(L.mesh.xyz))
+    ud, pd = direct.solve_direct(L, f, g)
+    assert rel_err(u[lat][L.free].T, ud) < 1e-8
+    mesh.close()
+    # zero right-hand side: nothing to do, zero solution
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 3)
+    mesh.set_rhs(None, None)
+    u, p, st = mesh.solve(tol=1e-8, max_cycles=10)
+    assert st.cycles == 0 and np.all(u == 0) and np.all(p == 0)
+    # call order
+    mesh2 = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 3)
+    with pytest.raises(pkg.HHGError) as e:
+        mesh2.solve()
+    assert e.value.code == -7
+    # coarsest level 0 hierarchy (deepest cycle)
+    mesh3 = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 4, coarsest_level=0, coarse_minres_max=50)
+    x = mesh3.node_coords()
+    mesh3.set_rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    _, _, st = mesh3.solve(tol=1e-8, max_cycles=30)
+    assert st.status == 0
+
+
+def test_paper_protocol_random_guess(pkg, golden):
+    """f = 0, u0 ~ U[0,1], p0 ~ U[0, 1/h_min] (Sec. 3.6), level 4 = paper L = 2:
+    GPU and oracle take the same number of cycles (paper: 9)."""
+    cube = W.unit_cube()
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 4)
+    H = MG.build_hierarchy(cube, 4)
+    L = H.levels[4]
+    dims = mesh.dims()
+    lat = lattice_index(L, dims)
+    h_min = (L.mesh.h ** 3 / 6.0) ** (1.0 / 3.0)
+    u0, p0 = W.random_initial_guess(mesh.num_nodes(), h_min, seed=0)
+    mesh.set_rhs(None, None)
+    mesh.set_initial(u0, p0)
+    _, _, st = mesh.solve(tol=1e-8, max_cycles=30)
+    f, g = L.rhs(None, None)
+    ref = MG.solve(H, f, g, u0=u0[lat][L.free].T, p0=p0[lat], tol=1e-8, max_cycles=30)
+    assert st.cycles == ref.cycles
+    assert abs(st.cycles - golden["itertime1_umg"]["rows"][0]["iter"]) <= 2
+
+
+# ---- adjoint ---------------------------------------------------------------------------------
+
+def test_adjoint_gradient_matches_oracle(pkg):
+    ch = W.obstacle_channel()
+    level = 2
+    mesh = pkg.Mesh(ch.vertices, ch.tets, ch.bc_flags, level, coarsest_level=1, coarse_minres_max=300)
+    L = MG.build_hierarchy(ch, level, coarsest=1).levels[level]
+    dims = mesh.dims()
+    lat = lattice_index(L, dims)
+    x = mesh.node_coords()
+    psi = W.outflow_flux_weight(x)
+    w = mesh.outflow_weights()
+    np.testing.assert_allclose(w[lat], L.ops.w_out, atol=1e-14)
+    mesh.set_rhs(None, W.channel_inflow(x))
+    mesh.solve(tol=1e-10, max_cycles=40)
+    grad, st = mesh.adjoint_gradient(ju=w * psi[:, None], tol=1e-12, max_cycles=80)
+    ref = adjoint.gradient_direct(L, psi[lat])
+    assert rel_err(grad[lat], ref) < 1e-9
+    # the forward iterate is left untouched
+    u2, _ = mesh.get_solution()
+    u1, _, _ = mesh.solve(tol=1e-10, max_cycles=0)
+    assert np.array_equal(u1, u2)
