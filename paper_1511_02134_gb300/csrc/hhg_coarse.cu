@@ -99,7 +99,7 @@ __device__ void applyA(const Ctx& C, const double* x, double* y) {
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
     const uint8_t fl = L.flags[c];
     if (!(fl & F_VFREE)) continue;
-    y[c] = (fl & F_IRR) ? L.nuh * irr_lap(L, x, i, j, k, c) : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
+    y[c] = (fl & F_IRR) ? irr_row_A1(L, x, i, j, k, c) : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
   }
   __syncthreads();
 }

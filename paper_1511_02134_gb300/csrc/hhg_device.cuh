@@ -196,6 +196,78 @@ __device__ __forceinline__ int irr_count(const LevelDev<T>& L, int i, int j, int
   return n;
 }
 
+// --- boundary-row paths ------------------------------------------------------
+// The element-sum rows run only on nodes flagged F_IRR.  They are kept out of
+// line: each gets its own stack frame, the regular fast path of every kernel
+// stays small, and no local array of a caller can share storage with the
+// temporaries of these loops.
+
+template <class T>
+__device__ __noinline__ void irr_row_A(const LevelDev<T>& L, const T* u0, const T* u1, const T* u2, int i, int j,
+                                       int k, int64_t c, T* out) {
+  out[0] = L.nuh * irr_lap(L, u0, i, j, k, c);
+  out[1] = L.nuh * irr_lap(L, u1, i, j, k, c);
+  out[2] = L.nuh * irr_lap(L, u2, i, j, k, c);
+}
+
+template <class T>
+__device__ __noinline__ T irr_row_A1(const LevelDev<T>& L, const T* x, int i, int j, int k, int64_t c) {
+  return L.nuh * irr_lap(L, x, i, j, k, c);
+}
+
+template <class T>
+__device__ __noinline__ void irr_row_BT(const LevelDev<T>& L, const T* p, int i, int j, int k, T* out) {
+  T gs[3];
+  irr_gradT(L, p, i, j, k, gs);
+  const T s = -L.h2 * (T)(1.0 / 24.0);
+  out[0] = s * gs[0];
+  out[1] = s * gs[1];
+  out[2] = s * gs[2];
+}
+
+template <class T>
+__device__ __noinline__ T irr_row_B(const LevelDev<T>& L, const T* u0, const T* u1, const T* u2, int i, int j,
+                                    int k) {
+  const T* x3[3] = {u0, u1, u2};
+  T gs[3];
+  irr_grad_sum(L, x3, i, j, k, gs);
+  return -L.h2 * (T)(1.0 / 24.0) * ((gs[0] + gs[1]) + gs[2]);
+}
+
+template <class T>
+__device__ __noinline__ T irr_row_C(const LevelDev<T>& L, const T* p, int i, int j, int k, int64_t c) {
+  return L.c * irr_lap(L, p, i, j, k, c);
+}
+
+// Diagonal and off-diagonal sum of the unit Laplacian row (Gauss-Seidel updates).
+template <class T>
+__device__ __noinline__ void irr_lap_parts(const LevelDev<T>& L, const T* x, int i, int j, int k, T* dg_of) {
+  T dg, of;
+  irr_lap_row(L, x, i, j, k, dg, of);
+  dg_of[0] = dg;
+  dg_of[1] = of;
+}
+
+template <class T>
+__device__ __noinline__ T irr_mass_row(const LevelDev<T>& L, const T* x, int i, int j, int k) {
+  return L.h3 * (T)(1.0 / 120.0) * irr_mass(L, x, i, j, k);
+}
+
+template <class T>
+__device__ __noinline__ void irr_grad_scalar_row(const LevelDev<T>& L, const T* x, int i, int j, int k, T* out) {
+  T gs[3];
+  irr_grad_scalar(L, x, i, j, k, gs);
+  const T s = -L.h2 * (T)(1.0 / 24.0);
+  out[0] = s * gs[0];
+  out[1] = s * gs[1];
+  out[2] = s * gs[2];
+}
+
+template <class T>
+__device__ __noinline__ T irr_lumped(const LevelDev<T>& L, int i, int j, int k) {
+  return L.h3 * (T)(1.0 / 24.0) * (T)irr_count(L, i, j, k);
+}
+
 // --- full rows of the Stokes operator ----------------------------------------
 
 // (A u_d)_node for all d (nodes with F_VFREE).
@@ -206,8 +278,7 @@ __device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, i
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[d] = L.nuh * ((T)6 * u[d][c] - nb6(u[d], c, L.px, L.pxy));
   } else {
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) out[d] = L.nuh * irr_lap(L, u[d], i, j, k, c);
+    irr_row_A(L, u[0], u[1], u[2], i, j, k, c, out);
   }
 }
 
@@ -223,11 +294,7 @@ __device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int i, 
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[d] = s * dv[d];
   } else {
-    T gs[3];
-    irr_gradT(L, p, i, j, k, gs);
-    const T s = -L.h2 * (T)(1.0 / 24.0);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) out[d] = s * gs[d];
+    irr_row_BT(L, p, i, j, k, out);
   }
 }
 
@@ -240,25 +307,22 @@ __device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, int 
     const T d1 = div12(diff7(u[1], c, L.px, L.pxy), 1);
     const T d2 = div12(diff7(u[2], c, L.px, L.pxy), 2);
     return L.h2 * (T)(1.0 / 12.0) * ((d0 + d1) + d2);
-  } else {
-    T gs[3];
-    irr_grad_sum(L, u, i, j, k, gs);
-    return -L.h2 * (T)(1.0 / 24.0) * ((gs[0] + gs[1]) + gs[2]);
   }
+  return irr_row_B(L, u[0], u[1], u[2], i, j, k);
 }
 
 // (C p)_node.
 template <class T>
 __device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, int i, int j, int k, int64_t c, uint8_t fl) {
   if (!(fl & F_IRR)) return L.c * ((T)6 * p[c] - nb6(p, c, L.px, L.pxy));
-  return L.c * irr_lap(L, p, i, j, k, c);
+  return irr_row_C(L, p, i, j, k, c);
 }
 
 // Lumped pressure mass m_i = int phi_i.
 template <class T>
 __device__ __forceinline__ T lumped_mass(const LevelDev<T>& L, int i, int j, int k, uint8_t fl) {
   if (!(fl & F_IRR)) return L.h3;
-  return L.h3 * (T)(1.0 / 24.0) * (T)irr_count(L, i, j, k);
+  return irr_lumped(L, i, j, k);
 }
 
 }  // namespace hhg

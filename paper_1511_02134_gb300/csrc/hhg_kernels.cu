@@ -73,9 +73,9 @@ __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   } else {
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
-      T dg, of;
-      irr_lap_row(L, L.u[d], i, j, k, dg, of);
-      L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
+      T dgof[2];
+      irr_lap_parts(L, L.u[d], i, j, k, dgof);
+      L.u[d][c] = (L.r[d][c] - L.nuh * dgof[1]) / (L.nuh * dgof[0]);
     }
   }
 }
@@ -106,10 +106,10 @@ __global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
     const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
     L.p[c] = pc + omega_over_6c * (L.rp[c] - cp);
   } else {
-    T dg, of;
-    irr_lap_row(L, L.p, i, j, k, dg, of);
-    const T cp = L.c * (dg * pc + of);
-    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
+    T dgof[2];
+    irr_lap_parts(L, L.p, i, j, k, dgof);
+    const T cp = L.c * (dgof[0] * pc + dgof[1]);
+    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dgof[0]);
   }
 }
 
@@ -303,7 +303,7 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
     row_A(L, ud, i, j, k, c, fl, au);
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
-      const double mf = irr ? L.h3 * (1.0 / 120.0) * irr_mass(L, fn[d], i, j, k) : mass_reg(fn[d], c, L.px, L.pxy, L.h3);
+      const double mf = irr ? irr_mass_row(L, fn[d], i, j, k) : mass_reg(fn[d], c, L.px, L.pxy, L.h3);
       L.f[d][c] = mf - au[d];
     }
   } else {
@@ -365,13 +365,11 @@ __global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, doub
 #pragma unroll
     for (int d = 0; d < 3; ++d) bl[d] *= L.h2 * (1.0 / 12.0);
   } else {
-    irr_grad_scalar(L, L.p, i, j, k, bl);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) bl[d] *= -L.h2 * (1.0 / 24.0);
+    irr_grad_scalar_row(L, L.p, i, j, k, bl);
   }
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    const double mu = irr ? L.h3 * (1.0 / 120.0) * irr_mass(L, L.u[d], i, j, k) : mass_reg(L.u[d], c, L.px, L.pxy, L.h3);
+    const double mu = irr ? irr_mass_row(L, L.u[d], i, j, k) : mass_reg(L.u[d], c, L.px, L.pxy, L.h3);
     out[d][c] = mu + L.dh2 * bl[d];
   }
 }
