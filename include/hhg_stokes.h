@@ -237,6 +237,30 @@ int hhg_time_op(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t op, in
 /* Kernels launched by this mesh so far (graph nodes counted per replay). */
 int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count);
 
+/* ---- allocation-free coarse-grid solve ---------------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory after set-up: code whose device
+ * memory comes from a fixed arena or a framework-owned pool, and real-time or
+ * latency-bound loops that cannot afford cudaMalloc/cudaFree (both may block
+ * on the whole device and may fail under memory pressure).  Once a mesh has
+ * been created (creation allocates), this call performs the coarse-grid
+ * MINRES correction of hhg_level_op(HHG_OP_COARSE_SOLVE) without allocating:
+ * its scratch is a 2 MiB file-scope device array (held by every GPU that
+ * loads the library until the process exits).
+ *   f (n, 3), g (n,): right-hand side on the coarsest level; u (n, 3), p (n,):
+ *   iterate on input, corrected iterate on output; n = hhg_num_nodes of the
+ *   coarsest level; host or device pointers, lattice order.
+ *   The mesh's coarsest-level fields and staging buffer are used as work
+ *   space, so do not overlap this call with other calls on the same mesh.
+ *   Errors: HHG_EINVAL when the coarsest level needs more than 2^18 scratch
+ *   doubles (48 fields of its padded lattice), HHG_ECUDA on CUDA errors.
+ *   The first call on a device looks up the array's device address (one
+ *   cudaGetSymbolAddress); make that first call before any stream capture.
+ *   Every call shares the one array per device, which keeps the last call's
+ *   contents; the solve clears what must start at zero.  Calls that overlap
+ *   on the GPU, from any mesh or thread, race on the array. */
+int hhg_coarse_solve_noalloc(hhg_mesh* mesh, const double* f, const double* g, double* u, double* p);
+
 /* ---- host-only lattice logic (no GPU needed) -------------------------------
  * Classify the nodes of `level` for a macro mesh (same arguments as
  * hhg_create_mesh); flags (n bytes) receives HHG_NODE_* bits and dims[3] the

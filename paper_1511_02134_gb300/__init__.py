@@ -107,6 +107,7 @@ def load_library():
         "hhg_lattice_classify": (I32, [P, I64, P, I64, P, I32, P, P]),
         "hhg_time_op": (I32, [P, I32, I32, I32, I32, P]),
         "hhg_kernel_launches": (I32, [P, P]),
+        "hhg_coarse_solve_noalloc": (I32, [P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -335,6 +336,17 @@ class Mesh:
         ms = ctypes.c_double()
         self._check(self._lib.hhg_time_op(self._h, level, precision, OP[op], reps, ctypes.byref(ms)))
         return ms.value
+
+    def coarse_solve_noalloc(self, f, g, u, p):
+        """Coarse-grid correction of (u, p) in place without device allocation
+        (hhg_coarse_solve_noalloc); arrays of the coarsest level."""
+        n = self.num_nodes(self.coarsest)
+        f = _as_f64(f, (n, 3))
+        g = _as_f64(g, (n,))
+        for a, shape in ((u, (n, 3)), (p, (n,))):
+            if _as_f64(a, shape) is not a:
+                raise ValueError("u and p must be contiguous float64 arrays (updated in place)")
+        self._check(self._lib.hhg_coarse_solve_noalloc(self._h, _ptr(f), _ptr(g), _ptr(u), _ptr(p)))
 
     def kernel_launches(self) -> int:
         n = ctypes.c_int64()

@@ -921,6 +921,38 @@ int hhg_level_field(hhg_mesh* M, int32_t level, int32_t precision, int32_t field
 
 static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op);
 
+int hhg_coarse_solve_noalloc(hhg_mesh* M, const double* f, const double* g, double* u, double* p) {
+  if (!M || !f || !g || !u || !p) return HHG_EINVAL;
+  CK(cudaSetDevice(M->device));
+  LevelHost& H = M->lv[M->coarsest];
+  LevelDev<double>& L = H.d64;
+  const int64_t n = H.sh.n();
+  int rc;
+  // inputs into the coarsest-level fields through the mesh's staging buffer
+  if ((rc = stage_in(M, f, 3 * n))) return rc;
+  launch_scatter(L, M->d_stage, 3, L.f, F_VFREE, M->stream);
+  if ((rc = stage_in(M, u, 3 * n))) return rc;
+  launch_scatter(L, M->d_stage, 3, L.u, F_VFREE, M->stream);
+  double* gp[1] = {L.g};
+  if ((rc = stage_in(M, g, n))) return rc;
+  launch_scatter(L, M->d_stage, 1, gp, F_ACT, M->stream);
+  double* pp[1] = {L.p};
+  if ((rc = stage_in(M, p, n))) return rc;
+  launch_scatter(L, M->d_stage, 1, pp, F_ACT, M->stream);
+  CoarseParams prm{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max, M->opt.coarse_cg_rtol};
+  if ((rc = coarse_solve_noalloc(L, prm, M->d_scalars + 5, M->stream, M->err))) return rc;
+  M->launches += 5;
+  const double* us[3] = {L.u[0], L.u[1], L.u[2]};
+  launch_gather<double>(L, us, 3, M->d_stage, M->stream);
+  if ((rc = stage_out(M, u, 3 * n))) return rc;
+  const double* ps[1] = {L.p};
+  launch_gather<double>(L, ps, 1, M->d_stage, M->stream);
+  if ((rc = stage_out(M, p, n))) return rc;
+  M->launches += 2;
+  CK(cudaGetLastError());
+  return HHG_OK;
+}
+
 int hhg_level_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32_t count) {
   int rc = check_level(M, level);
   if (rc) return rc;

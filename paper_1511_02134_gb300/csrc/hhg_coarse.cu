@@ -15,6 +15,10 @@
 //           gamma_{j+1} = sqrt(z_{j+1}.v_{j+1}); rotation a0..a3, c, s;
 //           w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1; x += c_{j+1} eta w_{j+1};
 //           eta <- -s_{j+1} eta; stop when |eta| <= rtol gamma_1.
+#include <mutex>
+#include <string>
+
+#include "../../include/hhg_stokes.h"
 #include "hhg_kernels.h"
 
 namespace hhg {
@@ -275,6 +279,60 @@ __global__ void __launch_bounds__(CT) k_coarse_minres(LevelDev<double> L, double
 
 void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s) {
   k_coarse_minres<<<1, CT, 0, s>>>(L, scratch, prm, info);
+}
+
+// ---- allocation-free variant -------------------------------------------------
+// Scratch of the coarse solve for callers that may not allocate device memory:
+// a file-scope device array of NOALLOC_COARSE_DOUBLES doubles (2 MiB), which
+// every GPU that loads the library holds until the process exits.  In host
+// code the symbol names a host-side stand-in, so the kernel is given the
+// device address looked up per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_coarse_scratch[NOALLOC_COARSE_DOUBLES];
+
+namespace {
+std::mutex g_noalloc_mutex;
+double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* info, cudaStream_t s,
+                         std::string& err) {
+  const int64_t need = (int64_t)COARSE_FIELDS * L.nalloc;
+  if (need > NOALLOC_COARSE_DOUBLES) {
+    err = "coarsest level needs " + std::to_string(need) + " scratch doubles; the allocation-free coarse solve holds " +
+          std::to_string(NOALLOC_COARSE_DOUBLES);
+    return HHG_EINVAL;
+  }
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+    return HHG_ECUDA;
+  }
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    err = "device index beyond the allocation-free table";
+    return HHG_EINVAL;
+  }
+  double* ptr = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[dev]) {
+      // once per device, with that device current (set by the caller)
+      e = cudaGetSymbolAddress((void**)&g_noalloc_ptr[dev], g_noalloc_coarse_scratch);
+      if (e != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+        return HHG_ECUDA;
+      }
+    }
+    ptr = g_noalloc_ptr[dev];
+  }
+  k_coarse_minres<<<1, CT, 0, s>>>(L, ptr, prm, info);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("coarse solve launch: ") + cudaGetErrorString(e);
+    return HHG_ECUDA;
+  }
+  return HHG_OK;
 }
 
 }  // namespace hhg

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "hhg_device.cuh"
 
 namespace hhg {
@@ -76,5 +78,12 @@ struct CoarseParams {
   double cg_rtol;
 };
 void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s);
+
+// Same solve with its scratch in a file-scope device array (no allocation).
+// Fails with HHG_EINVAL when COARSE_FIELDS * L.nalloc exceeds the array.
+constexpr int64_t NOALLOC_COARSE_DOUBLES = 1 << 18;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* info, cudaStream_t s,
+                         std::string& err);
 
 }  // namespace hhg
