@@ -27,6 +27,10 @@ struct LevelHost {
   double h = 0, hT2 = 0;
   std::vector<uint8_t> flags;  // lattice order
   uint8_t* d_flags = nullptr;
+  uint16_t* d_cls = nullptr;   // padded stencil class of boundary nodes
+  double* d_wt64 = nullptr;    // class row tables
+  float* d_wt32 = nullptr;
+  int n_classes = 0;
   int64_t n_vel = 0, n_pres = 0;
   double* mem64 = nullptr;
   float* mem32 = nullptr;
@@ -118,6 +122,7 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     L.nalloc = H.nalloc;
     L.flags = H.d_flags;
     L.mmask = M->d_mmask;
+    L.cls = H.d_cls;
     L.nuh = (T)(M->opt.nu * H.h);
     L.c = (T)(M->opt.delta * H.hT2 * H.h);
     L.h2 = (T)(H.h * H.h);
@@ -127,6 +132,8 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
   };
   set(H.d64);
   set(H.d32);
+  H.d64.wt = H.d_wt64;
+  H.d32.wt = H.d_wt32;
 }
 
 int ensure32(hhg_mesh* M) {
@@ -381,6 +388,9 @@ void release(hhg_mesh* M) {
     if (g) cudaGraphExecDestroy(g);
   for (auto& H : M->lv) {
     cudaFree(H.d_flags);
+    cudaFree(H.d_cls);
+    cudaFree(H.d_wt64);
+    cudaFree(H.d_wt32);
     cudaFree(H.mem64);
     cudaFree(H.mem32);
   }
@@ -528,6 +538,33 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     if ((e = cudaMemcpy(H.d_flags, padded.data(), H.nalloc, cudaMemcpyHostToDevice)) != cudaSuccess) {
       M->err = cudaGetErrorString(e);
       return bail(HHG_ECUDA);
+    }
+    // stencil classes of the boundary nodes and their row tables
+    {
+      std::vector<uint16_t> cls;
+      std::vector<double> table;
+      std::string cerr;
+      stencil_classes(M->macro, l, H.flags.data(), cls, table, H.n_classes, cerr);
+      if (!cerr.empty()) {
+        M->err = cerr;
+        return bail(HHG_EMESH);
+      }
+      std::vector<uint16_t> pcls(H.nalloc, 0);
+      for (int k = 0; k < H.sh.nz; ++k)
+        for (int j = 0; j < H.sh.ny; ++j)
+          for (int i = 0; i < H.sh.nx; ++i)
+            pcls[(i + 1) + H.px * (j + 1) + H.px * H.py * (k + 1)] =
+                cls[i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k)];
+      std::vector<float> table32(table.begin(), table.end());
+      if ((rc = dalloc(M, (void**)&H.d_cls, sizeof(uint16_t) * (size_t)H.nalloc))) return bail(rc);
+      if ((rc = dalloc(M, (void**)&H.d_wt64, sizeof(double) * table.size()))) return bail(rc);
+      if ((rc = dalloc(M, (void**)&H.d_wt32, sizeof(float) * table.size()))) return bail(rc);
+      if (cudaMemcpy(H.d_cls, pcls.data(), sizeof(uint16_t) * pcls.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(H.d_wt64, table.data(), sizeof(double) * table.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+          cudaMemcpy(H.d_wt32, table32.data(), sizeof(float) * table32.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        M->err = "upload of stencil tables failed";
+        return bail(HHG_ECUDA);
+      }
     }
     if ((rc = dalloc(M, (void**)&H.mem64, sizeof(double) * 12 * (size_t)H.nalloc))) return bail(rc);
     if ((e = cudaMemset(H.mem64, 0, sizeof(double) * 12 * (size_t)H.nalloc)) != cudaSuccess) {

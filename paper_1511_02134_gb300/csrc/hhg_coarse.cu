@@ -85,11 +85,11 @@ __device__ void applyK(const Ctx& C, const V4& x, const V4& y) {
     const uint8_t fl = L.flags[c];
     if (fl & F_VFREE) {
       double au[3], bt[3];
-      row_A(L, x.c, i, j, k, c, fl, au);
-      row_BT(L, L.p, i, j, k, c, fl, bt);
+      row_A(L, x.c, c, fl, au);
+      row_BT(L, L.p, c, fl, bt);
       for (int d = 0; d < 3; ++d) y.c[d][c] = au[d] + bt[d];
     }
-    if (fl & F_ACT) y.c[3][c] = row_B(L, x.c, i, j, k, c, fl) - row_C(L, L.p, i, j, k, c, fl);
+    if (fl & F_ACT) y.c[3][c] = row_B(L, x.c, c, fl) - row_C(L, L.p, c, fl);
   }
   __syncthreads();
 }
@@ -103,7 +103,7 @@ __device__ void applyA(const Ctx& C, const double* x, double* y) {
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
     const uint8_t fl = L.flags[c];
     if (!(fl & F_VFREE)) continue;
-    y[c] = (fl & F_IRR) ? irr_row_A1(L, x, i, j, k, c) : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
+    y[c] = (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP) : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
   }
   __syncthreads();
 }
@@ -157,7 +157,7 @@ __device__ int precond(const Ctx& C, const V4& v, const V4& z, double* r, double
     decode(L, q, i, j, k);
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
     const uint8_t fl = L.flags[c];
-    z.c[3][c] = (fl & F_ACT) ? v.c[3][c] / lumped_mass(L, i, j, k, fl) : 0.0;
+    z.c[3][c] = (fl & F_ACT) ? v.c[3][c] / lumped_mass(L, c, fl) : 0.0;
   }
   __syncthreads();
   return its;

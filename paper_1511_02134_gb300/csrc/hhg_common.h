@@ -29,6 +29,12 @@ enum : uint8_t {
   F_OUT = 16,   // lies on a do-nothing outflow face
 };
 
+// Layout of one stencil-class row table (unit lattice spacing): stiffness
+// row, B_d rows, B_d^T rows, mass row (15 weights each, offset order:
+// centre, +o then -o over the Kuhn directions e1, e2, e3, e1+e2, e2+e3,
+// e1+e3, e1+e2+e3), lumped mass.
+constexpr int W_LAP = 0, W_B = 15, W_BT = 60, W_M = 105, W_LUMP = 120, W_STRIDE = 128;
+
 // Kuhn path index of the axis permutation (a, b, c), lexicographic order:
 // (0,1,2)=0 (0,2,1)=1 (1,0,2)=2 (1,2,0)=3 (2,0,1)=4 (2,1,0)=5
 HHG_HD int path_index(int a, int b, int c) { return 2 * a + (b > c ? 1 : 0); }

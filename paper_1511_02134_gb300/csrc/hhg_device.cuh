@@ -15,9 +15,9 @@
 //     -1 on the face diagonals containing e_d, +1 on the other, -1 on (1,1,1)
 //   mass and g-map for the right-hand side.
 // These constant stencils hold on "regular" nodes (all 24 incident
-// tetrahedra active).  Nodes flagged F_IRR instead sum the element matrices
-// of their active incident tetrahedra (for_incident below), which is the
-// plain definition of the assembled row.
+// tetrahedra active).  A node flagged F_IRR belongs to a stencil class (the
+// set of its active incident tetrahedra); its rows are 15-point weights from
+// a per-level class table assembled at set-up from the element matrices.
 #pragma once
 #include <stdint.h>
 
@@ -34,6 +34,8 @@ struct LevelDev {
   int64_t nalloc;        // padded entries per field
   const uint8_t* flags;  // padded node flags
   const uint8_t* mmask;  // macro cell masks
+  const uint16_t* cls;   // padded stencil class of F_IRR nodes
+  const T* wt;           // class table, W_STRIDE weights per class
   T nuh;                 // nu * h
   T c;                   // delta * h_T^2 * h
   T h2;                  // h^2
@@ -93,199 +95,79 @@ __device__ __forceinline__ T div12(const Diff7<T>& d, int comp) {
   return s - (T)2 * (d.f13 + d.f23) - (T)4 * d.e3;
 }
 
-// Visit the active tetrahedra incident to node (i,j,k): fn(m, s, v) with m
-// the node's local vertex number along path s and v[4] the padded indices
-// of the tetrahedron's vertices in path order.
-template <class T, class F>
-__device__ __forceinline__ void for_incident(const LevelDev<T>& L, int i, int j, int k, F&& fn) {
-  const int64_t step[3] = {1, L.px, L.pxy};
-#pragma unroll 1
-  for (int q = 0; q < 8; ++q) {
-    const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
-    const int cx = i - qx, cy = j - qy, cz = k - qz;
-#pragma unroll 1
-    for (int s = 0; s < 6; ++s) {
-      const int m = corner_local(s, qx, qy, qz);
-      if (m < 0) continue;
-      if (!tet_active(L.mmask, L.mx, L.my, L.mz, L.level, cx, cy, cz, s)) continue;
-      int64_t v[4];
-      v[0] = pidx(L.px, L.pxy, cx, cy, cz);
-      v[1] = v[0] + step[path_axis(s, 0)];
-      v[2] = v[1] + step[path_axis(s, 1)];
-      v[3] = v[0] + 1 + L.px + L.pxy;
-      fn(m, s, v);
-    }
-  }
+// --- rows of boundary nodes from the class table ------------------------------
+// Table layout per class (unit lattice spacing): [W_LAP,+15) stiffness row,
+// [W_B+15d,+15) B_d row, [W_BT+15d,+15) B_d^T row, [W_M,+15) mass row,
+// [W_LUMP] lumped mass.  Offsets: 0 centre, 1..7 = +o, 8..14 = -o over the
+// Kuhn directions e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3.
+struct Off15 {
+  int64_t o[15];
+};
+
+__device__ __forceinline__ Off15 offsets15(int64_t px, int64_t pxy) {
+  const int64_t a = 1, b = px, e = pxy;
+  return Off15{{0, a, b, e, a + b, b + e, a + e, a + b + e, -a, -b, -e, -(a + b), -(b + e), -(a + e), -(a + b + e)}};
 }
 
-// --- element-sum rows for irregular nodes ---------------------------------
-
-// Row of the unit stiffness sum: diag = sum_T K6[m][m] / 6, off = sum_T sum_{n != m} K6[m][n] x_n / 6.
 template <class T>
-__device__ __forceinline__ void irr_lap_row(const LevelDev<T>& L, const T* x, int i, int j, int k,
-                                            T& diag, T& off) {
-  T dg = 0, of = 0;
-  for_incident(L, i, j, k, [&](int m, int, const int64_t* v) {
-    dg += (T)kuhn_stiff6(m, m);
-    if (m > 0) of -= x[v[m - 1]];
-    if (m < 3) of -= x[v[m + 1]];
-  });
-  diag = dg * (T)(1.0 / 6.0);
-  off = of * (T)(1.0 / 6.0);
-}
-
-// (Lap x)_node as an element sum (unit scale).
-template <class T>
-__device__ __forceinline__ T irr_lap(const LevelDev<T>& L, const T* x, int i, int j, int k, int64_t c) {
-  T dg, of;
-  irr_lap_row(L, x, i, j, k, dg, of);
-  return dg * x[c] + of;
-}
-
-// 24 * (B_d x)_node / (-h^2) summed over elements: sum_T (x_{s+1} - x_s) along
-// the path step s whose axis is d.  Returns the three components.
-template <class T>
-__device__ __forceinline__ void irr_grad_sum(const LevelDev<T>& L, const T* const* x3, int i, int j, int k,
-                                             T out[3]) {
-  out[0] = out[1] = out[2] = 0;
-  for_incident(L, i, j, k, [&](int, int s, const int64_t* v) {
+__device__ __forceinline__ T st15(const T* __restrict__ x, int64_t c, const Off15& off, const T* __restrict__ w) {
+  T acc = w[0] * x[c];
 #pragma unroll
-    for (int st = 0; st < 3; ++st) {
-      const int d = path_axis(s, st);
-      out[d] += x3[d][v[st + 1]] - x3[d][v[st]];
-    }
-  });
-}
-
-// Same for a single scalar field applied to all three directions.
-template <class T>
-__device__ __forceinline__ void irr_grad_scalar(const LevelDev<T>& L, const T* x, int i, int j, int k, T out[3]) {
-  out[0] = out[1] = out[2] = 0;
-  for_incident(L, i, j, k, [&](int, int s, const int64_t* v) {
-#pragma unroll
-    for (int st = 0; st < 3; ++st) out[path_axis(s, st)] += x[v[st + 1]] - x[v[st]];
-  });
-}
-
-// 24 * (B_d^T p)_node / (-h^2) = sum_T g_{m,d} sum_n p_n with the unit
-// barycentric gradient g_m = e_{a(m-1)} - e_{a(m)} (a = path axes).
-template <class T>
-__device__ __forceinline__ void irr_gradT(const LevelDev<T>& L, const T* p, int i, int j, int k, T out[3]) {
-  out[0] = out[1] = out[2] = 0;
-  for_incident(L, i, j, k, [&](int m, int s, const int64_t* v) {
-    const T sum = (p[v[0]] + p[v[1]]) + (p[v[2]] + p[v[3]]);
-    if (m >= 1) out[path_axis(s, m - 1)] += sum;
-    if (m <= 2) out[path_axis(s, m)] -= sum;
-  });
-}
-
-// 120/h^3 * (M x)_node = sum_T (x_m + sum_n x_n)
-template <class T>
-__device__ __forceinline__ T irr_mass(const LevelDev<T>& L, const T* x, int i, int j, int k) {
-  T acc = 0;
-  for_incident(L, i, j, k, [&](int m, int, const int64_t* v) {
-    acc += x[v[m]] + ((x[v[0]] + x[v[1]]) + (x[v[2]] + x[v[3]]));
-  });
+  for (int o = 1; o < 15; ++o) acc += w[o] * x[c + off.o[o]];
   return acc;
 }
 
 template <class T>
-__device__ __forceinline__ int irr_count(const LevelDev<T>& L, int i, int j, int k) {
-  int n = 0;
-  for_incident(L, i, j, k, [&](int, int, const int64_t*) { ++n; });
-  return n;
+__device__ __forceinline__ const T* class_row(const LevelDev<T>& L, int64_t c) {
+  return L.wt + (int64_t)W_STRIDE * L.cls[c];
 }
 
-// --- boundary-row paths ------------------------------------------------------
-// The element-sum rows run only on nodes flagged F_IRR.  They are kept out of
-// line: each gets its own stack frame, the regular fast path of every kernel
-// stays small, and no local array of a caller can share storage with the
-// temporaries of these loops.
-
+// Unit stiffness row split into diagonal and off-diagonal sum (Gauss-Seidel).
 template <class T>
-__device__ __noinline__ void irr_row_A(const LevelDev<T>& L, const T* u0, const T* u1, const T* u2, int i, int j,
-                                       int k, int64_t c, T* out) {
-  out[0] = L.nuh * irr_lap(L, u0, i, j, k, c);
-  out[1] = L.nuh * irr_lap(L, u1, i, j, k, c);
-  out[2] = L.nuh * irr_lap(L, u2, i, j, k, c);
+__device__ __forceinline__ void irr_lap_parts(const LevelDev<T>& L, const T* x, int64_t c, T& dg, T& of) {
+  const T* w = class_row(L, c) + W_LAP;
+  const Off15 off = offsets15(L.px, L.pxy);
+  dg = w[0];
+  T acc = 0;
+#pragma unroll
+  for (int o = 1; o < 15; ++o) acc += w[o] * x[c + off.o[o]];
+  of = acc;
 }
 
+// Consistent mass row (times h^3).
 template <class T>
-__device__ __noinline__ T irr_row_A1(const LevelDev<T>& L, const T* x, int i, int j, int k, int64_t c) {
-  return L.nuh * irr_lap(L, x, i, j, k, c);
+__device__ __forceinline__ T irr_mass_row(const LevelDev<T>& L, const T* x, int64_t c) {
+  return L.h3 * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_M);
 }
 
+// B_d row applied to one scalar field for the three d (times h^2).
 template <class T>
-__device__ __noinline__ void irr_row_BT(const LevelDev<T>& L, const T* p, int i, int j, int k, T* out) {
-  T gs[3];
-  irr_gradT(L, p, i, j, k, gs);
-  const T s = -L.h2 * (T)(1.0 / 24.0);
-  out[0] = s * gs[0];
-  out[1] = s * gs[1];
-  out[2] = s * gs[2];
-}
-
-template <class T>
-__device__ __noinline__ T irr_row_B(const LevelDev<T>& L, const T* u0, const T* u1, const T* u2, int i, int j,
-                                    int k) {
-  const T* x3[3] = {u0, u1, u2};
-  T gs[3];
-  irr_grad_sum(L, x3, i, j, k, gs);
-  return -L.h2 * (T)(1.0 / 24.0) * ((gs[0] + gs[1]) + gs[2]);
-}
-
-template <class T>
-__device__ __noinline__ T irr_row_C(const LevelDev<T>& L, const T* p, int i, int j, int k, int64_t c) {
-  return L.c * irr_lap(L, p, i, j, k, c);
-}
-
-// Diagonal and off-diagonal sum of the unit Laplacian row (Gauss-Seidel updates).
-template <class T>
-__device__ __noinline__ void irr_lap_parts(const LevelDev<T>& L, const T* x, int i, int j, int k, T* dg_of) {
-  T dg, of;
-  irr_lap_row(L, x, i, j, k, dg, of);
-  dg_of[0] = dg;
-  dg_of[1] = of;
-}
-
-template <class T>
-__device__ __noinline__ T irr_mass_row(const LevelDev<T>& L, const T* x, int i, int j, int k) {
-  return L.h3 * (T)(1.0 / 120.0) * irr_mass(L, x, i, j, k);
-}
-
-template <class T>
-__device__ __noinline__ void irr_grad_scalar_row(const LevelDev<T>& L, const T* x, int i, int j, int k, T* out) {
-  T gs[3];
-  irr_grad_scalar(L, x, i, j, k, gs);
-  const T s = -L.h2 * (T)(1.0 / 24.0);
-  out[0] = s * gs[0];
-  out[1] = s * gs[1];
-  out[2] = s * gs[2];
-}
-
-template <class T>
-__device__ __noinline__ T irr_lumped(const LevelDev<T>& L, int i, int j, int k) {
-  return L.h3 * (T)(1.0 / 24.0) * (T)irr_count(L, i, j, k);
+__device__ __forceinline__ void irr_B_scalar(const LevelDev<T>& L, const T* x, int64_t c, T out[3]) {
+  const T* w = class_row(L, c);
+  const Off15 off = offsets15(L.px, L.pxy);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15(x, c, off, w + W_B + 15 * d);
 }
 
 // --- full rows of the Stokes operator ----------------------------------------
 
 // (A u_d)_node for all d (nodes with F_VFREE).
 template <class T>
-__device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, int i, int j, int k, int64_t c,
-                                      uint8_t fl, T out[3]) {
+__device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl, T out[3]) {
   if (!(fl & F_IRR)) {
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[d] = L.nuh * ((T)6 * u[d][c] - nb6(u[d], c, L.px, L.pxy));
   } else {
-    irr_row_A(L, u[0], u[1], u[2], i, j, k, c, out);
+    const T* w = class_row(L, c) + W_LAP;
+    const Off15 off = offsets15(L.px, L.pxy);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[d] = L.nuh * st15(u[d], c, off, w);
   }
 }
 
 // (B_d^T p)_node for all d.
 template <class T>
-__device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int i, int j, int k, int64_t c, uint8_t fl,
-                                       T out[3]) {
+__device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl, T out[3]) {
   if (!(fl & F_IRR)) {
     const Diff7<T> dp = diff7(p, c, L.px, L.pxy);
     T dv[3];
@@ -294,35 +176,39 @@ __device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int i, 
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[d] = s * dv[d];
   } else {
-    irr_row_BT(L, p, i, j, k, out);
+    const T* w = class_row(L, c) + W_BT;
+    const Off15 off = offsets15(L.px, L.pxy);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15(p, c, off, w + 15 * d);
   }
 }
 
 // (sum_d B_d u_d)_node.
 template <class T>
-__device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, int i, int j, int k, int64_t c,
-                                   uint8_t fl) {
+__device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl) {
   if (!(fl & F_IRR)) {
     const T d0 = div12(diff7(u[0], c, L.px, L.pxy), 0);
     const T d1 = div12(diff7(u[1], c, L.px, L.pxy), 1);
     const T d2 = div12(diff7(u[2], c, L.px, L.pxy), 2);
     return L.h2 * (T)(1.0 / 12.0) * ((d0 + d1) + d2);
   }
-  return irr_row_B(L, u[0], u[1], u[2], i, j, k);
+  const T* w = class_row(L, c) + W_B;
+  const Off15 off = offsets15(L.px, L.pxy);
+  return L.h2 * ((st15(u[0], c, off, w) + st15(u[1], c, off, w + 15)) + st15(u[2], c, off, w + 30));
 }
 
 // (C p)_node.
 template <class T>
-__device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, int i, int j, int k, int64_t c, uint8_t fl) {
+__device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl) {
   if (!(fl & F_IRR)) return L.c * ((T)6 * p[c] - nb6(p, c, L.px, L.pxy));
-  return irr_row_C(L, p, i, j, k, c);
+  return L.c * st15(p, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP);
 }
 
 // Lumped pressure mass m_i = int phi_i.
 template <class T>
-__device__ __forceinline__ T lumped_mass(const LevelDev<T>& L, int i, int j, int k, uint8_t fl) {
+__device__ __forceinline__ T lumped_mass(const LevelDev<T>& L, int64_t c, uint8_t fl) {
   if (!(fl & F_IRR)) return L.h3;
-  return irr_lumped(L, i, j, k);
+  return L.h3 * class_row(L, c)[W_LUMP];
 }
 
 }  // namespace hhg

@@ -53,7 +53,7 @@ __global__ void k_vel_rhs(LevelDev<T> L) {
   const uint8_t fl = L.flags[c];
   if (!(fl & F_VFREE)) return;
   T bt[3];
-  row_BT(L, L.p, i, j, k, c, fl, bt);
+  row_BT(L, L.p, c, fl, bt);
 #pragma unroll
   for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - bt[d];
 }
@@ -73,9 +73,9 @@ __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   } else {
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
-      T dgof[2];
-      irr_lap_parts(L, L.u[d], i, j, k, dgof);
-      L.u[d][c] = (L.r[d][c] - L.nuh * dgof[1]) / (L.nuh * dgof[0]);
+      T dg, of;
+      irr_lap_parts(L, L.u[d], c, dg, of);
+      L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
     }
   }
 }
@@ -89,7 +89,7 @@ __global__ void k_pres_rhs(LevelDev<T> L) {
   const uint8_t fl = L.flags[c];
   if (!(fl & F_ACT)) return;
   const T* uu[3] = {L.u[0], L.u[1], L.u[2]};  // no address of kernel-parameter members
-  L.rp[c] = row_B(L, uu, i, j, k, c, fl) - L.g[c];
+  L.rp[c] = row_B(L, uu, c, fl) - L.g[c];
 }
 
 // Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour:
@@ -106,10 +106,10 @@ __global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
     const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
     L.p[c] = pc + omega_over_6c * (L.rp[c] - cp);
   } else {
-    T dgof[2];
-    irr_lap_parts(L, L.p, i, j, k, dgof);
-    const T cp = L.c * (dgof[0] * pc + dgof[1]);
-    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dgof[0]);
+    T dg, of;
+    irr_lap_parts(L, L.p, c, dg, of);
+    const T cp = L.c * (dg * pc + of);
+    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
   }
 }
 
@@ -124,8 +124,8 @@ __global__ void k_residual(LevelDev<T> L) {
   const T* uu[3] = {L.u[0], L.u[1], L.u[2]};  // no address of kernel-parameter members
   if (fl & F_VFREE) {
     T au[3], bt[3];
-    row_A(L, uu, i, j, k, c, fl, au);
-    row_BT(L, L.p, i, j, k, c, fl, bt);
+    row_A(L, uu, c, fl, au);
+    row_BT(L, L.p, c, fl, bt);
 #pragma unroll
     for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - au[d] - bt[d];
   } else {
@@ -133,7 +133,7 @@ __global__ void k_residual(LevelDev<T> L) {
     for (int d = 0; d < 3; ++d) L.r[d][c] = (T)0;
   }
   if (fl & F_ACT) {
-    L.rp[c] = L.g[c] - row_B(L, uu, i, j, k, c, fl) + row_C(L, L.p, i, j, k, c, fl);
+    L.rp[c] = L.g[c] - row_B(L, uu, c, fl) + row_C(L, L.p, c, fl);
   } else {
     L.rp[c] = (T)0;
   }
@@ -263,7 +263,7 @@ __global__ void k_mass_moments(LevelDev<T> L, double* partial) {
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
     const uint8_t fl = L.flags[c];
     if (!(fl & F_ACT)) continue;
-    const double m = (double)lumped_mass(L, i, j, k, fl);
+    const double m = (double)lumped_mass(L, c, fl);
     v[0] += m * (double)L.p[c];
     v[1] += m;
   }
@@ -300,10 +300,10 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
   const bool irr = fl & F_IRR;
   if (fl & F_VFREE) {
     double au[3];
-    row_A(L, ud, i, j, k, c, fl, au);
+    row_A(L, ud, c, fl, au);
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
-      const double mf = irr ? irr_mass_row(L, fn[d], i, j, k) : mass_reg(fn[d], c, L.px, L.pxy, L.h3);
+      const double mf = irr ? irr_mass_row(L, fn[d], c) : mass_reg(fn[d], c, L.px, L.pxy, L.h3);
       L.f[d][c] = mf - au[d];
     }
   } else {
@@ -316,10 +316,10 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       double bt[3];
-      row_BT(L, fn[d], i, j, k, c, fl, bt);
+      row_BT(L, fn[d], c, fl, bt);
       gs += bt[d];
     }
-    L.g[c] = L.dh2 * gs - row_B(L, ud, i, j, k, c, fl);
+    L.g[c] = L.dh2 * gs - row_B(L, ud, c, fl);
   } else {
     L.g[c] = 0.0;
   }
@@ -365,11 +365,11 @@ __global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, doub
 #pragma unroll
     for (int d = 0; d < 3; ++d) bl[d] *= L.h2 * (1.0 / 12.0);
   } else {
-    irr_grad_scalar_row(L, L.p, i, j, k, bl);
+    irr_B_scalar(L, L.p, c, bl);
   }
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    const double mu = irr ? irr_mass_row(L, L.u[d], i, j, k) : mass_reg(L.u[d], c, L.px, L.pxy, L.h3);
+    const double mu = irr ? irr_mass_row(L, L.u[d], c) : mass_reg(L.u[d], c, L.px, L.pxy, L.h3);
     out[d][c] = mu + L.dh2 * bl[d];
   }
 }
@@ -389,8 +389,8 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
     const double* uu[3] = {X.u[0], X.u[1], X.u[2]};  // no address of kernel-parameter members
     if (fl & F_VFREE) {
       double au[3], bt[3];
-      row_A(X, uu, i, j, k, c, fl, au);
-      row_BT(X, X.p, i, j, k, c, fl, bt);
+      row_A(X, uu, c, fl, au);
+      row_BT(X, X.p, c, fl, bt);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const double r = X.f[d][c] - au[d] - bt[d];
@@ -402,7 +402,7 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
       for (int d = 0; d < 3; ++d) E.f[d][c] = 0.f;
     }
     if (fl & F_ACT) {
-      const double r = X.g[c] - row_B(X, uu, i, j, k, c, fl) + row_C(X, X.p, i, j, k, c, fl);
+      const double r = X.g[c] - row_B(X, uu, c, fl) + row_C(X, X.p, c, fl);
       E.g[c] = (float)r;
       v[0] += r * r;
     } else {

@@ -8,6 +8,7 @@
 #include <cmath>
 #include <map>
 #include <thread>
+#include <unordered_map>
 
 #include "../../include/hhg_stokes.h"
 #include "hhg_common.h"
@@ -274,6 +275,105 @@ void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
     if ((f & F_ACT) && !(f & F_DIR)) f |= F_VFREE;
     flags[i] = f;
   }
+}
+
+const int STENCIL_OFFSETS[15][3] = {{0, 0, 0},  {1, 0, 0},  {0, 1, 0},   {0, 0, 1},  {1, 1, 0},
+                                    {0, 1, 1},  {1, 0, 1},  {1, 1, 1},   {-1, 0, 0}, {0, -1, 0},
+                                    {0, 0, -1}, {-1, -1, 0}, {0, -1, -1}, {-1, 0, -1}, {-1, -1, -1}};
+
+namespace {
+
+int offset_index(int dx, int dy, int dz) {
+  for (int o = 0; o < 15; ++o)
+    if (STENCIL_OFFSETS[o][0] == dx && STENCIL_OFFSETS[o][1] == dy && STENCIL_OFFSETS[o][2] == dz) return o;
+  return -1;
+}
+
+// Rows of one class from the element matrices of its active tetrahedra.
+// Tetrahedron (cell corner q of the node, path s) has vertices
+// o, o+e_a0, o+e_a0+e_a1, o+(1,1,1) with o = node - q; the unit barycentric
+// gradients are g0 = -e_a0, g1 = e_a0 - e_a1, g2 = e_a1 - e_a2, g3 = e_a2;
+// |T| = 1/6 at unit spacing.
+void class_rows(uint32_t pattern, double* w) {
+  std::fill(w, w + W_STRIDE, 0.0);
+  int bit = 0;
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+    for (int s = 0; s < 6; ++s) {
+      const int m = corner_local(s, qx, qy, qz);
+      if (m < 0) continue;
+      const bool active = (pattern >> bit) & 1u;
+      ++bit;
+      if (!active) continue;
+      const int a[3] = {path_axis(s, 0), path_axis(s, 1), path_axis(s, 2)};
+      int vx[4][3];
+      int p[3] = {0, 0, 0};
+      for (int n = 0; n < 4; ++n) {
+        if (n > 0) p[a[n - 1]] += 1;
+        vx[n][0] = p[0] - qx;
+        vx[n][1] = p[1] - qy;
+        vx[n][2] = p[2] - qz;
+      }
+      int idx[4];
+      for (int n = 0; n < 4; ++n) idx[n] = offset_index(vx[n][0], vx[n][1], vx[n][2]);
+      double g[4][3] = {};
+      g[0][a[0]] = -1;
+      g[1][a[0]] += 1;
+      g[1][a[1]] -= 1;
+      g[2][a[1]] += 1;
+      g[2][a[2]] -= 1;
+      g[3][a[2]] = 1;
+      for (int n = 0; n < 4; ++n) {
+        w[W_LAP + idx[n]] += kuhn_stiff6(m, n) / 6.0;
+        for (int d = 0; d < 3; ++d) {
+          w[W_B + 15 * d + idx[n]] += -g[n][d] / 24.0;
+          w[W_BT + 15 * d + idx[n]] += -g[m][d] / 24.0;
+        }
+        w[W_M + idx[n]] += 1.0 / 120.0;
+      }
+      w[W_M + 0] += 1.0 / 120.0;
+      w[W_LUMP] += 1.0 / 24.0;
+    }
+  }
+}
+
+}  // namespace
+
+void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
+                     std::vector<double>& table, int& n_classes, std::string& err) {
+  const LevelShape sh = level_shape(m, level);
+  cls.assign((size_t)sh.n(), 0);
+  table.assign(W_STRIDE, 0.0);  // class 0: regular nodes (rows not stored)
+  std::unordered_map<uint32_t, uint16_t> ids;
+  n_classes = 0;
+  for (int k = 0; k < sh.nz; ++k)
+    for (int j = 0; j < sh.ny; ++j)
+      for (int i = 0; i < sh.nx; ++i) {
+        const int64_t q = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
+        if (!(flags[q] & F_IRR)) continue;
+        uint32_t pattern = 0;
+        int bit = 0;
+        for (int c = 0; c < 8; ++c) {
+          const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
+          for (int s = 0; s < 6; ++s) {
+            if (corner_local(s, qx, qy, qz) < 0) continue;
+            if (tet_active(m.mask.data(), m.mx, m.my, m.mz, level, i - qx, j - qy, k - qz, s)) pattern |= 1u << bit;
+            ++bit;
+          }
+        }
+        auto it = ids.find(pattern);
+        if (it == ids.end()) {
+          if (n_classes >= 65535) {
+            err = "more than 65535 boundary stencil classes";
+            return;
+          }
+          ++n_classes;
+          it = ids.emplace(pattern, (uint16_t)n_classes).first;
+          table.resize((size_t)(n_classes + 1) * W_STRIDE);
+          class_rows(pattern, table.data() + (size_t)n_classes * W_STRIDE);
+        }
+        cls[q] = it->second;
+      }
 }
 
 void outflow_weights(const MacroLattice& m, int level, double* w) {

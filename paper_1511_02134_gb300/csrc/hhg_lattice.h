@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include "hhg_common.h"
+
 namespace hhg {
 
 struct BoundaryFace {
@@ -44,5 +46,24 @@ void outflow_weights(const MacroLattice& m, int level, double* w);
 
 // Number of active incident tetrahedra (0..24) of node (i, j, k) of a level.
 int active_incident(const MacroLattice& m, int level, int i, int j, int k);
+
+// Stencil classes of the nodes flagged F_IRR.  A node's class is the set of
+// its active incident tetrahedra (a 24-bit pattern); all nodes of a class
+// have the same assembled rows.  For every class the table holds, in
+// doubles and at unit lattice spacing, the 15-point row weights (offset
+// order of STENCIL_OFFSETS) of:
+//   [W_LAP, +15)   sum_T int grad phi_i . grad phi_j     (A = nu h *, C = delta h_T^2 h *)
+//   [W_B + 15 d)   B_d row  -sum_T int phi_i d_d phi_j   (times h^2)
+//   [W_BT + 15 d)  B_d^T row                             (times h^2)
+//   [W_M, +15)     consistent mass row                   (times h^3)
+//   [W_LUMP]       lumped mass int phi_i                 (times h^3)
+// cls receives the class of every lattice node (0 for nodes that are not
+// F_IRR; classes of F_IRR nodes start at 1), table receives
+// (n_classes + 1) * W_STRIDE doubles (class 0 unused).
+// Offsets of the 15-point pattern: 0 = centre, 1..7 = +o, 8..14 = -o over the
+// Kuhn directions o = e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3.
+extern const int STENCIL_OFFSETS[15][3];
+void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
+                     std::vector<double>& table, int& n_classes, std::string& err);
 
 }  // namespace hhg
