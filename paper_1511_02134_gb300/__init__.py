@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
                 ("coarsest_level", ctypes.c_int32), ("coarse_minres_max", ctypes.c_int32),
                 ("coarse_minres_rtol", ctypes.c_double), ("coarse_cg_max", ctypes.c_int32),
                 ("coarse_cg_rtol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 7)]
+                ("fuse_coarse_levels", ctypes.c_int32), ("reserved", ctypes.c_int32 * 6)]
 
 
 class _Stats(ctypes.Structure):

@@ -59,6 +59,7 @@ struct hhg_mesh {
   hhg_options opt{};
   MacroLattice macro;
   int finest = 0, coarsest = 0;
+  int small_top[2] = {-1, -1};  // top level of the fused coarse-levels cycle, FP64 / FP32 (-1: none)
   std::vector<LevelHost> lv;
   uint8_t* d_mmask = nullptr;
   int64_t ndir = 0;
@@ -204,11 +205,40 @@ int nu_steps(hhg_mesh* M, int l, bool pre) {
   return (pre ? M->opt.nu_pre : M->opt.nu_post) + M->opt.var_increment * (M->finest - l);
 }
 
+template <class T>
+int nu_steps(hhg_mesh* M, int l, bool pre);
+
+template <class T>
+void enq_small_cycle(hhg_mesh* M) {
+  SmallCycle<T> S;
+  std::memset(&S, 0, sizeof(S));
+  S.nlev = M->small_top[sizeof(T) == 4] - M->coarsest + 1;
+  for (int q = 0; q < S.nlev; ++q) {
+    const int l = M->coarsest + q;
+    S.lv[q] = view<T>(M, l);
+    S.nu_pre[q] = nu_steps<T>(M, l, true);
+    S.nu_post[q] = nu_steps<T>(M, l, false);
+    S.inv6nuh[q] = (T)(1.0 / (6.0 * (double)S.lv[q].nuh));
+    S.omc[q] = (T)((double)S.lv[q].omega / (6.0 * (double)S.lv[q].c));
+  }
+  S.c64 = M->lv[M->coarsest].d64;
+  S.scratch = M->d_coarse;
+  S.prm = CoarseParams{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max,
+                       M->opt.coarse_cg_rtol};
+  S.info = M->d_scalars + 5;
+  launch_small_cycle<T>(S, M->stream);
+  M->launches += 1;
+}
+
 // One V_var cycle rooted at level l (Sec. 3.5).
 template <class T>
 void enq_vcycle(hhg_mesh* M, int l) {
   if (l == M->coarsest) {
     enq_coarse<T>(M);
+    return;
+  }
+  if (l == M->small_top[sizeof(T) == 4]) {
+    enq_small_cycle<T>(M);
     return;
   }
   for (int s = 0; s < nu_steps<T>(M, l, true); ++s) enq_uzawa<T>(M, l);
@@ -428,6 +458,7 @@ void hhg_default_options(hhg_options* opt) {
   opt->coarse_cg_max = 50;
   opt->coarse_cg_rtol = 1e-3;
   opt->use_graphs = 1;
+  opt->fuse_coarse_levels = 1;
 }
 
 const char* hhg_strerror(int code) {
@@ -607,6 +638,13 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   }
   if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * COARSE_FIELDS * (size_t)M->lv[M->coarsest].nalloc)))
     return bail(rc);
+  // fused coarse levels: the largest level of at most SMALL_MAX_NODES nodes
+  if (o.fuse_coarse_levels) {
+    for (int l = M->coarsest + 1; l <= finest && l - M->coarsest < SMALL_MAX_LEVELS; ++l) {
+      if (M->lv[l].sh.n() <= SMALL_MAX_NODES_FP64) M->small_top[0] = l;
+      if (M->lv[l].sh.n() <= SMALL_MAX_NODES) M->small_top[1] = l;
+    }
+  }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) {
     M->err = std::string("set-up: ") + cudaGetErrorString(e);
     return bail(HHG_ECUDA);

@@ -1,280 +1,23 @@
-// Coarse-grid solver of the all-at-once multigrid (Sec. 3.7): MINRES on the
-// full saddle-point system, preconditioned block-diagonally (Sec. 3.2) with a
-// CG solve on each velocity block of A and the inverse lumped pressure mass.
-// Always FP64.  One thread block runs the whole solve: the coarsest level of
-// the paper's set-up (level 2 of the unit cube: 206 unknowns) is far too small
-// to fill more than one SM, and keeping it in one block needs no grid-wide
-// synchronisation.  Loops have fixed upper trip counts (max iterations).
-//
-// Recurrences (start from zero):
-//   CG:     stop before an iteration when r.r <= rtol^2 r0.r0 (or r.r = 0),
-//           or when d.Ad = 0; at most cg_max iterations.
-//   MINRES: Lanczos with Givens rotations; z_j <- z_j / gamma_j,
-//           delta_j = (K z_j).z_j, v_{j+1} = K z_j - delta_j/gamma_j v_j
-//           - gamma_j/gamma_{j-1} v_{j-1}, z_{j+1} = P^{-1} v_{j+1},
-//           gamma_{j+1} = sqrt(z_{j+1}.v_{j+1}); rotation a0..a3, c, s;
-//           w_{j+1} = (z_j - a3 w_{j-1} - a2 w_j)/a1; x += c_{j+1} eta w_{j+1};
-//           eta <- -s_{j+1} eta; stop when |eta| <= rtol gamma_1.
+// Coarse-grid solver kernel (Sec. 3.7): the block routine of
+// hhg_coarse_block.cuh run by one thread block.  The coarsest level of the
+// paper's set-up (level 2 of the unit cube: 206 unknowns) is far too small to
+// fill more than one SM, and one block needs no grid-wide synchronisation.
 #include <mutex>
 #include <string>
 
 #include "../../include/hhg_stokes.h"
+#include "hhg_coarse_block.cuh"
 #include "hhg_kernels.h"
 
 namespace hhg {
 
 namespace {
-
 constexpr int CT = 512;  // threads of the coarse block
-
-struct V4 {
-  double* c[4];
-};
-
-__device__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double acc = 0;
-    for (int q = 0; q < CT / 32; ++q) acc += sh[q];
-    sh[CT / 32] = acc;
-  }
-  __syncthreads();
-  const double r = sh[CT / 32];
-  __syncthreads();
-  return r;
-}
-
-struct Ctx {
-  LevelDev<double> L;
-  double* sh;
-  int64_t n;  // lattice nodes
-};
-
-__device__ __forceinline__ void decode(const LevelDev<double>& L, int64_t q, int& i, int& j, int& k) {
-  i = (int)(q % L.nx);
-  j = (int)((q / L.nx) % L.ny);
-  k = (int)(q / ((int64_t)L.nx * L.ny));
-}
-
-__device__ double dot4(const Ctx& C, const V4& a, const V4& b) {
-  double s = 0;
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += CT)
-    s += (a.c[0][q] * b.c[0][q] + a.c[1][q] * b.c[1][q]) + (a.c[2][q] * b.c[2][q] + a.c[3][q] * b.c[3][q]);
-  return block_sum(s, C.sh);
-}
-
-__device__ double dot1(const Ctx& C, const double* a, const double* b) {
-  double s = 0;
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += CT) s += a[q] * b[q];
-  return block_sum(s, C.sh);
-}
-
-// y = K x (zero on entries without unknowns)
-__device__ void applyK(const Ctx& C, const V4& x, const V4& y) {
-  LevelDev<double> L = C.L;
-  L.u[0] = x.c[0];
-  L.u[1] = x.c[1];
-  L.u[2] = x.c[2];
-  L.p = x.c[3];
-  for (int64_t q = threadIdx.x; q < C.n; q += CT) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    if (fl & F_VFREE) {
-      double au[3], bt[3];
-      row_A(L, x.c, c, fl, au);
-      row_BT(L, L.p, c, fl, bt);
-      for (int d = 0; d < 3; ++d) y.c[d][c] = au[d] + bt[d];
-    }
-    if (fl & F_ACT) y.c[3][c] = row_B(L, x.c, c, fl) - row_C(L, L.p, c, fl);
-  }
-  __syncthreads();
-}
-
-// y = A x for one velocity component
-__device__ void applyA(const Ctx& C, const double* x, double* y) {
-  const LevelDev<double>& L = C.L;
-  for (int64_t q = threadIdx.x; q < C.n; q += CT) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    if (!(fl & F_VFREE)) continue;
-    y[c] = (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP) : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
-  }
-  __syncthreads();
-}
-
-__device__ void zero1(const Ctx& C, double* a) {
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += CT) a[q] = 0.0;
-  __syncthreads();
-}
-
-// x = CG(A, b) from zero; r, d, w scratch.  Returns iterations.
-__device__ int cg(const Ctx& C, const double* b, double* x, double* r, double* d, double* w, int max_it,
-                  double rtol) {
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += CT) {
-    x[q] = 0.0;
-    r[q] = b[q];
-    d[q] = b[q];
-    w[q] = 0.0;
-  }
-  __syncthreads();
-  double rr = dot1(C, r, r);
-  const double stop = rtol * rtol * rr;
-  int it = 0;
-  for (; it < max_it; ++it) {
-    if (rr <= stop || rr == 0.0) break;
-    applyA(C, d, w);
-    const double dq = dot1(C, d, w);
-    if (dq == 0.0) break;
-    const double alpha = rr / dq;
-    for (int64_t q = threadIdx.x; q < C.L.nalloc; q += CT) {
-      x[q] += alpha * d[q];
-      r[q] -= alpha * w[q];
-    }
-    __syncthreads();
-    const double rr_new = dot1(C, r, r);
-    const double beta = rr_new / rr;
-    for (int64_t q = threadIdx.x; q < C.L.nalloc; q += CT) d[q] = r[q] + beta * d[q];
-    __syncthreads();
-    rr = rr_new;
-  }
-  return it;
-}
-
-// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.
-__device__ int precond(const Ctx& C, const V4& v, const V4& z, double* r, double* d, double* w, int cg_max,
-                       double cg_rtol) {
-  int its = 0;
-  for (int comp = 0; comp < 3; ++comp) its += cg(C, v.c[comp], z.c[comp], r, d, w, cg_max, cg_rtol);
-  const LevelDev<double>& L = C.L;
-  for (int64_t q = threadIdx.x; q < C.n; q += CT) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    z.c[3][c] = (fl & F_ACT) ? v.c[3][c] / lumped_mass(L, c, fl) : 0.0;
-  }
-  __syncthreads();
-  return its;
-}
 
 __global__ void __launch_bounds__(CT) k_coarse_minres(LevelDev<double> L, double* scratch, CoarseParams prm,
                                                       double* info) {
-  __shared__ double sh[CT / 32 + 1];
-  Ctx C{L, sh, (int64_t)L.nx * L.ny * L.nz};
-  const int64_t na = L.nalloc;
-  auto vec = [&](int first) {
-    V4 v;
-    for (int f = 0; f < 4; ++f) v.c[f] = scratch + (int64_t)(first + f) * na;
-    return v;
-  };
-  // 11 vectors of 4 fields + 3 CG fields = 47 fields
-  V4 b = vec(0), x = vec(4), Kz = vec(8);
-  V4 vv[3] = {vec(12), vec(16), vec(20)};  // v_prev, v, v_next (rotating)
-  V4 zz[2] = {vec(24), vec(28)};            // z, z_next
-  V4 ww[3] = {vec(32), vec(36), vec(40)};  // w_prev, w, w_next
-  double* cr = scratch + 44 * na;
-  double* cd = scratch + 45 * na;
-  double* cw = scratch + 46 * na;
-  for (int f = 0; f < 44; ++f) zero1(C, scratch + (int64_t)f * na);
-
-  // b = (F, G) - K (U, P): the residual equation of the current iterate
-  V4 up;
-  up.c[0] = L.u[0];
-  up.c[1] = L.u[1];
-  up.c[2] = L.u[2];
-  up.c[3] = L.p;
-  applyK(C, up, Kz);
-  for (int64_t q = threadIdx.x; q < na; q += CT) {
-    const uint8_t fl = L.flags[q];
-    for (int d = 0; d < 3; ++d) b.c[d][q] = (fl & F_VFREE) ? L.f[d][q] - Kz.c[d][q] : 0.0;
-    b.c[3][q] = (fl & F_ACT) ? L.g[q] - Kz.c[3][q] : 0.0;
-  }
-  __syncthreads();
-
-  int iv_prev = 0, iv = 1, iv_next = 2, iz = 0, iz_next = 1, iw_prev = 0, iw = 1, iw_next = 2;
-  // v_1 = b, z_1 = P^{-1} v_1
-  for (int f = 0; f < 4; ++f)
-    for (int64_t q = threadIdx.x; q < na; q += CT) vv[iv].c[f][q] = b.c[f][q];
-  __syncthreads();
-  int cg_total = precond(C, vv[iv], zz[iz], cr, cd, cw, prm.cg_max, prm.cg_rtol);
-  double gamma = sqrt(fmax(dot4(C, zz[iz], vv[iv]), 0.0));
-  int its = 0;
-  double rel = 0.0;
-  if (gamma > 0.0) {
-    const double gamma1 = gamma;
-    double gamma_prev = 1.0, eta = gamma;
-    double c_prev = 1.0, cc = 1.0, s_prev = 0.0, ss = 0.0;
-    for (; its < prm.minres_max;) {
-      for (int f = 0; f < 4; ++f)
-        for (int64_t q = threadIdx.x; q < na; q += CT) zz[iz].c[f][q] /= gamma;
-      __syncthreads();
-      applyK(C, zz[iz], Kz);
-      const double delta = dot4(C, Kz, zz[iz]);
-      const double r1 = delta / gamma, r2 = gamma / gamma_prev;
-      for (int f = 0; f < 4; ++f)
-        for (int64_t q = threadIdx.x; q < na; q += CT)
-          vv[iv_next].c[f][q] = Kz.c[f][q] - r1 * vv[iv].c[f][q] - r2 * vv[iv_prev].c[f][q];
-      __syncthreads();
-      cg_total += precond(C, vv[iv_next], zz[iz_next], cr, cd, cw, prm.cg_max, prm.cg_rtol);
-      const double gamma_next = sqrt(fmax(dot4(C, zz[iz_next], vv[iv_next]), 0.0));
-      const double a0 = cc * delta - c_prev * ss * gamma;
-      const double a1 = sqrt(a0 * a0 + gamma_next * gamma_next);
-      const double a2 = ss * delta + c_prev * cc * gamma;
-      const double a3 = s_prev * gamma;
-      if (a1 == 0.0) break;
-      const double c_next = a0 / a1, s_next = gamma_next / a1;
-      const double step = c_next * eta;
-      for (int f = 0; f < 4; ++f)
-        for (int64_t q = threadIdx.x; q < na; q += CT) {
-          const double wn = (zz[iz].c[f][q] - a3 * ww[iw_prev].c[f][q] - a2 * ww[iw].c[f][q]) / a1;
-          ww[iw_next].c[f][q] = wn;
-          x.c[f][q] += step * wn;
-        }
-      __syncthreads();
-      eta = -s_next * eta;
-      ++its;
-      // shift the recurrences
-      int t = iv_prev;
-      iv_prev = iv;
-      iv = iv_next;
-      iv_next = t;
-      t = iz;
-      iz = iz_next;
-      iz_next = t;
-      t = iw_prev;
-      iw_prev = iw;
-      iw = iw_next;
-      iw_next = t;
-      gamma_prev = gamma;
-      gamma = gamma_next;
-      c_prev = cc;
-      cc = c_next;
-      s_prev = ss;
-      ss = s_next;
-      rel = fabs(eta) / gamma1;
-      if (fabs(eta) <= prm.minres_rtol * gamma1 || gamma == 0.0) break;
-    }
-  }
-  // (U, P) += x
-  for (int64_t q = threadIdx.x; q < na; q += CT) {
-    L.u[0][q] += x.c[0][q];
-    L.u[1][q] += x.c[1][q];
-    L.u[2][q] += x.c[2][q];
-    L.p[q] += x.c[3][q];
-  }
-  if (threadIdx.x == 0 && info) {
-    info[0] = (double)its;
-    info[1] = rel;
-    info[2] = (double)cg_total;
-  }
+  coarse::minres_block(L, scratch, prm, info);
 }
-
 }  // namespace
 
 void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s) {

@@ -54,8 +54,10 @@ __device__ __forceinline__ int64_t pidx(int64_t px, int64_t pxy, int i, int j, i
   return (int64_t)(i + 1) + px * (j + 1) + pxy * (k + 1);
 }
 
+// The row helpers read fields that fused kernels also write in earlier
+// phases of the same launch, so they use plain (coherent) loads.
 template <class T>
-__device__ __forceinline__ T nb6(const T* __restrict__ x, int64_t c, int64_t px, int64_t pxy) {
+__device__ __forceinline__ T nb6(const T* x, int64_t c, int64_t px, int64_t pxy) {
   return ((x[c - 1] + x[c + 1]) + (x[c - px] + x[c + px])) + (x[c - pxy] + x[c + pxy]);
 }
 
@@ -66,7 +68,7 @@ struct Diff7 {
 };
 
 template <class T>
-__device__ __forceinline__ Diff7<T> diff7(const T* __restrict__ x, int64_t c, int64_t px, int64_t pxy) {
+__device__ __forceinline__ Diff7<T> diff7(const T* x, int64_t c, int64_t px, int64_t pxy) {
   Diff7<T> d;
   d.e1 = x[c + 1] - x[c - 1];
   d.e2 = x[c + px] - x[c - px];
@@ -110,7 +112,7 @@ __device__ __forceinline__ Off15 offsets15(int64_t px, int64_t pxy) {
 }
 
 template <class T>
-__device__ __forceinline__ T st15(const T* __restrict__ x, int64_t c, const Off15& off, const T* __restrict__ w) {
+__device__ __forceinline__ T st15(const T* x, int64_t c, const Off15& off, const T* w) {
   T acc = w[0] * x[c];
 #pragma unroll
   for (int o = 1; o < 15; ++o) acc += w[o] * x[c + off.o[o]];

@@ -5,6 +5,7 @@
 // are not coupled by the 15-point pattern of the operator, so one launch per
 // colour performs the Gauss-Seidel sweep in colour order.
 #include "hhg_kernels.h"
+#include "hhg_node_ops.cuh"
 
 namespace hhg {
 
@@ -41,7 +42,7 @@ __device__ __forceinline__ bool full_node(const LevelDev<T>& L, int& i, int& j, 
   return i < L.nx && j < L.ny;
 }
 
-// ---- smoother ----------------------------------------------------------------
+// ---- smoother, residual, transfers: grid kernels over the per-node bodies ----------
 
 // RU = F - B^T P on velocity nodes (the right-hand side of both velocity
 // sweeps of one Uzawa step, Sec. 3.3).
@@ -49,35 +50,15 @@ template <class T>
 __global__ void k_vel_rhs(LevelDev<T> L) {
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_VFREE)) return;
-  T bt[3];
-  row_BT(L, L.p, c, fl, bt);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - bt[d];
+  node_vel_rhs(L, pidx(L.px, L.pxy, i, j, k));
 }
 
-// Gauss-Seidel update of the velocity nodes of one colour:
-// u_d <- u_d + (RU_d - (A u_d)) / A_ii.
+// Gauss-Seidel update of the velocity nodes of one colour.
 template <class T>
 __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_VFREE)) return;
-  if (!(fl & F_IRR)) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) L.u[d][c] = (L.r[d][c] + L.nuh * nb6(L.u[d], c, L.px, L.pxy)) * inv6nuh;
-  } else {
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      T dg, of;
-      irr_lap_parts(L, L.u[d], c, dg, of);
-      L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
-    }
-  }
+  node_vel_gs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
 // RP = B U - G on pressure nodes.
@@ -85,116 +66,36 @@ template <class T>
 __global__ void k_pres_rhs(LevelDev<T> L) {
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_ACT)) return;
-  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};  // no address of kernel-parameter members
-  L.rp[c] = row_B(L, uu, c, fl) - L.g[c];
+  node_pres_rhs(L, pidx(L.px, L.pxy, i, j, k));
 }
 
-// Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour:
-// p <- p + omega (RP - C p) / C_ii  (forward SOR sweep from zero, Sec. 3.5).
+// Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour.
 template <class T>
 __global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_ACT)) return;
-  const T pc = L.p[c];
-  if (!(fl & F_IRR)) {
-    const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
-    L.p[c] = pc + omega_over_6c * (L.rp[c] - cp);
-  } else {
-    T dg, of;
-    irr_lap_parts(L, L.p, c, dg, of);
-    const T cp = L.c * (dg * pc + of);
-    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
-  }
+  node_pres_gs(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
 }
-
-// ---- residual and transfers ---------------------------------------------------
 
 template <class T>
 __global__ void k_residual(LevelDev<T> L) {
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
-  const uint8_t fl = L.flags[c];
-  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};  // no address of kernel-parameter members
-  if (fl & F_VFREE) {
-    T au[3], bt[3];
-    row_A(L, uu, c, fl, au);
-    row_BT(L, L.p, c, fl, bt);
-#pragma unroll
-    for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - au[d] - bt[d];
-  } else {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) L.r[d][c] = (T)0;
-  }
-  if (fl & F_ACT) {
-    L.rp[c] = L.g[c] - row_B(L, uu, c, fl) + row_C(L, L.p, c, fl);
-  } else {
-    L.rp[c] = (T)0;
-  }
+  node_residual(L, pidx(L.px, L.pxy, i, j, k));
 }
 
-// Coarse (F, G) = P^T (RU, RP): P1 interpolation is the identity on coarse
-// nodes and the mean of the two ends on coarse-edge midpoints, which on the
-// Kuhn lattice are the 14 neighbours along the Kuhn directions.  Coarse
-// (U, P) start from zero.
 template <class T>
 __global__ void k_restrict(LevelDev<T> Lf, LevelDev<T> Lc) {
   int i, j, k;
   if (!full_node(Lc, i, j, k)) return;
-  const int64_t cc = pidx(Lc.px, Lc.pxy, i, j, k);
-  const uint8_t fl = Lc.flags[cc];
-  const int64_t cf = pidx(Lf.px, Lf.pxy, 2 * i, 2 * j, 2 * k);
-  const int64_t a = 1, b = Lf.px, e = Lf.pxy;
-  const int64_t off[7] = {a, b, e, a + b, b + e, a + e, a + b + e};
-  T s[4];
-  const T* src[4] = {Lf.r[0], Lf.r[1], Lf.r[2], Lf.rp};
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const T* x = src[q];
-    T acc = 0;
-#pragma unroll
-    for (int o = 0; o < 7; ++o) acc += x[cf + off[o]] + x[cf - off[o]];
-    s[q] = x[cf] + (T)0.5 * acc;
-  }
-  const bool vf = fl & F_VFREE, ac = fl & F_ACT;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    Lc.f[d][cc] = vf ? s[d] : (T)0;
-    Lc.u[d][cc] = (T)0;
-  }
-  Lc.g[cc] = ac ? s[3] : (T)0;
-  Lc.p[cc] = (T)0;
+  node_restrict(Lf, Lc, i, j, k);
 }
 
-// Fine (U, P) += P (coarse U, P) on fine unknowns.
 template <class T>
 __global__ void k_prolong_add(LevelDev<T> Lf, LevelDev<T> Lc) {
   int i, j, k;
   if (!full_node(Lf, i, j, k)) return;
-  const int64_t cf = pidx(Lf.px, Lf.pxy, i, j, k);
-  const uint8_t fl = Lf.flags[cf];
-  if (!(fl & F_ACT)) return;
-  const int a = i & 1, b = j & 1, e = k & 1;
-  const int I = i >> 1, J = j >> 1, K = k >> 1;
-  const int64_t c0 = pidx(Lc.px, Lc.pxy, I, J, K);
-  const bool mid = (a | b | e) != 0;
-  const int64_t c1 = pidx(Lc.px, Lc.pxy, I + a, J + b, K + e);
-  if (fl & F_VFREE) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const T* x = Lc.u[d];
-      const T v = mid ? (T)0.5 * (x[c0] + x[c1]) : x[c0];
-      Lf.u[d][cf] += v;
-    }
-  }
-  const T v = mid ? (T)0.5 * (Lc.p[c0] + Lc.p[c1]) : Lc.p[c0];
-  Lf.p[cf] += v;
+  node_prolong_add(Lf, Lc, i, j, k);
 }
 
 // ---- reductions ---------------------------------------------------------------

@@ -86,4 +86,28 @@ constexpr int NOALLOC_MAX_DEVICES = 64;
 int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* info, cudaStream_t s,
                          std::string& err);
 
+// Fused cycle of the coarse levels (hhg_small.cu): levels lv[0] (coarsest)
+// .. lv[nlev-1] of one hierarchy, smoothing counts per level, FP64 view of the
+// coarsest level for the coarse solve, its scratch and parameters.
+constexpr int SMALL_MAX_LEVELS = 8;
+// largest level run by the fused block: FP32 work, and FP64 work (one SM
+// has 1/152 of the GPU's FP64 rate, so only the smallest levels pay off)
+constexpr int64_t SMALL_MAX_NODES = 8192;
+constexpr int64_t SMALL_MAX_NODES_FP64 = 1024;
+template <class T>
+struct SmallCycle {
+  LevelDev<T> lv[SMALL_MAX_LEVELS];
+  int nlev;
+  int nu_pre[SMALL_MAX_LEVELS];
+  int nu_post[SMALL_MAX_LEVELS];
+  T inv6nuh[SMALL_MAX_LEVELS];
+  T omc[SMALL_MAX_LEVELS];
+  LevelDev<double> c64;
+  double* scratch;
+  CoarseParams prm;
+  double* info;
+};
+template <class T>
+void launch_small_cycle(const SmallCycle<T>& S, cudaStream_t s);
+
 }  // namespace hhg

@@ -1,0 +1,141 @@
+// Per-node bodies of the smoother, residual and transfer steps (Sec. 3.3-3.5).
+// The grid kernels run one node per thread; the fused coarse-levels kernel
+// loops over the nodes of a level inside one thread block.  Both call these
+// functions, so the two paths do the same arithmetic in the same order.
+#pragma once
+#include "hhg_device.cuh"
+
+namespace hhg {
+
+// RU = F - B^T P (velocity nodes).
+template <class T>
+__device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, int64_t c) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_VFREE)) return;
+  T bt[3];
+  row_BT(L, L.p, c, fl, bt);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - bt[d];
+}
+
+// u_d <- u_d + (RU_d - (A u_d)) / A_ii  (one node of the current colour).
+template <class T>
+__device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_VFREE)) return;
+  if (!(fl & F_IRR)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.u[d][c] = (L.r[d][c] + L.nuh * nb6(L.u[d], c, L.px, L.pxy)) * inv6nuh;
+  } else {
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      T dg, of;
+      irr_lap_parts(L, L.u[d], c, dg, of);
+      L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
+    }
+  }
+}
+
+// RP = B U - G (pressure nodes).
+template <class T>
+__device__ __forceinline__ void node_pres_rhs(const LevelDev<T>& L, int64_t c) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_ACT)) return;
+  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};
+  L.rp[c] = row_B(L, uu, c, fl) - L.g[c];
+}
+
+// p <- p + omega (RP - C p) / C_ii  (forward SOR sweep from zero, Sec. 3.5).
+template <class T>
+__device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, int64_t c, T omega_over_6c) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_ACT)) return;
+  const T pc = L.p[c];
+  if (!(fl & F_IRR)) {
+    const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
+    L.p[c] = pc + omega_over_6c * (L.rp[c] - cp);
+  } else {
+    T dg, of;
+    irr_lap_parts(L, L.p, c, dg, of);
+    const T cp = L.c * (dg * pc + of);
+    L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
+  }
+}
+
+// (RU, RP) = (F, G) - K (U, P); zero on nodes without the unknown.
+template <class T>
+__device__ __forceinline__ void node_residual(const LevelDev<T>& L, int64_t c) {
+  const uint8_t fl = L.flags[c];
+  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};
+  if (fl & F_VFREE) {
+    T au[3], bt[3];
+    row_A(L, uu, c, fl, au);
+    row_BT(L, L.p, c, fl, bt);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - au[d] - bt[d];
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.r[d][c] = (T)0;
+  }
+  if (fl & F_ACT) {
+    L.rp[c] = L.g[c] - row_B(L, uu, c, fl) + row_C(L, L.p, c, fl);
+  } else {
+    L.rp[c] = (T)0;
+  }
+}
+
+// Coarse (F, G) at coarse node (i,j,k) = P^T (RU, RP): P1 interpolation is
+// the identity on coarse nodes and the mean of the two ends on coarse-edge
+// midpoints, which on the Kuhn lattice are the 14 neighbours along the Kuhn
+// directions.  The coarse iterate (U, P) starts from zero.
+template <class T>
+__device__ __forceinline__ void node_restrict(const LevelDev<T>& Lf, const LevelDev<T>& Lc, int i, int j, int k) {
+  const int64_t cc = pidx(Lc.px, Lc.pxy, i, j, k);
+  const uint8_t fl = Lc.flags[cc];
+  const int64_t cf = pidx(Lf.px, Lf.pxy, 2 * i, 2 * j, 2 * k);
+  const int64_t a = 1, b = Lf.px, e = Lf.pxy;
+  const int64_t off[7] = {a, b, e, a + b, b + e, a + e, a + b + e};
+  T s[4];
+  const T* src[4] = {Lf.r[0], Lf.r[1], Lf.r[2], Lf.rp};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const T* x = src[q];
+    T acc = 0;
+#pragma unroll
+    for (int o = 0; o < 7; ++o) acc += x[cf + off[o]] + x[cf - off[o]];
+    s[q] = x[cf] + (T)0.5 * acc;
+  }
+  const bool vf = fl & F_VFREE, ac = fl & F_ACT;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Lc.f[d][cc] = vf ? s[d] : (T)0;
+    Lc.u[d][cc] = (T)0;
+  }
+  Lc.g[cc] = ac ? s[3] : (T)0;
+  Lc.p[cc] = (T)0;
+}
+
+// Fine (U, P) += P (coarse U, P) at fine node (i,j,k).
+template <class T>
+__device__ __forceinline__ void node_prolong_add(const LevelDev<T>& Lf, const LevelDev<T>& Lc, int i, int j, int k) {
+  const int64_t cf = pidx(Lf.px, Lf.pxy, i, j, k);
+  const uint8_t fl = Lf.flags[cf];
+  if (!(fl & F_ACT)) return;
+  const int a = i & 1, b = j & 1, e = k & 1;
+  const int I = i >> 1, J = j >> 1, K = k >> 1;
+  const int64_t c0 = pidx(Lc.px, Lc.pxy, I, J, K);
+  const bool mid = (a | b | e) != 0;
+  const int64_t c1 = pidx(Lc.px, Lc.pxy, I + a, J + b, K + e);
+  if (fl & F_VFREE) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const T* x = Lc.u[d];
+      const T v = mid ? (T)0.5 * (x[c0] + x[c1]) : x[c0];
+      Lf.u[d][cf] += v;
+    }
+  }
+  const T v = mid ? (T)0.5 * (Lc.p[c0] + Lc.p[c1]) : Lc.p[c0];
+  Lf.p[cf] += v;
+}
+
+}  // namespace hhg

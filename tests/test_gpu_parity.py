@@ -355,3 +355,23 @@ def test_adjoint_gradient_matches_oracle(pkg):
     u2, _ = mesh.get_solution()
     u1, _, _ = mesh.solve(tol=1e-10, max_cycles=0)
     assert np.array_equal(u1, u2)
+
+
+@pytest.mark.parametrize("name,level,coarsest", [("cube", 5, 2), ("cube", 3, 2), ("channel", 2, 0), ("partial", 3, 1)])
+def test_fused_coarse_levels_match_per_level_kernels(pkg, name, level, coarsest):
+    """The single-block fused cycle of the coarse levels does the same
+    arithmetic as the per-level kernels (FP64 and FP32 hierarchies)."""
+    macro = macro_by_name(name)
+    meshes = [pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=coarsest,
+                       coarse_minres_max=30, fuse_coarse_levels=f) for f in (1, 0)]
+    H = MG.build_hierarchy(macro, level, coarsest=coarsest)
+    st = _random_state(H, level, 21)
+    for prec in (0, 1):
+        outs = []
+        for mesh in meshes:
+            _load(mesh, H, level, st, precision=prec)
+            mesh.level_op(level, "vcycle", precision=prec)
+            outs.append(_read_up(mesh, H, level, precision=prec))
+        tol = 1e-12 if prec == 0 else 1e-5
+        assert rel_err(outs[0][0], outs[1][0]) < tol
+        assert _p_err(H.levels[level], outs[0][1], outs[1][1]) < tol
