@@ -170,17 +170,28 @@ void enq_pres_sweep(hhg_mesh* M, int l) {
   M->launches += 4;
 }
 
-// One inexact Uzawa step (Sec. 3.3): velocity SHGS on f - B^T p, then the
-// pressure sweep on B u - g.
+// One inexact Uzawa step (Sec. 3.3): velocity SHGS on f - B^T p (colours
+// 0,1,2,3 then 3,2,1,0), then the relaxed pressure sweep on B u - g.  The
+// backward colour 3 repeats the forward one with unchanged neighbours and a
+// node's new value does not depend on its old one, so it is skipped (the
+// result is identical).  FP32 forms f - B^T p at each node inside the colour
+// kernels; FP64, bound by its arithmetic rate, stores it once per step.  The
+// pressure colours form B u - g at each node (every node is updated once).
 template <class T>
 void enq_uzawa(hhg_mesh* M, int l) {
-  launch_vel_rhs<T>(view<T>(M, l), M->stream);
-  M->launches += 1;
-  enq_vel_sweep<T>(M, l, true);
-  enq_vel_sweep<T>(M, l, false);
-  launch_pres_rhs<T>(view<T>(M, l), M->stream);
-  M->launches += 1;
-  enq_pres_sweep<T>(M, l);
+  const LevelDev<T>& L = view<T>(M, l);
+  if (sizeof(T) == 4) {
+    for (int q = 0; q < 4; ++q) launch_vel_colour_rhs<T>(L, q, M->stream);
+    for (int q = 2; q >= 0; --q) launch_vel_colour_rhs<T>(L, q, M->stream);
+    M->launches += 7;
+  } else {
+    launch_vel_rhs<T>(L, M->stream);
+    for (int q = 0; q < 4; ++q) launch_vel_colour<T>(L, q, M->stream);
+    for (int q = 2; q >= 0; --q) launch_vel_colour<T>(L, q, M->stream);
+    M->launches += 8;
+  }
+  for (int q = 0; q < 4; ++q) launch_pres_colour_rhs<T>(L, q, M->stream);
+  M->launches += 4;
 }
 
 template <class T>

@@ -20,8 +20,12 @@ __global__ void __launch_bounds__(CT) k_coarse_minres(LevelDev<double> L, double
 }
 }  // namespace
 
+// Threads of the coarse block: small levels are latency bound, and fewer
+// warps make each block-wide barrier and reduction cheaper.
+int coarse_threads(const LevelDev<double>& L) { return L.nalloc <= 4096 ? 128 : CT; }
+
 void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s) {
-  k_coarse_minres<<<1, CT, 0, s>>>(L, scratch, prm, info);
+  k_coarse_minres<<<1, coarse_threads(L), 0, s>>>(L, scratch, prm, info);
 }
 
 // ---- allocation-free variant -------------------------------------------------
@@ -69,7 +73,7 @@ int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* in
     }
     ptr = g_noalloc_ptr[dev];
   }
-  k_coarse_minres<<<1, CT, 0, s>>>(L, ptr, prm, info);
+  k_coarse_minres<<<1, coarse_threads(L), 0, s>>>(L, ptr, prm, info);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("coarse solve launch: ") + cudaGetErrorString(e);

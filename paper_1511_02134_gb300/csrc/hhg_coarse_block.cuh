@@ -142,11 +142,85 @@ __device__ inline int cg(const Ctx& C, const double* b, double* x, double* r, do
   return it;
 }
 
-// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.
-__device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* r, double* d, double* w, int cg_max,
-                       double cg_rtol) {
+// ---- warp-level CG: the three velocity blocks are solved concurrently ------
+
+// Sum over the warp, the same value in every lane (shuffle tree, lane 0 broadcast).
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return __shfl_sync(0xffffffffu, v, 0);
+}
+
+__device__ inline double wdot(const Ctx& C, const double* a, const double* b) {
+  double s = 0;
+  for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) s += a[q] * b[q];
+  return warp_sum(s);
+}
+
+__device__ inline void wapplyA(const Ctx& C, const double* x, double* y) {
+  const LevelDev<double>& L = C.L;
+  for (int64_t q = threadIdx.x & 31; q < C.n; q += 32) {
+    int i, j, k;
+    decode(L, q, i, j, k);
+    const int64_t c = pidx(L.px, L.pxy, i, j, k);
+    const uint8_t fl = L.flags[c];
+    if (!(fl & F_VFREE)) continue;
+    y[c] = (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP)
+                        : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
+  }
+  __syncwarp();
+}
+
+// x = CG(A, b) from zero by one warp (same stopping rule as cg()).
+__device__ inline int cg_warp(const Ctx& C, const double* b, double* x, double* r, double* d, double* w, int max_it,
+                              double rtol) {
+  for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) {
+    x[q] = 0.0;
+    r[q] = b[q];
+    d[q] = b[q];
+    w[q] = 0.0;
+  }
+  __syncwarp();
+  double rr = wdot(C, r, r);
+  const double stop = rtol * rtol * rr;
+  int it = 0;
+  for (; it < max_it; ++it) {
+    if (rr <= stop || rr == 0.0) break;
+    wapplyA(C, d, w);
+    const double dq = wdot(C, d, w);
+    if (dq == 0.0) break;
+    const double alpha = rr / dq;
+    for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) {
+      x[q] += alpha * d[q];
+      r[q] -= alpha * w[q];
+    }
+    __syncwarp();
+    const double rr_new = wdot(C, r, r);
+    const double beta = rr_new / rr;
+    for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) d[q] = r[q] + beta * d[q];
+    __syncwarp();
+    rr = rr_new;
+  }
+  return it;
+}
+
+// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.  With
+// at least three warps the three CG solves run concurrently (warp w solves
+// block w); cgf holds 9 scratch fields (3 per block).
+__device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* const* cgf, int cg_max,
+                              double cg_rtol) {
+  __shared__ int its_sh[3];
   int its = 0;
-  for (int comp = 0; comp < 3; ++comp) its += cg(C, v.c[comp], z.c[comp], r, d, w, cg_max, cg_rtol);
+  const int warp = threadIdx.x >> 5;
+  const bool par = blockDim.x >= 96;
+  if (par) {
+    if (warp < 3) {
+      const int n = cg_warp(C, v.c[warp], z.c[warp], cgf[3 * warp], cgf[3 * warp + 1], cgf[3 * warp + 2], cg_max,
+                            cg_rtol);
+      if ((threadIdx.x & 31) == 0) its_sh[warp] = n;
+    }
+  } else {
+    for (int comp = 0; comp < 3; ++comp) its += cg(C, v.c[comp], z.c[comp], cgf[0], cgf[1], cgf[2], cg_max, cg_rtol);
+  }
   const LevelDev<double>& L = C.L;
   for (int64_t q = threadIdx.x; q < C.n; q += blockDim.x) {
     int i, j, k;
@@ -155,6 +229,8 @@ __device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* r,
     const uint8_t fl = L.flags[c];
     z.c[3][c] = (fl & F_ACT) ? v.c[3][c] / lumped_mass(L, c, fl) : 0.0;
   }
+  __syncthreads();
+  if (par) its = its_sh[0] + its_sh[1] + its_sh[2];
   __syncthreads();
   return its;
 }
@@ -171,14 +247,14 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
     for (int f = 0; f < 4; ++f) v.c[f] = scratch + (int64_t)(first + f) * na;
     return v;
   };
-  // 11 vectors of 4 fields + 3 CG fields = 47 fields
+  // 11 vectors of 4 fields + 1 CG field = 45 fields (of COARSE_FIELDS)
   V4 b = vec(0), x = vec(4), Kz = vec(8);
   V4 vv[3] = {vec(12), vec(16), vec(20)};  // v_prev, v, v_next (rotating)
   V4 zz[2] = {vec(24), vec(28)};            // z, z_next
   V4 ww[3] = {vec(32), vec(36), vec(40)};  // w_prev, w, w_next
   double* cr = scratch + 44 * na;
-  double* cd = scratch + 45 * na;
-  double* cw = scratch + 46 * na;
+  // CG scratch: b and Kz are dead whenever the preconditioner runs
+  double* cgf[9] = {Kz.c[0], Kz.c[1], Kz.c[2], Kz.c[3], b.c[0], b.c[1], b.c[2], b.c[3], cr};
   for (int f = 0; f < 44; ++f) zero1(C, scratch + (int64_t)f * na);
 
   // b = (F, G) - K (U, P): the residual equation of the current iterate
@@ -200,7 +276,7 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
   for (int f = 0; f < 4; ++f)
     for (int64_t q = threadIdx.x; q < na; q += blockDim.x) vv[iv].c[f][q] = b.c[f][q];
   __syncthreads();
-  int cg_total = precond(C, vv[iv], zz[iz], cr, cd, cw, prm.cg_max, prm.cg_rtol);
+  int cg_total = precond(C, vv[iv], zz[iz], cgf, prm.cg_max, prm.cg_rtol);
   double gamma = sqrt(fmax(dot4(C, zz[iz], vv[iv]), 0.0));
   int its = 0;
   double rel = 0.0;
@@ -219,7 +295,7 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
         for (int64_t q = threadIdx.x; q < na; q += blockDim.x)
           vv[iv_next].c[f][q] = Kz.c[f][q] - r1 * vv[iv].c[f][q] - r2 * vv[iv_prev].c[f][q];
       __syncthreads();
-      cg_total += precond(C, vv[iv_next], zz[iz_next], cr, cd, cw, prm.cg_max, prm.cg_rtol);
+      cg_total += precond(C, vv[iv_next], zz[iz_next], cgf, prm.cg_max, prm.cg_rtol);
       const double gamma_next = sqrt(fmax(dot4(C, zz[iz_next], vv[iv_next]), 0.0));
       const double a0 = cc * delta - c_prev * ss * gamma;
       const double a1 = sqrt(a0 * a0 + gamma_next * gamma_next);

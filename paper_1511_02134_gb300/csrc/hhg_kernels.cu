@@ -61,6 +61,20 @@ __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   node_vel_gs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
+template <class T>
+__global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
+  int i, j, k;
+  if (!colour_node(L, colour, i, j, k)) return;
+  node_vel_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
+}
+
+template <class T>
+__global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
+  int i, j, k;
+  if (!colour_node(L, colour, i, j, k)) return;
+  node_pres_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
+}
+
 // RP = B U - G on pressure nodes.
 template <class T>
 __global__ void k_pres_rhs(LevelDev<T> L) {
@@ -415,6 +429,16 @@ void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   k_vel_colour<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, inv);
 }
 template <class T>
+void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
+  const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
+  k_vel_colour_rhs<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, inv);
+}
+template <class T>
+void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
+  const T w = (T)((double)L.omega / (6.0 * (double)L.c));
+  k_pres_colour_rhs<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, w);
+}
+template <class T>
 void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s) {
   k_pres_rhs<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
 }
@@ -509,6 +533,8 @@ void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s)
   template void launch_vel_rhs<T>(const LevelDev<T>&, cudaStream_t);                                    \
   template void launch_vel_colour<T>(const LevelDev<T>&, int, cudaStream_t);                            \
   template void launch_pres_rhs<T>(const LevelDev<T>&, cudaStream_t);                                   \
+  template void launch_vel_colour_rhs<T>(const LevelDev<T>&, int, cudaStream_t);                        \
+  template void launch_pres_colour_rhs<T>(const LevelDev<T>&, int, cudaStream_t);                       \
   template void launch_pres_colour<T>(const LevelDev<T>&, int, cudaStream_t);                           \
   template void launch_residual<T>(const LevelDev<T>&, cudaStream_t);                                   \
   template void launch_restrict<T>(const LevelDev<T>&, const LevelDev<T>&, cudaStream_t);               \

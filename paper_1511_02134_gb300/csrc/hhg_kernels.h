@@ -14,6 +14,10 @@ template <class T> void launch_vel_rhs(const LevelDev<T>& L, cudaStream_t s);
 template <class T> void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s);
 template <class T> void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s);
 template <class T> void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s);
+// Colour sweeps that form their right-hand side at each node (f - B^T p for
+// velocity, B u - g for pressure) instead of reading RU / RP.
+template <class T> void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s);
+template <class T> void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s);
 
 // Residual (RU, RP) = (F, G) - K (U, P); zero on nodes without unknowns.
 template <class T> void launch_residual(const LevelDev<T>& L, cudaStream_t s);

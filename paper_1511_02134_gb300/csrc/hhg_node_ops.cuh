@@ -36,6 +36,28 @@ __device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, int64_t c, T i
   }
 }
 
+// Same update with the right-hand side f - B^T p formed at the node (p does
+// not change during the velocity sweeps, Sec. 3.3), RU is not touched.
+template <class T>
+__device__ __forceinline__ void node_vel_gs_rhs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_VFREE)) return;
+  T bt[3];
+  row_BT(L, L.p, c, fl, bt);
+  if (!(fl & F_IRR)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d)
+      L.u[d][c] = ((L.f[d][c] - bt[d]) + L.nuh * nb6(L.u[d], c, L.px, L.pxy)) * inv6nuh;
+  } else {
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      T dg, of;
+      irr_lap_parts(L, L.u[d], c, dg, of);
+      L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
+    }
+  }
+}
+
 // RP = B U - G (pressure nodes).
 template <class T>
 __device__ __forceinline__ void node_pres_rhs(const LevelDev<T>& L, int64_t c) {
@@ -59,6 +81,26 @@ __device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, int64_t c, T 
     irr_lap_parts(L, L.p, c, dg, of);
     const T cp = L.c * (dg * pc + of);
     L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
+  }
+}
+
+// Same update with B u - g formed at the node (u does not change during the
+// pressure sweep), RP is not touched.
+template <class T>
+__device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, int64_t c, T omega_over_6c) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_ACT)) return;
+  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};
+  const T rp = row_B(L, uu, c, fl) - L.g[c];
+  const T pc = L.p[c];
+  if (!(fl & F_IRR)) {
+    const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
+    L.p[c] = pc + omega_over_6c * (rp - cp);
+  } else {
+    T dg, of;
+    irr_lap_parts(L, L.p, c, dg, of);
+    const T cp = L.c * (dg * pc + of);
+    L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
   }
 }
 

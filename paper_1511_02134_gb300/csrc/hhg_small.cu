@@ -35,17 +35,6 @@ __device__ void b_vel_rhs(const LevelDev<T>& L) {
 }
 
 template <class T>
-__device__ void b_pres_rhs(const LevelDev<T>& L) {
-  const int n = L.nx * L.ny * L.nz;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
-    int i, j, k;
-    decode3(L, q, i, j, k);
-    node_pres_rhs(L, pidx(L.px, L.pxy, i, j, k));
-  }
-  __syncthreads();
-}
-
-template <class T>
 __device__ void b_residual(const LevelDev<T>& L) {
   const int n = L.nx * L.ny * L.nz;
   for (int q = threadIdx.x; q < n; q += blockDim.x) {
@@ -56,7 +45,9 @@ __device__ void b_residual(const LevelDev<T>& L) {
   __syncthreads();
 }
 
-// One colour phase: velocity (vel = true) or pressure Gauss-Seidel.
+// One colour phase: velocity (vel = true) or pressure Gauss-Seidel, with the
+// right-hand side formed at each node (FP32 velocity, and pressure), or the
+// velocity right-hand side read from RU (FP64).
 template <class T>
 __device__ void b_colour(const LevelDev<T>& L, int colour, bool vel, T w) {
   const int nq = (L.nx + 3) / 4;
@@ -68,20 +59,25 @@ __device__ void b_colour(const LevelDev<T>& L, int colour, bool vel, T w) {
     const int i = ((colour - j - k) & 3) + 4 * t;
     if (i >= L.nx) continue;
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    if (vel)
-      node_vel_gs(L, c, w);
-    else
-      node_pres_gs(L, c, w);
+    if (vel) {
+      if (sizeof(T) == 4)
+        node_vel_gs_rhs(L, c, w);
+      else
+        node_vel_gs(L, c, w);
+    } else {
+      node_pres_gs_rhs(L, c, w);
+    }
   }
   __syncthreads();
 }
 
+// The same step sequence as the grid path (backward colour 3 skipped: it
+// would repeat the forward one exactly).
 template <class T>
 __device__ void b_uzawa(const LevelDev<T>& L, T inv6nuh, T omc) {
-  b_vel_rhs(L);
+  if (sizeof(T) != 4) b_vel_rhs(L);
   for (int q = 0; q < 4; ++q) b_colour(L, q, true, inv6nuh);
-  for (int q = 3; q >= 0; --q) b_colour(L, q, true, inv6nuh);
-  b_pres_rhs(L);
+  for (int q = 2; q >= 0; --q) b_colour(L, q, true, inv6nuh);
   for (int q = 0; q < 4; ++q) b_colour(L, q, false, omc);
 }
 
