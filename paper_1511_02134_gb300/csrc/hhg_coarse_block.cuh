@@ -203,15 +203,18 @@ __device__ inline int cg_warp(const Ctx& C, const double* b, double* x, double* 
   return it;
 }
 
-// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.  With
-// at least three warps the three CG solves run concurrently (warp w solves
-// block w); cgf holds 9 scratch fields (3 per block).
+// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.  On
+// small levels (at most 2048 padded entries) with at least three warps the
+// three CG solves run concurrently (warp w solves block w); otherwise the
+// whole block solves them one after the other.  cgf holds 9 scratch fields
+// (3 per block).
 __device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* const* cgf, int cg_max,
                               double cg_rtol) {
   __shared__ int its_sh[3];
   int its = 0;
   const int warp = threadIdx.x >> 5;
-  const bool par = blockDim.x >= 96;
+  // one warp per block pays off only while a warp's share of a vector is small
+  const bool par = blockDim.x >= 96 && C.L.nalloc <= 2048;
   if (par) {
     if (warp < 3) {
       const int n = cg_warp(C, v.c[warp], z.c[warp], cgf[3 * warp], cgf[3 * warp + 1], cgf[3 * warp + 2], cg_max,

@@ -5,9 +5,10 @@ psi = y z / 16 (the unweighted flux does not depend on the body force, see
 the oracle pins).  Checked against the oracle's direct adjoint gradient on a
 small level, and against central finite differences at level 5 on 32 seeded
 directions with step 1e-6: each perturbed solve starts from the base
-solution (solved to 1e-12) and is iterated to 1e-8 relative to its own
+solution (solved to 1e-12) and is iterated to 1e-10 relative to its own
 initial residual, so the finite difference carries only that algebraic
-error (J is affine in f).
+error (J is affine in f).  (At 1e-8 the residual-to-error amplification
+leaves about 3e-6 in the difference, above the 1e-6 target.)
 """
 import numpy as np
 import pytest
@@ -71,7 +72,7 @@ def test_gradient_vs_finite_differences_level5(pkg):
         for sgn in (1.0, -1.0):
             mesh.set_rhs(f0 + sgn * eps * d, ud)
             mesh.set_initial(u0, p0)
-            u, _, s = mesh.solve(tol=1e-8, max_cycles=40)
+            u, _, s = mesh.solve(tol=1e-10, max_cycles=40)
             js.append(float(np.sum(Wj * u)))
         fd = (js[0] - js[1]) / (2 * eps)
         an = float(np.sum(grad * d))
