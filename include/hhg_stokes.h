@@ -84,10 +84,12 @@ typedef struct hhg_options {
   int32_t coarse_cg_max;     /* inner CG iterations at most (50) */
   double coarse_cg_rtol;     /* inner CG relative tolerance (1e-3, Sec. 3.7) */
   int32_t use_graphs;        /* 1: replay each V-cycle as a captured CUDA graph */
-  int32_t fuse_coarse_levels;/* 1: run the coarse levels (at most 8192 lattice nodes in FP32,
-                                1024 in FP64) and the coarse solve as one fused single-block
-                                kernel per cycle */
-  int32_t reserved[6];
+  int32_t fuse_coarse_levels;/* 1: run the coarse levels (see fuse_max_nodes) and the coarse
+                                solve as one fused kernel per cycle */
+  int32_t fuse_max_nodes;    /* largest level (lattice nodes) of the fused kernel; 0 = default (1024) */
+  int32_t team_blocks;       /* CTAs of the fused kernel's thread-block cluster (1 = one block,
+                                at most 16); 0 = default (1) */
+  int32_t reserved[4];
 } hhg_options;
 
 /* Per-solve statistics. */

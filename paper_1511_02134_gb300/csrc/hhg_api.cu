@@ -60,6 +60,7 @@ struct hhg_mesh {
   MacroLattice macro;
   int finest = 0, coarsest = 0;
   int small_top[2] = {-1, -1};  // top level of the fused coarse-levels cycle, FP64 / FP32 (-1: none)
+  unsigned small_cluster[2] = {1, 8};  // CTAs of the fused team, FP64 / FP32
   std::vector<LevelHost> lv;
   uint8_t* d_mmask = nullptr;
   int64_t ndir = 0;
@@ -223,6 +224,7 @@ template <class T>
 void enq_small_cycle(hhg_mesh* M) {
   SmallCycle<T> S;
   std::memset(&S, 0, sizeof(S));
+  S.nblocks = M->small_cluster[sizeof(T) == 4];
   S.nlev = M->small_top[sizeof(T) == 4] - M->coarsest + 1;
   for (int q = 0; q < S.nlev; ++q) {
     const int l = M->coarsest + q;
@@ -649,11 +651,21 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   }
   if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * COARSE_FIELDS * (size_t)M->lv[M->coarsest].nalloc)))
     return bail(rc);
-  // fused coarse levels: the largest level of at most SMALL_MAX_NODES nodes
+  // cluster kernels (fused coarse levels, coarse solve)
+  prepare_coarse_solve();
+  {
+    const unsigned cl = prepare_small_cycle();
+    M->small_cluster[0] = o.team_blocks > 0 ? std::min<unsigned>((unsigned)o.team_blocks, cl) : SMALL_TEAM_BLOCKS_FP64;
+    M->small_cluster[1] = o.team_blocks > 0 ? std::min<unsigned>((unsigned)o.team_blocks, cl)
+                                            : std::min<unsigned>(SMALL_TEAM_BLOCKS, cl);
+  }
+  // fused coarse levels: the largest level of at most fuse_max_nodes nodes
   if (o.fuse_coarse_levels) {
+    const int64_t lim32 = o.fuse_max_nodes > 0 ? o.fuse_max_nodes : SMALL_MAX_NODES;
+    const int64_t lim64 = o.fuse_max_nodes > 0 ? o.fuse_max_nodes : SMALL_MAX_NODES_FP64;
     for (int l = M->coarsest + 1; l <= finest && l - M->coarsest < SMALL_MAX_LEVELS; ++l) {
-      if (M->lv[l].sh.n() <= SMALL_MAX_NODES_FP64) M->small_top[0] = l;
-      if (M->lv[l].sh.n() <= SMALL_MAX_NODES) M->small_top[1] = l;
+      if (M->lv[l].sh.n() <= lim64) M->small_top[0] = l;
+      if (M->lv[l].sh.n() <= lim32) M->small_top[1] = l;
     }
   }
   if ((e = cudaDeviceSynchronize()) != cudaSuccess) {

@@ -8,6 +8,7 @@
 #include "../../include/hhg_stokes.h"
 #include "hhg_coarse_block.cuh"
 #include "hhg_kernels.h"
+#include "hhg_launch.cuh"
 
 namespace hhg {
 
@@ -15,18 +16,33 @@ namespace {
 constexpr int CT = 512;  // threads of the coarse block
 
 __global__ void __launch_bounds__(CT) k_coarse_minres(LevelDev<double> L, double* scratch, CoarseParams prm,
-                                                      double* info) {
-  coarse::minres_block(L, scratch, prm, info);
+                                                      double* info, unsigned nblocks) {
+  coarse::minres_team(Team{nblocks}, L, scratch, prm, info);
 }
+
+unsigned g_coarse_cluster = 8;
 }  // namespace
 
-// Threads of the coarse block: small levels are latency bound, and fewer
-// warps make each block-wide barrier and reduction cheaper.
-int coarse_threads(const LevelDev<double>& L) { return L.nalloc <= 4096 ? 128 : CT; }
+// Launch shape of the coarse solve: small levels are latency bound and run in
+// one block of 128 threads (cheap barriers, one warp per CG); larger ones run
+// on a cluster.
+void coarse_shape(const LevelDev<double>& L, unsigned& nblocks, unsigned& threads) {
+  if (L.nalloc <= 2048) {
+    nblocks = 1;
+    threads = 128;
+  } else {
+    nblocks = g_coarse_cluster;
+    threads = CT;
+  }
+}
 
 void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s) {
-  k_coarse_minres<<<1, coarse_threads(L), 0, s>>>(L, scratch, prm, info);
+  unsigned nb, th;
+  coarse_shape(L, nb, th);
+  launch_team(k_coarse_minres, nb, th, s, L, scratch, prm, info, nb);
 }
+
+void prepare_coarse_solve() { g_coarse_cluster = prepare_team_kernel(k_coarse_minres, CT); }
 
 // ---- allocation-free variant -------------------------------------------------
 // Scratch of the coarse solve for callers that may not allocate device memory:
@@ -73,8 +89,10 @@ int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* in
     }
     ptr = g_noalloc_ptr[dev];
   }
-  k_coarse_minres<<<1, coarse_threads(L), 0, s>>>(L, ptr, prm, info);
-  e = cudaGetLastError();
+  unsigned nb, th;
+  coarse_shape(L, nb, th);
+  e = launch_team(k_coarse_minres, nb, th, s, L, ptr, prm, info, nb);
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("coarse solve launch: ") + cudaGetErrorString(e);
     return HHG_ECUDA;

@@ -1,9 +1,9 @@
 // Coarse-grid solver of the all-at-once multigrid (Sec. 3.7) as a routine of
-// one thread block: MINRES on the full saddle-point system, preconditioned
-// block-diagonally (Sec. 3.2) with a CG solve on each velocity block of A and
-// the inverse lumped pressure mass.  Always FP64.  Loops have fixed upper
-// trip counts (max iterations).  Used by the coarse-solve kernel and by the
-// fused coarse-levels cycle.
+// one team (a thread-block cluster, or one block; hhg_team.cuh): MINRES on the
+// full saddle-point system, preconditioned block-diagonally (Sec. 3.2) with a
+// CG solve on each velocity block of A and the inverse lumped pressure mass.
+// Always FP64.  Loops have fixed upper trip counts (max iterations).  Used by
+// the coarse-solve kernel and by the fused coarse-levels cycle.
 //
 // Recurrences (start from zero):
 //   CG:     stop before an iteration when r.r <= rtol^2 r0.r0 (or r.r = 0),
@@ -16,6 +16,7 @@
 //           eta <- -s_{j+1} eta; stop when |eta| <= rtol gamma_1.
 #pragma once
 #include "hhg_kernels.h"
+#include "hhg_team.cuh"
 
 namespace hhg {
 namespace coarse {
@@ -25,26 +26,9 @@ struct V4 {
   double* c[4];
 };
 
-// Sum over the block (fixed order: warp shuffles, then warp partials in
-// order), returned to every thread.  sh: 33 doubles of shared memory.
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double acc = 0;
-    for (unsigned q = 0; q < blockDim.x / 32; ++q) acc += sh[q];
-    sh[32] = acc;
-  }
-  __syncthreads();
-  const double r = sh[32];
-  __syncthreads();
-  return r;
-}
-
 struct Ctx {
   LevelDev<double> L;
-  double* sh;
+  Team T;
   int64_t n;  // lattice nodes
 };
 
@@ -56,25 +40,16 @@ __device__ __forceinline__ void decode(const LevelDev<double>& L, int64_t q, int
 
 __device__ inline double dot4(const Ctx& C, const V4& a, const V4& b) {
   double s = 0;
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += blockDim.x)
+  for (int64_t q = C.T.rank(); q < C.L.nalloc; q += C.T.size())
     s += (a.c[0][q] * b.c[0][q] + a.c[1][q] * b.c[1][q]) + (a.c[2][q] * b.c[2][q] + a.c[3][q] * b.c[3][q]);
-  return block_sum(s, C.sh);
-}
-
-__device__ inline double dot1(const Ctx& C, const double* a, const double* b) {
-  double s = 0;
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += blockDim.x) s += a[q] * b[q];
-  return block_sum(s, C.sh);
+  return team_sum1(C.T, s);
 }
 
 // y = K x (zero on entries without unknowns)
 __device__ inline void applyK(const Ctx& C, const V4& x, const V4& y) {
   LevelDev<double> L = C.L;
-  L.u[0] = x.c[0];
-  L.u[1] = x.c[1];
-  L.u[2] = x.c[2];
   L.p = x.c[3];
-  for (int64_t q = threadIdx.x; q < C.n; q += blockDim.x) {
+  for (int64_t q = C.T.rank(); q < C.n; q += C.T.size()) {
     int i, j, k;
     decode(L, q, i, j, k);
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
@@ -87,59 +62,97 @@ __device__ inline void applyK(const Ctx& C, const V4& x, const V4& y) {
     }
     if (fl & F_ACT) y.c[3][c] = row_B(L, x.c, c, fl) - row_C(L, L.p, c, fl);
   }
-  __syncthreads();
+  C.T.sync();
 }
 
-// y = A x for one velocity component
-__device__ inline void applyA(const Ctx& C, const double* x, double* y) {
+__device__ __forceinline__ double a_row(const LevelDev<double>& L, const double* x, int64_t c, uint8_t fl) {
+  return (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP)
+                      : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
+}
+
+// x_d = CG(A, b_d) from zero for the three velocity blocks in lockstep over
+// the team: each block follows the stopping rule of cg() on its own (it stops
+// before an iteration when r.r <= rtol^2 r0.r0 or r.r = 0, or when d.Ad = 0),
+// the others go on; sums of the three blocks share one team reduction.
+// f9: 3 scratch fields per block (r, d, A d).  Returns the iterations summed.
+__device__ inline int cg3(const Ctx& C, const V4& b, const V4& x, double* const* f9, int max_it, double rtol) {
   const LevelDev<double>& L = C.L;
-  for (int64_t q = threadIdx.x; q < C.n; q += blockDim.x) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    if (!(fl & F_VFREE)) continue;
-    y[c] = (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP) : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
-  }
-  __syncthreads();
-}
-
-__device__ inline void zero1(const Ctx& C, double* a) {
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += blockDim.x) a[q] = 0.0;
-  __syncthreads();
-}
-
-// x = CG(A, b) from zero; r, d, w scratch.  Returns iterations.
-__device__ inline int cg(const Ctx& C, const double* b, double* x, double* r, double* d, double* w, int max_it,
-                  double rtol) {
-  for (int64_t q = threadIdx.x; q < C.L.nalloc; q += blockDim.x) {
-    x[q] = 0.0;
-    r[q] = b[q];
-    d[q] = b[q];
-    w[q] = 0.0;
-  }
-  __syncthreads();
-  double rr = dot1(C, r, r);
-  const double stop = rtol * rtol * rr;
-  int it = 0;
-  for (; it < max_it; ++it) {
-    if (rr <= stop || rr == 0.0) break;
-    applyA(C, d, w);
-    const double dq = dot1(C, d, w);
-    if (dq == 0.0) break;
-    const double alpha = rr / dq;
-    for (int64_t q = threadIdx.x; q < C.L.nalloc; q += blockDim.x) {
-      x[q] += alpha * d[q];
-      r[q] -= alpha * w[q];
+  for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size()) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      x.c[d][q] = 0.0;
+      f9[3 * d][q] = b.c[d][q];
+      f9[3 * d + 1][q] = b.c[d][q];
+      f9[3 * d + 2][q] = 0.0;
     }
-    __syncthreads();
-    const double rr_new = dot1(C, r, r);
-    const double beta = rr_new / rr;
-    for (int64_t q = threadIdx.x; q < C.L.nalloc; q += blockDim.x) d[q] = r[q] + beta * d[q];
-    __syncthreads();
-    rr = rr_new;
   }
-  return it;
+  C.T.sync();
+  double rr[3] = {0, 0, 0};
+  for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+#pragma unroll
+    for (int d = 0; d < 3; ++d) rr[d] += f9[3 * d][q] * f9[3 * d][q];
+  team_sum<3>(C.T, rr);
+  double stop[3];
+  bool run[3];
+  for (int d = 0; d < 3; ++d) {
+    stop[d] = rtol * rtol * rr[d];
+    run[d] = true;
+  }
+  int its = 0;
+  for (int it = 0; it < max_it; ++it) {
+    for (int d = 0; d < 3; ++d)
+      if (rr[d] <= stop[d] || rr[d] == 0.0) run[d] = false;
+    if (!(run[0] || run[1] || run[2])) break;
+    for (int64_t q = C.T.rank(); q < C.n; q += C.T.size()) {
+      int i, j, k;
+      decode(L, q, i, j, k);
+      const int64_t c = pidx(L.px, L.pxy, i, j, k);
+      const uint8_t fl = L.flags[c];
+      if (!(fl & F_VFREE)) continue;
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (run[d]) f9[3 * d + 2][c] = a_row(L, f9[3 * d + 1], c, fl);
+    }
+    C.T.sync();
+    double dq[3] = {0, 0, 0};
+    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (run[d]) dq[d] += f9[3 * d + 1][q] * f9[3 * d + 2][q];
+    team_sum<3>(C.T, dq);
+    double alpha[3];
+    for (int d = 0; d < 3; ++d) {
+      if (run[d] && dq[d] == 0.0) run[d] = false;
+      alpha[d] = run[d] ? rr[d] / dq[d] : 0.0;
+    }
+    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (run[d]) {
+          x.c[d][q] += alpha[d] * f9[3 * d + 1][q];
+          f9[3 * d][q] -= alpha[d] * f9[3 * d + 2][q];
+        }
+    C.T.sync();
+    double rn[3] = {0, 0, 0};
+    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (run[d]) rn[d] += f9[3 * d][q] * f9[3 * d][q];
+    team_sum<3>(C.T, rn);
+    double beta[3];
+    for (int d = 0; d < 3; ++d) beta[d] = run[d] ? rn[d] / rr[d] : 0.0;
+    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+        if (run[d]) f9[3 * d + 1][q] = f9[3 * d][q] + beta[d] * f9[3 * d + 1][q];
+    C.T.sync();
+    for (int d = 0; d < 3; ++d)
+      if (run[d]) {
+        rr[d] = rn[d];
+        ++its;
+      }
+  }
+  return its;
 }
 
 // ---- warp-level CG: the three velocity blocks are solved concurrently ------
@@ -203,18 +216,17 @@ __device__ inline int cg_warp(const Ctx& C, const double* b, double* x, double* 
   return it;
 }
 
-// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.  On
-// small levels (at most 2048 padded entries) with at least three warps the
-// three CG solves run concurrently (warp w solves block w); otherwise the
-// whole block solves them one after the other.  cgf holds 9 scratch fields
-// (3 per block).
+// z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.  On a
+// single block and a small level (at most 2048 padded entries) the three CG
+// solves run concurrently, warp w solving block w with warp-level
+// synchronisation only; otherwise the team runs them in lockstep (cg3).
+// cgf holds 9 scratch fields (3 per block).
 __device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* const* cgf, int cg_max,
                               double cg_rtol) {
   __shared__ int its_sh[3];
   int its = 0;
   const int warp = threadIdx.x >> 5;
-  // one warp per block pays off only while a warp's share of a vector is small
-  const bool par = blockDim.x >= 96 && C.L.nalloc <= 2048;
+  const bool par = C.T.nblocks == 1 && blockDim.x >= 96 && C.L.nalloc <= 2048;
   if (par) {
     if (warp < 3) {
       const int n = cg_warp(C, v.c[warp], z.c[warp], cgf[3 * warp], cgf[3 * warp + 1], cgf[3 * warp + 2], cg_max,
@@ -222,28 +234,28 @@ __device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* co
       if ((threadIdx.x & 31) == 0) its_sh[warp] = n;
     }
   } else {
-    for (int comp = 0; comp < 3; ++comp) its += cg(C, v.c[comp], z.c[comp], cgf[0], cgf[1], cgf[2], cg_max, cg_rtol);
+    V4 vu = v, zu = z;
+    its = cg3(C, vu, zu, cgf, cg_max, cg_rtol);
   }
   const LevelDev<double>& L = C.L;
-  for (int64_t q = threadIdx.x; q < C.n; q += blockDim.x) {
+  for (int64_t q = C.T.rank(); q < C.n; q += C.T.size()) {
     int i, j, k;
     decode(L, q, i, j, k);
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
     const uint8_t fl = L.flags[c];
     z.c[3][c] = (fl & F_ACT) ? v.c[3][c] / lumped_mass(L, c, fl) : 0.0;
   }
-  __syncthreads();
+  C.T.sync();
   if (par) its = its_sh[0] + its_sh[1] + its_sh[2];
-  __syncthreads();
+  C.T.sync();
   return its;
 }
 
 // (U, P) += PMINRES correction of the residual equation on level L; every
-// thread of the block must call it.  scratch: COARSE_FIELDS fields of L.
-__device__ inline void minres_block(const LevelDev<double>& L, double* scratch, const CoarseParams& prm, double* info) {
-  __shared__ double sh[33];
-
-  Ctx C{L, sh, (int64_t)L.nx * L.ny * L.nz};
+// thread of the team must call it.  scratch: COARSE_FIELDS fields of L.
+__device__ inline void minres_team(const Team& T, const LevelDev<double>& L, double* scratch, const CoarseParams& prm,
+                                   double* info) {
+  Ctx C{L, T, (int64_t)L.nx * L.ny * L.nz};
   const int64_t na = L.nalloc;
   auto vec = [&](int first) {
     V4 v;
@@ -258,7 +270,8 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
   double* cr = scratch + 44 * na;
   // CG scratch: b and Kz are dead whenever the preconditioner runs
   double* cgf[9] = {Kz.c[0], Kz.c[1], Kz.c[2], Kz.c[3], b.c[0], b.c[1], b.c[2], b.c[3], cr};
-  for (int f = 0; f < 44; ++f) zero1(C, scratch + (int64_t)f * na);
+  for (int64_t q = T.rank(); q < 44 * na; q += T.size()) scratch[q] = 0.0;
+  T.sync();
 
   // b = (F, G) - K (U, P): the residual equation of the current iterate
   V4 up;
@@ -267,18 +280,18 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
   up.c[2] = L.u[2];
   up.c[3] = L.p;
   applyK(C, up, Kz);
-  for (int64_t q = threadIdx.x; q < na; q += blockDim.x) {
+  for (int64_t q = T.rank(); q < na; q += T.size()) {
     const uint8_t fl = L.flags[q];
     for (int d = 0; d < 3; ++d) b.c[d][q] = (fl & F_VFREE) ? L.f[d][q] - Kz.c[d][q] : 0.0;
     b.c[3][q] = (fl & F_ACT) ? L.g[q] - Kz.c[3][q] : 0.0;
   }
-  __syncthreads();
+  T.sync();
 
   int iv_prev = 0, iv = 1, iv_next = 2, iz = 0, iz_next = 1, iw_prev = 0, iw = 1, iw_next = 2;
   // v_1 = b, z_1 = P^{-1} v_1
   for (int f = 0; f < 4; ++f)
-    for (int64_t q = threadIdx.x; q < na; q += blockDim.x) vv[iv].c[f][q] = b.c[f][q];
-  __syncthreads();
+    for (int64_t q = T.rank(); q < na; q += T.size()) vv[iv].c[f][q] = b.c[f][q];
+  T.sync();
   int cg_total = precond(C, vv[iv], zz[iz], cgf, prm.cg_max, prm.cg_rtol);
   double gamma = sqrt(fmax(dot4(C, zz[iz], vv[iv]), 0.0));
   int its = 0;
@@ -289,15 +302,15 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
     double c_prev = 1.0, cc = 1.0, s_prev = 0.0, ss = 0.0;
     for (; its < prm.minres_max;) {
       for (int f = 0; f < 4; ++f)
-        for (int64_t q = threadIdx.x; q < na; q += blockDim.x) zz[iz].c[f][q] /= gamma;
-      __syncthreads();
+        for (int64_t q = T.rank(); q < na; q += T.size()) zz[iz].c[f][q] /= gamma;
+      T.sync();
       applyK(C, zz[iz], Kz);
       const double delta = dot4(C, Kz, zz[iz]);
       const double r1 = delta / gamma, r2 = gamma / gamma_prev;
       for (int f = 0; f < 4; ++f)
-        for (int64_t q = threadIdx.x; q < na; q += blockDim.x)
+        for (int64_t q = T.rank(); q < na; q += T.size())
           vv[iv_next].c[f][q] = Kz.c[f][q] - r1 * vv[iv].c[f][q] - r2 * vv[iv_prev].c[f][q];
-      __syncthreads();
+      T.sync();
       cg_total += precond(C, vv[iv_next], zz[iz_next], cgf, prm.cg_max, prm.cg_rtol);
       const double gamma_next = sqrt(fmax(dot4(C, zz[iz_next], vv[iv_next]), 0.0));
       const double a0 = cc * delta - c_prev * ss * gamma;
@@ -308,12 +321,12 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
       const double c_next = a0 / a1, s_next = gamma_next / a1;
       const double step = c_next * eta;
       for (int f = 0; f < 4; ++f)
-        for (int64_t q = threadIdx.x; q < na; q += blockDim.x) {
+        for (int64_t q = T.rank(); q < na; q += T.size()) {
           const double wn = (zz[iz].c[f][q] - a3 * ww[iw_prev].c[f][q] - a2 * ww[iw].c[f][q]) / a1;
           ww[iw_next].c[f][q] = wn;
           x.c[f][q] += step * wn;
         }
-      __syncthreads();
+      T.sync();
       eta = -s_next * eta;
       ++its;
       // shift the recurrences
@@ -339,13 +352,13 @@ __device__ inline void minres_block(const LevelDev<double>& L, double* scratch, 
     }
   }
   // (U, P) += x
-  for (int64_t q = threadIdx.x; q < na; q += blockDim.x) {
+  for (int64_t q = T.rank(); q < na; q += T.size()) {
     L.u[0][q] += x.c[0][q];
     L.u[1][q] += x.c[1][q];
     L.u[2][q] += x.c[2][q];
     L.p[q] += x.c[3][q];
   }
-  if (threadIdx.x == 0 && info) {
+  if (T.rank() == 0 && info) {
     info[0] = (double)its;
     info[1] = rel;
     info[2] = (double)cg_total;

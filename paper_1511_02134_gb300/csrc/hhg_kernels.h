@@ -82,6 +82,8 @@ struct CoarseParams {
   double cg_rtol;
 };
 void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s);
+// Cluster set-up of the coarse solve (call once per device before launches).
+void prepare_coarse_solve();
 
 // Same solve with its scratch in a file-scope device array (no allocation).
 // Fails with HHG_EINVAL when COARSE_FIELDS * L.nalloc exceeds the array.
@@ -91,15 +93,22 @@ int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* in
                          std::string& err);
 
 // Fused cycle of the coarse levels (hhg_small.cu): levels lv[0] (coarsest)
-// .. lv[nlev-1] of one hierarchy, smoothing counts per level, FP64 view of the
-// coarsest level for the coarse solve, its scratch and parameters.
+// .. lv[nlev-1] of one hierarchy run by one cluster of nblocks CTAs,
+// smoothing counts per level, FP64 view of the coarsest level for the coarse
+// solve, its scratch and parameters.
 constexpr int SMALL_MAX_LEVELS = 8;
-// largest level run by the fused block: FP32 work, and FP64 work (one SM
-// has 1/152 of the GPU's FP64 rate, so only the smallest levels pay off)
-constexpr int64_t SMALL_MAX_NODES = 8192;
+// Defaults, measured on GB300 with whole level-7 cube solves: fusing only the
+// levels of at most 1024 nodes into one block is fastest in both precisions.
+// Larger fused levels lose to the per-level kernels (FP64: one SM has 1/152
+// of the FP64 rate), and cluster-wide fusion, although its V-cycles are fast
+// in isolation, slows the solve down between the other kernels of a cycle.
+constexpr int64_t SMALL_MAX_NODES = 1024;
 constexpr int64_t SMALL_MAX_NODES_FP64 = 1024;
+constexpr unsigned SMALL_TEAM_BLOCKS = 1;
+constexpr unsigned SMALL_TEAM_BLOCKS_FP64 = 1;
 template <class T>
 struct SmallCycle {
+  unsigned nblocks;
   LevelDev<T> lv[SMALL_MAX_LEVELS];
   int nlev;
   int nu_pre[SMALL_MAX_LEVELS];
@@ -113,5 +122,7 @@ struct SmallCycle {
 };
 template <class T>
 void launch_small_cycle(const SmallCycle<T>& S, cudaStream_t s);
+// Cluster size for the fused cycle (16, else 8); sets kernel attributes.
+unsigned prepare_small_cycle();
 
 }  // namespace hhg
