@@ -17,6 +17,7 @@ constexpr int CT = 512;  // threads of the coarse block
 
 __global__ void __launch_bounds__(CT) k_coarse_minres(LevelDev<double> L, double* scratch, CoarseParams prm,
                                                       double* info, unsigned nblocks) {
+  pdl_enter();
   coarse::minres_team(Team{nblocks}, L, scratch, prm, info);
 }
 

@@ -50,6 +50,17 @@ struct LevelDev {
   T* rp;
 };
 
+// Programmatic dependent launch: every kernel of the library is launched so
+// that the next one may be scheduled while it runs.  A kernel first waits
+// until the grid it depends on has completed and its writes are visible
+// (griddepcontrol.wait returns at once when there is no such grid), then lets
+// its own dependent grid be scheduled; no kernel touches device memory before
+// the wait.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ int64_t pidx(int64_t px, int64_t pxy, int i, int j, int k) {
   return (int64_t)(i + 1) + px * (j + 1) + pxy * (k + 1);
 }

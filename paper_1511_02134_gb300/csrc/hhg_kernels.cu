@@ -48,6 +48,7 @@ __device__ __forceinline__ bool full_node(const LevelDev<T>& L, int& i, int& j, 
 // sweeps of one Uzawa step, Sec. 3.3).
 template <class T>
 __global__ void k_vel_rhs(LevelDev<T> L) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   node_vel_rhs(L, pidx(L.px, L.pxy, i, j, k));
@@ -56,6 +57,7 @@ __global__ void k_vel_rhs(LevelDev<T> L) {
 // Gauss-Seidel update of the velocity nodes of one colour.
 template <class T>
 __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
+  pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
   node_vel_gs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
@@ -63,6 +65,7 @@ __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
 
 template <class T>
 __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
+  pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
   node_vel_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
@@ -70,6 +73,7 @@ __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
 
 template <class T>
 __global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
+  pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
   node_pres_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
@@ -78,6 +82,7 @@ __global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
 // RP = B U - G on pressure nodes.
 template <class T>
 __global__ void k_pres_rhs(LevelDev<T> L) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   node_pres_rhs(L, pidx(L.px, L.pxy, i, j, k));
@@ -86,6 +91,7 @@ __global__ void k_pres_rhs(LevelDev<T> L) {
 // Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour.
 template <class T>
 __global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
+  pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
   node_pres_gs(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
@@ -93,6 +99,7 @@ __global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
 
 template <class T>
 __global__ void k_residual(LevelDev<T> L) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   node_residual(L, pidx(L.px, L.pxy, i, j, k));
@@ -100,6 +107,7 @@ __global__ void k_residual(LevelDev<T> L) {
 
 template <class T>
 __global__ void k_restrict(LevelDev<T> Lf, LevelDev<T> Lc) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(Lc, i, j, k)) return;
   node_restrict(Lf, Lc, i, j, k);
@@ -107,6 +115,7 @@ __global__ void k_restrict(LevelDev<T> Lf, LevelDev<T> Lc) {
 
 template <class T>
 __global__ void k_prolong_add(LevelDev<T> Lf, LevelDev<T> Lc) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(Lf, i, j, k)) return;
   node_prolong_add(Lf, Lc, i, j, k);
@@ -136,6 +145,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[W], double* out) 
 
 template <int W>
 __global__ void k_final_sum(const double* partial, int nblocks, double* out) {
+  pdl_enter();
   __shared__ double sh[W][32];
   const int lane = threadIdx.x;  // 32 threads
 #pragma unroll
@@ -157,6 +167,7 @@ __global__ void k_final_sum(const double* partial, int nblocks, double* out) {
 
 template <class T>
 __global__ void k_residual_norm2(LevelDev<T> L, double* partial) {
+  pdl_enter();
   double v[1] = {0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L.nalloc; q += stride) {
@@ -168,6 +179,7 @@ __global__ void k_residual_norm2(LevelDev<T> L, double* partial) {
 
 template <class T>
 __global__ void k_mass_moments(LevelDev<T> L, double* partial) {
+  pdl_enter();
   double v[2] = {0.0, 0.0};
   const int64_t n = (int64_t)L.nx * L.ny * L.nz;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -187,6 +199,7 @@ __global__ void k_mass_moments(LevelDev<T> L, double* partial) {
 
 template <class T>
 __global__ void k_project(LevelDev<T> L, const double* mom) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   const int64_t c = pidx(L.px, L.pxy, i, j, k);
@@ -206,6 +219,7 @@ __device__ __forceinline__ double mass_reg(const double* x, int64_t c, int64_t p
 
 __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1, const double* f2,
                           const double* d0, const double* d1, const double* d2) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   const int64_t c = pidx(L.px, L.pxy, i, j, k);
@@ -241,6 +255,7 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
 }
 
 __global__ void k_sum_g(LevelDev<double> L, double* partial) {
+  pdl_enter();
   double v[2] = {0.0, 0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L.nalloc; q += stride) {
@@ -253,6 +268,7 @@ __global__ void k_sum_g(LevelDev<double> L, double* partial) {
 }
 
 __global__ void k_sub_mean_g(LevelDev<double> L, const double* s) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const double mean = s[0] / s[1];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < L.nalloc; q += stride)
@@ -262,6 +278,7 @@ __global__ void k_sub_mean_g(LevelDev<double> L, const double* s) {
 // grad_f_d = M lam_u,d + delta h_T^2 B_d lam_p on active nodes (transpose of
 // the right-hand side map f -> (M f, sum_d G_d f_d), with G_d = delta h_T^2 B_d^T).
 __global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, double* o2) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   const int64_t c = pidx(L.px, L.pxy, i, j, k);
@@ -292,6 +309,7 @@ __global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, doub
 // ---- mixed precision -------------------------------------------------------------------
 
 __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* partial) {
+  pdl_enter();
   double v[1] = {0.0};
   const int64_t n = (int64_t)X.nx * X.ny * X.nz;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -328,6 +346,7 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
 }
 
 __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
     X.u[0][q] += (double)E.u[0][q];
@@ -338,6 +357,7 @@ __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
 }
 
 __global__ void k_coarse_in(LevelDev<float> S, LevelDev<double> D) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D.nalloc; q += stride) {
 #pragma unroll
@@ -351,6 +371,7 @@ __global__ void k_coarse_in(LevelDev<float> S, LevelDev<double> D) {
 }
 
 __global__ void k_coarse_out(LevelDev<float> S, LevelDev<double> D) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D.nalloc; q += stride) {
 #pragma unroll
@@ -363,6 +384,7 @@ __global__ void k_coarse_out(LevelDev<float> S, LevelDev<double> D) {
 
 __global__ void k_scatter(LevelDev<double> L, const double* src, int ncomp, double* d0, double* d1, double* d2,
                           uint8_t mask) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   const int64_t c = pidx(L.px, L.pxy, i, j, k);
@@ -374,6 +396,7 @@ __global__ void k_scatter(LevelDev<double> L, const double* src, int ncomp, doub
 
 template <class T>
 __global__ void k_gather(LevelDev<T> L, const T* s0, const T* s1, const T* s2, int ncomp, double* dst) {
+  pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
   const int64_t c = pidx(L.px, L.pxy, i, j, k);
@@ -383,6 +406,7 @@ __global__ void k_gather(LevelDev<T> L, const T* s0, const T* s1, const T* s2, i
 }
 
 __global__ void k_dirichlet_fill(const int64_t* idx, const double* val, int64_t ndir, double* dst) {
+  pdl_enter();
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= ndir) return;
   const int64_t n = idx[q];
@@ -392,6 +416,7 @@ __global__ void k_dirichlet_fill(const int64_t* idx, const double* val, int64_t 
 
 __global__ void k_dirichlet_gather(const int64_t* pad, int64_t ndir, const double* u0, const double* u1,
                                    const double* u2, double* val) {
+  pdl_enter();
   const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (q >= ndir) return;
   const int64_t c = pad[q];
@@ -401,13 +426,31 @@ __global__ void k_dirichlet_gather(const int64_t* pad, int64_t ndir, const doubl
 }
 
 __global__ void k_scale(double* x, int64_t n, double a) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) x[q] *= a;
 }
 
 __global__ void k_cast(const double* src, float* dst, int64_t n) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) dst[q] = (float)src[q];
+}
+
+// Launch with programmatic stream serialization (see pdl_enter).
+template <class... KArgs, class... Args>
+void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 int flat_blocks(int64_t n) {
@@ -421,57 +464,57 @@ int flat_blocks(int64_t n) {
 
 template <class T>
 void launch_vel_rhs(const LevelDev<T>& L, cudaStream_t s) {
-  k_vel_rhs<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
+  launch_k(k_vel_rhs<T>, full_grid(L), dim3(FX, FY), s, L);
 }
 template <class T>
 void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
-  k_vel_colour<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, inv);
+  launch_k(k_vel_colour<T>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
-  k_vel_colour_rhs<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, inv);
+  launch_k(k_vel_colour_rhs<T>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
 }
 template <class T>
 void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
-  k_pres_colour_rhs<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, w);
+  launch_k(k_pres_colour_rhs<T>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
 }
 template <class T>
 void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s) {
-  k_pres_rhs<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
+  launch_k(k_pres_rhs<T>, full_grid(L), dim3(FX, FY), s, L);
 }
 template <class T>
 void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
-  k_pres_colour<T><<<colour_grid(L), dim3(CX, CY), 0, s>>>(L, colour, w);
+  launch_k(k_pres_colour<T>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
 }
 template <class T>
 void launch_residual(const LevelDev<T>& L, cudaStream_t s) {
-  k_residual<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L);
+  launch_k(k_residual<T>, full_grid(L), dim3(FX, FY), s, L);
 }
 template <class T>
 void launch_restrict(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s) {
-  k_restrict<T><<<full_grid(coarse), dim3(FX, FY), 0, s>>>(fine, coarse);
+  launch_k(k_restrict<T>, full_grid(coarse), dim3(FX, FY), s, fine, coarse);
 }
 template <class T>
 void launch_prolong_add(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s) {
-  k_prolong_add<T><<<full_grid(fine), dim3(FX, FY), 0, s>>>(fine, coarse);
+  launch_k(k_prolong_add<T>, full_grid(fine), dim3(FX, FY), s, fine, coarse);
 }
 template <class T>
 void launch_residual_norm2(const LevelDev<T>& L, double* partial, double* out, cudaStream_t s) {
-  k_residual_norm2<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(L, partial);
-  k_final_sum<1><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+  launch_k(k_residual_norm2<T>, REDUCE_BLOCKS, REDUCE_THREADS, s, L, partial);
+  launch_k(k_final_sum<1>, 1, 32, s, partial, REDUCE_BLOCKS, out);
 }
 template <class T>
 void launch_mass_moments(const LevelDev<T>& L, double* partial, double* out, cudaStream_t s) {
-  k_mass_moments<T><<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(L, partial);
-  k_final_sum<2><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+  launch_k(k_mass_moments<T>, REDUCE_BLOCKS, REDUCE_THREADS, s, L, partial);
+  launch_k(k_final_sum<2>, 1, 32, s, partial, REDUCE_BLOCKS, out);
 }
 template <class T>
 void launch_project(const LevelDev<T>& L, const double* moments, cudaStream_t s) {
-  k_project<T><<<full_grid(L), dim3(FX, FY), 0, s>>>(L, moments);
+  launch_k(k_project<T>, full_grid(L), dim3(FX, FY), s, L, moments);
 }
 template <class T>
 void launch_zero(const LevelDev<T>& L, int what, cudaStream_t s) {
@@ -480,29 +523,29 @@ void launch_zero(const LevelDev<T>& L, int what, cudaStream_t s) {
 }
 
 void launch_set_rhs(const LevelDev<double>& L, const double* const* fnod, const double* const* uD, cudaStream_t s) {
-  k_set_rhs<<<full_grid(L), dim3(FX, FY), 0, s>>>(L, fnod[0], fnod[1], fnod[2], uD[0], uD[1], uD[2]);
+  launch_k(k_set_rhs, full_grid(L), dim3(FX, FY), s, L, fnod[0], fnod[1], fnod[2], uD[0], uD[1], uD[2]);
 }
 void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s) {
-  k_sum_g<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(L, partial);
-  k_final_sum<2><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
-  k_sub_mean_g<<<flat_blocks(L.nalloc), 256, 0, s>>>(L, out);
+  launch_k(k_sum_g, REDUCE_BLOCKS, REDUCE_THREADS, s, L, partial);
+  launch_k(k_final_sum<2>, 1, 32, s, partial, REDUCE_BLOCKS, out);
+  launch_k(k_sub_mean_g, flat_blocks(L.nalloc), 256, s, L, out);
 }
 void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStream_t s) {
-  k_rhs_transpose<<<full_grid(L), dim3(FX, FY), 0, s>>>(L, out[0], out[1], out[2]);
+  launch_k(k_rhs_transpose, full_grid(L), dim3(FX, FY), s, L, out[0], out[1], out[2]);
 }
 void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
                         cudaStream_t s) {
-  k_ir_residual<<<REDUCE_BLOCKS, REDUCE_THREADS, 0, s>>>(x, e, partial);
-  k_final_sum<1><<<1, 32, 0, s>>>(partial, REDUCE_BLOCKS, out);
+  launch_k(k_ir_residual, REDUCE_BLOCKS, REDUCE_THREADS, s, x, e, partial);
+  launch_k(k_final_sum<1>, 1, 32, s, partial, REDUCE_BLOCKS, out);
 }
 void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
-  k_ir_update<<<flat_blocks(x.nalloc), 256, 0, s>>>(x, e);
+  launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e);
 }
 void launch_coarse_in(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s) {
-  k_coarse_in<<<flat_blocks(l64.nalloc), 256, 0, s>>>(l32, l64);
+  launch_k(k_coarse_in, flat_blocks(l64.nalloc), 256, s, l32, l64);
 }
 void launch_coarse_out(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s) {
-  k_coarse_out<<<flat_blocks(l64.nalloc), 256, 0, s>>>(l32, l64);
+  launch_k(k_coarse_out, flat_blocks(l64.nalloc), 256, s, l32, l64);
 }
 void launch_scatter(const LevelDev<double>& L, const double* src, int ncomp, double* const* dst, uint8_t mask,
                     cudaStream_t s) {
@@ -517,16 +560,16 @@ void launch_gather(const LevelDev<T>& L, const T* const* src, int ncomp, double*
 void launch_dirichlet_fill(const int64_t* idx, const double* val, int64_t ndir, const LevelDev<double>&, double* dst,
                            cudaStream_t s) {
   if (ndir == 0) return;
-  k_dirichlet_fill<<<(unsigned)((ndir + 255) / 256), 256, 0, s>>>(idx, val, ndir, dst);
+  launch_k(k_dirichlet_fill, (unsigned)((ndir + 255) / 256), 256, s, idx, val, ndir, dst);
 }
 void launch_dirichlet_gather(const int64_t* pad, int64_t ndir, const LevelDev<double>& L, double* val,
                              cudaStream_t s) {
   if (ndir == 0) return;
-  k_dirichlet_gather<<<(unsigned)((ndir + 255) / 256), 256, 0, s>>>(pad, ndir, L.u[0], L.u[1], L.u[2], val);
+  launch_k(k_dirichlet_gather, (unsigned)((ndir + 255) / 256), 256, s, pad, ndir, L.u[0], L.u[1], L.u[2], val);
 }
-void launch_scale(double* x, int64_t n, double a, cudaStream_t s) { k_scale<<<flat_blocks(n), 256, 0, s>>>(x, n, a); }
+void launch_scale(double* x, int64_t n, double a, cudaStream_t s) { launch_k(k_scale, flat_blocks(n), 256, s, x, n, a); }
 void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s) {
-  k_cast<<<flat_blocks(n), 256, 0, s>>>(src, dst, n);
+  launch_k(k_cast, flat_blocks(n), 256, s, src, dst, n);
 }
 
 #define HHG_INST(T)                                                                                    \

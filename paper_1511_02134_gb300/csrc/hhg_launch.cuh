@@ -1,5 +1,6 @@
 // Launch of a one-cluster grid: nblocks CTAs forming a single thread-block
-// cluster (a plain single-block launch when nblocks == 1).
+// cluster (a plain single-block launch when nblocks == 1), with programmatic
+// stream serialization like every other kernel of the library.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -13,13 +14,15 @@ cudaError_t launch_team(void (*kernel)(KArgs...), unsigned nblocks, unsigned thr
   cfg.blockDim = dim3(threads, 1, 1);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = nblocks;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = nblocks;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = nblocks > 1 ? 1 : 0;
+  cfg.numAttrs = nblocks > 1 ? 2 : 1;
   return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 

@@ -137,6 +137,7 @@ __device__ void b_coarse(const Team& tm, const SmallCycle<float>& S) {
 
 template <class R>
 __global__ void __launch_bounds__(ST) k_small_cycle(SmallCycle<R> S) {
+  pdl_enter();
   const Team tm{S.nblocks};
   const int top = S.nlev - 1;
   for (int l = top; l >= 1; --l) {
