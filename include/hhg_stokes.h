@@ -258,7 +258,8 @@ int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count);
  *   The mesh's coarsest-level fields and staging buffer are used as work
  *   space, so do not overlap this call with other calls on the same mesh.
  *   Errors: HHG_EINVAL when the coarsest level needs more than 2^18 scratch
- *   doubles (48 fields of its padded lattice), HHG_ECUDA on CUDA errors.
+ *   doubles (11 (3 nv + np) + 9 nv for nv free velocity nodes and np
+ *   pressure nodes), HHG_ECUDA on CUDA errors.
  *   The first call on a device looks up the array's device address (one
  *   cudaGetSymbolAddress); make that first call before any stream capture.
  *   Every call shares the one array per device, which keeps the last call's

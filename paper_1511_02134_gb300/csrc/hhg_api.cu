@@ -71,7 +71,9 @@ struct hhg_mesh {
   double* d_partial = nullptr;
   double* d_scalars = nullptr;  // [0] norm2, [1..2] moments, [3..4] g-mean, [5..7] coarse info
   double* h_scalars = nullptr;  // pinned mirror
-  double* d_coarse = nullptr;
+  double* d_coarse = nullptr;  // coarse-solve scratch
+  CoarseSys coarse_sys{};       // compact coarsest-level system (device arrays)
+  void* d_coarse_sys = nullptr;  // one allocation holding its arrays
   double* d_backup = nullptr;  // 8 finest FP64 fields (adjoint)
   cudaGraphExec_t graph[2] = {nullptr, nullptr};
   int64_t graph_launches[2] = {0, 0};
@@ -196,20 +198,10 @@ void enq_uzawa(hhg_mesh* M, int l) {
 }
 
 template <class T>
-void enq_coarse(hhg_mesh* M);
-template <>
-void enq_coarse<double>(hhg_mesh* M) {
+void enq_coarse(hhg_mesh* M) {
   CoarseParams prm{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max, M->opt.coarse_cg_rtol};
-  launch_coarse_solve(M->lv[M->coarsest].d64, M->d_coarse, prm, M->d_scalars + 5, M->stream);
+  launch_coarse_solve<T>(M->coarse_sys, view<T>(M, M->coarsest), M->d_coarse, prm, M->d_scalars + 5, M->stream);
   M->launches += 1;
-}
-template <>
-void enq_coarse<float>(hhg_mesh* M) {
-  LevelHost& H = M->lv[M->coarsest];
-  launch_coarse_in(H.d32, H.d64, M->stream);
-  enq_coarse<double>(M);
-  launch_coarse_out(H.d32, H.d64, M->stream);
-  M->launches += 2;
 }
 
 template <class T>
@@ -234,7 +226,7 @@ void enq_small_cycle(hhg_mesh* M) {
     S.inv6nuh[q] = (T)(1.0 / (6.0 * (double)S.lv[q].nuh));
     S.omc[q] = (T)((double)S.lv[q].omega / (6.0 * (double)S.lv[q].c));
   }
-  S.c64 = M->lv[M->coarsest].d64;
+  S.cs = M->coarse_sys;
   S.scratch = M->d_coarse;
   S.prm = CoarseParams{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max,
                        M->opt.coarse_cg_rtol};
@@ -445,6 +437,7 @@ void release(hhg_mesh* M) {
   cudaFree(M->d_partial);
   cudaFree(M->d_scalars);
   cudaFree(M->d_coarse);
+  cudaFree(M->d_coarse_sys);
   cudaFree(M->d_backup);
   if (M->h_scalars) cudaFreeHost(M->h_scalars);
   if (M->own_stream && M->stream) cudaStreamDestroy(M->stream);
@@ -649,7 +642,62 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     M->err = cudaGetErrorString(e);
     return bail(HHG_ENOMEM);
   }
-  if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * COARSE_FIELDS * (size_t)M->lv[M->coarsest].nalloc)))
+  // compact coarsest-level system for the coarse solver
+  {
+    LevelHost& H = M->lv[M->coarsest];
+    std::vector<uint16_t> cls;
+    std::vector<double> table;
+    std::string cerr;
+    int ncls = 0;
+    stencil_classes(M->macro, H.level, H.flags.data(), cls, table, ncls, cerr);
+    CoarseMatrix cm;
+    if (cerr.empty() &&
+        (rc = assemble_coarse(H.sh, H.px, H.px * H.py, H.flags.data(), cls.data(), table.data(), H.d64.nuh, H.d64.c,
+                              H.d64.h2, H.d64.h3, cm, cerr))) {
+      M->err = cerr;
+      return bail(rc);
+    }
+    if (!cerr.empty()) {
+      M->err = cerr;
+      return bail(HHG_EMESH);
+    }
+    // one allocation, 8-byte aligned parts: doubles first, then the indices
+    const size_t nd = cm.kval.size() + cm.aval.size() + cm.mass.size();
+    const size_t ni = cm.vidx.size() + cm.pidx.size() + cm.kptr.size() + cm.kcol.size() + cm.aptr.size() +
+                      cm.acol.size();
+    if ((rc = dalloc(M, &M->d_coarse_sys, sizeof(double) * nd + sizeof(int32_t) * ni + 16))) return bail(rc);
+    double* dp = (double*)M->d_coarse_sys;
+    int32_t* ip = (int32_t*)(dp + nd);
+    auto put_d = [&](const std::vector<double>& v) {
+      double* at = dp;
+      if (!v.empty()) cudaMemcpy(at, v.data(), sizeof(double) * v.size(), cudaMemcpyHostToDevice);
+      dp += v.size();
+      return at;
+    };
+    auto put_i = [&](const std::vector<int32_t>& v) {
+      int32_t* at = ip;
+      if (!v.empty()) cudaMemcpy(at, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+      ip += v.size();
+      return at;
+    };
+    CoarseSys& S = M->coarse_sys;
+    S.nv = cm.nv;
+    S.np = cm.np;
+    S.kval = put_d(cm.kval);
+    S.aval = put_d(cm.aval);
+    S.mass = put_d(cm.mass);
+    S.vidx = put_i(cm.vidx);
+    S.pidx = put_i(cm.pidx);
+    S.kptr = put_i(cm.kptr);
+    S.kcol = put_i(cm.kcol);
+    S.aptr = put_i(cm.aptr);
+    S.acol = put_i(cm.acol);
+    if ((e = cudaGetLastError()) != cudaSuccess) {
+      M->err = std::string("upload of the coarse system: ") + cudaGetErrorString(e);
+      return bail(HHG_ECUDA);
+    }
+  }
+  if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * (size_t)std::max<int64_t>(1, coarse_scratch_doubles(M->coarse_sys)))))
     return bail(rc);
   // cluster kernels (fused coarse levels, coarse solve)
   prepare_coarse_solve();
@@ -1038,7 +1086,7 @@ int hhg_coarse_solve_noalloc(hhg_mesh* M, const double* f, const double* g, doub
   if ((rc = stage_in(M, p, n))) return rc;
   launch_scatter(L, M->d_stage, 1, pp, F_ACT, M->stream);
   CoarseParams prm{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max, M->opt.coarse_cg_rtol};
-  if ((rc = coarse_solve_noalloc(L, prm, M->d_scalars + 5, M->stream, M->err))) return rc;
+  if ((rc = coarse_solve_noalloc(M->coarse_sys, L, prm, M->d_scalars + 5, M->stream, M->err))) return rc;
   M->launches += 5;
   const double* us[3] = {L.u[0], L.u[1], L.u[2]};
   launch_gather<double>(L, us, 3, M->d_stage, M->stream);

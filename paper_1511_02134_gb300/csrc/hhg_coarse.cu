@@ -1,7 +1,8 @@
-// Coarse-grid solver kernel (Sec. 3.7): the block routine of
-// hhg_coarse_block.cuh run by one thread block.  The coarsest level of the
-// paper's set-up (level 2 of the unit cube: 206 unknowns) is far too small to
-// fill more than one SM, and one block needs no grid-wide synchronisation.
+// Coarse-grid solver kernel (Sec. 3.7): the team routine of
+// hhg_coarse_block.cuh run by one thread block or one cluster.  The coarsest
+// level of the paper's set-up (level 2 of the unit cube: 206 unknowns) is far
+// too small to fill more than one SM, and one block needs no grid-wide
+// synchronisation; coarsest levels of larger macro meshes use a cluster.
 #include <mutex>
 #include <string>
 
@@ -13,22 +14,23 @@
 namespace hhg {
 
 namespace {
-constexpr int CT = 512;  // threads of the coarse block
+constexpr int CT = 512;  // threads per CTA of a cluster solve
 
-__global__ void __launch_bounds__(CT) k_coarse_minres(LevelDev<double> L, double* scratch, CoarseParams prm,
+template <class T>
+__global__ void __launch_bounds__(CT) k_coarse_minres(CoarseSys S, LevelDev<T> L, double* scratch, CoarseParams prm,
                                                       double* info, unsigned nblocks) {
   pdl_enter();
-  coarse::minres_team(Team{nblocks}, L, scratch, prm, info);
+  coarse::minres_team(Team{nblocks}, S, L, scratch, prm, info);
 }
 
 unsigned g_coarse_cluster = 8;
 }  // namespace
 
-// Launch shape of the coarse solve: small levels are latency bound and run in
-// one block of 128 threads (cheap barriers, one warp per CG); larger ones run
-// on a cluster.
-void coarse_shape(const LevelDev<double>& L, unsigned& nblocks, unsigned& threads) {
-  if (L.nalloc <= 2048) {
+// Launch shape of the coarse solve: small coarse systems are latency bound
+// and run in one block of 128 threads (cheap barriers, one warp per CG);
+// larger ones run on a cluster.
+void coarse_shape(const CoarseSys& S, unsigned& nblocks, unsigned& threads) {
+  if (coarse_fits_block(S)) {
     nblocks = 1;
     threads = 128;
   } else {
@@ -37,13 +39,24 @@ void coarse_shape(const LevelDev<double>& L, unsigned& nblocks, unsigned& thread
   }
 }
 
-void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s) {
+template <class T>
+void launch_coarse_solve(const CoarseSys& S, const LevelDev<T>& L, double* scratch, CoarseParams prm, double* info,
+                         cudaStream_t s) {
   unsigned nb, th;
-  coarse_shape(L, nb, th);
-  launch_team(k_coarse_minres, nb, th, s, L, scratch, prm, info, nb);
+  coarse_shape(S, nb, th);
+  launch_team(k_coarse_minres<T>, nb, th, s, S, L, scratch, prm, info, nb);
 }
 
-void prepare_coarse_solve() { g_coarse_cluster = prepare_team_kernel(k_coarse_minres, CT); }
+template void launch_coarse_solve<double>(const CoarseSys&, const LevelDev<double>&, double*, CoarseParams, double*,
+                                          cudaStream_t);
+template void launch_coarse_solve<float>(const CoarseSys&, const LevelDev<float>&, double*, CoarseParams, double*,
+                                         cudaStream_t);
+
+void prepare_coarse_solve() {
+  const unsigned a = prepare_team_kernel(k_coarse_minres<double>, CT);
+  const unsigned b = prepare_team_kernel(k_coarse_minres<float>, CT);
+  g_coarse_cluster = a < b ? a : b;
+}
 
 // ---- allocation-free variant -------------------------------------------------
 // Scratch of the coarse solve for callers that may not allocate device memory:
@@ -58,9 +71,9 @@ std::mutex g_noalloc_mutex;
 double* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
 }  // namespace
 
-int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* info, cudaStream_t s,
-                         std::string& err) {
-  const int64_t need = (int64_t)COARSE_FIELDS * L.nalloc;
+int coarse_solve_noalloc(const CoarseSys& S, const LevelDev<double>& L, CoarseParams prm, double* info,
+                         cudaStream_t s, std::string& err) {
+  const int64_t need = coarse_scratch_doubles(S);
   if (need > NOALLOC_COARSE_DOUBLES) {
     err = "coarsest level needs " + std::to_string(need) + " scratch doubles; the allocation-free coarse solve holds " +
           std::to_string(NOALLOC_COARSE_DOUBLES);
@@ -91,8 +104,8 @@ int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* in
     ptr = g_noalloc_ptr[dev];
   }
   unsigned nb, th;
-  coarse_shape(L, nb, th);
-  e = launch_team(k_coarse_minres, nb, th, s, L, ptr, prm, info, nb);
+  coarse_shape(S, nb, th);
+  e = launch_team(k_coarse_minres<double>, nb, th, s, S, L, ptr, prm, info, nb);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("coarse solve launch: ") + cudaGetErrorString(e);

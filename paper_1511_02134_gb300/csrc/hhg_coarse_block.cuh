@@ -2,8 +2,11 @@
 // one team (a thread-block cluster, or one block; hhg_team.cuh): MINRES on the
 // full saddle-point system, preconditioned block-diagonally (Sec. 3.2) with a
 // CG solve on each velocity block of A and the inverse lumped pressure mass.
-// Always FP64.  Loops have fixed upper trip counts (max iterations).  Used by
-// the coarse-solve kernel and by the fused coarse-levels cycle.
+// Always FP64, on the compact unknown vector x = (u_0, u_1, u_2, p) of the
+// coarsest level with K and A in CSR (CoarseSys), so no work is spent on the
+// ghost frame, Dirichlet nodes or inactive nodes of the lattice.  Loops have
+// fixed upper trip counts (max iterations).  Used by the coarse-solve kernel
+// and by the fused coarse-levels cycle.
 //
 // Recurrences (start from zero):
 //   CG:     stop before an iteration when r.r <= rtol^2 r0.r0 (or r.r = 0),
@@ -21,76 +24,54 @@
 namespace hhg {
 namespace coarse {
 
-
-struct V4 {
-  double* c[4];
-};
-
 struct Ctx {
-  LevelDev<double> L;
+  CoarseSys S;
   Team T;
-  int64_t n;  // lattice nodes
+  int n;  // 3 nv + np
 };
 
-__device__ __forceinline__ void decode(const LevelDev<double>& L, int64_t q, int& i, int& j, int& k) {
-  i = (int)(q % L.nx);
-  j = (int)((q / L.nx) % L.ny);
-  k = (int)(q / ((int64_t)L.nx * L.ny));
+__device__ __forceinline__ double csr_row(const int32_t* ptr, const int32_t* col, const double* val, int r,
+                                          const double* x) {
+  double s = 0.0;
+  const int e = ptr[r + 1];
+  for (int k = ptr[r]; k < e; ++k) s += val[k] * x[col[k]];
+  return s;
 }
 
-__device__ inline double dot4(const Ctx& C, const V4& a, const V4& b) {
+__device__ inline double dot(const Ctx& C, const double* a, const double* b) {
   double s = 0;
-  for (int64_t q = C.T.rank(); q < C.L.nalloc; q += C.T.size())
-    s += (a.c[0][q] * b.c[0][q] + a.c[1][q] * b.c[1][q]) + (a.c[2][q] * b.c[2][q] + a.c[3][q] * b.c[3][q]);
+  for (int q = (int)C.T.rank(); q < C.n; q += (int)C.T.size()) s += a[q] * b[q];
   return team_sum1(C.T, s);
 }
 
-// y = K x (zero on entries without unknowns)
-__device__ inline void applyK(const Ctx& C, const V4& x, const V4& y) {
-  LevelDev<double> L = C.L;
-  L.p = x.c[3];
-  for (int64_t q = C.T.rank(); q < C.n; q += C.T.size()) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    if (fl & F_VFREE) {
-      double au[3], bt[3];
-      row_A(L, x.c, c, fl, au);
-      row_BT(L, L.p, c, fl, bt);
-      for (int d = 0; d < 3; ++d) y.c[d][c] = au[d] + bt[d];
-    }
-    if (fl & F_ACT) y.c[3][c] = row_B(L, x.c, c, fl) - row_C(L, L.p, c, fl);
-  }
+// y = K x
+__device__ inline void applyK(const Ctx& C, const double* x, double* y) {
+  for (int r = (int)C.T.rank(); r < C.n; r += (int)C.T.size()) y[r] = csr_row(C.S.kptr, C.S.kcol, C.S.kval, r, x);
   C.T.sync();
-}
-
-__device__ __forceinline__ double a_row(const LevelDev<double>& L, const double* x, int64_t c, uint8_t fl) {
-  return (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP)
-                      : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
 }
 
 // x_d = CG(A, b_d) from zero for the three velocity blocks in lockstep over
-// the team: each block follows the stopping rule of cg() on its own (it stops
-// before an iteration when r.r <= rtol^2 r0.r0 or r.r = 0, or when d.Ad = 0),
-// the others go on; sums of the three blocks share one team reduction.
-// f9: 3 scratch fields per block (r, d, A d).  Returns the iterations summed.
-__device__ inline int cg3(const Ctx& C, const V4& b, const V4& x, double* const* f9, int max_it, double rtol) {
-  const LevelDev<double>& L = C.L;
-  for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size()) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      x.c[d][q] = 0.0;
-      f9[3 * d][q] = b.c[d][q];
-      f9[3 * d + 1][q] = b.c[d][q];
-      f9[3 * d + 2][q] = 0.0;
-    }
+// the team: each block follows the stopping rule of the single CG on its own
+// (it stops before an iteration when r.r <= rtol^2 r0.r0 or r.r = 0, or when
+// d.Ad = 0), the others go on; sums of the three blocks share one team
+// reduction.  b, x: 3 nv entries; cg: 9 nv scratch (r, d, A d per block).
+// Returns the iterations summed over the blocks.
+__device__ inline int cg3(const Ctx& C, const double* b, double* x, double* cg, int max_it, double rtol) {
+  const int nv = C.S.nv;
+  double* R = cg;
+  double* D = cg + 3 * nv;
+  double* Q = cg + 6 * nv;
+  for (int q = (int)C.T.rank(); q < 3 * nv; q += (int)C.T.size()) {
+    x[q] = 0.0;
+    R[q] = b[q];
+    D[q] = b[q];
+    Q[q] = 0.0;
   }
   C.T.sync();
   double rr[3] = {0, 0, 0};
-  for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+  for (int q = (int)C.T.rank(); q < nv; q += (int)C.T.size())
 #pragma unroll
-    for (int d = 0; d < 3; ++d) rr[d] += f9[3 * d][q] * f9[3 * d][q];
+    for (int d = 0; d < 3; ++d) rr[d] += R[d * nv + q] * R[d * nv + q];
   team_sum<3>(C.T, rr);
   double stop[3];
   bool run[3];
@@ -103,48 +84,39 @@ __device__ inline int cg3(const Ctx& C, const V4& b, const V4& x, double* const*
     for (int d = 0; d < 3; ++d)
       if (rr[d] <= stop[d] || rr[d] == 0.0) run[d] = false;
     if (!(run[0] || run[1] || run[2])) break;
-    for (int64_t q = C.T.rank(); q < C.n; q += C.T.size()) {
-      int i, j, k;
-      decode(L, q, i, j, k);
-      const int64_t c = pidx(L.px, L.pxy, i, j, k);
-      const uint8_t fl = L.flags[c];
-      if (!(fl & F_VFREE)) continue;
+    for (int q = (int)C.T.rank(); q < nv; q += (int)C.T.size())
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (run[d]) f9[3 * d + 2][c] = a_row(L, f9[3 * d + 1], c, fl);
-    }
+        if (run[d]) Q[d * nv + q] = csr_row(C.S.aptr, C.S.acol, C.S.aval, q, D + d * nv);
     C.T.sync();
     double dq[3] = {0, 0, 0};
-    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+    for (int q = (int)C.T.rank(); q < nv; q += (int)C.T.size())
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (run[d]) dq[d] += f9[3 * d + 1][q] * f9[3 * d + 2][q];
+        if (run[d]) dq[d] += D[d * nv + q] * Q[d * nv + q];
     team_sum<3>(C.T, dq);
     double alpha[3];
     for (int d = 0; d < 3; ++d) {
       if (run[d] && dq[d] == 0.0) run[d] = false;
       alpha[d] = run[d] ? rr[d] / dq[d] : 0.0;
     }
-    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+    double rn[3] = {0, 0, 0};
+    for (int q = (int)C.T.rank(); q < nv; q += (int)C.T.size())
 #pragma unroll
       for (int d = 0; d < 3; ++d)
         if (run[d]) {
-          x.c[d][q] += alpha[d] * f9[3 * d + 1][q];
-          f9[3 * d][q] -= alpha[d] * f9[3 * d + 2][q];
+          const int i = d * nv + q;
+          x[i] += alpha[d] * D[i];
+          R[i] -= alpha[d] * Q[i];
+          rn[d] += R[i] * R[i];
         }
-    C.T.sync();
-    double rn[3] = {0, 0, 0};
-    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
-#pragma unroll
-      for (int d = 0; d < 3; ++d)
-        if (run[d]) rn[d] += f9[3 * d][q] * f9[3 * d][q];
     team_sum<3>(C.T, rn);
     double beta[3];
     for (int d = 0; d < 3; ++d) beta[d] = run[d] ? rn[d] / rr[d] : 0.0;
-    for (int64_t q = C.T.rank(); q < L.nalloc; q += C.T.size())
+    for (int q = (int)C.T.rank(); q < nv; q += (int)C.T.size())
 #pragma unroll
       for (int d = 0; d < 3; ++d)
-        if (run[d]) f9[3 * d + 1][q] = f9[3 * d][q] + beta[d] * f9[3 * d + 1][q];
+        if (run[d]) D[d * nv + q] = R[d * nv + q] + beta[d] * D[d * nv + q];
     C.T.sync();
     for (int d = 0; d < 3; ++d)
       if (run[d]) {
@@ -163,137 +135,127 @@ __device__ __forceinline__ double warp_sum(double v) {
   return __shfl_sync(0xffffffffu, v, 0);
 }
 
-__device__ inline double wdot(const Ctx& C, const double* a, const double* b) {
-  double s = 0;
-  for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) s += a[q] * b[q];
-  return warp_sum(s);
-}
-
-__device__ inline void wapplyA(const Ctx& C, const double* x, double* y) {
-  const LevelDev<double>& L = C.L;
-  for (int64_t q = threadIdx.x & 31; q < C.n; q += 32) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    if (!(fl & F_VFREE)) continue;
-    y[c] = (fl & F_IRR) ? L.nuh * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP)
-                        : L.nuh * (6.0 * x[c] - nb6(x, c, L.px, L.pxy));
-  }
-  __syncwarp();
-}
-
-// x = CG(A, b) from zero by one warp (same stopping rule as cg()).
-__device__ inline int cg_warp(const Ctx& C, const double* b, double* x, double* r, double* d, double* w, int max_it,
-                              double rtol) {
-  for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) {
+// x = CG(A, b) from zero by one warp (same stopping rule as cg3).
+__device__ inline int cg_warp(const CoarseSys& S, const double* b, double* x, double* r, double* d, double* w,
+                              int max_it, double rtol) {
+  const int lane = threadIdx.x & 31, nv = S.nv;
+  double rr = 0.0;
+  for (int q = lane; q < nv; q += 32) {
     x[q] = 0.0;
     r[q] = b[q];
     d[q] = b[q];
-    w[q] = 0.0;
+    rr += b[q] * b[q];
   }
+  rr = warp_sum(rr);
   __syncwarp();
-  double rr = wdot(C, r, r);
   const double stop = rtol * rtol * rr;
   int it = 0;
   for (; it < max_it; ++it) {
     if (rr <= stop || rr == 0.0) break;
-    wapplyA(C, d, w);
-    const double dq = wdot(C, d, w);
+    double dq = 0.0;
+    for (int q = lane; q < nv; q += 32) {
+      const double aq = csr_row(S.aptr, S.acol, S.aval, q, d);
+      w[q] = aq;
+      dq += d[q] * aq;
+    }
+    dq = warp_sum(dq);
     if (dq == 0.0) break;
     const double alpha = rr / dq;
-    for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) {
+    double rn = 0.0;
+    for (int q = lane; q < nv; q += 32) {
       x[q] += alpha * d[q];
-      r[q] -= alpha * w[q];
+      const double rq = r[q] - alpha * w[q];
+      r[q] = rq;
+      rn += rq * rq;
     }
+    rn = warp_sum(rn);
+    const double beta = rn / rr;
+    // every lane has read d (the products above) before any lane rewrites it
     __syncwarp();
-    const double rr_new = wdot(C, r, r);
-    const double beta = rr_new / rr;
-    for (int64_t q = threadIdx.x & 31; q < C.L.nalloc; q += 32) d[q] = r[q] + beta * d[q];
+    for (int q = lane; q < nv; q += 32) d[q] = r[q] + beta * d[q];
     __syncwarp();
-    rr = rr_new;
+    rr = rn;
   }
   return it;
 }
 
+// Largest velocity block solved by one warp in the single-block solver.
+constexpr int WARP_CG_MAX_NV = 1024;
+
 // z = P^{-1} v: CG on each velocity block, lumped mass on the pressure.  On a
-// single block and a small level (at most 2048 padded entries) the three CG
-// solves run concurrently, warp w solving block w with warp-level
-// synchronisation only; otherwise the team runs them in lockstep (cg3).
-// cgf holds 9 scratch fields (3 per block).
-__device__ inline int precond(const Ctx& C, const V4& v, const V4& z, double* const* cgf, int cg_max,
-                              double cg_rtol) {
+// single block with small blocks the three CG solves run concurrently, warp
+// w solving block w with warp-level synchronisation only; otherwise the team
+// runs them in lockstep (cg3).  cg holds 9 nv scratch entries.
+__device__ inline int precond(const Ctx& C, const double* v, double* z, double* cg, int cg_max, double cg_rtol) {
   __shared__ int its_sh[3];
   int its = 0;
+  const int nv = C.S.nv;
   const int warp = threadIdx.x >> 5;
-  const bool par = C.T.nblocks == 1 && blockDim.x >= 96 && C.L.nalloc <= 2048;
+  const bool par = C.T.nblocks == 1 && blockDim.x >= 96 && nv <= WARP_CG_MAX_NV;
   if (par) {
     if (warp < 3) {
-      const int n = cg_warp(C, v.c[warp], z.c[warp], cgf[3 * warp], cgf[3 * warp + 1], cgf[3 * warp + 2], cg_max,
-                            cg_rtol);
+      const int n = cg_warp(C.S, v + warp * nv, z + warp * nv, cg + 3 * warp * nv, cg + (3 * warp + 1) * nv,
+                            cg + (3 * warp + 2) * nv, cg_max, cg_rtol);
       if ((threadIdx.x & 31) == 0) its_sh[warp] = n;
     }
   } else {
-    V4 vu = v, zu = z;
-    its = cg3(C, vu, zu, cgf, cg_max, cg_rtol);
+    its = cg3(C, v, z, cg, cg_max, cg_rtol);
   }
-  const LevelDev<double>& L = C.L;
-  for (int64_t q = C.T.rank(); q < C.n; q += C.T.size()) {
-    int i, j, k;
-    decode(L, q, i, j, k);
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    const uint8_t fl = L.flags[c];
-    z.c[3][c] = (fl & F_ACT) ? v.c[3][c] / lumped_mass(L, c, fl) : 0.0;
-  }
+  for (int q = (int)C.T.rank(); q < C.S.np; q += (int)C.T.size()) z[3 * nv + q] = v[3 * nv + q] / C.S.mass[q];
   C.T.sync();
   if (par) its = its_sh[0] + its_sh[1] + its_sh[2];
   C.T.sync();
   return its;
 }
 
-// (U, P) += PMINRES correction of the residual equation on level L; every
-// thread of the team must call it.  scratch: COARSE_FIELDS fields of L.
-__device__ inline void minres_team(const Team& T, const LevelDev<double>& L, double* scratch, const CoarseParams& prm,
-                                   double* info) {
-  Ctx C{L, T, (int64_t)L.nx * L.ny * L.nz};
-  const int64_t na = L.nalloc;
-  auto vec = [&](int first) {
-    V4 v;
-    for (int f = 0; f < 4; ++f) v.c[f] = scratch + (int64_t)(first + f) * na;
-    return v;
-  };
-  // 11 vectors of 4 fields + 1 CG field = 45 fields (of COARSE_FIELDS)
-  V4 b = vec(0), x = vec(4), Kz = vec(8);
-  V4 vv[3] = {vec(12), vec(16), vec(20)};  // v_prev, v, v_next (rotating)
-  V4 zz[2] = {vec(24), vec(28)};            // z, z_next
-  V4 ww[3] = {vec(32), vec(36), vec(40)};  // w_prev, w, w_next
-  double* cr = scratch + 44 * na;
-  // CG scratch: b and Kz are dead whenever the preconditioner runs
-  double* cgf[9] = {Kz.c[0], Kz.c[1], Kz.c[2], Kz.c[3], b.c[0], b.c[1], b.c[2], b.c[3], cr};
-  for (int64_t q = T.rank(); q < 44 * na; q += T.size()) scratch[q] = 0.0;
-  T.sync();
+// (U, P) += PMINRES correction of the residual equation (F, G) - K (U, P) on
+// the coarsest level L (fields of type T, the solve in FP64); every thread of
+// the team must call it.  scratch: coarse_scratch_doubles(S) entries.
+template <class T>
+__device__ inline void minres_team(const Team& tm, const CoarseSys& S, const LevelDev<T>& L, double* scratch,
+                                   const CoarseParams& prm, double* info) {
+  const int nv = S.nv, n = 3 * S.nv + S.np;
+  Ctx C{S, tm, n};
+  double* vec[11];
+  for (int f = 0; f < 11; ++f) vec[f] = scratch + (int64_t)f * n;
+  double* cg = scratch + (int64_t)11 * n;
+  double *b = vec[0], *x = vec[1], *Kz = vec[2];
+  double* vv[3] = {vec[3], vec[4], vec[5]};  // v_prev, v, v_next (rotating)
+  double* zz[2] = {vec[6], vec[7]};          // z, z_next
+  double* ww[3] = {vec[8], vec[9], vec[10]};  // w_prev, w, w_next
 
-  // b = (F, G) - K (U, P): the residual equation of the current iterate
-  V4 up;
-  up.c[0] = L.u[0];
-  up.c[1] = L.u[1];
-  up.c[2] = L.u[2];
-  up.c[3] = L.p;
-  applyK(C, up, Kz);
-  for (int64_t q = T.rank(); q < na; q += T.size()) {
-    const uint8_t fl = L.flags[q];
-    for (int d = 0; d < 3; ++d) b.c[d][q] = (fl & F_VFREE) ? L.f[d][q] - Kz.c[d][q] : 0.0;
-    b.c[3][q] = (fl & F_ACT) ? L.g[q] - Kz.c[3][q] : 0.0;
+  // gather (U, P) into Kz and (F, G) into b; zero x, v_prev, w_prev, w
+  for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) {
+    double up, fg;
+    if (q < 3 * nv) {
+      const int d = q / nv;
+      const int c = S.vidx[q - d * nv];
+      up = (double)L.u[d][c];
+      fg = (double)L.f[d][c];
+    } else {
+      const int c = S.pidx[q - 3 * nv];
+      up = (double)L.p[c];
+      fg = (double)L.g[c];
+    }
+    Kz[q] = up;
+    b[q] = fg;
+    x[q] = 0.0;
+    vv[0][q] = 0.0;
+    ww[0][q] = 0.0;
+    ww[1][q] = 0.0;
   }
-  T.sync();
+  tm.sync();
+  // b = (F, G) - K (U, P), v_1 = b
+  for (int r = (int)tm.rank(); r < n; r += (int)tm.size()) {
+    const double br = b[r] - csr_row(S.kptr, S.kcol, S.kval, r, Kz);
+    b[r] = br;
+    vv[1][r] = br;
+  }
+  tm.sync();
 
   int iv_prev = 0, iv = 1, iv_next = 2, iz = 0, iz_next = 1, iw_prev = 0, iw = 1, iw_next = 2;
-  // v_1 = b, z_1 = P^{-1} v_1
-  for (int f = 0; f < 4; ++f)
-    for (int64_t q = T.rank(); q < na; q += T.size()) vv[iv].c[f][q] = b.c[f][q];
-  T.sync();
-  int cg_total = precond(C, vv[iv], zz[iz], cgf, prm.cg_max, prm.cg_rtol);
-  double gamma = sqrt(fmax(dot4(C, zz[iz], vv[iv]), 0.0));
+  int cg_total = precond(C, vv[iv], zz[iz], cg, prm.cg_max, prm.cg_rtol);
+  double gamma = sqrt(fmax(dot(C, zz[iz], vv[iv]), 0.0));
   int its = 0;
   double rel = 0.0;
   if (gamma > 0.0) {
@@ -301,18 +263,16 @@ __device__ inline void minres_team(const Team& T, const LevelDev<double>& L, dou
     double gamma_prev = 1.0, eta = gamma;
     double c_prev = 1.0, cc = 1.0, s_prev = 0.0, ss = 0.0;
     for (; its < prm.minres_max;) {
-      for (int f = 0; f < 4; ++f)
-        for (int64_t q = T.rank(); q < na; q += T.size()) zz[iz].c[f][q] /= gamma;
-      T.sync();
+      for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) zz[iz][q] /= gamma;
+      tm.sync();
       applyK(C, zz[iz], Kz);
-      const double delta = dot4(C, Kz, zz[iz]);
+      const double delta = dot(C, Kz, zz[iz]);
       const double r1 = delta / gamma, r2 = gamma / gamma_prev;
-      for (int f = 0; f < 4; ++f)
-        for (int64_t q = T.rank(); q < na; q += T.size())
-          vv[iv_next].c[f][q] = Kz.c[f][q] - r1 * vv[iv].c[f][q] - r2 * vv[iv_prev].c[f][q];
-      T.sync();
-      cg_total += precond(C, vv[iv_next], zz[iz_next], cgf, prm.cg_max, prm.cg_rtol);
-      const double gamma_next = sqrt(fmax(dot4(C, zz[iz_next], vv[iv_next]), 0.0));
+      for (int q = (int)tm.rank(); q < n; q += (int)tm.size())
+        vv[iv_next][q] = Kz[q] - r1 * vv[iv][q] - r2 * vv[iv_prev][q];
+      tm.sync();
+      cg_total += precond(C, vv[iv_next], zz[iz_next], cg, prm.cg_max, prm.cg_rtol);
+      const double gamma_next = sqrt(fmax(dot(C, zz[iz_next], vv[iv_next]), 0.0));
       const double a0 = cc * delta - c_prev * ss * gamma;
       const double a1 = sqrt(a0 * a0 + gamma_next * gamma_next);
       const double a2 = ss * delta + c_prev * cc * gamma;
@@ -320,13 +280,12 @@ __device__ inline void minres_team(const Team& T, const LevelDev<double>& L, dou
       if (a1 == 0.0) break;
       const double c_next = a0 / a1, s_next = gamma_next / a1;
       const double step = c_next * eta;
-      for (int f = 0; f < 4; ++f)
-        for (int64_t q = T.rank(); q < na; q += T.size()) {
-          const double wn = (zz[iz].c[f][q] - a3 * ww[iw_prev].c[f][q] - a2 * ww[iw].c[f][q]) / a1;
-          ww[iw_next].c[f][q] = wn;
-          x.c[f][q] += step * wn;
-        }
-      T.sync();
+      for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) {
+        const double wn = (zz[iz][q] - a3 * ww[iw_prev][q] - a2 * ww[iw][q]) / a1;
+        ww[iw_next][q] = wn;
+        x[q] += step * wn;
+      }
+      tm.sync();
       eta = -s_next * eta;
       ++its;
       // shift the recurrences
@@ -352,17 +311,22 @@ __device__ inline void minres_team(const Team& T, const LevelDev<double>& L, dou
     }
   }
   // (U, P) += x
-  for (int64_t q = T.rank(); q < na; q += T.size()) {
-    L.u[0][q] += x.c[0][q];
-    L.u[1][q] += x.c[1][q];
-    L.u[2][q] += x.c[2][q];
-    L.p[q] += x.c[3][q];
+  for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) {
+    if (q < 3 * nv) {
+      const int d = q / nv;
+      const int c = S.vidx[q - d * nv];
+      L.u[d][c] = (T)((double)L.u[d][c] + x[q]);
+    } else {
+      const int c = S.pidx[q - 3 * nv];
+      L.p[c] = (T)((double)L.p[c] + x[q]);
+    }
   }
-  if (T.rank() == 0 && info) {
+  if (tm.rank() == 0 && info) {
     info[0] = (double)its;
     info[1] = rel;
     info[2] = (double)cg_total;
-  }}
+  }
+}
 
 }  // namespace coarse
 }  // namespace hhg

@@ -1,0 +1,148 @@
+// Host assembly of the coarsest-level saddle-point matrix in CSR (Sec. 3.7
+// coarse solver; rows of Sec. 2 on the Kuhn lattice).  Full-star nodes take
+// the closed-form rows the stencil kernels apply: the 7-point Laplacian
+// (6 at the centre, -1 on the six axis neighbours) and B_d = h^2/12 times
+// the antisymmetric difference weights along the seven Kuhn directions;
+// boundary nodes take their class rows.
+#include <limits>
+
+#include "../../include/hhg_stokes.h"
+#include "hhg_lattice.h"
+
+namespace hhg {
+
+namespace {
+
+// 12 * (B_d row) on the "+o" neighbour along direction q of
+// (e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3); the "-o" neighbour takes the
+// opposite sign and the centre weight is zero.
+const double DIV12[3][7] = {{-3, 1, 1, -1, 1, -1, -1}, {1, -3, 1, -1, -1, 1, -1}, {1, 1, -3, 1, -1, -1, -1}};
+
+struct Rows {
+  double lap[15], b[3][15], bt[3][15], lump;
+};
+
+Rows rows_of(uint16_t cls, const double* table) {
+  Rows r{};
+  if (cls == 0) {
+    r.lap[0] = 6.0;
+    for (int o : {1, 2, 3, 8, 9, 10}) r.lap[o] = -1.0;
+    for (int d = 0; d < 3; ++d)
+      for (int q = 0; q < 7; ++q) {
+        r.b[d][1 + q] = DIV12[d][q] / 12.0;
+        r.b[d][8 + q] = -DIV12[d][q] / 12.0;
+        r.bt[d][1 + q] = -DIV12[d][q] / 12.0;
+        r.bt[d][8 + q] = DIV12[d][q] / 12.0;
+      }
+    r.lump = 1.0;
+    return r;
+  }
+  const double* w = table + (size_t)cls * W_STRIDE;
+  for (int o = 0; o < 15; ++o) {
+    r.lap[o] = w[W_LAP + o];
+    for (int d = 0; d < 3; ++d) {
+      r.b[d][o] = w[W_B + 15 * d + o];
+      r.bt[d][o] = w[W_BT + 15 * d + o];
+    }
+  }
+  r.lump = w[W_LUMP];
+  return r;
+}
+
+}  // namespace
+
+int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t* flags, const uint16_t* cls,
+                    const double* table, double nuh, double c, double h2, double h3, CoarseMatrix& out,
+                    std::string& err) {
+  out = CoarseMatrix{};
+  const int64_t n = sh.n();
+  const int64_t nalloc = pxy * (sh.nz + 2);
+  if (nalloc > std::numeric_limits<int32_t>::max() / 2) {
+    err = "coarsest level too large for the assembled coarse solver";
+    return HHG_EINVAL;
+  }
+  std::vector<int32_t> iv(nalloc, -1), ip(nalloc, -1);
+  std::vector<int64_t> lat_of(nalloc, -1);
+  for (int k = 0; k < sh.nz; ++k)
+    for (int j = 0; j < sh.ny; ++j)
+      for (int i = 0; i < sh.nx; ++i) {
+        const int64_t q = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
+        const int64_t pc = (i + 1) + px * (j + 1) + pxy * (k + 1);
+        lat_of[pc] = q;
+        if (flags[q] & F_VFREE) {
+          iv[pc] = out.nv++;
+          out.vidx.push_back((int32_t)pc);
+        }
+        if (flags[q] & F_ACT) {
+          ip[pc] = out.np++;
+          out.pidx.push_back((int32_t)pc);
+        }
+      }
+  (void)n;
+  int64_t off[15];
+  for (int o = 0; o < 15; ++o)
+    off[o] = STENCIL_OFFSETS[o][0] + px * STENCIL_OFFSETS[o][1] + pxy * STENCIL_OFFSETS[o][2];
+  const int32_t nv = out.nv, np = out.np;
+  int64_t nnz = 0;
+  auto push = [&](std::vector<int32_t>& col, std::vector<double>& val, int64_t j, double v) {
+    if (v == 0.0) return;
+    col.push_back((int32_t)j);
+    val.push_back(v);
+    ++nnz;
+  };
+  // velocity rows, component by component
+  out.kptr.push_back(0);
+  for (int d = 0; d < 3; ++d)
+    for (int32_t r = 0; r < nv; ++r) {
+      const int64_t pc = out.vidx[r];
+      const Rows w = rows_of(cls[lat_of[pc]], table);
+      for (int o = 0; o < 15; ++o) {
+        const int64_t nb = pc + off[o];
+        if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], nuh * w.lap[o]);
+      }
+      for (int o = 0; o < 15; ++o) {
+        const int64_t nb = pc + off[o];
+        if (ip[nb] >= 0) push(out.kcol, out.kval, 3 * (int64_t)nv + ip[nb], h2 * w.bt[d][o]);
+      }
+      if (nnz > std::numeric_limits<int32_t>::max() / 2) {
+        err = "coarsest level too large for the assembled coarse solver";
+        return HHG_EINVAL;
+      }
+      out.kptr.push_back((int32_t)nnz);
+    }
+  // pressure rows: B u - C p
+  for (int32_t r = 0; r < np; ++r) {
+    const int64_t pc = out.pidx[r];
+    const Rows w = rows_of(cls[lat_of[pc]], table);
+    for (int d = 0; d < 3; ++d)
+      for (int o = 0; o < 15; ++o) {
+        const int64_t nb = pc + off[o];
+        if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], h2 * w.b[d][o]);
+      }
+    for (int o = 0; o < 15; ++o) {
+      const int64_t nb = pc + off[o];
+      if (ip[nb] >= 0) push(out.kcol, out.kval, 3 * (int64_t)nv + ip[nb], -c * w.lap[o]);
+    }
+    if (nnz > std::numeric_limits<int32_t>::max() / 2) {
+      err = "coarsest level too large for the assembled coarse solver";
+      return HHG_EINVAL;
+    }
+    out.kptr.push_back((int32_t)nnz);
+    out.mass.push_back(h3 * w.lump);
+  }
+  // scalar A
+  nnz = 0;
+  out.aptr.push_back(0);
+  for (int32_t r = 0; r < nv; ++r) {
+    const int64_t pc = out.vidx[r];
+    const Rows w = rows_of(cls[lat_of[pc]], table);
+    for (int o = 0; o < 15; ++o) {
+      const int64_t nb = pc + off[o];
+      if (iv[nb] >= 0) push(out.acol, out.aval, iv[nb], nuh * w.lap[o]);
+    }
+    out.aptr.push_back((int32_t)nnz);
+  }
+  return HHG_OK;
+}
+
+}  // namespace hhg

@@ -356,30 +356,6 @@ __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
   }
 }
 
-__global__ void k_coarse_in(LevelDev<float> S, LevelDev<double> D) {
-  pdl_enter();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D.nalloc; q += stride) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      D.f[d][q] = (double)S.f[d][q];
-      D.u[d][q] = (double)S.u[d][q];
-    }
-    D.g[q] = (double)S.g[q];
-    D.p[q] = (double)S.p[q];
-  }
-}
-
-__global__ void k_coarse_out(LevelDev<float> S, LevelDev<double> D) {
-  pdl_enter();
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < D.nalloc; q += stride) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) S.u[d][q] = (float)D.u[d][q];
-    S.p[q] = (float)D.p[q];
-  }
-}
-
 // ---- layout conversion ---------------------------------------------------------------------
 
 __global__ void k_scatter(LevelDev<double> L, const double* src, int ncomp, double* d0, double* d1, double* d2,
@@ -540,12 +516,6 @@ void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, dou
 }
 void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
   launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e);
-}
-void launch_coarse_in(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s) {
-  launch_k(k_coarse_in, flat_blocks(l64.nalloc), 256, s, l32, l64);
-}
-void launch_coarse_out(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s) {
-  launch_k(k_coarse_out, flat_blocks(l64.nalloc), 256, s, l32, l64);
 }
 void launch_scatter(const LevelDev<double>& L, const double* src, int ncomp, double* const* dst, uint8_t mask,
                     cudaStream_t s) {

@@ -53,9 +53,6 @@ void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStr
 void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
                         cudaStream_t s);
 void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s);
-// Coarsest level of the FP32 hierarchy through the FP64 coarse solver.
-void launch_coarse_in(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s);
-void launch_coarse_out(const LevelDev<float>& l32, const LevelDev<double>& l64, cudaStream_t s);
 
 // Layout conversion between contiguous (n, 3)/(n,) arrays and padded fields.
 // mask: nodes whose value is kept (others get 0); 0 = keep all.
@@ -73,29 +70,52 @@ void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s)
 void launch_scale(double* x, int64_t n, double a, cudaStream_t s);
 
 // Coarse-grid solver (hhg_coarse.cu): (U, P) += PMINRES correction of the
-// residual equation, FP64, one thread block.  scratch: COARSE_VECTORS fields.
-constexpr int COARSE_FIELDS = 48;
+// residual equation, FP64 on the compact unknowns of the coarsest level.
+// CoarseSys is the device view of the assembled CoarseMatrix (hhg_lattice.h).
+struct CoarseSys {
+  int32_t nv, np;         // velocity unknowns per component, pressure unknowns
+  const int32_t* vidx;    // padded lattice index of each velocity unknown's node
+  const int32_t* pidx;    // padded lattice index of each pressure unknown's node
+  const int32_t* kptr;    // K in CSR, 3 nv + np rows
+  const int32_t* kcol;
+  const double* kval;
+  const int32_t* aptr;    // scalar A in CSR, nv rows
+  const int32_t* acol;
+  const double* aval;
+  const double* mass;     // lumped mass of each pressure unknown
+};
 struct CoarseParams {
   int minres_max;
   double minres_rtol;
   int cg_max;
   double cg_rtol;
 };
-void launch_coarse_solve(const LevelDev<double>& L, double* scratch, CoarseParams prm, double* info, cudaStream_t s);
+// Scratch doubles of one coarse solve: 11 vectors of 3 nv + np entries and 9 nv.
+__host__ __device__ inline int64_t coarse_scratch_doubles(const CoarseSys& S) {
+  return 11 * (3 * (int64_t)S.nv + S.np) + 9 * (int64_t)S.nv;
+}
+// A coarsest level this small is solved by one thread block (one warp per CG).
+constexpr int64_t COARSE_BLOCK_MAX_UNKNOWNS = 4096;
+__host__ __device__ inline bool coarse_fits_block(const CoarseSys& S) {
+  return 3 * (int64_t)S.nv + S.np <= COARSE_BLOCK_MAX_UNKNOWNS;
+}
+template <class T>
+void launch_coarse_solve(const CoarseSys& S, const LevelDev<T>& L, double* scratch, CoarseParams prm, double* info,
+                         cudaStream_t s);
 // Cluster set-up of the coarse solve (call once per device before launches).
 void prepare_coarse_solve();
 
 // Same solve with its scratch in a file-scope device array (no allocation).
-// Fails with HHG_EINVAL when COARSE_FIELDS * L.nalloc exceeds the array.
+// Fails with HHG_EINVAL when coarse_scratch_doubles(S) exceeds the array.
 constexpr int64_t NOALLOC_COARSE_DOUBLES = 1 << 18;
 constexpr int NOALLOC_MAX_DEVICES = 64;
-int coarse_solve_noalloc(const LevelDev<double>& L, CoarseParams prm, double* info, cudaStream_t s,
-                         std::string& err);
+int coarse_solve_noalloc(const CoarseSys& S, const LevelDev<double>& L, CoarseParams prm, double* info,
+                         cudaStream_t s, std::string& err);
 
 // Fused cycle of the coarse levels (hhg_small.cu): levels lv[0] (coarsest)
 // .. lv[nlev-1] of one hierarchy run by one cluster of nblocks CTAs,
-// smoothing counts per level, FP64 view of the coarsest level for the coarse
-// solve, its scratch and parameters.
+// smoothing counts per level, the compact system of the coarsest level for
+// the coarse solve, its scratch and parameters.
 constexpr int SMALL_MAX_LEVELS = 8;
 // Defaults, measured on GB300 with whole level-7 cube solves: fusing only the
 // levels of at most 1024 nodes into one block is fastest in both precisions.
@@ -115,7 +135,7 @@ struct SmallCycle {
   int nu_post[SMALL_MAX_LEVELS];
   T inv6nuh[SMALL_MAX_LEVELS];
   T omc[SMALL_MAX_LEVELS];
-  LevelDev<double> c64;
+  CoarseSys cs;
   double* scratch;
   CoarseParams prm;
   double* info;

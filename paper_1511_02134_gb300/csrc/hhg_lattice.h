@@ -67,3 +67,33 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
                      std::vector<double>& table, int& n_classes, std::string& err);
 
 }  // namespace hhg
+
+namespace hhg {
+
+// Compact form of the coarsest level for the coarse solver (Sec. 3.7).  The
+// unknowns are numbered component by component over the free velocity nodes
+// (lattice order), then over the active pressure nodes (lattice order):
+// x = (u_0, u_1, u_2, p), 3 nv + np entries.  K is the saddle-point matrix
+// [A 0 0 B_0^T; 0 A 0 B_1^T; 0 0 A B_2^T; B_0 B_1 B_2 -C] and A the scalar
+// vector-Laplacian block, both in CSR with the rows of the stencil kernels:
+// the class tables for boundary nodes, the closed forms for full-star nodes,
+// the same scale factors (A = nu h *, B = h^2 *, C = delta h_T^2 h *).
+// Zero weights are not stored.
+struct CoarseMatrix {
+  int32_t nv = 0, np = 0;
+  std::vector<int32_t> vidx, pidx;  // padded lattice index of each velocity / pressure unknown
+  std::vector<int32_t> kptr, kcol;
+  std::vector<double> kval;
+  std::vector<int32_t> aptr, acol;
+  std::vector<double> aval;
+  std::vector<double> mass;  // lumped mass of each pressure unknown
+};
+
+// flags and cls in lattice order (x fastest); table as from stencil_classes;
+// px, pxy the padded strides of the level's fields (ghost frame of one node).
+// Returns 0, or HHG_EINVAL when the matrix would not fit 32-bit indices.
+int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t* flags, const uint16_t* cls,
+                    const double* table, double nuh, double c, double h2, double h3, CoarseMatrix& out,
+                    std::string& err);
+
+}  // namespace hhg

@@ -106,31 +106,16 @@ __device__ void b_prolong(const Team& tm, const LevelDev<T>& Lf, const LevelDev<
   tm.sync();
 }
 
-// Coarsest level: FP64 solve; an FP32 hierarchy goes through its FP64 copy.
-__device__ void b_coarse(const Team& tm, const SmallCycle<double>& S) {
-  coarse::minres_team(tm, S.lv[0], S.scratch, S.prm, S.info);
-  tm.sync();
-}
-
-__device__ void b_coarse(const Team& tm, const SmallCycle<float>& S) {
-  const LevelDev<float>& L = S.lv[0];
-  const LevelDev<double>& D = S.c64;
-  for (int64_t q = tm.rank(); q < D.nalloc; q += tm.size()) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      D.f[d][q] = (double)L.f[d][q];
-      D.u[d][q] = (double)L.u[d][q];
-    }
-    D.g[q] = (double)L.g[q];
-    D.p[q] = (double)L.p[q];
-  }
-  tm.sync();
-  coarse::minres_team(tm, D, S.scratch, S.prm, S.info);
-  tm.sync();
-  for (int64_t q = tm.rank(); q < D.nalloc; q += tm.size()) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) L.u[d][q] = (float)D.u[d][q];
-    L.p[q] = (float)D.p[q];
+// Coarsest level: the FP64 coarse solve on the compact unknowns, reading and
+// updating the level's fields in their own precision.  A coarse system that
+// fits one block runs on the first CTA alone: its sums then need no cluster
+// barrier and its three CG solves run on one warp each.
+template <class T>
+__device__ void b_coarse(const Team& tm, const SmallCycle<T>& S) {
+  if (tm.nblocks > 1 && coarse_fits_block(S.cs)) {
+    if (blockIdx.x == 0) coarse::minres_team(Team{1}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
+  } else {
+    coarse::minres_team(tm, S.cs, S.lv[0], S.scratch, S.prm, S.info);
   }
   tm.sync();
 }

@@ -357,13 +357,20 @@ def test_adjoint_gradient_matches_oracle(pkg):
     assert np.array_equal(u1, u2)
 
 
+FUSED = {"block": dict(fuse_coarse_levels=1),
+         "cluster16": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=16),
+         "cluster4": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=4)}
+
+
+@pytest.mark.parametrize("fused", sorted(FUSED))
 @pytest.mark.parametrize("name,level,coarsest", [("cube", 5, 2), ("cube", 3, 2), ("channel", 2, 0), ("partial", 3, 1)])
-def test_fused_coarse_levels_match_per_level_kernels(pkg, name, level, coarsest):
-    """The single-block fused cycle of the coarse levels does the same
-    arithmetic as the per-level kernels (FP64 and FP32 hierarchies)."""
+def test_fused_coarse_levels_match_per_level_kernels(pkg, name, level, coarsest, fused):
+    """The fused cycle of the coarse levels (one block, or a thread-block
+    cluster) does the same arithmetic as the per-level kernels (FP64 and
+    FP32 hierarchies)."""
     macro = macro_by_name(name)
     meshes = [pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=coarsest,
-                       coarse_minres_max=30, fuse_coarse_levels=f) for f in (1, 0)]
+                       coarse_minres_max=30, **o) for o in (FUSED[fused], dict(fuse_coarse_levels=0))]
     H = MG.build_hierarchy(macro, level, coarsest=coarsest)
     st = _random_state(H, level, 21)
     for prec in (0, 1):

@@ -68,8 +68,8 @@ def test_noalloc_matches_coarse_solve(pkg, name, finest, coarsest, mx):
 
 def test_noalloc_rejects_large_coarse_level(pkg):
     cube = W.unit_cube()
-    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 4, coarsest_level=4)
-    n = mesh.num_nodes(4)
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, coarsest_level=5)
+    n = mesh.num_nodes(5)
     with pytest.raises(pkg.HHGError) as e:
         mesh.coarse_solve_noalloc(np.zeros((n, 3)), np.zeros(n), np.zeros((n, 3)), np.zeros(n))
     assert e.value.code == -1 and "scratch" in str(e.value)
