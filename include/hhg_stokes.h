@@ -89,7 +89,10 @@ typedef struct hhg_options {
   int32_t fuse_max_nodes;    /* largest level (lattice nodes) of the fused kernel; 0 = default (1024) */
   int32_t team_blocks;       /* CTAs of the fused kernel's thread-block cluster (1 = one block,
                                 at most 16); 0 = default (1) */
-  int32_t reserved[4];
+  int32_t tile_min_nodes;    /* levels of at least this many lattice nodes run the colour sweeps
+                                on shared-memory tiles staged by tensor copies; 0 = default
+                                (never), -1 = never */
+  int32_t reserved[3];
 } hhg_options;
 
 /* Per-solve statistics. */

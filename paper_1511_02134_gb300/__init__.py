@@ -47,7 +47,8 @@ class Options(ctypes.Structure):
                 ("coarse_minres_rtol", ctypes.c_double), ("coarse_cg_max", ctypes.c_int32),
                 ("coarse_cg_rtol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("fuse_coarse_levels", ctypes.c_int32), ("fuse_max_nodes", ctypes.c_int32),
-                ("team_blocks", ctypes.c_int32), ("reserved", ctypes.c_int32 * 4)]
+                ("team_blocks", ctypes.c_int32), ("tile_min_nodes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
 
 
 class _Stats(ctypes.Structure):

@@ -32,6 +32,9 @@ struct LevelHost {
   float* d_wt32 = nullptr;
   int n_classes = 0;
   int64_t n_vel = 0, n_pres = 0;
+  bool tiled = false;  // colour sweeps on shared-memory tiles
+  int kz = 4;          // planes per CTA of the tiled sweeps
+  TileMaps tm64{}, tm32{};
   double* mem64 = nullptr;
   float* mem32 = nullptr;
   LevelDev<double> d64{};
@@ -148,6 +151,7 @@ int ensure32(hhg_mesh* M) {
     if (rc) return rc;
     CK(cudaMemsetAsync(H.mem32, 0, sizeof(float) * 12 * (size_t)H.nalloc, M->stream));
     bind_fields(H.d32, H.mem32, H.nalloc);
+    if (H.tiled && (rc = make_tile_maps<float>(H.d32, H.tm32, M->err))) return rc;
   }
   return HHG_OK;
 }
@@ -162,8 +166,23 @@ template <>
 LevelDev<float>& view<float>(hhg_mesh* M, int l) { return M->lv[l].d32; }
 
 template <class T>
+const TileMaps& maps(hhg_mesh* M, int l);
+template <>
+const TileMaps& maps<double>(hhg_mesh* M, int l) { return M->lv[l].tm64; }
+template <>
+const TileMaps& maps<float>(hhg_mesh* M, int l) { return M->lv[l].tm32; }
+
+// Error word of the tiled kernels (the last slot of the scalar block).
+unsigned* err_word(hhg_mesh* M) { return reinterpret_cast<unsigned*>(M->d_scalars + 15); }
+
+template <class T>
 void enq_vel_sweep(hhg_mesh* M, int l, bool forward) {
-  for (int q = 0; q < 4; ++q) launch_vel_colour<T>(view<T>(M, l), forward ? q : 3 - q, M->stream);
+  for (int q = 0; q < 4; ++q) {
+    const int colour = forward ? q : 3 - q;
+    M->lv[l].tiled
+        ? launch_vel_colour_ru_tile<T>(maps<T>(M, l), view<T>(M, l), colour, M->lv[l].kz, err_word(M), M->stream)
+        : launch_vel_colour<T>(view<T>(M, l), colour, M->stream);
+  }
   M->launches += 4;
 }
 
@@ -183,17 +202,28 @@ void enq_pres_sweep(hhg_mesh* M, int l) {
 template <class T>
 void enq_uzawa(hhg_mesh* M, int l) {
   const LevelDev<T>& L = view<T>(M, l);
+  const bool tiled = M->lv[l].tiled;
+  const TileMaps& tm = maps<T>(M, l);
+  const int kz = M->lv[l].kz;
+  unsigned* err = err_word(M);
   if (sizeof(T) == 4) {
-    for (int q = 0; q < 4; ++q) launch_vel_colour_rhs<T>(L, q, M->stream);
-    for (int q = 2; q >= 0; --q) launch_vel_colour_rhs<T>(L, q, M->stream);
+    for (int q = 0; q < 7; ++q) {
+      const int colour = q < 4 ? q : 6 - q;
+      tiled ? launch_vel_colour_tile<T>(tm, L, colour, kz, err, M->stream)
+            : launch_vel_colour_rhs<T>(L, colour, M->stream);
+    }
     M->launches += 7;
   } else {
     launch_vel_rhs<T>(L, M->stream);
-    for (int q = 0; q < 4; ++q) launch_vel_colour<T>(L, q, M->stream);
-    for (int q = 2; q >= 0; --q) launch_vel_colour<T>(L, q, M->stream);
+    for (int q = 0; q < 7; ++q) {
+      const int colour = q < 4 ? q : 6 - q;
+      tiled ? launch_vel_colour_ru_tile<T>(tm, L, colour, kz, err, M->stream)
+            : launch_vel_colour<T>(L, colour, M->stream);
+    }
     M->launches += 8;
   }
-  for (int q = 0; q < 4; ++q) launch_pres_colour_rhs<T>(L, q, M->stream);
+  for (int q = 0; q < 4; ++q)
+    tiled ? launch_pres_colour_tile<T>(tm, L, q, kz, err, M->stream) : launch_pres_colour_rhs<T>(L, q, M->stream);
   M->launches += 4;
 }
 
@@ -285,6 +315,14 @@ void enq_cycle32(hhg_mesh* M) {
   M->launches += 2;
 }
 
+// Reads the error word copied with the scalar block: a tiled sweep whose
+// tensor copy did not complete in time leaves HHG_TILE_TIMEOUT there.
+int tile_status(hhg_mesh* M) {
+  const unsigned w = *reinterpret_cast<const unsigned*>(M->h_scalars + 15);
+  if (w == HHG_TILE_TIMEOUT) return fail(M, HHG_ECUDA, "a tiled colour sweep gave up waiting for its tensor copies");
+  return HHG_OK;
+}
+
 int run_cycle(hhg_mesh* M, int mode, double* norm2) {
   if (M->opt.use_graphs) {
     if (!M->graph[mode]) {
@@ -312,10 +350,10 @@ int run_cycle(hhg_mesh* M, int mode, double* norm2) {
       enq_cycle32(M);
     CK(cudaGetLastError());
   }
-  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
   CK(cudaStreamSynchronize(M->stream));
   *norm2 = M->h_scalars[0];
-  return HHG_OK;
+  return tile_status(M);
 }
 
 int residual_norm2(hhg_mesh* M, int mode, double* norm2) {
@@ -329,10 +367,10 @@ int residual_norm2(hhg_mesh* M, int mode, double* norm2) {
     M->launches += 2;
   }
   CK(cudaGetLastError());
-  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double), cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
   CK(cudaStreamSynchronize(M->stream));
   *norm2 = M->h_scalars[0];
-  return HHG_OK;
+  return tile_status(M);
 }
 
 int check_level(hhg_mesh* M, int level) {
@@ -699,6 +737,16 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   }
   if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * (size_t)std::max<int64_t>(1, coarse_scratch_doubles(M->coarse_sys)))))
     return bail(rc);
+  // colour sweeps on shared-memory tiles on the large levels
+  prepare_tiled();
+  for (int l = M->coarsest; l <= finest; ++l) {
+    LevelHost& H = M->lv[l];
+    const int64_t lim = o.tile_min_nodes != 0 ? o.tile_min_nodes : TILE_MIN_NODES;
+    H.tiled = lim > 0 && H.sh.n() >= lim;
+    // long runs of planes where the level streams from HBM, short ones (more CTAs) below
+    H.kz = H.sh.n() >= (int64_t)1 << 24 ? 16 : 4;
+    if (H.tiled && (rc = make_tile_maps<double>(H.d64, H.tm64, M->err))) return bail(rc);
+  }
   // cluster kernels (fused coarse levels, coarse solve)
   prepare_coarse_solve();
   {
@@ -1109,8 +1157,9 @@ int hhg_level_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int3
     if ((rc = enqueue_op(M, level, precision, op))) return rc;
     CK(cudaGetLastError());
   }
+  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
   CK(cudaStreamSynchronize(M->stream));
-  return HHG_OK;
+  return tile_status(M);
 }
 
 int hhg_time_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32_t reps, double* ms) {
@@ -1135,7 +1184,8 @@ int hhg_time_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(M, e, "time_op");
   *ms = (double)t / reps;
-  return HHG_OK;
+  CK(cudaMemcpy(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost));
+  return tile_status(M);
 }
 
 int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count) {

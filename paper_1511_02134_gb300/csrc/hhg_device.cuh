@@ -65,11 +65,37 @@ __device__ __forceinline__ int64_t pidx(int64_t px, int64_t pxy, int i, int j, i
   return (int64_t)(i + 1) + px * (j + 1) + pxy * (k + 1);
 }
 
-// The row helpers read fields that fused kernels also write in earlier
-// phases of the same launch, so they use plain (coherent) loads.
+// ---- neighbour views -----------------------------------------------------------
+// V(dx, dy, dz) is a field's value at the node offset by (dx, dy, dz) from the
+// node the view is centred on.  The stencil arithmetic below is written once
+// over views, so kernels that read the padded arrays in global memory and
+// kernels that read a shared-memory tile do the same operations in the same
+// order.
+//
+// GNb: padded array in global memory.  The row helpers read fields that fused
+// kernels also write in earlier phases of the same launch, so they use plain
+// (coherent) loads.
+template <class T>
+struct GNb {
+  const T* x;
+  int64_t c, px, pxy;
+  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const { return x[c + dx + px * dy + pxy * dz]; }
+};
+
+template <class T>
+__device__ __forceinline__ GNb<T> gnb(const T* x, int64_t c, int64_t px, int64_t pxy) {
+  return GNb<T>{x, c, px, pxy};
+}
+
+// Sum of the six axis neighbours.
+template <class V>
+__device__ __forceinline__ auto nb6v(const V& x) {
+  return ((x(-1, 0, 0) + x(1, 0, 0)) + (x(0, -1, 0) + x(0, 1, 0))) + (x(0, 0, -1) + x(0, 0, 1));
+}
+
 template <class T>
 __device__ __forceinline__ T nb6(const T* x, int64_t c, int64_t px, int64_t pxy) {
-  return ((x[c - 1] + x[c + 1]) + (x[c - px] + x[c + px])) + (x[c - pxy] + x[c + pxy]);
+  return nb6v(gnb(x, c, px, pxy));
 }
 
 // Antisymmetric differences x(c+o) - x(c-o) over the 7 Kuhn directions.
@@ -78,17 +104,22 @@ struct Diff7 {
   T e1, e2, e3, f12, f23, f13, b;
 };
 
+template <class T, class V>
+__device__ __forceinline__ Diff7<T> diff7v(const V& x) {
+  Diff7<T> d;
+  d.e1 = x(1, 0, 0) - x(-1, 0, 0);
+  d.e2 = x(0, 1, 0) - x(0, -1, 0);
+  d.e3 = x(0, 0, 1) - x(0, 0, -1);
+  d.f12 = x(1, 1, 0) - x(-1, -1, 0);
+  d.f23 = x(0, 1, 1) - x(0, -1, -1);
+  d.f13 = x(1, 0, 1) - x(-1, 0, -1);
+  d.b = x(1, 1, 1) - x(-1, -1, -1);
+  return d;
+}
+
 template <class T>
 __device__ __forceinline__ Diff7<T> diff7(const T* x, int64_t c, int64_t px, int64_t pxy) {
-  Diff7<T> d;
-  d.e1 = x[c + 1] - x[c - 1];
-  d.e2 = x[c + px] - x[c - px];
-  d.e3 = x[c + pxy] - x[c - pxy];
-  d.f12 = x[c + 1 + px] - x[c - 1 - px];
-  d.f23 = x[c + px + pxy] - x[c - px - pxy];
-  d.f13 = x[c + 1 + pxy] - x[c - 1 - pxy];
-  d.b = x[c + 1 + px + pxy] - x[c - 1 - px - pxy];
-  return d;
+  return diff7v<T>(gnb(x, c, px, pxy));
 }
 
 // 12 * Div_d from the differences.
@@ -113,21 +144,30 @@ __device__ __forceinline__ T div12(const Diff7<T>& d, int comp) {
 // [W_B+15d,+15) B_d row, [W_BT+15d,+15) B_d^T row, [W_M,+15) mass row,
 // [W_LUMP] lumped mass.  Offsets: 0 centre, 1..7 = +o, 8..14 = -o over the
 // Kuhn directions e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3.
-struct Off15 {
-  int64_t o[15];
-};
 
-__device__ __forceinline__ Off15 offsets15(int64_t px, int64_t pxy) {
-  const int64_t a = 1, b = px, e = pxy;
-  return Off15{{0, a, b, e, a + b, b + e, a + e, a + b + e, -a, -b, -e, -(a + b), -(b + e), -(a + e), -(a + b + e)}};
+// Off-centre part sum_{o=1..14} w[o] x(c+o), in offset order.
+template <class T, class V>
+__device__ __forceinline__ T st14v(const V& x, const T* w, T acc) {
+  acc += w[1] * x(1, 0, 0);
+  acc += w[2] * x(0, 1, 0);
+  acc += w[3] * x(0, 0, 1);
+  acc += w[4] * x(1, 1, 0);
+  acc += w[5] * x(0, 1, 1);
+  acc += w[6] * x(1, 0, 1);
+  acc += w[7] * x(1, 1, 1);
+  acc += w[8] * x(-1, 0, 0);
+  acc += w[9] * x(0, -1, 0);
+  acc += w[10] * x(0, 0, -1);
+  acc += w[11] * x(-1, -1, 0);
+  acc += w[12] * x(0, -1, -1);
+  acc += w[13] * x(-1, 0, -1);
+  acc += w[14] * x(-1, -1, -1);
+  return acc;
 }
 
-template <class T>
-__device__ __forceinline__ T st15(const T* x, int64_t c, const Off15& off, const T* w) {
-  T acc = w[0] * x[c];
-#pragma unroll
-  for (int o = 1; o < 15; ++o) acc += w[o] * x[c + off.o[o]];
-  return acc;
+template <class T, class V>
+__device__ __forceinline__ T st15v(const V& x, const T* w) {
+  return st14v<T>(x, w, w[0] * x(0, 0, 0));
 }
 
 template <class T>
@@ -136,85 +176,108 @@ __device__ __forceinline__ const T* class_row(const LevelDev<T>& L, int64_t c) {
 }
 
 // Unit stiffness row split into diagonal and off-diagonal sum (Gauss-Seidel).
+template <class T, class V>
+__device__ __forceinline__ void irr_lap_parts_v(const V& x, const T* w, T& dg, T& of) {
+  dg = w[W_LAP];
+  of = st14v<T>(x, w + W_LAP, (T)0);
+}
+
 template <class T>
 __device__ __forceinline__ void irr_lap_parts(const LevelDev<T>& L, const T* x, int64_t c, T& dg, T& of) {
-  const T* w = class_row(L, c) + W_LAP;
-  const Off15 off = offsets15(L.px, L.pxy);
-  dg = w[0];
-  T acc = 0;
-#pragma unroll
-  for (int o = 1; o < 15; ++o) acc += w[o] * x[c + off.o[o]];
-  of = acc;
+  irr_lap_parts_v<T>(gnb(x, c, L.px, L.pxy), class_row(L, c), dg, of);
 }
 
 // Consistent mass row (times h^3).
 template <class T>
 __device__ __forceinline__ T irr_mass_row(const LevelDev<T>& L, const T* x, int64_t c) {
-  return L.h3 * st15(x, c, offsets15(L.px, L.pxy), class_row(L, c) + W_M);
+  return L.h3 * st15v<T>(gnb(x, c, L.px, L.pxy), class_row(L, c) + W_M);
 }
 
 // B_d row applied to one scalar field for the three d (times h^2).
 template <class T>
 __device__ __forceinline__ void irr_B_scalar(const LevelDev<T>& L, const T* x, int64_t c, T out[3]) {
   const T* w = class_row(L, c);
-  const Off15 off = offsets15(L.px, L.pxy);
+  const GNb<T> v = gnb(x, c, L.px, L.pxy);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15(x, c, off, w + W_B + 15 * d);
+  for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15v<T>(v, w + W_B + 15 * d);
 }
 
 // --- full rows of the Stokes operator ----------------------------------------
+// View forms take the class row w of the node (used when fl has F_IRR).
 
 // (A u_d)_node for all d (nodes with F_VFREE).
-template <class T>
-__device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl, T out[3]) {
+template <class T, class V>
+__device__ __forceinline__ void row_A_v(const LevelDev<T>& L, const V* u, const T* w, uint8_t fl, T out[3]) {
   if (!(fl & F_IRR)) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) out[d] = L.nuh * ((T)6 * u[d][c] - nb6(u[d], c, L.px, L.pxy));
+    for (int d = 0; d < 3; ++d) out[d] = L.nuh * ((T)6 * u[d](0, 0, 0) - nb6v(u[d]));
   } else {
-    const T* w = class_row(L, c) + W_LAP;
-    const Off15 off = offsets15(L.px, L.pxy);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) out[d] = L.nuh * st15(u[d], c, off, w);
+    for (int d = 0; d < 3; ++d) out[d] = L.nuh * st15v<T>(u[d], w + W_LAP);
   }
 }
 
 // (B_d^T p)_node for all d.
-template <class T>
-__device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl, T out[3]) {
+template <class T, class V>
+__device__ __forceinline__ void row_BT_v(const LevelDev<T>& L, const V& p, const T* w, uint8_t fl, T out[3]) {
   if (!(fl & F_IRR)) {
-    const Diff7<T> dp = diff7(p, c, L.px, L.pxy);
+    const Diff7<T> dp = diff7v<T>(p);
     T dv[3];
     div12_all(dp, dv);
     const T s = -L.h2 * (T)(1.0 / 12.0);
 #pragma unroll
     for (int d = 0; d < 3; ++d) out[d] = s * dv[d];
   } else {
-    const T* w = class_row(L, c) + W_BT;
-    const Off15 off = offsets15(L.px, L.pxy);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15(p, c, off, w + 15 * d);
+    for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15v<T>(p, w + W_BT + 15 * d);
   }
 }
 
 // (sum_d B_d u_d)_node.
-template <class T>
-__device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl) {
+template <class T, class V>
+__device__ __forceinline__ T row_B_v(const LevelDev<T>& L, const V* u, const T* w, uint8_t fl) {
   if (!(fl & F_IRR)) {
-    const T d0 = div12(diff7(u[0], c, L.px, L.pxy), 0);
-    const T d1 = div12(diff7(u[1], c, L.px, L.pxy), 1);
-    const T d2 = div12(diff7(u[2], c, L.px, L.pxy), 2);
+    const T d0 = div12(diff7v<T>(u[0]), 0);
+    const T d1 = div12(diff7v<T>(u[1]), 1);
+    const T d2 = div12(diff7v<T>(u[2]), 2);
     return L.h2 * (T)(1.0 / 12.0) * ((d0 + d1) + d2);
   }
-  const T* w = class_row(L, c) + W_B;
-  const Off15 off = offsets15(L.px, L.pxy);
-  return L.h2 * ((st15(u[0], c, off, w) + st15(u[1], c, off, w + 15)) + st15(u[2], c, off, w + 30));
+  return L.h2 * ((st15v<T>(u[0], w + W_B) + st15v<T>(u[1], w + W_B + 15)) + st15v<T>(u[2], w + W_B + 30));
 }
 
 // (C p)_node.
+template <class T, class V>
+__device__ __forceinline__ T row_C_v(const LevelDev<T>& L, const V& p, const T* w, uint8_t fl) {
+  if (!(fl & F_IRR)) return L.c * ((T)6 * p(0, 0, 0) - nb6v(p));
+  return L.c * st15v<T>(p, w + W_LAP);
+}
+
+// Pointer forms over the padded global arrays.
+template <class T>
+__device__ __forceinline__ const T* row_of(const LevelDev<T>& L, int64_t c, uint8_t fl) {
+  return (fl & F_IRR) ? class_row(L, c) : nullptr;
+}
+
+template <class T>
+__device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl, T out[3]) {
+  const GNb<T> v[3] = {gnb(u[0], c, L.px, L.pxy), gnb(u[1], c, L.px, L.pxy), gnb(u[2], c, L.px, L.pxy)};
+  row_A_v(L, v, row_of(L, c, fl), fl, out);
+}
+
+template <class T>
+__device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl, T out[3]) {
+  row_BT_v(L, gnb(p, c, L.px, L.pxy), row_of(L, c, fl), fl, out);
+}
+
+template <class T>
+__device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl) {
+  const GNb<T> v[3] = {gnb(u[0], c, L.px, L.pxy), gnb(u[1], c, L.px, L.pxy), gnb(u[2], c, L.px, L.pxy)};
+  return row_B_v(L, v, row_of(L, c, fl), fl);
+}
+
 template <class T>
 __device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl) {
-  if (!(fl & F_IRR)) return L.c * ((T)6 * p[c] - nb6(p, c, L.px, L.pxy));
-  return L.c * st15(p, c, offsets15(L.px, L.pxy), class_row(L, c) + W_LAP);
+  return row_C_v(L, gnb(p, c, L.px, L.pxy), row_of(L, c, fl), fl);
 }
 
 // Lumped pressure mass m_i = int phi_i.

@@ -1,5 +1,6 @@
 // Host-side launchers of the level kernels (hhg_kernels.cu, hhg_coarse.cu).
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -18,6 +19,31 @@ template <class T> void launch_pres_colour(const LevelDev<T>& L, int colour, cud
 // velocity, B u - g for pressure) instead of reading RU / RP.
 template <class T> void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s);
 template <class T> void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s);
+// The same colour sweeps on shared-memory tiles staged by tensor copies
+// (hhg_tiled.cu): f - B^T p at the node, stored RU, and B u - g at the node.
+// TileMaps holds the tensor maps of u_0, u_1, u_2, p of one level and
+// precision (make_tile_maps); kz is the run of planes per CTA.  A CTA whose
+// bounded wait for a copy runs out writes HHG_TILE_TIMEOUT to *err and stops.
+// prepare_tiled() sets the kernels' shared-memory limits (once per device).
+struct alignas(64) TileMaps {
+  CUtensorMap m[4];
+};
+constexpr unsigned HHG_TILE_TIMEOUT = 0x7117u;
+template <class T> int make_tile_maps(const LevelDev<T>& L, TileMaps& out, std::string& err);
+template <class T>
+void launch_vel_colour_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
+                            cudaStream_t s);
+template <class T>
+void launch_vel_colour_ru_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
+                               cudaStream_t s);
+template <class T>
+void launch_pres_colour_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
+                             cudaStream_t s);
+void prepare_tiled();
+// Default of hhg_options.tile_min_nodes: off.  Measured on GB300, the tile
+// kernels move the same bytes per colour launch as the grid kernels (the
+// own-node reads of f and the writes of u stay strided) and run 25% slower.
+constexpr int64_t TILE_MIN_NODES = -1;
 
 // Residual (RU, RP) = (F, G) - K (U, P); zero on nodes without unknowns.
 template <class T> void launch_residual(const LevelDev<T>& L, cudaStream_t s);

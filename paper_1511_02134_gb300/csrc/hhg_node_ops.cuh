@@ -19,43 +19,59 @@ __device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, int64_t c) {
 }
 
 // u_d <- u_d + (RU_d - (A u_d)) / A_ii  (one node of the current colour).
-template <class T>
-__device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_VFREE)) return;
+// View forms: u, p are neighbour views centred on the node (global arrays or
+// a shared-memory tile); the caller has checked the node's flag.
+template <class T, class V>
+__device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, T inv6nuh) {
   if (!(fl & F_IRR)) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) L.u[d][c] = (L.r[d][c] + L.nuh * nb6(L.u[d], c, L.px, L.pxy)) * inv6nuh;
+    for (int d = 0; d < 3; ++d) L.u[d][c] = (L.r[d][c] + L.nuh * nb6v(u[d])) * inv6nuh;
   } else {
-#pragma unroll 1
+    const T* w = class_row(L, c);
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
       T dg, of;
-      irr_lap_parts(L, L.u[d], c, dg, of);
+      irr_lap_parts_v<T>(u[d], w, dg, of);
       L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
     }
   }
 }
 
+template <class T>
+__device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
+  const uint8_t fl = L.flags[c];
+  if (!(fl & F_VFREE)) return;
+  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
+  node_vel_gs_v(L, c, fl, u, inv6nuh);
+}
+
 // Same update with the right-hand side f - B^T p formed at the node (p does
 // not change during the velocity sweeps, Sec. 3.3), RU is not touched.
+template <class T, class V>
+__device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, const V& p,
+                                                  T inv6nuh) {
+  const T* w = row_of(L, c, fl);
+  T bt[3];
+  row_BT_v(L, p, w, fl, bt);
+  if (!(fl & F_IRR)) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.u[d][c] = ((L.f[d][c] - bt[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      T dg, of;
+      irr_lap_parts_v<T>(u[d], w, dg, of);
+      L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
+    }
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void node_vel_gs_rhs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
   const uint8_t fl = L.flags[c];
   if (!(fl & F_VFREE)) return;
-  T bt[3];
-  row_BT(L, L.p, c, fl, bt);
-  if (!(fl & F_IRR)) {
-#pragma unroll
-    for (int d = 0; d < 3; ++d)
-      L.u[d][c] = ((L.f[d][c] - bt[d]) + L.nuh * nb6(L.u[d], c, L.px, L.pxy)) * inv6nuh;
-  } else {
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      T dg, of;
-      irr_lap_parts(L, L.u[d], c, dg, of);
-      L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
-    }
-  }
+  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
+  node_vel_gs_rhs_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), inv6nuh);
 }
 
 // RP = B U - G (pressure nodes).
@@ -86,22 +102,29 @@ __device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, int64_t c, T 
 
 // Same update with B u - g formed at the node (u does not change during the
 // pressure sweep), RP is not touched.
+template <class T, class V>
+__device__ __forceinline__ void node_pres_gs_rhs_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, const V& p,
+                                                   T omega_over_6c) {
+  const T* w = row_of(L, c, fl);
+  const T rp = row_B_v(L, u, w, fl) - L.g[c];
+  const T pc = p(0, 0, 0);
+  if (!(fl & F_IRR)) {
+    const T cp = L.c * ((T)6 * pc - nb6v(p));
+    L.p[c] = pc + omega_over_6c * (rp - cp);
+  } else {
+    T dg, of;
+    irr_lap_parts_v<T>(p, w, dg, of);
+    const T cp = L.c * (dg * pc + of);
+    L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
+  }
+}
+
 template <class T>
 __device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, int64_t c, T omega_over_6c) {
   const uint8_t fl = L.flags[c];
   if (!(fl & F_ACT)) return;
-  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};
-  const T rp = row_B(L, uu, c, fl) - L.g[c];
-  const T pc = L.p[c];
-  if (!(fl & F_IRR)) {
-    const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
-    L.p[c] = pc + omega_over_6c * (rp - cp);
-  } else {
-    T dg, of;
-    irr_lap_parts(L, L.p, c, dg, of);
-    const T cp = L.c * (dg * pc + of);
-    L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
-  }
+  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
+  node_pres_gs_rhs_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), omega_over_6c);
 }
 
 // (RU, RP) = (F, G) - K (U, P); zero on nodes without the unknown.

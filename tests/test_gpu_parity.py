@@ -114,9 +114,13 @@ def test_set_rhs(pkg, name, level):
 
 # ---- smoother pieces, transfers, coarse solve ---------------------------------------------
 
+@pytest.mark.parametrize("tiles", [-1, 1])
 @pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3)])
-def test_smoother_pieces(pkg, name, level):
-    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level))
+def test_smoother_pieces(pkg, name, level, tiles):
+    """Smoother steps against the oracle, with the colour sweeps run by the
+    grid kernels (tiles = -1) and by the shared-memory tile kernels (tiles = 1:
+    every level tiled, ragged tiles included)."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), tile_min_nodes=tiles)
     L = H.levels[level]
     dims = mesh.dims()
     st = _random_state(H, level, 7)
@@ -158,6 +162,29 @@ def test_smoother_pieces(pkg, name, level):
     ru, rp = L.residual(u, p, f, g)
     assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU")), ru) < 1e-11
     assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP")), rp) < 1e-11
+
+
+@pytest.mark.parametrize("name,level", [("cube", 5), ("channel", 3), ("partial", 4)])
+def test_tiled_sweeps_match_grid_kernels(pkg, name, level):
+    """The shared-memory tile kernels evaluate the same per-node expressions
+    as the grid kernels: Uzawa steps agree to rounding in FP64 and FP32
+    (both read the same neighbour values; only the compiler's contraction
+    of the expressions into fused multiply-adds may differ)."""
+    macro = macro_by_name(name)
+    H = MG.build_hierarchy(macro, level, coarsest=level - 1)
+    st = _random_state(H, level, 17)
+    meshes = [pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=level - 1,
+                       tile_min_nodes=t) for t in (-1, 1)]
+    for prec, tol in ((0, 1e-14), (1, 1e-6)):
+        outs = []
+        for mesh in meshes:
+            _load(mesh, H, level, st, precision=prec)
+            mesh.level_op(level, "uzawa_step", precision=prec, count=2)
+            outs.append(_read_up(mesh, H, level, precision=prec))
+        assert rel_err(outs[1][0], outs[0][0]) < tol, prec
+        assert rel_err(outs[1][1], outs[0][1]) < tol, prec
+    for mesh in meshes:
+        mesh.close()
 
 
 @pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
@@ -208,10 +235,11 @@ def test_coarse_solve(pkg, name, level, mx):
 
 # ---- cycles and solves ------------------------------------------------------------------------
 
+@pytest.mark.parametrize("tiles", [-1, 1])
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 3, 2, 5), ("cube", 5, 2, 5), ("channel", 2, 1, 200),
                                                     ("partial", 3, 1, 30)])
-def test_vcycle_iterates(pkg, name, level, coarsest, mx):
-    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx)
+def test_vcycle_iterates(pkg, name, level, coarsest, mx, tiles):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles)
     L = H.levels[level]
     st = _random_state(H, level, 9)
     _load(mesh, H, level, st)
@@ -253,12 +281,13 @@ def test_fp64_solve_matches_oracle(pkg, name, level, coarsest, mx):
         assert abs(np.dot(m, p[lat])) < 1e-12 * np.abs(p).max()
 
 
+@pytest.mark.parametrize("tiles", [0, 1])
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 5, 2, 5), ("channel", 3, 1, 200)])
-def test_fp32_ir_solve(pkg, name, level, coarsest, mx):
+def test_fp32_ir_solve(pkg, name, level, coarsest, mx, tiles):
     """FP32 V-cycles inside FP64 refinement reach the FP64 tolerance; the
     solution differs from the FP64 solution by far less than it differs from
     the exact discrete solution at that tolerance."""
-    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx)
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles)
     L = H.levels[level]
     dims = mesh.dims()
     x = mesh.node_coords()
