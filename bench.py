@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Stokes DoF solved/s to 1e-8 rel. residual, FP32+refine vs FP64; HBM % of peak"
 LEVEL = 7
 TOL = 1e-8
+# DRAM bytes (read + write) of one k_vel_colour_rhs<float> launch, from an ncu
+# capture of `bench.py --roofline-only` at that level (cold caches: ncu
+# flushes them before each pass); None where no capture of the current kernel
+# exists.
+TRAFFIC_PER_LAUNCH = {7: 62997760 + 863488}
 
 
 def _peaks():
@@ -207,31 +212,14 @@ def run_gpu(args):
     e2e = {"value": world * dofs * args.steps / (e2e_ms / 1e3), "unit": "DoF/s",
            "h2d_bytes_per_step": int(2 * 3 * n * 8), "d2h_bytes_per_step": int(4 * n * 8)}
 
-    # ---- roofline of the dominant kernel: FP32 velocity colour sweep on the finest level ----
-    peak, peak_kind = _peaks()
-    lvl = args.level
-    reps = 20
-    with torch.cuda.stream(stream):
-        flush.fill_(1.0)
-    ms_sweep = mesh.time_op(lvl, "vel_forward", precision=1, reps=reps)  # 4 colour launches
-    ms_launch = ms_sweep / 4.0
-    nodes = mesh.num_nodes(lvl)
-    # algorithmic bytes of one colour launch: the forward sweep reads u (3) and
-    # its right-hand side (3) and writes u (3), FP32, once per node; one of the
-    # four colour launches carries a quarter of that
-    alg_bytes = nodes * 9 * 4 / 4.0
-    achieved = alg_bytes / (ms_launch / 1e3) / 1e9
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": None,
-                "kernel": "k_vel_colour<float> (level %d)" % lvl, "peak_kind": peak_kind,
-                "ms_per_launch": ms_launch}
+    roofline = measure_roofline(mesh, args.level, stream, flush)
 
     out = {
         "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms32_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle + f64 refinement", "data": "synthetic",
-        "config": {"workload": f"unit cube, 6 Kuhn tetrahedra, level {lvl} ({dofs} free DoFs), manufactured "
-                               "solution, V_var(3,3) from zero to 1e-8", "level": lvl, "free_dofs": dofs,
+        "config": {"workload": f"unit cube, 6 Kuhn tetrahedra, level {args.level} ({dofs} free DoFs), manufactured "
+                               "solution, V_var(3,3) from zero to 1e-8", "level": args.level, "free_dofs": dofs,
                    "mode": "FP32 V-cycle inside FP64 iterative refinement", "l2": "flushed (256 MB write) "
                    "between timed steps", "parallelism": "replicas" if world > 1 else "single GPU"},
         "cycles": cyc32, "fp64": {"value": value64, "ms_per_step": ms64_max / n64, "cycles": cyc64,
@@ -246,6 +234,48 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def measure_roofline(mesh, lvl, stream, flush):
+    """Roofline of the dominant kernel of the FP32 path: the velocity colour
+    sweep with f - B^T p formed at each node (k_vel_colour_rhs<float>) on the
+    finest level, timed with CUDA events on the mesh's stream (hhg_time_op).
+    Algorithmic bytes of one forward sweep (four colour launches): u read and
+    written (2 x 3 x 4 B), f (3 x 4 B), p (4 B) and the node flag (1 B) once per
+    node; one colour launch carries a quarter of that."""
+    import torch
+    peak, peak_kind = _peaks()
+    reps = 20
+    with torch.cuda.stream(stream):
+        flush.fill_(1.0)
+    stream.synchronize()
+    ms_sweep = mesh.time_op(lvl, "vel_forward_f", precision=1, reps=reps)  # 4 colour launches
+    ms_launch = ms_sweep / 4.0
+    nodes = mesh.num_nodes(lvl)
+    alg_bytes = nodes * (2 * 3 * 4 + 3 * 4 + 4 + 1) / 4.0
+    achieved = alg_bytes / (ms_launch / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": TRAFFIC_PER_LAUNCH.get(lvl),
+            "kernel": "k_vel_colour_rhs<float> (level %d)" % lvl, "peak_kind": peak_kind,
+            "ms_per_launch": ms_launch, "alg_bytes_per_launch": alg_bytes}
+
+
+def roofline_only(args):
+    """Set up the bench workload, run one FP32+IR solve and print the roofline
+    measurement alone (the command the kernel profiles are taken with)."""
+    import torch
+    import paper_1511_02134_gb300 as pkg
+    import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    cube = W.unit_cube()
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, args.level, stream=stream.cuda_stream)
+    x = mesh.node_coords()
+    mesh.set_rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    mesh.solve(tol=TOL, max_cycles=50, mode=pkg.MODE_FP32_IR, want_solution=False)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+    print(json.dumps(measure_roofline(mesh, args.level, stream, flush)))
+    mesh.close()
 
 
 def _oracle_sample(level: int, seconds: float):
@@ -305,12 +335,17 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="print only the roofline measurement of the dominant kernel")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     import __graft_entry__ as g
     g.build()
+    if args.roofline_only:
+        roofline_only(args)
+        return
     run_gpu(args)
 
 

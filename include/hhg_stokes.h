@@ -85,10 +85,14 @@ typedef struct hhg_options {
   double coarse_cg_rtol;     /* inner CG relative tolerance (1e-3, Sec. 3.7) */
   int32_t use_graphs;        /* 1: replay each V-cycle as a captured CUDA graph */
   int32_t fuse_coarse_levels;/* 1: run the coarse levels (see fuse_max_nodes) and the coarse
-                                solve as one fused kernel per cycle */
-  int32_t fuse_max_nodes;    /* largest level (lattice nodes) of the fused kernel; 0 = default (1024) */
+                                solve as one fused kernel per cycle; 2: the same with the
+                                levels held in the shared memory of one thread-block cluster
+                                (falls back to 1 where they do not fit; default); 0: off */
+  int32_t fuse_max_nodes;    /* largest level (lattice nodes) of the fused kernel; 0 = default
+                                (1024 for mode 1, 65536 for mode 2) */
   int32_t team_blocks;       /* CTAs of the fused kernel's thread-block cluster (1 = one block,
-                                at most 16); 0 = default (1) */
+                                at most 16); 0 = default (1 for mode 1; for mode 2, 8 in FP32
+                                and 16 in FP64) */
   int32_t tile_min_nodes;    /* levels of at least this many lattice nodes run the colour sweeps
                                 on shared-memory tiles staged by tensor copies; 0 = default
                                 (never), -1 = never */
@@ -232,6 +236,10 @@ int hhg_level_field(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t fi
 #define HHG_OP_COARSE_SOLVE 9 /* (U, P) += MINRES correction on the coarsest level */
 #define HHG_OP_VCYCLE 10      /* one V_var cycle rooted at `level` */
 #define HHG_OP_PROJECT 11     /* remove the m-weighted pressure mean */
+#define HHG_OP_VEL_FORWARD_F 12 /* forward velocity colour sweep with F - B^T P formed at each node
+                                   (the velocity colours of an FP32 Uzawa step) */
+#define HHG_OP_PRES_SWEEP_F 13  /* forward pressure colour sweep with B U - G formed at each node
+                                   (the pressure colours of an Uzawa step) */
 
 /* Run `op` `count` times on `level` in `precision`. */
 int hhg_level_op(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t op, int32_t count);

@@ -29,7 +29,7 @@ NODE_ACTIVE, NODE_VFREE, NODE_IRREG, NODE_DIRICHLET, NODE_OUTFLOW = 1, 2, 4, 8, 
 FIELD = {"U": 0, "P": 1, "F": 2, "G": 3, "RU": 4, "RP": 5}
 OP = {"uzawa_step": 0, "vel_forward": 1, "vel_backward": 2, "vel_rhs": 3, "pres_rhs": 4,
       "pres_sweep": 5, "residual": 6, "restrict": 7, "prolong_add": 8, "coarse_solve": 9,
-      "vcycle": 10, "project": 11}
+      "vcycle": 10, "project": 11, "vel_forward_f": 12, "pres_sweep_f": 13}
 ERRORS = {0: "ok", -1: "HHG_EINVAL", -2: "HHG_EMESH", -3: "HHG_ENOMEM", -4: "HHG_EDIVERGED",
           -5: "HHG_EMAXIT", -6: "HHG_ECUDA", -7: "HHG_ESTATE"}
 

@@ -63,6 +63,9 @@ struct hhg_mesh {
   MacroLattice macro;
   int finest = 0, coarsest = 0;
   int small_top[2] = {-1, -1};  // top level of the fused coarse-levels cycle, FP64 / FP32 (-1: none)
+  int res_top[2] = {-1, -1};    // top level of the cluster-resident cycle, FP64 / FP32 (-1: none)
+  unsigned res_nb[2] = {16, 16};  // its cluster size
+  size_t res_smem[2] = {0, 0};    // its shared-memory limit per CTA
   unsigned small_cluster[2] = {1, 8};  // CTAs of the fused team, FP64 / FP32
   std::vector<LevelHost> lv;
   uint8_t* d_mmask = nullptr;
@@ -192,6 +195,27 @@ void enq_pres_sweep(hhg_mesh* M, int l) {
   M->launches += 4;
 }
 
+// The colour kernels of an Uzawa step on their own: the forward velocity
+// sweep with f - B^T p formed at each node, and the pressure sweep with
+// B u - g formed at each node.
+template <class T>
+void enq_vel_sweep_f(hhg_mesh* M, int l) {
+  const LevelDev<T>& L = view<T>(M, l);
+  for (int q = 0; q < 4; ++q)
+    M->lv[l].tiled ? launch_vel_colour_tile<T>(maps<T>(M, l), L, q, M->lv[l].kz, err_word(M), M->stream)
+                   : launch_vel_colour_rhs<T>(L, q, M->stream);
+  M->launches += 4;
+}
+
+template <class T>
+void enq_pres_sweep_f(hhg_mesh* M, int l) {
+  const LevelDev<T>& L = view<T>(M, l);
+  for (int q = 0; q < 4; ++q)
+    M->lv[l].tiled ? launch_pres_colour_tile<T>(maps<T>(M, l), L, q, M->lv[l].kz, err_word(M), M->stream)
+                   : launch_pres_colour_rhs<T>(L, q, M->stream);
+  M->launches += 4;
+}
+
 // One inexact Uzawa step (Sec. 3.3): velocity SHGS on f - B^T p (colours
 // 0,1,2,3 then 3,2,1,0), then the relaxed pressure sweep on B u - g.  The
 // backward colour 3 repeats the forward one with unchanged neighbours and a
@@ -265,11 +289,45 @@ void enq_small_cycle(hhg_mesh* M) {
   M->launches += 1;
 }
 
+template <class T>
+void fill_resident(hhg_mesh* M, ResidentCycle<T>& S, int top) {
+  std::memset(&S, 0, sizeof(S));
+  const int pr = sizeof(T) == 4;
+  S.nblocks = M->res_nb[pr];
+  S.nres = top - M->coarsest;
+  for (int q = 0; q <= S.nres; ++q) {
+    const int l = M->coarsest + q;
+    S.lv[q] = view<T>(M, l);
+    S.nu_pre[q] = nu_steps<T>(M, l, true);
+    S.nu_post[q] = nu_steps<T>(M, l, false);
+    S.inv6nuh[q] = (T)(1.0 / (6.0 * (double)S.lv[q].nuh));
+    S.omc[q] = (T)((double)S.lv[q].omega / (6.0 * (double)S.lv[q].c));
+  }
+  S.cs = M->coarse_sys;
+  S.scratch = M->d_coarse;
+  S.prm = CoarseParams{M->opt.coarse_minres_max, M->opt.coarse_minres_rtol, M->opt.coarse_cg_max,
+                       M->opt.coarse_cg_rtol};
+  S.info = M->d_scalars + 5;
+}
+
+template <class T>
+void enq_resident_cycle(hhg_mesh* M) {
+  ResidentCycle<T> S;
+  fill_resident<T>(M, S, M->res_top[sizeof(T) == 4]);
+  plan_resident<T>(S, M->res_smem[sizeof(T) == 4]);
+  launch_resident_cycle<T>(S, M->stream);
+  M->launches += 1;
+}
+
 // One V_var cycle rooted at level l (Sec. 3.5).
 template <class T>
 void enq_vcycle(hhg_mesh* M, int l) {
   if (l == M->coarsest) {
     enq_coarse<T>(M);
+    return;
+  }
+  if (l == M->res_top[sizeof(T) == 4]) {
+    enq_resident_cycle<T>(M);
     return;
   }
   if (l == M->small_top[sizeof(T) == 4]) {
@@ -502,7 +560,7 @@ void hhg_default_options(hhg_options* opt) {
   opt->coarse_cg_max = 50;
   opt->coarse_cg_rtol = 1e-3;
   opt->use_graphs = 1;
-  opt->fuse_coarse_levels = 1;
+  opt->fuse_coarse_levels = 2;
 }
 
 const char* hhg_strerror(int code) {
@@ -755,8 +813,35 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     M->small_cluster[1] = o.team_blocks > 0 ? std::min<unsigned>((unsigned)o.team_blocks, cl)
                                             : std::min<unsigned>(SMALL_TEAM_BLOCKS, cl);
   }
+  // cluster-resident coarse levels: the largest level whose sub-hierarchy fits
+  // the shared memory of one cluster (and has at most fuse_max_nodes nodes)
+  if (o.fuse_coarse_levels == 2) {
+    const int64_t lim = o.fuse_max_nodes > 0 ? o.fuse_max_nodes : RES_MAX_NODES;
+    for (int pr = 0; pr < 2; ++pr) {
+      M->res_nb[pr] = pr ? prepare_resident<float>(M->res_smem[pr]) : prepare_resident<double>(M->res_smem[pr]);
+      const unsigned want = o.team_blocks > 0 ? (unsigned)o.team_blocks : (pr ? RES_CTAS_FP32 : RES_CTAS_FP64);
+      M->res_nb[pr] = std::min<unsigned>(M->res_nb[pr], want);
+      for (int l = std::min(finest, M->coarsest + RES_MAX_LEVELS); l > M->coarsest; --l) {
+        if (M->lv[l].sh.n() > lim) continue;
+        bool fits;
+        if (pr) {
+          ResidentCycle<float> S;
+          fill_resident<float>(M, S, l);
+          fits = plan_resident<float>(S, M->res_smem[pr]);
+        } else {
+          ResidentCycle<double> S;
+          fill_resident<double>(M, S, l);
+          fits = plan_resident<double>(S, M->res_smem[pr]);
+        }
+        if (fits) {
+          M->res_top[pr] = l;
+          break;
+        }
+      }
+    }
+  }
   // fused coarse levels: the largest level of at most fuse_max_nodes nodes
-  if (o.fuse_coarse_levels) {
+  if (o.fuse_coarse_levels == 1 || (o.fuse_coarse_levels == 2 && (M->res_top[0] < 0 || M->res_top[1] < 0))) {
     const int64_t lim32 = o.fuse_max_nodes > 0 ? o.fuse_max_nodes : SMALL_MAX_NODES;
     const int64_t lim64 = o.fuse_max_nodes > 0 ? o.fuse_max_nodes : SMALL_MAX_NODES_FP64;
     for (int l = M->coarsest + 1; l <= finest && l - M->coarsest < SMALL_MAX_LEVELS; ++l) {
@@ -1234,6 +1319,12 @@ static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op)
         break;
       case HHG_OP_VCYCLE:
         precision ? enq_vcycle<float>(M, level) : enq_vcycle<double>(M, level);
+        break;
+      case HHG_OP_VEL_FORWARD_F:
+        precision ? enq_vel_sweep_f<float>(M, level) : enq_vel_sweep_f<double>(M, level);
+        break;
+      case HHG_OP_PRES_SWEEP_F:
+        precision ? enq_pres_sweep_f<float>(M, level) : enq_pres_sweep_f<double>(M, level);
         break;
       case HHG_OP_PROJECT:
         precision ? enq_project<float>(M, level) : enq_project<double>(M, level);

@@ -25,7 +25,7 @@ template <class T> void launch_pres_colour_rhs(const LevelDev<T>& L, int colour,
 // precision (make_tile_maps); kz is the run of planes per CTA.  A CTA whose
 // bounded wait for a copy runs out writes HHG_TILE_TIMEOUT to *err and stops.
 // prepare_tiled() sets the kernels' shared-memory limits (once per device).
-struct alignas(64) TileMaps {
+struct TileMaps {
   CUtensorMap m[4];
 };
 constexpr unsigned HHG_TILE_TIMEOUT = 0x7117u;
@@ -168,6 +168,62 @@ struct SmallCycle {
 };
 template <class T>
 void launch_small_cycle(const SmallCycle<T>& S, cudaStream_t s);
+// Cluster-resident cycle of the coarse levels (hhg_resident.cu): levels
+// lv[1..nres] live in the shared memory of one thread-block cluster of
+// nblocks CTAs, split into runs of z-planes (CTA r holds node planes
+// [kb[q][r], kb[q][r+1]) of level q, kb[q][r] = ceil(r nz / nblocks)), and are
+// read across CTAs through distributed shared memory; lv[0], the coarsest
+// level, stays in global memory for the coarse solve.  The kernel runs the
+// part of the V_var cycle from lv[nres] (whose u, p, f, g it reads from and
+// whose u, p it writes back to global memory) down to the coarse solve and
+// back up.  Each CTA's dynamic shared memory holds, at the byte offsets
+// below, a table of plane pointers per level (RES_TAB_FIELDS rows of pz
+// generic pointers), one zero plane and a block per level: RES_FIELDS fields
+// of type T (u_0, u_1, u_2, p, f_0, f_1, f_2, g), then the node flags (bytes)
+// and stencil classes (16 bit), each maxpl[q] padded planes.
+constexpr int RES_MAX_LEVELS = 4;
+constexpr int64_t RES_MAX_NODES = 1 << 16;  // default cap on the top level's lattice nodes
+// Default cluster sizes, from whole level-7 cube solves on GB300 (FP32+IR
+// 38.4 -> 37.3 ms with 8 CTAs, FP64 112.5 -> 109.5 ms with 16; both hold
+// levels 3 and 4, level 5 does not fit).  Each colour phase still costs
+// about 2.5 us: the chain of dependent loads of a boundary node (flags,
+// class, weights, neighbours) sets it, whether the phase is a launch, a
+// phase of the global-memory fused kernel or a phase here.
+constexpr unsigned RES_CTAS_FP32 = 8;
+constexpr unsigned RES_CTAS_FP64 = 16;
+constexpr int RES_MAX_CTAS = 16;
+constexpr int RES_FIELDS = 8;
+constexpr int RES_TAB_FIELDS = 10;
+template <class T>
+struct ResidentCycle {
+  unsigned nblocks;
+  int nres;
+  LevelDev<T> lv[RES_MAX_LEVELS + 1];
+  int nu_pre[RES_MAX_LEVELS + 1];
+  int nu_post[RES_MAX_LEVELS + 1];
+  T inv6nuh[RES_MAX_LEVELS + 1];
+  T omc[RES_MAX_LEVELS + 1];
+  int kb[RES_MAX_LEVELS + 1][RES_MAX_CTAS + 1];
+  int maxpl[RES_MAX_LEVELS + 1];
+  uint32_t tab[RES_MAX_LEVELS + 1];
+  uint32_t blk[RES_MAX_LEVELS + 1];
+  uint32_t zero;
+  uint32_t smem;
+  CoarseSys cs;
+  double* scratch;
+  CoarseParams prm;
+  double* info;
+};
+// Plans the shared-memory layout of levels lv[1..nres] for nblocks CTAs
+// (fills kb, maxpl, tab, blk, zero, smem); false if it exceeds the limit.
+template <class T>
+bool plan_resident(ResidentCycle<T>& S, size_t smem_limit);
+template <class T>
+cudaError_t launch_resident_cycle(const ResidentCycle<T>& S, cudaStream_t s);
+// Cluster size (16, else 8) and the dynamic shared memory available to one
+// CTA of the resident kernel; sets the kernel attributes.
+template <class T>
+unsigned prepare_resident(size_t& smem_limit);
 // Cluster size for the fused cycle (16, else 8); sets kernel attributes.
 unsigned prepare_small_cycle();
 

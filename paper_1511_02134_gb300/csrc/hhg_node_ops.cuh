@@ -127,26 +127,34 @@ __device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, int64_t c
   node_pres_gs_rhs_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), omega_over_6c);
 }
 
-// (RU, RP) = (F, G) - K (U, P); zero on nodes without the unknown.
+// (RU, RP) = (F, G) - K (U, P) at one node, returned in r[0..3]; zero for
+// unknowns the node does not carry.
+template <class T, class V>
+__device__ __forceinline__ void node_residual_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, const V& p,
+                                                T r[4]) {
+  const T* w = row_of(L, c, fl);
+  if (fl & F_VFREE) {
+    T au[3], bt[3];
+    row_A_v(L, u, w, fl, au);
+    row_BT_v(L, p, w, fl, bt);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r[d] = L.f[d][c] - au[d] - bt[d];
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) r[d] = (T)0;
+  }
+  r[3] = (fl & F_ACT) ? L.g[c] - row_B_v(L, u, w, fl) + row_C_v(L, p, w, fl) : (T)0;
+}
+
 template <class T>
 __device__ __forceinline__ void node_residual(const LevelDev<T>& L, int64_t c) {
   const uint8_t fl = L.flags[c];
-  const T* uu[3] = {L.u[0], L.u[1], L.u[2]};
-  if (fl & F_VFREE) {
-    T au[3], bt[3];
-    row_A(L, uu, c, fl, au);
-    row_BT(L, L.p, c, fl, bt);
+  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
+  T r[4];
+  node_residual_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), r);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - au[d] - bt[d];
-  } else {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) L.r[d][c] = (T)0;
-  }
-  if (fl & F_ACT) {
-    L.rp[c] = L.g[c] - row_B(L, uu, c, fl) + row_C(L, L.p, c, fl);
-  } else {
-    L.rp[c] = (T)0;
-  }
+  for (int d = 0; d < 3; ++d) L.r[d][c] = r[d];
+  L.rp[c] = r[3];
 }
 
 // Coarse (F, G) at coarse node (i,j,k) = P^T (RU, RP): P1 interpolation is

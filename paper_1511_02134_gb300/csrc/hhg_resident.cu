@@ -1,0 +1,458 @@
+// Cluster-resident cycle of the coarse levels (Sec. 3.5 V_var cycle below a
+// mid-sized level, Sec. 3.7 coarse solve).
+//
+// On the small levels of the hierarchy a colour phase updates a few thousand
+// nodes, and its cost is the latency of one launch or of the dependent loads
+// from L2.  Here the levels lv[1..nres] are held in the shared memory of one
+// thread-block cluster for the whole sub-cycle: every level is split into
+// runs of z-planes, one run per CTA, each CTA updates the nodes of its own
+// planes, and reads neighbours on other CTAs' planes through distributed
+// shared memory.  Phases are separated by the cluster barrier (release /
+// acquire at cluster scope).  The coarsest level stays in global memory, where
+// the first CTA runs the coarse solve (hhg_coarse_block.cuh) while the others
+// wait at the barrier.
+//
+// The per-node arithmetic is the view form of the grid kernels' bodies
+// (hhg_node_ops.cuh): the node's own fields are reached through a LevelDev
+// whose field pointers point at the node's plane, its neighbours through
+// plane-pointer tables.  The residual is evaluated inside the restriction
+// (the 15 fine nodes of each coarse node), so no residual fields are stored.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "hhg_coarse_block.cuh"
+#include "hhg_kernels.h"
+#include "hhg_node_ops.cuh"
+#include "hhg_team.cuh"
+
+namespace hhg {
+
+namespace {
+
+namespace cg = cooperative_groups;
+
+constexpr int RT = 512;  // threads per CTA
+
+__host__ __device__ inline uint32_t align16(uint64_t x) { return (uint32_t)((x + 15) & ~(uint64_t)15); }
+
+// Neighbour view over a plane-pointer table row: row[z] is the generic
+// address (local or another CTA's shared memory) of padded plane z.
+template <class T>
+struct DNb {
+  T* const* row;
+  int z, xy, px;
+  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const { return row[z + dz][xy + dx + px * dy]; }
+};
+
+template <class T>
+struct Res {
+  const ResidentCycle<T>& S;
+  unsigned char* sm;
+  unsigned rank;
+
+  __device__ __forceinline__ void* const* table(int q) const {
+    return reinterpret_cast<void* const*>(sm + S.tab[q]);
+  }
+  template <class E>
+  __device__ __forceinline__ E* row_ptr(int q, int f, int z) const {
+    return reinterpret_cast<E*>(table(q)[f * (S.lv[q].nz + 2) + z]);
+  }
+  // The level with its field pointers at padded plane z (node plane z - 1):
+  // node (i, j) of that plane is entry (j + 1) px + (i + 1).
+  __device__ __forceinline__ LevelDev<T> at_plane(int q, int z) const {
+    LevelDev<T> L = S.lv[q];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      L.u[d] = row_ptr<T>(q, d, z);
+      L.f[d] = row_ptr<T>(q, 4 + d, z);
+    }
+    L.p = row_ptr<T>(q, 3, z);
+    L.g = row_ptr<T>(q, 7, z);
+    L.flags = row_ptr<const uint8_t>(q, 8, z);
+    L.cls = row_ptr<const uint16_t>(q, 9, z);
+    return L;
+  }
+  __device__ __forceinline__ DNb<T> view(int q, int f, int z, int xy) const {
+    void* const* t = table(q) + f * (S.lv[q].nz + 2);
+    return DNb<T>{reinterpret_cast<T* const*>(t), z, xy, (int)S.lv[q].px};
+  }
+};
+
+__device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
+
+// ---- set-up: plane tables, zero plane, flags / classes, top-level fields ------
+
+template <class T>
+__device__ void r_setup(const Res<T>& R) {
+  const ResidentCycle<T>& S = R.S;
+  cg::cluster_group cl = cg::this_cluster();
+  // zero everything this CTA holds (blocks and zero plane)
+  {
+    uint4* z = reinterpret_cast<uint4*>(R.sm + S.zero);
+    const uint4* e = reinterpret_cast<const uint4*>(R.sm + S.smem);
+    for (uint4* p = z + threadIdx.x; p < e; p += blockDim.x) *p = make_uint4(0, 0, 0, 0);
+  }
+  for (int q = 1; q <= S.nres; ++q) {
+    const LevelDev<T>& L = S.lv[q];
+    const int pz = L.nz + 2;
+    const int64_t plane = L.pxy;
+    const int64_t fb = (int64_t)S.maxpl[q] * plane;  // entries per field block
+    void** tab = reinterpret_cast<void**>(R.sm + S.tab[q]);
+    for (int e = threadIdx.x; e < RES_TAB_FIELDS * pz; e += blockDim.x) {
+      const int f = e / pz, z = e - f * pz;
+      void* ptr = R.sm + S.zero;
+      if (z >= 1 && z <= L.nz) {
+        const int k = z - 1;
+        const unsigned r = (unsigned)(((int64_t)k * S.nblocks) / L.nz);
+        const int64_t lp = k - S.kb[q][r];
+        unsigned char* base = R.sm + S.blk[q];
+        unsigned char* loc;
+        if (f < RES_FIELDS)
+          loc = base + sizeof(T) * (f * fb + lp * plane);
+        else if (f == 8)
+          loc = base + sizeof(T) * RES_FIELDS * fb + lp * plane;
+        else
+          loc = base + align16(sizeof(T) * RES_FIELDS * fb + fb) + 2 * lp * plane;
+        // own planes through the CTA's own shared window, others' through the cluster's
+        ptr = r == R.rank ? (void*)loc : cl.map_shared_rank(loc, r);
+      }
+      tab[e] = ptr;
+    }
+  }
+  __syncthreads();
+  // flags and classes of every resident level, fields of the top level
+  for (int q = 1; q <= S.nres; ++q) {
+    const LevelDev<T>& L = S.lv[q];
+    const int k0 = S.kb[q][R.rank], k1 = S.kb[q][R.rank + 1];
+    const int64_t plane = L.pxy, fb = (int64_t)S.maxpl[q] * plane;
+    const int64_t n = (int64_t)(k1 - k0) * plane;
+    const int64_t g0 = (int64_t)(k0 + 1) * plane;  // first padded entry of plane k0
+    unsigned char* base = R.sm + S.blk[q];
+    uint8_t* fl = base + sizeof(T) * RES_FIELDS * fb;
+    uint16_t* cs = reinterpret_cast<uint16_t*>(base + align16(sizeof(T) * RES_FIELDS * fb + fb));
+    T* fld = reinterpret_cast<T*>(base);
+    const bool top = q == S.nres;
+    for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+      fl[e] = L.flags[g0 + e];
+      cs[e] = L.cls[g0 + e];
+      if (top) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          fld[d * fb + e] = L.u[d][g0 + e];
+          fld[(4 + d) * fb + e] = L.f[d][g0 + e];
+        }
+        fld[3 * fb + e] = L.p[g0 + e];
+        fld[7 * fb + e] = L.g[g0 + e];
+      }
+    }
+  }
+  cluster_sync();
+}
+
+// u, p of the top level back to global memory
+template <class T>
+__device__ void r_writeback(const Res<T>& R) {
+  const ResidentCycle<T>& S = R.S;
+  const int q = S.nres;
+  const LevelDev<T>& L = S.lv[q];
+  const int k0 = S.kb[q][R.rank], k1 = S.kb[q][R.rank + 1];
+  const int64_t plane = L.pxy, fb = (int64_t)S.maxpl[q] * plane;
+  const int64_t n = (int64_t)(k1 - k0) * plane;
+  const int64_t g0 = (int64_t)(k0 + 1) * plane;
+  const T* fld = reinterpret_cast<const T*>(R.sm + S.blk[q]);
+  for (int64_t e = threadIdx.x; e < n; e += blockDim.x) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.u[d][g0 + e] = fld[d * fb + e];
+    L.p[g0 + e] = fld[3 * fb + e];
+  }
+}
+
+// ---- phases --------------------------------------------------------------------
+
+// One colour phase of level q on this CTA's planes: velocity Gauss-Seidel with
+// f - B^T p formed at the node, or the relaxed pressure update with B u - g.
+template <class T>
+__device__ void r_colour(const Res<T>& R, int q, int colour, bool vel) {
+  const ResidentCycle<T>& S = R.S;
+  const LevelDev<T>& L = S.lv[q];
+  const int k0 = S.kb[q][R.rank], k1 = S.kb[q][R.rank + 1];
+  const int nq = (L.nx + 3) / 4;
+  const int n = (k1 - k0) * L.ny * nq;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int tq = t % nq;
+    const int j = (t / nq) % L.ny;
+    const int k = k0 + t / (nq * L.ny);
+    const int i = ((colour - j - k) & 3) + 4 * tq;
+    if (i >= L.nx) continue;
+    const LevelDev<T> Ln = R.at_plane(q, k + 1);
+    const int c = (j + 1) * (int)L.px + (i + 1);
+    const uint8_t fl = Ln.flags[c];
+    if (!(fl & (vel ? F_VFREE : F_ACT))) continue;
+    const DNb<T> u[3] = {R.view(q, 0, k + 1, c), R.view(q, 1, k + 1, c), R.view(q, 2, k + 1, c)};
+    const DNb<T> p = R.view(q, 3, k + 1, c);
+    if (vel)
+      node_vel_gs_rhs_v(Ln, c, fl, u, p, S.inv6nuh[q]);
+    else
+      node_pres_gs_rhs_v(Ln, c, fl, u, p, S.omc[q]);
+  }
+  cluster_sync();
+}
+
+template <class T>
+__device__ void r_uzawa(const Res<T>& R, int q) {
+  for (int c = 0; c < 4; ++c) r_colour(R, q, c, true);
+  for (int c = 2; c >= 0; --c) r_colour(R, q, c, true);
+  for (int c = 0; c < 4; ++c) r_colour(R, q, c, false);
+}
+
+// Residual of level q at fine node (i, j, k) (zero outside the lattice).
+template <class T>
+__device__ __forceinline__ void r_residual_at(const Res<T>& R, int q, int i, int j, int k, T r[4]) {
+  const LevelDev<T>& L = R.S.lv[q];
+  if (i < 0 || j < 0 || k < 0 || i >= L.nx || j >= L.ny || k >= L.nz) {
+    r[0] = r[1] = r[2] = r[3] = (T)0;
+    return;
+  }
+  const LevelDev<T> Ln = R.at_plane(q, k + 1);
+  const int c = (j + 1) * (int)L.px + (i + 1);
+  const uint8_t fl = Ln.flags[c];
+  const DNb<T> u[3] = {R.view(q, 0, k + 1, c), R.view(q, 1, k + 1, c), R.view(q, 2, k + 1, c)};
+  node_residual_v(Ln, c, fl, u, R.view(q, 3, k + 1, c), r);
+}
+
+// (F, G) of level q - 1 = P^T (residual of level q), (U, P) of level q - 1 = 0,
+// the arithmetic of node_restrict with the residual evaluated at the 15 fine
+// nodes.  The coarse level is resident (its nodes on this CTA's planes) or
+// the coarsest level in global memory (its nodes shared by the team).
+template <class T>
+__device__ void r_restrict(const Res<T>& R, int q) {
+  const ResidentCycle<T>& S = R.S;
+  const LevelDev<T>& Lc = S.lv[q - 1];
+  const bool resident = q - 1 >= 1;
+  int k0, k1, t0, ts;
+  if (resident) {
+    k0 = S.kb[q - 1][R.rank];
+    k1 = S.kb[q - 1][R.rank + 1];
+    t0 = threadIdx.x;
+    ts = blockDim.x;
+  } else {
+    k0 = 0;
+    k1 = Lc.nz;
+    t0 = R.rank * blockDim.x + threadIdx.x;
+    ts = S.nblocks * blockDim.x;
+  }
+  const int n = (k1 - k0) * Lc.ny * Lc.nx;
+  // Kuhn directions e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3
+  const int ox[7] = {1, 0, 0, 1, 0, 1, 1}, oy[7] = {0, 1, 0, 1, 1, 0, 1}, oz[7] = {0, 0, 1, 0, 1, 1, 1};
+  for (int t = t0; t < n; t += ts) {
+    const int I = t % Lc.nx;
+    const int J = (t / Lc.nx) % Lc.ny;
+    const int K = k0 + t / (Lc.nx * Lc.ny);
+    T r0[4], acc[4] = {0, 0, 0, 0};
+    r_residual_at(R, q, 2 * I, 2 * J, 2 * K, r0);
+#pragma unroll
+    for (int o = 0; o < 7; ++o) {
+      T rp[4], rm[4];
+      r_residual_at(R, q, 2 * I + ox[o], 2 * J + oy[o], 2 * K + oz[o], rp);
+      r_residual_at(R, q, 2 * I - ox[o], 2 * J - oy[o], 2 * K - oz[o], rm);
+#pragma unroll
+      for (int w = 0; w < 4; ++w) acc[w] += rp[w] + rm[w];
+    }
+    T s[4];
+#pragma unroll
+    for (int w = 0; w < 4; ++w) s[w] = r0[w] + (T)0.5 * acc[w];
+    LevelDev<T> C;
+    int64_t cc;
+    if (resident) {
+      C = R.at_plane(q - 1, K + 1);
+      cc = (J + 1) * Lc.px + (I + 1);
+    } else {
+      C = Lc;
+      cc = pidx(Lc.px, Lc.pxy, I, J, K);
+    }
+    const uint8_t fl = C.flags[cc];
+    const bool vf = fl & F_VFREE, ac = fl & F_ACT;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      C.f[d][cc] = vf ? s[d] : (T)0;
+      C.u[d][cc] = (T)0;
+    }
+    C.g[cc] = ac ? s[3] : (T)0;
+    C.p[cc] = (T)0;
+  }
+  cluster_sync();
+}
+
+// Fine (U, P) of level q += P (U, P) of level q - 1 (node_prolong_add).
+template <class T>
+__device__ void r_prolong(const Res<T>& R, int q) {
+  const ResidentCycle<T>& S = R.S;
+  const LevelDev<T>& Lf = S.lv[q];
+  const LevelDev<T>& Lc = S.lv[q - 1];
+  const bool resident = q - 1 >= 1;
+  const int k0 = S.kb[q][R.rank], k1 = S.kb[q][R.rank + 1];
+  const int n = (k1 - k0) * Lf.ny * Lf.nx;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = t % Lf.nx;
+    const int j = (t / Lf.nx) % Lf.ny;
+    const int k = k0 + t / (Lf.nx * Lf.ny);
+    const LevelDev<T> F = R.at_plane(q, k + 1);
+    const int cf = (j + 1) * (int)Lf.px + (i + 1);
+    const uint8_t fl = F.flags[cf];
+    if (!(fl & F_ACT)) continue;
+    const int a = i & 1, b = j & 1, e = k & 1;
+    const int I = i >> 1, J = j >> 1, K = k >> 1;
+    const bool mid = (a | b | e) != 0;
+    const T* cu0[4];
+    const T* cu1[4];
+    int64_t c0, c1;
+    if (resident) {
+      const LevelDev<T> A = R.at_plane(q - 1, K + 1), B = R.at_plane(q - 1, K + e + 1);
+      cu0[0] = A.u[0];
+      cu0[1] = A.u[1];
+      cu0[2] = A.u[2];
+      cu0[3] = A.p;
+      cu1[0] = B.u[0];
+      cu1[1] = B.u[1];
+      cu1[2] = B.u[2];
+      cu1[3] = B.p;
+      c0 = (J + 1) * Lc.px + (I + 1);
+      c1 = (J + b + 1) * Lc.px + (I + a + 1);
+    } else {
+      cu0[0] = cu1[0] = Lc.u[0];
+      cu0[1] = cu1[1] = Lc.u[1];
+      cu0[2] = cu1[2] = Lc.u[2];
+      cu0[3] = cu1[3] = Lc.p;
+      c0 = pidx(Lc.px, Lc.pxy, I, J, K);
+      c1 = pidx(Lc.px, Lc.pxy, I + a, J + b, K + e);
+    }
+    if (fl & F_VFREE) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const T v = mid ? (T)0.5 * (cu0[d][c0] + cu1[d][c1]) : cu0[d][c0];
+        F.u[d][cf] += v;
+      }
+    }
+    const T v = mid ? (T)0.5 * (cu0[3][c0] + cu1[3][c1]) : cu0[3][c0];
+    F.p[cf] += v;
+  }
+  cluster_sync();
+}
+
+template <class T>
+__device__ void r_coarse(const Res<T>& R) {
+  const ResidentCycle<T>& S = R.S;
+  if (coarse_fits_block(S.cs)) {
+    if (R.rank == 0) coarse::minres_team(Team{1}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
+  } else {
+    coarse::minres_team(Team{S.nblocks}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
+  }
+  cluster_sync();
+}
+
+template <class T>
+__global__ void __launch_bounds__(RT) k_resident(const __grid_constant__ ResidentCycle<T> S) {
+  pdl_enter();
+  extern __shared__ __align__(16) unsigned char sm[];
+  const Res<T> R{S, sm, blockIdx.x};
+  r_setup(R);
+  for (int q = S.nres; q >= 1; --q) {
+    for (int s = 0; s < S.nu_pre[q]; ++s) r_uzawa(R, q);
+    r_restrict(R, q);
+  }
+  r_coarse(R);
+  for (int q = 1; q <= S.nres; ++q) {
+    r_prolong(R, q);
+    for (int s = 0; s < S.nu_post[q]; ++s) r_uzawa(R, q);
+  }
+  r_writeback(R);
+}
+
+}  // namespace
+
+template <class T>
+bool plan_resident(ResidentCycle<T>& S, size_t smem_limit) {
+  const unsigned nb = S.nblocks;
+  if (nb < 1 || nb > RES_MAX_CTAS || S.nres < 1 || S.nres > RES_MAX_LEVELS) return false;
+  uint64_t off = 0;
+  for (int q = 1; q <= S.nres; ++q) {
+    S.tab[q] = (uint32_t)off;
+    off = align16(off + sizeof(void*) * RES_TAB_FIELDS * (uint64_t)(S.lv[q].nz + 2));
+  }
+  int64_t zero_bytes = 0;
+  for (int q = 1; q <= S.nres; ++q) {
+    const LevelDev<T>& L = S.lv[q];
+    int mx = 0;
+    for (unsigned r = 0; r <= nb; ++r) S.kb[q][r] = (int)(((int64_t)r * L.nz + nb - 1) / nb);
+    for (unsigned r = 0; r < nb; ++r) mx = std::max(mx, S.kb[q][r + 1] - S.kb[q][r]);
+    S.maxpl[q] = mx;
+    zero_bytes = std::max<int64_t>(zero_bytes, (int64_t)L.pxy * (int64_t)std::max<size_t>(sizeof(T), 2));
+  }
+  S.zero = (uint32_t)off;
+  off = align16(off + zero_bytes);
+  for (int q = 1; q <= S.nres; ++q) {
+    const int64_t fb = (int64_t)S.maxpl[q] * S.lv[q].pxy;
+    S.blk[q] = (uint32_t)off;
+    off = align16(off + align16(sizeof(T) * RES_FIELDS * fb + fb) + 2 * fb);
+  }
+  S.smem = (uint32_t)off;
+  return off <= smem_limit;
+}
+
+template <class T>
+cudaError_t launch_resident_cycle(const ResidentCycle<T>& S, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(S.nblocks, 1, 1);
+  cfg.blockDim = dim3(RT, 1, 1);
+  cfg.dynamicSmemBytes = S.smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = S.nblocks;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, k_resident<T>, S);
+}
+
+template <class T>
+unsigned prepare_resident(size_t& smem_limit) {
+  int dev = 0, optin = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa{};
+  cudaFuncGetAttributes(&fa, k_resident<T>);
+  smem_limit = optin > (int)fa.sharedSizeBytes ? (size_t)(optin - fa.sharedSizeBytes) : 0;
+  cudaFuncSetAttribute(k_resident<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_limit);
+  unsigned nb = 8;
+  if (cudaFuncSetAttribute(k_resident<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(16, 1, 1);
+    cfg.blockDim = dim3(RT, 1, 1);
+    cfg.dynamicSmemBytes = smem_limit;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 16;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, (const void*)k_resident<T>, &cfg) == cudaSuccess && n >= 1) nb = 16;
+  }
+  cudaGetLastError();
+  return nb;
+}
+
+template bool plan_resident<float>(ResidentCycle<float>&, size_t);
+template bool plan_resident<double>(ResidentCycle<double>&, size_t);
+template cudaError_t launch_resident_cycle<float>(const ResidentCycle<float>&, cudaStream_t);
+template cudaError_t launch_resident_cycle<double>(const ResidentCycle<double>&, cudaStream_t);
+template unsigned prepare_resident<float>(size_t&);
+template unsigned prepare_resident<double>(size_t&);
+
+}  // namespace hhg

@@ -149,6 +149,20 @@ def test_smoother_pieces(pkg, name, level, tiles):
     MG._gs_sweep(L.C, L.C_diag, p, rp, H.colours_p[level], (0, 1, 2, 3), relax=H.opt.omega)
     _, gp = _read_up(mesh, H, level)
     assert rel_err(gp, p) < TOL64
+    # the same sweeps with the right-hand sides formed at each node
+    _load(mesh, H, level, st)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(level, "vel_forward_f")
+    ru = np.stack([f[d] - L.BT[d] @ p for d in range(3)])
+    for d in range(3):
+        MG._gs_sweep(L.A, L.A_diag, u[d], ru[d], H.colours_u[level], (0, 1, 2, 3))
+    gu, _ = _read_up(mesh, H, level)
+    assert rel_err(gu, u) < TOL64
+    mesh.level_op(level, "pres_sweep_f")
+    rp = sum(L.B[d] @ u[d] for d in range(3)) - g
+    MG._gs_sweep(L.C, L.C_diag, p, rp, H.colours_p[level], (0, 1, 2, 3), relax=H.opt.omega)
+    _, gp = _read_up(mesh, H, level)
+    assert rel_err(gp, p) < TOL64
     # whole Uzawa steps
     _load(mesh, H, level, st)
     mesh.level_op(level, "uzawa_step", count=3)
@@ -388,15 +402,17 @@ def test_adjoint_gradient_matches_oracle(pkg):
 
 FUSED = {"block": dict(fuse_coarse_levels=1),
          "cluster16": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=16),
-         "cluster4": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=4)}
+         "cluster4": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=4),
+         "resident16": dict(fuse_coarse_levels=2, team_blocks=16),
+         "resident8": dict(fuse_coarse_levels=2, team_blocks=8)}
 
 
 @pytest.mark.parametrize("fused", sorted(FUSED))
 @pytest.mark.parametrize("name,level,coarsest", [("cube", 5, 2), ("cube", 3, 2), ("channel", 2, 0), ("partial", 3, 1)])
 def test_fused_coarse_levels_match_per_level_kernels(pkg, name, level, coarsest, fused):
-    """The fused cycle of the coarse levels (one block, or a thread-block
-    cluster) does the same arithmetic as the per-level kernels (FP64 and
-    FP32 hierarchies)."""
+    """The fused cycle of the coarse levels (one block, a thread-block
+    cluster, or levels resident in a cluster's shared memory) does the same
+    arithmetic as the per-level kernels (FP64 and FP32 hierarchies)."""
     macro = macro_by_name(name)
     meshes = [pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=coarsest,
                        coarse_minres_max=30, **o) for o in (FUSED[fused], dict(fuse_coarse_levels=0))]
