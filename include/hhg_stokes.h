@@ -96,7 +96,9 @@ typedef struct hhg_options {
   int32_t tile_min_nodes;    /* levels of at least this many lattice nodes run the colour sweeps
                                 on shared-memory tiles staged by tensor copies; 0 = default
                                 (never), -1 = never */
-  int32_t reserved[3];
+  int32_t ir_fixed_point;    /* FP32+IR mode: 1 (default) evaluates the FP64 refinement residual's
+                                regular-node stencils exactly in 64-bit fixed point, 0 in FP64 */
+  int32_t reserved[2];
 } hhg_options;
 
 /* Per-solve statistics. */

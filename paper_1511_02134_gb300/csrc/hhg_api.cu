@@ -77,6 +77,9 @@ struct hhg_mesh {
   double* d_partial = nullptr;
   double* d_scalars = nullptr;  // [0] norm2, [1..2] moments, [3..4] g-mean, [5..7] coarse info
   double* h_scalars = nullptr;  // pinned mirror
+  unsigned long long* d_fxmax = nullptr;  // per-field |x| maxima of the fixed-point residual
+  FxIterate fx{};                          // fixed-point finest iterate (FP32+IR mode)
+  int64_t* d_fx = nullptr;
   double* d_coarse = nullptr;  // coarse-solve scratch
   CoarseSys coarse_sys{};       // compact coarsest-level system (device arrays)
   void* d_coarse_sys = nullptr;  // one allocation holding its arrays
@@ -156,6 +159,14 @@ int ensure32(hhg_mesh* M) {
     bind_fields(H.d32, H.mem32, H.nalloc);
     if (H.tiled && (rc = make_tile_maps<float>(H.d32, H.tm32, M->err))) return rc;
   }
+  if (M->opt.ir_fixed_point && !M->d_fx) {
+    const LevelHost& H = M->lv[M->finest];
+    int rc = dalloc(M, (void**)&M->d_fx, sizeof(int64_t) * 4 * (size_t)H.nalloc);
+    if (rc) return rc;
+    for (int d = 0; d < 3; ++d) M->fx.u[d] = M->d_fx + (int64_t)d * H.nalloc;
+    M->fx.p = M->d_fx + 3 * H.nalloc;
+    if ((rc = dalloc(M, (void**)&M->d_fxmax, 4 * sizeof(unsigned long long)))) return rc;
+  }
   return HHG_OK;
 }
 
@@ -223,6 +234,8 @@ void enq_pres_sweep_f(hhg_mesh* M, int l) {
 // result is identical).  FP32 forms f - B^T p at each node inside the colour
 // kernels; FP64, bound by its arithmetic rate, stores it once per step.  The
 // pressure colours form B u - g at each node (every node is updated once).
+// The last velocity colour and the first pressure colour share a launch
+// (k_vel_pres_colour0): 10 launches per step.
 template <class T>
 void enq_uzawa(hhg_mesh* M, int l) {
   const LevelDev<T>& L = view<T>(M, l);
@@ -230,25 +243,29 @@ void enq_uzawa(hhg_mesh* M, int l) {
   const TileMaps& tm = maps<T>(M, l);
   const int kz = M->lv[l].kz;
   unsigned* err = err_word(M);
-  if (sizeof(T) == 4) {
-    for (int q = 0; q < 7; ++q) {
-      const int colour = q < 4 ? q : 6 - q;
-      tiled ? launch_vel_colour_tile<T>(tm, L, colour, kz, err, M->stream)
-            : launch_vel_colour_rhs<T>(L, colour, M->stream);
-    }
-    M->launches += 7;
-  } else {
+  const bool ru = sizeof(T) != 4;
+  if (ru) {
     launch_vel_rhs<T>(L, M->stream);
+    M->launches += 1;
+  }
+  if (tiled) {
     for (int q = 0; q < 7; ++q) {
       const int colour = q < 4 ? q : 6 - q;
-      tiled ? launch_vel_colour_ru_tile<T>(tm, L, colour, kz, err, M->stream)
-            : launch_vel_colour<T>(L, colour, M->stream);
+      ru ? launch_vel_colour_ru_tile<T>(tm, L, colour, kz, err, M->stream)
+         : launch_vel_colour_tile<T>(tm, L, colour, kz, err, M->stream);
     }
-    M->launches += 8;
+    for (int q = 0; q < 4; ++q) launch_pres_colour_tile<T>(tm, L, q, kz, err, M->stream);
+    M->launches += 11;
+    return;
   }
-  for (int q = 0; q < 4; ++q)
-    tiled ? launch_pres_colour_tile<T>(tm, L, q, kz, err, M->stream) : launch_pres_colour_rhs<T>(L, q, M->stream);
-  M->launches += 4;
+  // velocity colours 0 1 2 3 2 1, then backward colour 0 with pressure colour 0, then pressure 1 2 3
+  for (int q = 0; q < 6; ++q) {
+    const int colour = q < 4 ? q : 6 - q;
+    ru ? launch_vel_colour<T>(L, colour, M->stream) : launch_vel_colour_rhs<T>(L, colour, M->stream);
+  }
+  launch_vel_pres_colour0<T>(L, ru, M->stream);
+  for (int q = 1; q < 4; ++q) launch_pres_colour_rhs<T>(L, q, M->stream);
+  M->launches += 10;
 }
 
 template <class T>
@@ -298,6 +315,7 @@ void fill_resident(hhg_mesh* M, ResidentCycle<T>& S, int top) {
   for (int q = 0; q <= S.nres; ++q) {
     const int l = M->coarsest + q;
     S.lv[q] = view<T>(M, l);
+    S.ncls[q] = M->lv[l].n_classes;
     S.nu_pre[q] = nu_steps<T>(M, l, true);
     S.nu_post[q] = nu_steps<T>(M, l, false);
     S.inv6nuh[q] = (T)(1.0 / (6.0 * (double)S.lv[q].nuh));
@@ -362,6 +380,19 @@ void enq_cycle64(hhg_mesh* M) {
 
 // FP32+IR cycle body: correction V-cycle in FP32 from zero on the FP32
 // residual, x += e in FP64, projection in FP64, FP64 residual -> FP32 rhs.
+// FP64 residual of the finest FP64 iterate into the FP32 right-hand side,
+// its squared norm into d_scalars[0].
+void enq_ir_residual(hhg_mesh* M) {
+  LevelHost& H = M->lv[M->finest];
+  if (M->opt.ir_fixed_point) {
+    launch_ir_residual_fx(H.d64, M->fx, H.d32, M->d_fxmax, M->d_partial, M->d_scalars, M->stream);
+    M->launches += 4;
+  } else {
+    launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
+    M->launches += 2;
+  }
+}
+
 void enq_cycle32(hhg_mesh* M) {
   LevelHost& H = M->lv[M->finest];
   launch_zero<float>(H.d32, 0, M->stream);
@@ -369,8 +400,7 @@ void enq_cycle32(hhg_mesh* M) {
   launch_ir_update(H.d64, H.d32, M->stream);
   M->launches += 1;
   if (!M->macro.has_outflow) enq_project<double>(M, M->finest);
-  launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
-  M->launches += 2;
+  enq_ir_residual(M);
 }
 
 // Reads the error word copied with the scalar block: a tiled sweep whose
@@ -421,8 +451,7 @@ int residual_norm2(hhg_mesh* M, int mode, double* norm2) {
     launch_residual_norm2<double>(H.d64, M->d_partial, M->d_scalars, M->stream);
     M->launches += 3;
   } else {
-    launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
-    M->launches += 2;
+    enq_ir_residual(M);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
@@ -533,6 +562,8 @@ void release(hhg_mesh* M) {
   cudaFree(M->d_partial);
   cudaFree(M->d_scalars);
   cudaFree(M->d_coarse);
+  cudaFree(M->d_fx);
+  cudaFree(M->d_fxmax);
   cudaFree(M->d_coarse_sys);
   cudaFree(M->d_backup);
   if (M->h_scalars) cudaFreeHost(M->h_scalars);
@@ -561,6 +592,7 @@ void hhg_default_options(hhg_options* opt) {
   opt->coarse_cg_rtol = 1e-3;
   opt->use_graphs = 1;
   opt->fuse_coarse_levels = 2;
+  opt->ir_fixed_point = 1;
 }
 
 const char* hhg_strerror(int code) {

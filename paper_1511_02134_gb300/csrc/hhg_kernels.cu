@@ -71,6 +71,28 @@ __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
   node_vel_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
+// The last velocity colour of a step (backward colour 0) and the first
+// pressure colour in one launch.  A pressure node of colour 0 reads the
+// velocity of its neighbours, which are of the other colours and final
+// after the earlier colour launches, and its own velocity, which the same
+// thread has just updated; the velocity update reads the old pressure of
+// the node and of its neighbours, none of which this launch changes before
+// the node's own pressure update.  So the sequential order is kept.
+// RU: the velocity right-hand side is read from RU (FP64 path) instead of
+// being formed at the node.
+template <class T, bool RU>
+__global__ void k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
+  pdl_enter();
+  int i, j, k;
+  if (!colour_node(L, 0, i, j, k)) return;
+  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  if (RU)
+    node_vel_gs(L, c, inv6nuh);
+  else
+    node_vel_gs_rhs(L, c, inv6nuh);
+  node_pres_gs_rhs(L, c, omega_over_6c);
+}
+
 template <class T>
 __global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
   pdl_enter();
@@ -345,6 +367,132 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
   block_reduce_store<1>(v, partial);
 }
 
+// ---- the refinement residual in 64-bit fixed point ------------------------------
+// On GB300 an FP64 operation costs about 58 FP32 or integer operations, and
+// the FP64 residual of a regular node takes about 130 of them.  Its stencils
+// are integer combinations of the iterate (the 7-point Laplacian for A and
+// C, twelve times the divergence differences for B and B^T), so they are
+// evaluated exactly in 64-bit integers on the iterate quantized per field to
+// X = round(x 2^e), with 2^e the power of two that puts max |x| just below
+// 2^55: every sum stays below 2^62.  The quantization error is at most
+// 2^-56 max |x| per value, of the order of the rounding of the FP64
+// evaluation itself.  Each stencil result then takes one conversion and one
+// fused multiply-add in FP64 (its scale folded into the operator constant).
+// Boundary nodes (class rows) keep the FP64 evaluation.
+
+// max |x| of u_0, u_1, u_2, p as bit patterns of non-negative doubles, which
+// order like unsigned integers; mx[0..3] start at zero.
+__global__ void k_ir_absmax(LevelDev<double> X, unsigned long long* mx) {
+  pdl_enter();
+  __shared__ double sh[4][REDUCE_THREADS / 32];
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) m[d] = fmax(m[d], fabs(X.u[d][q]));
+    m[3] = fmax(m[3], fabs(X.p[q]));
+  }
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    double x = m[w];
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) sh[w][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0.0;
+    for (int q = 0; q < REDUCE_THREADS / 32; ++q) x = fmax(x, sh[threadIdx.x][q]);
+    atomicMax(&mx[threadIdx.x], (unsigned long long)__double_as_longlong(x));
+  }
+}
+
+// 2^e with max |x| 2^e < 2^55 (e capped so that 2^e stays finite).
+__device__ __forceinline__ int fx_exponent(unsigned long long bits) {
+  const double m = __longlong_as_double((long long)bits);
+  if (!(m > 0.0)) return 0;
+  int E;
+  frexp(m, &E);  // m < 2^E
+  return 55 - max(E, -940);
+}
+
+__global__ void k_ir_quantize(LevelDev<double> X, FxIterate Q, const unsigned long long* mx) {
+  pdl_enter();
+  double s[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) s[f] = ldexp(1.0, fx_exponent(mx[f]));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Q.u[d][q] = __double2ll_rn(X.u[d][q] * s[d]);
+    Q.p[q] = __double2ll_rn(X.p[q] * s[3]);
+  }
+}
+
+// (F, G) - K (U, P) in FP64 from the fixed-point iterate on regular nodes,
+// FP32 output, and the partial sums of its squared norm.
+__global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float> E, const unsigned long long* mx,
+                                 double* partial) {
+  pdl_enter();
+  double is[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) is[f] = ldexp(1.0, -fx_exponent(mx[f]));
+  double kA[3], kB[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    kA[d] = X.nuh * is[d];
+    kB[d] = X.h2 * (1.0 / 12.0) * is[d];
+  }
+  const double kBT = X.h2 * (1.0 / 12.0) * is[3], kC = X.c * is[3];
+  double v[1] = {0.0};
+  const int64_t n = (int64_t)X.nx * X.ny * X.nz;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) {
+    const int i = (int)(q % X.nx);
+    const int j = (int)((q / X.nx) % X.ny);
+    const int k = (int)(q / ((int64_t)X.nx * X.ny));
+    const int64_t c = pidx(X.px, X.pxy, i, j, k);
+    const uint8_t fl = X.flags[c];
+    double r[4];
+    if (!(fl & F_IRR)) {
+      const GNb<int64_t> gu[3] = {gnb(Q.u[0], c, X.px, X.pxy), gnb(Q.u[1], c, X.px, X.pxy),
+                                  gnb(Q.u[2], c, X.px, X.pxy)};
+      const GNb<int64_t> gp = gnb(Q.p, c, X.px, X.pxy);
+      if (fl & F_VFREE) {
+        int64_t ibt[3];
+        div12_all(diff7v<int64_t>(gp), ibt);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const int64_t ia = 6 * gu[d](0, 0, 0) - nb6v(gu[d]);
+          r[d] = (X.f[d][c] - kA[d] * (double)ia) + kBT * (double)ibt[d];
+        }
+      } else {
+        r[0] = r[1] = r[2] = 0.0;
+      }
+      if (fl & F_ACT) {
+        const int64_t ic = 6 * gp(0, 0, 0) - nb6v(gp);
+        double b = 0.0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) b += kB[d] * (double)div12(diff7v<int64_t>(gu[d]), d);
+        r[3] = (X.g[c] - b) + kC * (double)ic;
+      } else {
+        r[3] = 0.0;
+      }
+    } else {
+      const GNb<double> u[3] = {gnb(X.u[0], c, X.px, X.pxy), gnb(X.u[1], c, X.px, X.pxy),
+                                gnb(X.u[2], c, X.px, X.pxy)};
+      node_residual_v(X, c, fl, u, gnb(X.p, c, X.px, X.pxy), r);
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      E.f[d][c] = (float)r[d];
+      v[0] += r[d] * r[d];
+    }
+    E.g[c] = (float)r[3];
+    v[0] += r[3] * r[3];
+  }
+  block_reduce_store<1>(v, partial);
+}
+
 __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
   pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -453,6 +601,16 @@ void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   launch_k(k_vel_colour_rhs<T>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
 }
 template <class T>
+void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
+  const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
+  const T w = (T)((double)L.omega / (6.0 * (double)L.c));
+  if (ru)
+    launch_k(k_vel_pres_colour0<T, true>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+  else
+    launch_k(k_vel_pres_colour0<T, false>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+}
+
+template <class T>
 void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
   launch_k(k_pres_colour_rhs<T>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
@@ -514,6 +672,15 @@ void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, dou
   launch_k(k_ir_residual, REDUCE_BLOCKS, REDUCE_THREADS, s, x, e, partial);
   launch_k(k_final_sum<1>, 1, 32, s, partial, REDUCE_BLOCKS, out);
 }
+void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e,
+                           unsigned long long* mx, double* partial, double* out, cudaStream_t s) {
+  cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned long long), s);
+  launch_k(k_ir_absmax, REDUCE_BLOCKS, REDUCE_THREADS, s, x, mx);
+  launch_k(k_ir_quantize, flat_blocks(x.nalloc), 256, s, x, q, (const unsigned long long*)mx);
+  launch_k(k_ir_residual_fx, REDUCE_BLOCKS, REDUCE_THREADS, s, x, q, e, (const unsigned long long*)mx, partial);
+  launch_k(k_final_sum<1>, 1, 32, s, (const double*)partial, REDUCE_BLOCKS, out);
+}
+
 void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
   launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e);
 }
@@ -548,6 +715,7 @@ void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s)
   template void launch_pres_rhs<T>(const LevelDev<T>&, cudaStream_t);                                   \
   template void launch_vel_colour_rhs<T>(const LevelDev<T>&, int, cudaStream_t);                        \
   template void launch_pres_colour_rhs<T>(const LevelDev<T>&, int, cudaStream_t);                       \
+  template void launch_vel_pres_colour0<T>(const LevelDev<T>&, bool, cudaStream_t);                      \
   template void launch_pres_colour<T>(const LevelDev<T>&, int, cudaStream_t);                           \
   template void launch_residual<T>(const LevelDev<T>&, cudaStream_t);                                   \
   template void launch_restrict<T>(const LevelDev<T>&, const LevelDev<T>&, cudaStream_t);               \

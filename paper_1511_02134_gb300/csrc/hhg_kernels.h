@@ -19,6 +19,9 @@ template <class T> void launch_pres_colour(const LevelDev<T>& L, int colour, cud
 // velocity, B u - g for pressure) instead of reading RU / RP.
 template <class T> void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s);
 template <class T> void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s);
+// Backward velocity colour 0 and pressure colour 0 in one launch (the
+// velocity right-hand side read from RU when ru, else formed at the node).
+template <class T> void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s);
 // The same colour sweeps on shared-memory tiles staged by tensor copies
 // (hhg_tiled.cu): f - B^T p at the node, stored RU, and B u - g at the node.
 // TileMaps holds the tensor maps of u_0, u_1, u_2, p of one level and
@@ -79,6 +82,15 @@ void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStr
 void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
                         cudaStream_t s);
 void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s);
+// The same residual with the regular-node stencils evaluated exactly in
+// 64-bit fixed point (hhg_kernels.cu): per-field |x| maxima into mx[0..4)
+// (zeroed first), quantization into q, residual, norm into out[0].
+struct FxIterate {
+  int64_t* u[3];
+  int64_t* p;
+};
+void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e,
+                           unsigned long long* mx, double* partial, double* out, cudaStream_t s);
 
 // Layout conversion between contiguous (n, 3)/(n,) arrays and padded fields.
 // mask: nodes whose value is kept (others get 0); 0 = keep all.
@@ -178,7 +190,8 @@ void launch_small_cycle(const SmallCycle<T>& S, cudaStream_t s);
 // whose u, p it writes back to global memory) down to the coarse solve and
 // back up.  Each CTA's dynamic shared memory holds, at the byte offsets
 // below, a table of plane pointers per level (RES_TAB_FIELDS rows of pz
-// generic pointers), one zero plane and a block per level: RES_FIELDS fields
+// generic pointers), a copy of its class-row table, one zero plane and a
+// block per level: RES_FIELDS fields
 // of type T (u_0, u_1, u_2, p, f_0, f_1, f_2, g), then the node flags (bytes)
 // and stencil classes (16 bit), each maxpl[q] padded planes.
 constexpr int RES_MAX_LEVELS = 4;
@@ -205,7 +218,9 @@ struct ResidentCycle {
   T omc[RES_MAX_LEVELS + 1];
   int kb[RES_MAX_LEVELS + 1][RES_MAX_CTAS + 1];
   int maxpl[RES_MAX_LEVELS + 1];
+  int ncls[RES_MAX_LEVELS + 1];  // boundary stencil classes of the level (table rows 0..ncls)
   uint32_t tab[RES_MAX_LEVELS + 1];
+  uint32_t wts[RES_MAX_LEVELS + 1];  // byte offset of the level's class table copy
   uint32_t blk[RES_MAX_LEVELS + 1];
   uint32_t zero;
   uint32_t smem;

@@ -15,7 +15,8 @@
 // The per-node arithmetic is the view form of the grid kernels' bodies
 // (hhg_node_ops.cuh): the node's own fields are reached through a LevelDev
 // whose field pointers point at the node's plane, its neighbours through
-// plane-pointer tables.  The residual is evaluated inside the restriction
+// plane-pointer tables, the boundary-class rows from a copy of the level's
+// table in shared memory.  The residual is evaluated inside the restriction
 // (the 15 fine nodes of each coarse node), so no residual fields are stored.
 #include <cooperative_groups.h>
 
@@ -62,6 +63,7 @@ struct Res {
   // node (i, j) of that plane is entry (j + 1) px + (i + 1).
   __device__ __forceinline__ LevelDev<T> at_plane(int q, int z) const {
     LevelDev<T> L = S.lv[q];
+    L.wt = reinterpret_cast<const T*>(sm + S.wts[q]);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       L.u[d] = row_ptr<T>(q, d, z);
@@ -120,6 +122,12 @@ __device__ void r_setup(const Res<T>& R) {
       tab[e] = ptr;
     }
   }
+  // class-row tables of the resident levels
+  for (int q = 1; q <= S.nres; ++q) {
+    T* w = reinterpret_cast<T*>(R.sm + S.wts[q]);
+    const int n = (S.ncls[q] + 1) * W_STRIDE;
+    for (int e = threadIdx.x; e < n; e += blockDim.x) w[e] = S.lv[q].wt[e];
+  }
   __syncthreads();
   // flags and classes of every resident level, fields of the top level
   for (int q = 1; q <= S.nres; ++q) {
@@ -171,9 +179,11 @@ __device__ void r_writeback(const Res<T>& R) {
 // ---- phases --------------------------------------------------------------------
 
 // One colour phase of level q on this CTA's planes: velocity Gauss-Seidel with
-// f - B^T p formed at the node, or the relaxed pressure update with B u - g.
+// f - B^T p formed at the node (what = 0), the relaxed pressure update with
+// B u - g (what = 1), or both at each node (what = 2: the last velocity
+// colour of a step with the first pressure colour).
 template <class T>
-__device__ void r_colour(const Res<T>& R, int q, int colour, bool vel) {
+__device__ void r_colour(const Res<T>& R, int q, int colour, int what) {
   const ResidentCycle<T>& S = R.S;
   const LevelDev<T>& L = S.lv[q];
   const int k0 = S.kb[q][R.rank], k1 = S.kb[q][R.rank + 1];
@@ -188,22 +198,20 @@ __device__ void r_colour(const Res<T>& R, int q, int colour, bool vel) {
     const LevelDev<T> Ln = R.at_plane(q, k + 1);
     const int c = (j + 1) * (int)L.px + (i + 1);
     const uint8_t fl = Ln.flags[c];
-    if (!(fl & (vel ? F_VFREE : F_ACT))) continue;
     const DNb<T> u[3] = {R.view(q, 0, k + 1, c), R.view(q, 1, k + 1, c), R.view(q, 2, k + 1, c)};
     const DNb<T> p = R.view(q, 3, k + 1, c);
-    if (vel)
-      node_vel_gs_rhs_v(Ln, c, fl, u, p, S.inv6nuh[q]);
-    else
-      node_pres_gs_rhs_v(Ln, c, fl, u, p, S.omc[q]);
+    if (what != 1 && (fl & F_VFREE)) node_vel_gs_rhs_v(Ln, c, fl, u, p, S.inv6nuh[q]);
+    if (what != 0 && (fl & F_ACT)) node_pres_gs_rhs_v(Ln, c, fl, u, p, S.omc[q]);
   }
   cluster_sync();
 }
 
 template <class T>
 __device__ void r_uzawa(const Res<T>& R, int q) {
-  for (int c = 0; c < 4; ++c) r_colour(R, q, c, true);
-  for (int c = 2; c >= 0; --c) r_colour(R, q, c, true);
-  for (int c = 0; c < 4; ++c) r_colour(R, q, c, false);
+  for (int c = 0; c < 4; ++c) r_colour(R, q, c, 0);
+  for (int c = 2; c >= 1; --c) r_colour(R, q, c, 0);
+  r_colour(R, q, 0, 2);
+  for (int c = 1; c < 4; ++c) r_colour(R, q, c, 1);
 }
 
 // Residual of level q at fine node (i, j, k) (zero outside the lattice).
@@ -379,6 +387,10 @@ bool plan_resident(ResidentCycle<T>& S, size_t smem_limit) {
   for (int q = 1; q <= S.nres; ++q) {
     S.tab[q] = (uint32_t)off;
     off = align16(off + sizeof(void*) * RES_TAB_FIELDS * (uint64_t)(S.lv[q].nz + 2));
+  }
+  for (int q = 1; q <= S.nres; ++q) {
+    S.wts[q] = (uint32_t)off;
+    off = align16(off + sizeof(T) * (uint64_t)(S.ncls[q] + 1) * W_STRIDE);
   }
   int64_t zero_bytes = 0;
   for (int q = 1; q <= S.nres; ++q) {

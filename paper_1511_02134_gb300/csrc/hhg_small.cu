@@ -48,11 +48,13 @@ __device__ void b_residual(const Team& tm, const LevelDev<T>& L) {
   tm.sync();
 }
 
-// One colour phase: velocity (vel = true) or pressure Gauss-Seidel, with the
+// One colour phase: velocity Gauss-Seidel (what = 0), pressure Gauss-Seidel
+// (what = 1), or both at each node of the colour (what = 2: the last
+// velocity colour of a step with the first pressure colour), with the
 // right-hand side formed at each node (FP32 velocity, and pressure), or the
 // velocity right-hand side read from RU (FP64).
 template <class T>
-__device__ void b_colour(const Team& tm, const LevelDev<T>& L, int colour, bool vel, T w) {
+__device__ void b_colour(const Team& tm, const LevelDev<T>& L, int colour, int what, T inv6nuh, T omc) {
   const int nq = (L.nx + 3) / 4;
   const int n = nq * L.ny * L.nz;
   for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) {
@@ -62,26 +64,27 @@ __device__ void b_colour(const Team& tm, const LevelDev<T>& L, int colour, bool 
     const int i = ((colour - j - k) & 3) + 4 * t;
     if (i >= L.nx) continue;
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
-    if (vel) {
+    if (what != 1) {
       if (sizeof(T) == 4)
-        node_vel_gs_rhs(L, c, w);
+        node_vel_gs_rhs(L, c, inv6nuh);
       else
-        node_vel_gs(L, c, w);
-    } else {
-      node_pres_gs_rhs(L, c, w);
+        node_vel_gs(L, c, inv6nuh);
     }
+    if (what != 0) node_pres_gs_rhs(L, c, omc);
   }
   tm.sync();
 }
 
 // The same step sequence as the grid path (backward colour 3 skipped: it
-// would repeat the forward one exactly).
+// would repeat the forward one exactly; backward colour 0 shares its phase
+// with pressure colour 0).
 template <class T>
 __device__ void b_uzawa(const Team& tm, const LevelDev<T>& L, T inv6nuh, T omc) {
   if (sizeof(T) != 4) b_vel_rhs(tm, L);
-  for (int q = 0; q < 4; ++q) b_colour(tm, L, q, true, inv6nuh);
-  for (int q = 2; q >= 0; --q) b_colour(tm, L, q, true, inv6nuh);
-  for (int q = 0; q < 4; ++q) b_colour(tm, L, q, false, omc);
+  for (int q = 0; q < 4; ++q) b_colour(tm, L, q, 0, inv6nuh, omc);
+  for (int q = 2; q >= 1; --q) b_colour(tm, L, q, 0, inv6nuh, omc);
+  b_colour(tm, L, 0, 2, inv6nuh, omc);
+  for (int q = 1; q < 4; ++q) b_colour(tm, L, q, 1, inv6nuh, omc);
 }
 
 template <class T>
