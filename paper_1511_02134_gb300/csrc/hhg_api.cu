@@ -332,7 +332,7 @@ template <class T>
 void enq_resident_cycle(hhg_mesh* M) {
   ResidentCycle<T> S;
   fill_resident<T>(M, S, M->res_top[sizeof(T) == 4]);
-  plan_resident<T>(S, M->res_smem[sizeof(T) == 4]);
+  plan_resident<T>(S, M->res_smem[sizeof(T) == 4], M->res_nb[sizeof(T) == 4]);
   launch_resident_cycle<T>(S, M->stream);
   M->launches += 1;
 }
@@ -859,11 +859,11 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
         if (pr) {
           ResidentCycle<float> S;
           fill_resident<float>(M, S, l);
-          fits = plan_resident<float>(S, M->res_smem[pr]);
+          fits = plan_resident<float>(S, M->res_smem[pr], M->res_nb[pr]);
         } else {
           ResidentCycle<double> S;
           fill_resident<double>(M, S, l);
-          fits = plan_resident<double>(S, M->res_smem[pr]);
+          fits = plan_resident<double>(S, M->res_smem[pr], M->res_nb[pr]);
         }
         if (fits) {
           M->res_top[pr] = l;

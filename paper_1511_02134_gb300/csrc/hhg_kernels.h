@@ -182,8 +182,9 @@ template <class T>
 void launch_small_cycle(const SmallCycle<T>& S, cudaStream_t s);
 // Cluster-resident cycle of the coarse levels (hhg_resident.cu): levels
 // lv[1..nres] live in the shared memory of one thread-block cluster of
-// nblocks CTAs, split into runs of z-planes (CTA r holds node planes
-// [kb[q][r], kb[q][r+1]) of level q, kb[q][r] = ceil(r nz / nblocks)), and are
+// nblocks CTAs, split into runs of z-planes over the first nbq[q] CTAs (CTA r
+// holds node planes [kb[q][r], kb[q][r+1]) of level q, kb[q][r] =
+// ceil(r nz / nbq[q])), and are
 // read across CTAs through distributed shared memory; lv[0], the coarsest
 // level, stays in global memory for the coarse solve.  The kernel runs the
 // part of the V_var cycle from lv[nres] (whose u, p, f, g it reads from and
@@ -216,6 +217,7 @@ struct ResidentCycle {
   int nu_post[RES_MAX_LEVELS + 1];
   T inv6nuh[RES_MAX_LEVELS + 1];
   T omc[RES_MAX_LEVELS + 1];
+  int nbq[RES_MAX_LEVELS + 1];  // CTAs holding level q (the first nbq[q] of the cluster)
   int kb[RES_MAX_LEVELS + 1][RES_MAX_CTAS + 1];
   int maxpl[RES_MAX_LEVELS + 1];
   int ncls[RES_MAX_LEVELS + 1];  // boundary stencil classes of the level (table rows 0..ncls)
@@ -229,10 +231,11 @@ struct ResidentCycle {
   CoarseParams prm;
   double* info;
 };
-// Plans the shared-memory layout of levels lv[1..nres] for nblocks CTAs
-// (fills kb, maxpl, tab, blk, zero, smem); false if it exceeds the limit.
+// Plans the shared-memory layout of levels lv[1..nres]: the CTAs per level
+// (nbq, at most max_ctas; nblocks = the largest), kb, maxpl, and the offsets;
+// false if it cannot fit smem_limit bytes per CTA.
 template <class T>
-bool plan_resident(ResidentCycle<T>& S, size_t smem_limit);
+bool plan_resident(ResidentCycle<T>& S, size_t smem_limit, unsigned max_ctas);
 template <class T>
 cudaError_t launch_resident_cycle(const ResidentCycle<T>& S, cudaStream_t s);
 // Cluster size (16, else 8) and the dynamic shared memory available to one

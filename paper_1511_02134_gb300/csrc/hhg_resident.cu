@@ -83,6 +83,17 @@ struct Res {
 
 __device__ __forceinline__ void cluster_sync() { cg::this_cluster().sync(); }
 
+// End of a phase of level q: the cluster barrier when the level is spread
+// over several CTAs, the block barrier when the first CTA holds it alone
+// (the other CTAs skip the level's phases).
+template <class T>
+__device__ __forceinline__ void level_sync(const ResidentCycle<T>& S, int q) {
+  if (S.nbq[q] > 1)
+    cluster_sync();
+  else
+    __syncthreads();
+}
+
 // ---- set-up: plane tables, zero plane, flags / classes, top-level fields ------
 
 template <class T>
@@ -106,7 +117,7 @@ __device__ void r_setup(const Res<T>& R) {
       void* ptr = R.sm + S.zero;
       if (z >= 1 && z <= L.nz) {
         const int k = z - 1;
-        const unsigned r = (unsigned)(((int64_t)k * S.nblocks) / L.nz);
+        const unsigned r = (unsigned)(((int64_t)k * S.nbq[q]) / L.nz);
         const int64_t lp = k - S.kb[q][r];
         unsigned char* base = R.sm + S.blk[q];
         unsigned char* loc;
@@ -203,11 +214,12 @@ __device__ void r_colour(const Res<T>& R, int q, int colour, int what) {
     if (what != 1 && (fl & F_VFREE)) node_vel_gs_rhs_v(Ln, c, fl, u, p, S.inv6nuh[q]);
     if (what != 0 && (fl & F_ACT)) node_pres_gs_rhs_v(Ln, c, fl, u, p, S.omc[q]);
   }
-  cluster_sync();
+  level_sync(S, q);
 }
 
 template <class T>
 __device__ void r_uzawa(const Res<T>& R, int q) {
+  if (R.S.nbq[q] == 1 && R.rank != 0) return;
   for (int c = 0; c < 4; ++c) r_colour(R, q, c, 0);
   for (int c = 2; c >= 1; --c) r_colour(R, q, c, 0);
   r_colour(R, q, 0, 2);
@@ -236,6 +248,7 @@ __device__ __forceinline__ void r_residual_at(const Res<T>& R, int q, int i, int
 template <class T>
 __device__ void r_restrict(const Res<T>& R, int q) {
   const ResidentCycle<T>& S = R.S;
+  cluster_sync();  // the fine level's last phase may have run on the first CTA alone
   const LevelDev<T>& Lc = S.lv[q - 1];
   const bool resident = q - 1 >= 1;
   int k0, k1, t0, ts;
@@ -296,6 +309,7 @@ __device__ void r_restrict(const Res<T>& R, int q) {
 template <class T>
 __device__ void r_prolong(const Res<T>& R, int q) {
   const ResidentCycle<T>& S = R.S;
+  cluster_sync();  // the coarse level's last phase may have run on the first CTA alone
   const LevelDev<T>& Lf = S.lv[q];
   const LevelDev<T>& Lc = S.lv[q - 1];
   const bool resident = q - 1 >= 1;
@@ -351,6 +365,7 @@ __device__ void r_prolong(const Res<T>& R, int q) {
 template <class T>
 __device__ void r_coarse(const Res<T>& R) {
   const ResidentCycle<T>& S = R.S;
+  cluster_sync();
   if (coarse_fits_block(S.cs)) {
     if (R.rank == 0) coarse::minres_team(Team{1}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
   } else {
@@ -374,15 +389,19 @@ __global__ void __launch_bounds__(RT) k_resident(const __grid_constant__ Residen
     r_prolong(R, q);
     for (int s = 0; s < S.nu_post[q]; ++s) r_uzawa(R, q);
   }
+  if (S.nbq[S.nres] == 1) __syncthreads();
   r_writeback(R);
 }
 
 }  // namespace
 
+// Lays out the shared memory for per-level CTA counts nbq (cluster size the
+// largest of them); returns the bytes per CTA.
 template <class T>
-bool plan_resident(ResidentCycle<T>& S, size_t smem_limit) {
-  const unsigned nb = S.nblocks;
-  if (nb < 1 || nb > RES_MAX_CTAS || S.nres < 1 || S.nres > RES_MAX_LEVELS) return false;
+uint64_t layout_resident(ResidentCycle<T>& S) {
+  unsigned nb = 1;
+  for (int q = 1; q <= S.nres; ++q) nb = std::max(nb, (unsigned)S.nbq[q]);
+  S.nblocks = nb;
   uint64_t off = 0;
   for (int q = 1; q <= S.nres; ++q) {
     S.tab[q] = (uint32_t)off;
@@ -395,8 +414,10 @@ bool plan_resident(ResidentCycle<T>& S, size_t smem_limit) {
   int64_t zero_bytes = 0;
   for (int q = 1; q <= S.nres; ++q) {
     const LevelDev<T>& L = S.lv[q];
+    const int nbq = S.nbq[q];
     int mx = 0;
-    for (unsigned r = 0; r <= nb; ++r) S.kb[q][r] = (int)(((int64_t)r * L.nz + nb - 1) / nb);
+    for (unsigned r = 0; r <= nb; ++r)
+      S.kb[q][r] = r <= (unsigned)nbq ? (int)(((int64_t)r * L.nz + nbq - 1) / nbq) : L.nz;
     for (unsigned r = 0; r < nb; ++r) mx = std::max(mx, S.kb[q][r + 1] - S.kb[q][r]);
     S.maxpl[q] = mx;
     zero_bytes = std::max<int64_t>(zero_bytes, (int64_t)L.pxy * (int64_t)std::max<size_t>(sizeof(T), 2));
@@ -409,7 +430,20 @@ bool plan_resident(ResidentCycle<T>& S, size_t smem_limit) {
     off = align16(off + align16(sizeof(T) * RES_FIELDS * fb + fb) + 2 * fb);
   }
   S.smem = (uint32_t)off;
-  return off <= smem_limit;
+  return off;
+}
+
+// Every level is spread over all max_ctas CTAs of the cluster.  Measured on
+// GB300 (cube, levels 3-4 resident), a phase costs 1.8 us spread over 8 or 16
+// CTAs and 2.4 us with each level on the fewest CTAs whose shared memory
+// holds it (level 3 on one CTA with block barriers, level 4 on two): the
+// cost is the instruction latency of one node update, and more CTAs put
+// fewer nodes on each thread.
+template <class T>
+bool plan_resident(ResidentCycle<T>& S, size_t smem_limit, unsigned max_ctas) {
+  if (S.nres < 1 || S.nres > RES_MAX_LEVELS || max_ctas < 1 || max_ctas > RES_MAX_CTAS) return false;
+  for (int q = 1; q <= S.nres; ++q) S.nbq[q] = (int)max_ctas;
+  return layout_resident(S) <= smem_limit;
 }
 
 template <class T>
@@ -460,8 +494,8 @@ unsigned prepare_resident(size_t& smem_limit) {
   return nb;
 }
 
-template bool plan_resident<float>(ResidentCycle<float>&, size_t);
-template bool plan_resident<double>(ResidentCycle<double>&, size_t);
+template bool plan_resident<float>(ResidentCycle<float>&, size_t, unsigned);
+template bool plan_resident<double>(ResidentCycle<double>&, size_t, unsigned);
 template cudaError_t launch_resident_cycle<float>(const ResidentCycle<float>&, cudaStream_t);
 template cudaError_t launch_resident_cycle<double>(const ResidentCycle<double>&, cudaStream_t);
 template unsigned prepare_resident<float>(size_t&);
