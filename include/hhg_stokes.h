@@ -98,7 +98,10 @@ typedef struct hhg_options {
                                 (never), -1 = never */
   int32_t ir_fixed_point;    /* FP32+IR mode: 1 (default) evaluates the FP64 refinement residual's
                                 regular-node stencils exactly in 64-bit fixed point, 0 in FP64 */
-  int32_t reserved[2];
+  int32_t spec_max_nodes;    /* levels with fewer lattice nodes evaluate the regular-node update
+                                before reading a node's flags (hides load latency on small,
+                                latency-bound levels); 0 = default (2^20), -1 = never */
+  int32_t reserved[1];
 } hhg_options;
 
 /* Per-solve statistics. */

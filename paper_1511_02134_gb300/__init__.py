@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("coarse_cg_rtol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("fuse_coarse_levels", ctypes.c_int32), ("fuse_max_nodes", ctypes.c_int32),
                 ("team_blocks", ctypes.c_int32), ("tile_min_nodes", ctypes.c_int32),
-                ("ir_fixed_point", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("ir_fixed_point", ctypes.c_int32), ("spec_max_nodes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 1)]
 
 
 class _Stats(ctypes.Structure):

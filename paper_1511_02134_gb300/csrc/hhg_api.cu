@@ -142,6 +142,8 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     L.h3 = (T)(H.h * H.h * H.h);
     L.dh2 = (T)(M->opt.delta * H.hT2);
     L.omega = (T)M->opt.omega;
+    const int64_t lim = M->opt.spec_max_nodes != 0 ? M->opt.spec_max_nodes : SPEC_MAX_NODES;
+    L.spec = lim > 0 && H.sh.n() < lim;
   };
   set(H.d64);
   set(H.d32);

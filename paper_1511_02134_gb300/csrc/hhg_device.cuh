@@ -42,6 +42,7 @@ struct LevelDev {
   T h3;                  // h^3
   T dh2;                 // delta * h_T^2
   T omega;               // pressure under-relaxation
+  int spec;              // colour updates in the speculative node form (small levels)
   T* u[3];
   T* p;
   T* f[3];

@@ -24,6 +24,13 @@ dim3 full_grid(const LevelDev<T>& L) {
   return dim3((L.nx + FX - 1) / FX, (L.ny + FY - 1) / FY, L.nz);
 }
 
+// Whether the level's colour kernels use the speculative node form
+// (hhg_node_ops.cuh); set per level by the host (hhg_options.spec_max_nodes).
+template <class T>
+bool spec_level(const LevelDev<T>& L) {
+  return L.spec != 0;
+}
+
 // Colour-kernel node: returns false if outside the lattice.
 template <class T>
 __device__ __forceinline__ bool colour_node(const LevelDev<T>& L, int colour, int& i, int& j, int& k) {
@@ -54,21 +61,22 @@ __global__ void k_vel_rhs(LevelDev<T> L) {
   node_vel_rhs(L, pidx(L.px, L.pxy, i, j, k));
 }
 
-// Gauss-Seidel update of the velocity nodes of one colour.
-template <class T>
+// Gauss-Seidel update of the velocity nodes of one colour.  SPEC: the
+// speculative node form of small levels (hhg_node_ops.cuh).
+template <class T, bool SPEC>
 __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_vel_gs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
+  node_vel_gs<SPEC>(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
-template <class T>
+template <class T, bool SPEC>
 __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_vel_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
+  node_vel_gs_rhs<SPEC>(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
 // The last velocity colour of a step (backward colour 0) and the first
@@ -80,25 +88,25 @@ __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
 // the node's own pressure update.  So the sequential order is kept.
 // RU: the velocity right-hand side is read from RU (FP64 path) instead of
 // being formed at the node.
-template <class T, bool RU>
+template <class T, bool RU, bool SPEC>
 __global__ void k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, 0, i, j, k)) return;
   const int64_t c = pidx(L.px, L.pxy, i, j, k);
   if (RU)
-    node_vel_gs(L, c, inv6nuh);
+    node_vel_gs<SPEC>(L, c, inv6nuh);
   else
-    node_vel_gs_rhs(L, c, inv6nuh);
-  node_pres_gs_rhs(L, c, omega_over_6c);
+    node_vel_gs_rhs<SPEC>(L, c, inv6nuh);
+  node_pres_gs_rhs<SPEC>(L, c, omega_over_6c);
 }
 
-template <class T>
+template <class T, bool SPEC>
 __global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_pres_gs_rhs(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
+  node_pres_gs_rhs<SPEC>(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
 }
 
 // RP = B U - G on pressure nodes.
@@ -593,27 +601,41 @@ void launch_vel_rhs(const LevelDev<T>& L, cudaStream_t s) {
 template <class T>
 void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
-  launch_k(k_vel_colour<T>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+  if (spec_level(L))
+    launch_k(k_vel_colour<T, true>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+  else
+    launch_k(k_vel_colour<T, false>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
-  launch_k(k_vel_colour_rhs<T>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+  if (spec_level(L))
+    launch_k(k_vel_colour_rhs<T, true>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+  else
+    launch_k(k_vel_colour_rhs<T, false>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
-  if (ru)
-    launch_k(k_vel_pres_colour0<T, true>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+  const bool sp = spec_level(L);
+  if (ru && sp)
+    launch_k(k_vel_pres_colour0<T, true, true>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+  else if (ru)
+    launch_k(k_vel_pres_colour0<T, true, false>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+  else if (sp)
+    launch_k(k_vel_pres_colour0<T, false, true>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
   else
-    launch_k(k_vel_pres_colour0<T, false>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+    launch_k(k_vel_pres_colour0<T, false, false>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
 }
 
 template <class T>
 void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
-  launch_k(k_pres_colour_rhs<T>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
+  if (spec_level(L))
+    launch_k(k_pres_colour_rhs<T, true>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
+  else
+    launch_k(k_pres_colour_rhs<T, false>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
 }
 template <class T>
 void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s) {

@@ -43,6 +43,11 @@ template <class T>
 void launch_pres_colour_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
                              cudaStream_t s);
 void prepare_tiled();
+// Default of hhg_options.spec_max_nodes: levels below 2^20 lattice nodes are
+// latency bound and use the speculative node form of the colour updates
+// (hhg_node_ops.cuh).  Measured on GB300: a level-5 FP32 Uzawa step 37.9 ->
+// 28.2 us, level 6 60 -> 49 us, while level 7 went 170 -> 191 us.
+constexpr int64_t SPEC_MAX_NODES = 1 << 20;
 // Default of hhg_options.tile_min_nodes: off.  Measured on GB300, the tile
 // kernels move the same bytes per colour launch as the grid kernels (the
 // own-node reads of f and the writes of u stay strided) and run 25% slower.

@@ -18,60 +18,101 @@ __device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, int64_t c) {
   for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - bt[d];
 }
 
+// The colour updates come in two forms.  SPEC (for small, latency-bound
+// levels) evaluates the regular-node (closed-form stencil) update before it
+// reads the node's flags, so that its loads are not gated by the flag load;
+// a boundary node then recomputes with its class rows, and a node without
+// the unknown stores nothing.  The other form (for large, throughput-bound
+// levels, where the speculative loads and arithmetic of boundary and
+// Dirichlet nodes cost more than the latency they hide) reads the flags
+// first.  Both store the same values.  u, p are neighbour views centred on
+// the node (global arrays, a shared-memory tile, or plane-pointer tables).
+
 // u_d <- u_d + (RU_d - (A u_d)) / A_ii  (one node of the current colour).
-// View forms: u, p are neighbour views centred on the node (global arrays or
-// a shared-memory tile); the caller has checked the node's flag.
-template <class T, class V>
-__device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, T inv6nuh) {
+template <bool SPEC, class T, class V>
+__device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, const V* u, T inv6nuh) {
+  T reg[3];
+  uint8_t fl;
+  if (SPEC) {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) reg[d] = (L.r[d][c] + L.nuh * nb6v(u[d])) * inv6nuh;
+    fl = L.flags[c];
+    if (!(fl & F_VFREE)) return;
+  } else {
+    fl = L.flags[c];
+    if (!(fl & F_VFREE)) return;
+    if (!(fl & F_IRR)) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) reg[d] = (L.r[d][c] + L.nuh * nb6v(u[d])) * inv6nuh;
+    }
+  }
   if (!(fl & F_IRR)) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) L.u[d][c] = (L.r[d][c] + L.nuh * nb6v(u[d])) * inv6nuh;
-  } else {
-    const T* w = class_row(L, c);
+    for (int d = 0; d < 3; ++d) L.u[d][c] = reg[d];
+    return;
+  }
+  const T* w = class_row(L, c);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T dg, of;
-      irr_lap_parts_v<T>(u[d], w, dg, of);
-      L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
-    }
+  for (int d = 0; d < 3; ++d) {
+    T dg, of;
+    irr_lap_parts_v<T>(u[d], w, dg, of);
+    L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
   }
 }
 
-template <class T>
+template <bool SPEC, class T>
 __device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_VFREE)) return;
   const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
-  node_vel_gs_v(L, c, fl, u, inv6nuh);
+  node_vel_gs_v<SPEC>(L, c, u, inv6nuh);
+}
+
+// Regular-node velocity update with f - B^T p formed at the node.
+template <class T, class V>
+__device__ __forceinline__ void vel_rhs_regular(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T inv6nuh,
+                                                T reg[3]) {
+  T dv[3];
+  div12_all(diff7v<T>(p), dv);
+  const T s = -L.h2 * (T)(1.0 / 12.0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) reg[d] = ((L.f[d][c] - s * dv[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
 }
 
 // Same update with the right-hand side f - B^T p formed at the node (p does
 // not change during the velocity sweeps, Sec. 3.3), RU is not touched.
-template <class T, class V>
-__device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, const V& p,
+template <bool SPEC, class T, class V>
+__device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t c, const V* u, const V& p,
                                                   T inv6nuh) {
-  const T* w = row_of(L, c, fl);
-  T bt[3];
-  row_BT_v(L, p, w, fl, bt);
+  T reg[3];
+  uint8_t fl;
+  if (SPEC) {
+    vel_rhs_regular(L, c, u, p, inv6nuh, reg);
+    fl = L.flags[c];
+    if (!(fl & F_VFREE)) return;
+  } else {
+    fl = L.flags[c];
+    if (!(fl & F_VFREE)) return;
+    if (!(fl & F_IRR)) vel_rhs_regular(L, c, u, p, inv6nuh, reg);
+  }
   if (!(fl & F_IRR)) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) L.u[d][c] = ((L.f[d][c] - bt[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
-  } else {
+    for (int d = 0; d < 3; ++d) L.u[d][c] = reg[d];
+    return;
+  }
+  const T* w = class_row(L, c);
+  T bt[3];
+  row_BT_v(L, p, w, fl, bt);
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      T dg, of;
-      irr_lap_parts_v<T>(u[d], w, dg, of);
-      L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
-    }
+  for (int d = 0; d < 3; ++d) {
+    T dg, of;
+    irr_lap_parts_v<T>(u[d], w, dg, of);
+    L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
   }
 }
 
-template <class T>
+template <bool SPEC, class T>
 __device__ __forceinline__ void node_vel_gs_rhs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_VFREE)) return;
   const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
-  node_vel_gs_rhs_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), inv6nuh);
+  node_vel_gs_rhs_v<SPEC>(L, c, u, gnb(L.p, c, L.px, L.pxy), inv6nuh);
 }
 
 // RP = B U - G (pressure nodes).
@@ -100,31 +141,52 @@ __device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, int64_t c, T 
   }
 }
 
-// Same update with B u - g formed at the node (u does not change during the
-// pressure sweep), RP is not touched.
+// Regular-node pressure update with B u - g formed at the node.
 template <class T, class V>
-__device__ __forceinline__ void node_pres_gs_rhs_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, const V& p,
-                                                   T omega_over_6c) {
-  const T* w = row_of(L, c, fl);
-  const T rp = row_B_v(L, u, w, fl) - L.g[c];
-  const T pc = p(0, 0, 0);
-  if (!(fl & F_IRR)) {
-    const T cp = L.c * ((T)6 * pc - nb6v(p));
-    L.p[c] = pc + omega_over_6c * (rp - cp);
-  } else {
-    T dg, of;
-    irr_lap_parts_v<T>(p, w, dg, of);
-    const T cp = L.c * (dg * pc + of);
-    L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
-  }
+__device__ __forceinline__ T pres_rhs_regular(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T pc,
+                                              T omega_over_6c) {
+  const T d0 = div12(diff7v<T>(u[0]), 0);
+  const T d1 = div12(diff7v<T>(u[1]), 1);
+  const T d2 = div12(diff7v<T>(u[2]), 2);
+  const T rp = L.h2 * (T)(1.0 / 12.0) * ((d0 + d1) + d2) - L.g[c];
+  const T cp = L.c * ((T)6 * pc - nb6v(p));
+  return pc + omega_over_6c * (rp - cp);
 }
 
-template <class T>
+// Same update with B u - g formed at the node (u does not change during the
+// pressure sweep), RP is not touched.
+template <bool SPEC, class T, class V>
+__device__ __forceinline__ void node_pres_gs_rhs_v(const LevelDev<T>& L, int64_t c, const V* u, const V& p,
+                                                   T omega_over_6c) {
+  T reg = (T)0, pc;
+  uint8_t fl;
+  if (SPEC) {
+    pc = p(0, 0, 0);
+    reg = pres_rhs_regular(L, c, u, p, pc, omega_over_6c);
+    fl = L.flags[c];
+    if (!(fl & F_ACT)) return;
+  } else {
+    fl = L.flags[c];
+    if (!(fl & F_ACT)) return;
+    pc = p(0, 0, 0);
+    if (!(fl & F_IRR)) reg = pres_rhs_regular(L, c, u, p, pc, omega_over_6c);
+  }
+  if (!(fl & F_IRR)) {
+    L.p[c] = reg;
+    return;
+  }
+  const T* w = class_row(L, c);
+  const T rp = row_B_v(L, u, w, fl) - L.g[c];
+  T dg, of;
+  irr_lap_parts_v<T>(p, w, dg, of);
+  const T cp = L.c * (dg * pc + of);
+  L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
+}
+
+template <bool SPEC, class T>
 __device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, int64_t c, T omega_over_6c) {
-  const uint8_t fl = L.flags[c];
-  if (!(fl & F_ACT)) return;
   const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
-  node_pres_gs_rhs_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), omega_over_6c);
+  node_pres_gs_rhs_v<SPEC>(L, c, u, gnb(L.p, c, L.px, L.pxy), omega_over_6c);
 }
 
 // (RU, RP) = (F, G) - K (U, P) at one node, returned in r[0..3]; zero for

@@ -208,11 +208,10 @@ __device__ void r_colour(const Res<T>& R, int q, int colour, int what) {
     if (i >= L.nx) continue;
     const LevelDev<T> Ln = R.at_plane(q, k + 1);
     const int c = (j + 1) * (int)L.px + (i + 1);
-    const uint8_t fl = Ln.flags[c];
     const DNb<T> u[3] = {R.view(q, 0, k + 1, c), R.view(q, 1, k + 1, c), R.view(q, 2, k + 1, c)};
     const DNb<T> p = R.view(q, 3, k + 1, c);
-    if (what != 1 && (fl & F_VFREE)) node_vel_gs_rhs_v(Ln, c, fl, u, p, S.inv6nuh[q]);
-    if (what != 0 && (fl & F_ACT)) node_pres_gs_rhs_v(Ln, c, fl, u, p, S.omc[q]);
+    if (what != 1) node_vel_gs_rhs_v<true>(Ln, c, u, p, S.inv6nuh[q]);
+    if (what != 0) node_pres_gs_rhs_v<true>(Ln, c, u, p, S.omc[q]);
   }
   level_sync(S, q);
 }

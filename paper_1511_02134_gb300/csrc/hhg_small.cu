@@ -66,11 +66,11 @@ __device__ void b_colour(const Team& tm, const LevelDev<T>& L, int colour, int w
     const int64_t c = pidx(L.px, L.pxy, i, j, k);
     if (what != 1) {
       if (sizeof(T) == 4)
-        node_vel_gs_rhs(L, c, inv6nuh);
+        node_vel_gs_rhs<true>(L, c, inv6nuh);
       else
-        node_vel_gs(L, c, inv6nuh);
+        node_vel_gs<true>(L, c, inv6nuh);
     }
-    if (what != 0) node_pres_gs_rhs(L, c, omc);
+    if (what != 0) node_pres_gs_rhs<true>(L, c, omc);
   }
   tm.sync();
 }

@@ -150,7 +150,6 @@ __global__ void __launch_bounds__(TT) k_colour_tma(const __grid_constant__ TileM
     const int i = x0 + 4 * q4 + ((colour - j - k) & 3);
     if (i < L.nx && j < L.ny) {
       const int64_t c = pidx(L.px, L.pxy, i, j, k);
-      const uint8_t fl = L.flags[c];
       const int sc = (i - x0 + 1) + BX * (yq + 1);
       const T* pl[3];
 #pragma unroll
@@ -159,15 +158,12 @@ __global__ void __launch_bounds__(TT) k_colour_tma(const __grid_constant__ TileM
       SNb<T> u[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) u[d] = SNb<T>{{pl[0] + d * FS, pl[1] + d * FS, pl[2] + d * FS}, sc};
-      if (MODE == 0) {
-        if (fl & F_VFREE)
-          node_vel_gs_rhs_v(L, c, fl, u, SNb<T>{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, sc}, wfac);
-      } else if (MODE == 1) {
-        if (fl & F_VFREE) node_vel_gs_v(L, c, fl, u, wfac);
-      } else {
-        if (fl & F_ACT)
-          node_pres_gs_rhs_v(L, c, fl, u, SNb<T>{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, sc}, wfac);
-      }
+      if (MODE == 0)
+        node_vel_gs_rhs_v<false>(L, c, u, SNb<T>{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, sc}, wfac);
+      else if (MODE == 1)
+        node_vel_gs_v<false>(L, c, u, wfac);
+      else
+        node_pres_gs_rhs_v<false>(L, c, u, SNb<T>{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, sc}, wfac);
     }
     __syncthreads();
     // the slot of plane q is free: stage the next plane into it

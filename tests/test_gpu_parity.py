@@ -114,13 +114,15 @@ def test_set_rhs(pkg, name, level):
 
 # ---- smoother pieces, transfers, coarse solve ---------------------------------------------
 
-@pytest.mark.parametrize("tiles", [-1, 1])
+@pytest.mark.parametrize("tiles,spec", [(-1, 0), (-1, -1), (1, 0)])
 @pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3)])
-def test_smoother_pieces(pkg, name, level, tiles):
+def test_smoother_pieces(pkg, name, level, tiles, spec):
     """Smoother steps against the oracle, with the colour sweeps run by the
-    grid kernels (tiles = -1) and by the shared-memory tile kernels (tiles = 1:
-    every level tiled, ragged tiles included)."""
-    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), tile_min_nodes=tiles)
+    grid kernels (tiles = -1) in the speculative node form of small levels
+    (spec = 0, the default here) or the flags-first form of large levels
+    (spec = -1), and by the shared-memory tile kernels (tiles = 1: every
+    level tiled, ragged tiles included)."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), tile_min_nodes=tiles, spec_max_nodes=spec)
     L = H.levels[level]
     dims = mesh.dims()
     st = _random_state(H, level, 7)
@@ -249,11 +251,12 @@ def test_coarse_solve(pkg, name, level, mx):
 
 # ---- cycles and solves ------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tiles", [-1, 1])
+@pytest.mark.parametrize("tiles,spec", [(-1, 0), (-1, -1), (1, 0)])
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 3, 2, 5), ("cube", 5, 2, 5), ("channel", 2, 1, 200),
                                                     ("partial", 3, 1, 30)])
-def test_vcycle_iterates(pkg, name, level, coarsest, mx, tiles):
-    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles)
+def test_vcycle_iterates(pkg, name, level, coarsest, mx, tiles, spec):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles,
+                           spec_max_nodes=spec)
     L = H.levels[level]
     st = _random_state(H, level, 9)
     _load(mesh, H, level, st)
