@@ -101,7 +101,8 @@ typedef struct hhg_options {
   int32_t spec_max_nodes;    /* levels with fewer lattice nodes evaluate the regular-node update
                                 before reading a node's flags (hides load latency on small,
                                 latency-bound levels); 0 = default (2^20), -1 = never */
-  int32_t reserved[1];
+  int32_t colour_block_z;    /* planes per thread block of the colour kernels (1, 2 or 4; 0 =
+                                default: 2 on levels of at least 2^22 lattice nodes, else 1) */
 } hhg_options;
 
 /* Per-solve statistics. */

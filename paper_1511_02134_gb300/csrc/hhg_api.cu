@@ -144,6 +144,11 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     L.omega = (T)M->opt.omega;
     const int64_t lim = M->opt.spec_max_nodes != 0 ? M->opt.spec_max_nodes : SPEC_MAX_NODES;
     L.spec = lim > 0 && H.sh.n() < lim;
+    // two planes per block on levels that stream from HBM (level 9: 5 % per
+    // Uzawa step); no effect measured at level 7
+    const int want = M->opt.colour_block_z;
+    L.cbz = want == 1 || want == 2 || want == 4 ? want : (H.sh.n() >= ((int64_t)1 << 22) ? 2 : 1);
+    L.cby = 4;
   };
   set(H.d64);
   set(H.d32);

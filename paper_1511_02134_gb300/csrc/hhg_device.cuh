@@ -43,6 +43,7 @@ struct LevelDev {
   T dh2;                 // delta * h_T^2
   T omega;               // pressure under-relaxation
   int spec;              // colour updates in the speculative node form (small levels)
+  int cby, cbz;          // rows and planes per thread block of the colour kernels
   T* u[3];
   T* p;
   T* f[3];

@@ -11,13 +11,17 @@ namespace hhg {
 
 namespace {
 
-constexpr int CX = 32, CY = 4;  // colour kernels: quarter-rows x rows
+constexpr int CX = 32;  // colour kernels: quarter-rows per block; rows and planes per level (cby, cbz)
 constexpr int FX = 64, FY = 4;  // full kernels
 
 template <class T>
+dim3 colour_block(const LevelDev<T>& L) {
+  return dim3(CX, L.cby, L.cbz);
+}
+template <class T>
 dim3 colour_grid(const LevelDev<T>& L) {
   const int nq = (L.nx + 3) / 4;
-  return dim3((nq + CX - 1) / CX, (L.ny + CY - 1) / CY, L.nz);
+  return dim3((nq + CX - 1) / CX, (L.ny + L.cby - 1) / L.cby, (L.nz + L.cbz - 1) / L.cbz);
 }
 template <class T>
 dim3 full_grid(const LevelDev<T>& L) {
@@ -35,10 +39,10 @@ bool spec_level(const LevelDev<T>& L) {
 template <class T>
 __device__ __forceinline__ bool colour_node(const LevelDev<T>& L, int colour, int& i, int& j, int& k) {
   const int t = blockIdx.x * CX + threadIdx.x;
-  j = blockIdx.y * CY + threadIdx.y;
-  k = blockIdx.z;
+  j = blockIdx.y * blockDim.y + threadIdx.y;
+  k = blockIdx.z * blockDim.z + threadIdx.z;
   i = ((colour - j - k) & 3) + 4 * t;
-  return i < L.nx && j < L.ny;
+  return i < L.nx && j < L.ny && k < L.nz;
 }
 
 template <class T>
@@ -602,17 +606,17 @@ template <class T>
 void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
   if (spec_level(L))
-    launch_k(k_vel_colour<T, true>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+    launch_k(k_vel_colour<T, true>, colour_grid(L), colour_block(L), s, L, colour, inv);
   else
-    launch_k(k_vel_colour<T, false>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+    launch_k(k_vel_colour<T, false>, colour_grid(L), colour_block(L), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
   if (spec_level(L))
-    launch_k(k_vel_colour_rhs<T, true>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+    launch_k(k_vel_colour_rhs<T, true>, colour_grid(L), colour_block(L), s, L, colour, inv);
   else
-    launch_k(k_vel_colour_rhs<T, false>, colour_grid(L), dim3(CX, CY), s, L, colour, inv);
+    launch_k(k_vel_colour_rhs<T, false>, colour_grid(L), colour_block(L), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
@@ -620,22 +624,22 @@ void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
   const bool sp = spec_level(L);
   if (ru && sp)
-    launch_k(k_vel_pres_colour0<T, true, true>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+    launch_k(k_vel_pres_colour0<T, true, true>, colour_grid(L), colour_block(L), s, L, inv, w);
   else if (ru)
-    launch_k(k_vel_pres_colour0<T, true, false>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+    launch_k(k_vel_pres_colour0<T, true, false>, colour_grid(L), colour_block(L), s, L, inv, w);
   else if (sp)
-    launch_k(k_vel_pres_colour0<T, false, true>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+    launch_k(k_vel_pres_colour0<T, false, true>, colour_grid(L), colour_block(L), s, L, inv, w);
   else
-    launch_k(k_vel_pres_colour0<T, false, false>, colour_grid(L), dim3(CX, CY), s, L, inv, w);
+    launch_k(k_vel_pres_colour0<T, false, false>, colour_grid(L), colour_block(L), s, L, inv, w);
 }
 
 template <class T>
 void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
   if (spec_level(L))
-    launch_k(k_pres_colour_rhs<T, true>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
+    launch_k(k_pres_colour_rhs<T, true>, colour_grid(L), colour_block(L), s, L, colour, w);
   else
-    launch_k(k_pres_colour_rhs<T, false>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
+    launch_k(k_pres_colour_rhs<T, false>, colour_grid(L), colour_block(L), s, L, colour, w);
 }
 template <class T>
 void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s) {
@@ -644,7 +648,7 @@ void launch_pres_rhs(const LevelDev<T>& L, cudaStream_t s) {
 template <class T>
 void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
-  launch_k(k_pres_colour<T>, colour_grid(L), dim3(CX, CY), s, L, colour, w);
+  launch_k(k_pres_colour<T>, colour_grid(L), colour_block(L), s, L, colour, w);
 }
 template <class T>
 void launch_residual(const LevelDev<T>& L, cudaStream_t s) {
