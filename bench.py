@@ -38,7 +38,7 @@ TOL = 1e-8
 # capture of `bench.py --roofline-only` at that level (cold caches: ncu
 # flushes them before each pass); None where no capture of the current kernel
 # exists.
-TRAFFIC_PER_LAUNCH = {7: 62997760 + 863488}
+TRAFFIC_PER_LAUNCH = {}
 
 
 def _peaks():

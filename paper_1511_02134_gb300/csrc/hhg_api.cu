@@ -689,7 +689,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     LevelHost& H = M->lv[l];
     H.level = l;
     H.sh = level_shape(M->macro, l);
-    H.px = ((H.sh.nx + 2 + 3) / 4) * 4;
+    H.px = ((H.sh.nx + 2 + 15) / 16) * 16;  // rows grouped by x mod 4 (hhg_common.h), 16-byte aligned groups
     H.py = H.sh.ny + 2;
     H.pz = H.sh.nz + 2;
     H.nalloc = H.px * H.py * H.pz;
@@ -702,7 +702,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
       for (int j = 0; j < H.sh.ny; ++j)
         for (int i = 0; i < H.sh.nx; ++i) {
           const uint8_t f = H.flags[i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k)];
-          padded[(i + 1) + H.px * (j + 1) + H.px * H.py * (k + 1)] = f;
+          padded[pad_index(H.px, H.px * H.py, i, j, k)] = f;
           if (f & F_VFREE) H.n_vel++;
           if (f & F_ACT) H.n_pres++;
         }
@@ -725,7 +725,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
       for (int k = 0; k < H.sh.nz; ++k)
         for (int j = 0; j < H.sh.ny; ++j)
           for (int i = 0; i < H.sh.nx; ++i)
-            pcls[(i + 1) + H.px * (j + 1) + H.px * H.py * (k + 1)] =
+            pcls[pad_index(H.px, H.px * H.py, i, j, k)] =
                 cls[i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k)];
       std::vector<float> table32(table.begin(), table.end());
       if ((rc = dalloc(M, (void**)&H.d_cls, sizeof(uint16_t) * (size_t)H.nalloc))) return bail(rc);
@@ -756,7 +756,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
           const int64_t q = i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k);
           if ((H.flags[q] & F_DIR) && (H.flags[q] & F_ACT)) {
             lat.push_back(q);
-            pad.push_back((i + 1) + H.px * (j + 1) + H.px * H.py * (k + 1));
+            pad.push_back(pad_index(H.px, H.px * H.py, i, j, k));
           }
         }
     M->ndir = (int64_t)lat.size();

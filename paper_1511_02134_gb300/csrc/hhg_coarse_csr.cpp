@@ -63,25 +63,34 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
   }
   std::vector<int32_t> iv(nalloc, -1), ip(nalloc, -1);
   std::vector<int64_t> lat_of(nalloc, -1);
+  std::vector<int32_t> vi, vj, vk, qi, qj, qk;  // lattice coordinates of the unknowns' nodes
   for (int k = 0; k < sh.nz; ++k)
     for (int j = 0; j < sh.ny; ++j)
       for (int i = 0; i < sh.nx; ++i) {
         const int64_t q = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
-        const int64_t pc = (i + 1) + px * (j + 1) + pxy * (k + 1);
+        const int64_t pc = pad_index(px, pxy, i, j, k);
         lat_of[pc] = q;
         if (flags[q] & F_VFREE) {
           iv[pc] = out.nv++;
           out.vidx.push_back((int32_t)pc);
+          vi.push_back(i);
+          vj.push_back(j);
+          vk.push_back(k);
         }
         if (flags[q] & F_ACT) {
           ip[pc] = out.np++;
           out.pidx.push_back((int32_t)pc);
+          qi.push_back(i);
+          qj.push_back(j);
+          qk.push_back(k);
         }
       }
   (void)n;
-  int64_t off[15];
-  for (int o = 0; o < 15; ++o)
-    off[o] = STENCIL_OFFSETS[o][0] + px * STENCIL_OFFSETS[o][1] + pxy * STENCIL_OFFSETS[o][2];
+  // padded index of the neighbour along stencil offset o (the ghost frame
+  // holds the neighbours of boundary nodes; they carry no unknown)
+  auto nbr = [&](int i, int j, int k, int o) {
+    return pad_index(px, pxy, i + STENCIL_OFFSETS[o][0], j + STENCIL_OFFSETS[o][1], k + STENCIL_OFFSETS[o][2]);
+  };
   const int32_t nv = out.nv, np = out.np;
   int64_t nnz = 0;
   auto push = [&](std::vector<int32_t>& col, std::vector<double>& val, int64_t j, double v) {
@@ -97,11 +106,11 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
       const int64_t pc = out.vidx[r];
       const Rows w = rows_of(cls[lat_of[pc]], table);
       for (int o = 0; o < 15; ++o) {
-        const int64_t nb = pc + off[o];
+        const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
         if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], nuh * w.lap[o]);
       }
       for (int o = 0; o < 15; ++o) {
-        const int64_t nb = pc + off[o];
+        const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
         if (ip[nb] >= 0) push(out.kcol, out.kval, 3 * (int64_t)nv + ip[nb], h2 * w.bt[d][o]);
       }
       if (nnz > std::numeric_limits<int32_t>::max() / 2) {
@@ -116,11 +125,11 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
     const Rows w = rows_of(cls[lat_of[pc]], table);
     for (int d = 0; d < 3; ++d)
       for (int o = 0; o < 15; ++o) {
-        const int64_t nb = pc + off[o];
+        const int64_t nb = nbr(qi[r], qj[r], qk[r], o);
         if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], h2 * w.b[d][o]);
       }
     for (int o = 0; o < 15; ++o) {
-      const int64_t nb = pc + off[o];
+      const int64_t nb = nbr(qi[r], qj[r], qk[r], o);
       if (ip[nb] >= 0) push(out.kcol, out.kval, 3 * (int64_t)nv + ip[nb], -c * w.lap[o]);
     }
     if (nnz > std::numeric_limits<int32_t>::max() / 2) {
@@ -137,7 +146,7 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
     const int64_t pc = out.vidx[r];
     const Rows w = rows_of(cls[lat_of[pc]], table);
     for (int o = 0; o < 15; ++o) {
-      const int64_t nb = pc + off[o];
+      const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
       if (iv[nb] >= 0) push(out.acol, out.aval, iv[nb], nuh * w.lap[o]);
     }
     out.aptr.push_back((int32_t)nnz);

@@ -29,6 +29,20 @@ enum : uint8_t {
   F_OUT = 16,   // lies on a do-nothing outflow face
 };
 
+// Padded level arrays: node (i, j, k) of an nx x ny x nz lattice, with a
+// ghost frame of one node, has padded coordinates (i+1, j+1, k+1).  Rows
+// (px entries, px a multiple of 16) store their entries grouped by padded x
+// index q mod 4: entry (q mod 4) px/4 + q div 4.  The nodes of one colour,
+// (i + j + k) mod 4 fixed, are then contiguous within each row, so a colour
+// sweep reads and writes whole sectors.  Planes hold px * py entries.
+HHG_HD int64_t row_pos(int64_t q, int64_t px) { return (q & 3) * (px >> 2) + (q >> 2); }
+HHG_HD int64_t pad_index(int64_t px, int64_t pxy, int i, int j, int k) {
+  return row_pos(i + 1, px) + px * (j + 1) + pxy * (k + 1);
+}
+// Row distance from padded x index q to q - 1 and to q + 1.
+HHG_HD int64_t row_step_minus(int64_t q, int64_t px) { return (q & 3) == 0 ? 3 * (px >> 2) - 1 : -(px >> 2); }
+HHG_HD int64_t row_step_plus(int64_t q, int64_t px) { return (q & 3) == 3 ? 1 - 3 * (px >> 2) : (px >> 2); }
+
 // Layout of one stencil-class row table (unit lattice spacing): stiffness
 // row, B_d rows, B_d^T rows, mass row (15 weights each, offset order:
 // centre, +o then -o over the Kuhn directions e1, e2, e3, e1+e2, e2+e3,

@@ -2,8 +2,10 @@
 // on the Kuhn lattice.
 //
 // Storage: every field of a level is one padded 3-D array over the lattice
-// with a zero ghost frame of one node, x fastest: node (i,j,k) lives at
-// (i+1) + px (j+1) + pxy (k+1).  Fields are zero on nodes without the
+// with a zero ghost frame of one node; node (i,j,k) lives at
+// pad_index(px, pxy, i, j, k) (rows grouped by x mod 4, hhg_common.h), and a
+// Node carries that index with the row steps to its x-neighbours.  Fields
+// are zero on nodes without the
 // corresponding unknown (velocity: not F_VFREE, pressure: not F_ACT); every
 // kernel keeps that invariant, so stencils need no neighbour masks.
 //
@@ -64,7 +66,16 @@ __device__ __forceinline__ void pdl_enter() {
 }
 
 __device__ __forceinline__ int64_t pidx(int64_t px, int64_t pxy, int i, int j, int k) {
-  return (int64_t)(i + 1) + px * (j + 1) + pxy * (k + 1);
+  return pad_index(px, pxy, i, j, k);
+}
+
+// A node's padded index and the steps to its x-neighbours within the row.
+struct Node {
+  int64_t c, dxm, dxp;
+};
+
+__device__ __forceinline__ Node node_at(int64_t px, int64_t pxy, int i, int j, int k) {
+  return Node{pad_index(px, pxy, i, j, k), row_step_minus(i + 1, px), row_step_plus(i + 1, px)};
 }
 
 // ---- neighbour views -----------------------------------------------------------
@@ -80,13 +91,16 @@ __device__ __forceinline__ int64_t pidx(int64_t px, int64_t pxy, int i, int j, i
 template <class T>
 struct GNb {
   const T* x;
-  int64_t c, px, pxy;
-  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const { return x[c + dx + px * dy + pxy * dz]; }
+  Node n;
+  int64_t px, pxy;
+  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const {
+    return x[n.c + (dx < 0 ? n.dxm : (dx > 0 ? n.dxp : 0)) + px * dy + pxy * dz];
+  }
 };
 
 template <class T>
-__device__ __forceinline__ GNb<T> gnb(const T* x, int64_t c, int64_t px, int64_t pxy) {
-  return GNb<T>{x, c, px, pxy};
+__device__ __forceinline__ GNb<T> gnb(const T* x, const Node& n, int64_t px, int64_t pxy) {
+  return GNb<T>{x, n, px, pxy};
 }
 
 // Sum of the six axis neighbours.
@@ -96,8 +110,8 @@ __device__ __forceinline__ auto nb6v(const V& x) {
 }
 
 template <class T>
-__device__ __forceinline__ T nb6(const T* x, int64_t c, int64_t px, int64_t pxy) {
-  return nb6v(gnb(x, c, px, pxy));
+__device__ __forceinline__ T nb6(const T* x, const Node& n, int64_t px, int64_t pxy) {
+  return nb6v(gnb(x, n, px, pxy));
 }
 
 // Antisymmetric differences x(c+o) - x(c-o) over the 7 Kuhn directions.
@@ -120,8 +134,8 @@ __device__ __forceinline__ Diff7<T> diff7v(const V& x) {
 }
 
 template <class T>
-__device__ __forceinline__ Diff7<T> diff7(const T* x, int64_t c, int64_t px, int64_t pxy) {
-  return diff7v<T>(gnb(x, c, px, pxy));
+__device__ __forceinline__ Diff7<T> diff7(const T* x, const Node& n, int64_t px, int64_t pxy) {
+  return diff7v<T>(gnb(x, n, px, pxy));
 }
 
 // 12 * Div_d from the differences.
@@ -185,21 +199,21 @@ __device__ __forceinline__ void irr_lap_parts_v(const V& x, const T* w, T& dg, T
 }
 
 template <class T>
-__device__ __forceinline__ void irr_lap_parts(const LevelDev<T>& L, const T* x, int64_t c, T& dg, T& of) {
-  irr_lap_parts_v<T>(gnb(x, c, L.px, L.pxy), class_row(L, c), dg, of);
+__device__ __forceinline__ void irr_lap_parts(const LevelDev<T>& L, const T* x, const Node& n, T& dg, T& of) {
+  irr_lap_parts_v<T>(gnb(x, n, L.px, L.pxy), class_row(L, n.c), dg, of);
 }
 
 // Consistent mass row (times h^3).
 template <class T>
-__device__ __forceinline__ T irr_mass_row(const LevelDev<T>& L, const T* x, int64_t c) {
-  return L.h3 * st15v<T>(gnb(x, c, L.px, L.pxy), class_row(L, c) + W_M);
+__device__ __forceinline__ T irr_mass_row(const LevelDev<T>& L, const T* x, const Node& n) {
+  return L.h3 * st15v<T>(gnb(x, n, L.px, L.pxy), class_row(L, n.c) + W_M);
 }
 
 // B_d row applied to one scalar field for the three d (times h^2).
 template <class T>
-__device__ __forceinline__ void irr_B_scalar(const LevelDev<T>& L, const T* x, int64_t c, T out[3]) {
-  const T* w = class_row(L, c);
-  const GNb<T> v = gnb(x, c, L.px, L.pxy);
+__device__ __forceinline__ void irr_B_scalar(const LevelDev<T>& L, const T* x, const Node& n, T out[3]) {
+  const T* w = class_row(L, n.c);
+  const GNb<T> v = gnb(x, n, L.px, L.pxy);
 #pragma unroll
   for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15v<T>(v, w + W_B + 15 * d);
 }
@@ -261,25 +275,25 @@ __device__ __forceinline__ const T* row_of(const LevelDev<T>& L, int64_t c, uint
 }
 
 template <class T>
-__device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl, T out[3]) {
-  const GNb<T> v[3] = {gnb(u[0], c, L.px, L.pxy), gnb(u[1], c, L.px, L.pxy), gnb(u[2], c, L.px, L.pxy)};
-  row_A_v(L, v, row_of(L, c, fl), fl, out);
+__device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, const Node& n, uint8_t fl, T out[3]) {
+  const GNb<T> v[3] = {gnb(u[0], n, L.px, L.pxy), gnb(u[1], n, L.px, L.pxy), gnb(u[2], n, L.px, L.pxy)};
+  row_A_v(L, v, row_of(L, n.c, fl), fl, out);
 }
 
 template <class T>
-__device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl, T out[3]) {
-  row_BT_v(L, gnb(p, c, L.px, L.pxy), row_of(L, c, fl), fl, out);
+__device__ __forceinline__ void row_BT(const LevelDev<T>& L, const T* p, const Node& n, uint8_t fl, T out[3]) {
+  row_BT_v(L, gnb(p, n, L.px, L.pxy), row_of(L, n.c, fl), fl, out);
 }
 
 template <class T>
-__device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, int64_t c, uint8_t fl) {
-  const GNb<T> v[3] = {gnb(u[0], c, L.px, L.pxy), gnb(u[1], c, L.px, L.pxy), gnb(u[2], c, L.px, L.pxy)};
-  return row_B_v(L, v, row_of(L, c, fl), fl);
+__device__ __forceinline__ T row_B(const LevelDev<T>& L, const T* const* u, const Node& n, uint8_t fl) {
+  const GNb<T> v[3] = {gnb(u[0], n, L.px, L.pxy), gnb(u[1], n, L.px, L.pxy), gnb(u[2], n, L.px, L.pxy)};
+  return row_B_v(L, v, row_of(L, n.c, fl), fl);
 }
 
 template <class T>
-__device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, int64_t c, uint8_t fl) {
-  return row_C_v(L, gnb(p, c, L.px, L.pxy), row_of(L, c, fl), fl);
+__device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, const Node& n, uint8_t fl) {
+  return row_C_v(L, gnb(p, n, L.px, L.pxy), row_of(L, n.c, fl), fl);
 }
 
 // Lumped pressure mass m_i = int phi_i.

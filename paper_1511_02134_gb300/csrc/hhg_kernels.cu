@@ -62,7 +62,7 @@ __global__ void k_vel_rhs(LevelDev<T> L) {
   pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  node_vel_rhs(L, pidx(L.px, L.pxy, i, j, k));
+  node_vel_rhs(L, node_at(L.px, L.pxy, i, j, k));
 }
 
 // Gauss-Seidel update of the velocity nodes of one colour.  SPEC: the
@@ -72,7 +72,7 @@ __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_vel_gs<SPEC>(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
+  node_vel_gs<SPEC>(L, node_at(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
 template <class T, bool SPEC>
@@ -80,7 +80,7 @@ __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_vel_gs_rhs<SPEC>(L, pidx(L.px, L.pxy, i, j, k), inv6nuh);
+  node_vel_gs_rhs<SPEC>(L, node_at(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
 // The last velocity colour of a step (backward colour 0) and the first
@@ -97,12 +97,12 @@ __global__ void k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, 0, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const Node n = node_at(L.px, L.pxy, i, j, k);
   if (RU)
-    node_vel_gs<SPEC>(L, c, inv6nuh);
+    node_vel_gs<SPEC>(L, n, inv6nuh);
   else
-    node_vel_gs_rhs<SPEC>(L, c, inv6nuh);
-  node_pres_gs_rhs<SPEC>(L, c, omega_over_6c);
+    node_vel_gs_rhs<SPEC>(L, n, inv6nuh);
+  node_pres_gs_rhs<SPEC>(L, n, omega_over_6c);
 }
 
 template <class T, bool SPEC>
@@ -110,7 +110,7 @@ __global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_pres_gs_rhs<SPEC>(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
+  node_pres_gs_rhs<SPEC>(L, node_at(L.px, L.pxy, i, j, k), omega_over_6c);
 }
 
 // RP = B U - G on pressure nodes.
@@ -119,7 +119,7 @@ __global__ void k_pres_rhs(LevelDev<T> L) {
   pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  node_pres_rhs(L, pidx(L.px, L.pxy, i, j, k));
+  node_pres_rhs(L, node_at(L.px, L.pxy, i, j, k));
 }
 
 // Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour.
@@ -128,7 +128,7 @@ __global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_pres_gs(L, pidx(L.px, L.pxy, i, j, k), omega_over_6c);
+  node_pres_gs(L, node_at(L.px, L.pxy, i, j, k), omega_over_6c);
 }
 
 template <class T>
@@ -136,7 +136,7 @@ __global__ void k_residual(LevelDev<T> L) {
   pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  node_residual(L, pidx(L.px, L.pxy, i, j, k));
+  node_residual(L, node_at(L.px, L.pxy, i, j, k));
 }
 
 template <class T>
@@ -244,11 +244,11 @@ __global__ void k_project(LevelDev<T> L, const double* mom) {
 // ---- right-hand side and its transpose (FP64) ------------------------------------
 
 // (M x)_node on a regular node: h^3 [2/5 x_c + 1/20 (axis and body neighbours) + 1/30 (face diagonals)].
-__device__ __forceinline__ double mass_reg(const double* x, int64_t c, int64_t px, int64_t pxy, double h3) {
-  const double ax = nb6(x, c, px, pxy) + (x[c + 1 + px + pxy] + x[c - 1 - px - pxy]);
-  const double fc = (x[c + 1 + px] + x[c - 1 - px]) + (x[c + px + pxy] + x[c - px - pxy]) +
-                    (x[c + 1 + pxy] + x[c - 1 - pxy]);
-  return h3 * (0.4 * x[c] + 0.05 * ax + fc * (1.0 / 30.0));
+__device__ __forceinline__ double mass_reg(const double* x, const Node& n, int64_t px, int64_t pxy, double h3) {
+  const GNb<double> v = gnb(x, n, px, pxy);
+  const double ax = nb6v(v) + (v(1, 1, 1) + v(-1, -1, -1));
+  const double fc = (v(1, 1, 0) + v(-1, -1, 0)) + (v(0, 1, 1) + v(0, -1, -1)) + (v(1, 0, 1) + v(-1, 0, -1));
+  return h3 * (0.4 * v(0, 0, 0) + 0.05 * ax + fc * (1.0 / 30.0));
 }
 
 __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1, const double* f2,
@@ -256,17 +256,18 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
   pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const Node n = node_at(L.px, L.pxy, i, j, k);
+  const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
   const double* fn[3] = {f0, f1, f2};
   const double* ud[3] = {d0, d1, d2};
   const bool irr = fl & F_IRR;
   if (fl & F_VFREE) {
     double au[3];
-    row_A(L, ud, c, fl, au);
+    row_A(L, ud, n, fl, au);
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
-      const double mf = irr ? irr_mass_row(L, fn[d], c) : mass_reg(fn[d], c, L.px, L.pxy, L.h3);
+      const double mf = irr ? irr_mass_row(L, fn[d], n) : mass_reg(fn[d], n, L.px, L.pxy, L.h3);
       L.f[d][c] = mf - au[d];
     }
   } else {
@@ -279,10 +280,10 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
 #pragma unroll 1
     for (int d = 0; d < 3; ++d) {
       double bt[3];
-      row_BT(L, fn[d], c, fl, bt);
+      row_BT(L, fn[d], n, fl, bt);
       gs += bt[d];
     }
-    L.g[c] = L.dh2 * gs - row_B(L, ud, c, fl);
+    L.g[c] = L.dh2 * gs - row_B(L, ud, n, fl);
   } else {
     L.g[c] = 0.0;
   }
@@ -315,7 +316,8 @@ __global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, doub
   pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  const int64_t c = pidx(L.px, L.pxy, i, j, k);
+  const Node n = node_at(L.px, L.pxy, i, j, k);
+  const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
   double* out[3] = {o0, o1, o2};
   if (!(fl & F_ACT)) {
@@ -326,16 +328,16 @@ __global__ void k_rhs_transpose(LevelDev<double> L, double* o0, double* o1, doub
   const bool irr = fl & F_IRR;
   double bl[3];
   if (!irr) {
-    const Diff7<double> dl = diff7(L.p, c, L.px, L.pxy);
+    const Diff7<double> dl = diff7(L.p, n, L.px, L.pxy);
     div12_all(dl, bl);
 #pragma unroll
     for (int d = 0; d < 3; ++d) bl[d] *= L.h2 * (1.0 / 12.0);
   } else {
-    irr_B_scalar(L, L.p, c, bl);
+    irr_B_scalar(L, L.p, n, bl);
   }
 #pragma unroll 1
   for (int d = 0; d < 3; ++d) {
-    const double mu = irr ? irr_mass_row(L, L.u[d], c) : mass_reg(L.u[d], c, L.px, L.pxy, L.h3);
+    const double mu = irr ? irr_mass_row(L, L.u[d], n) : mass_reg(L.u[d], n, L.px, L.pxy, L.h3);
     out[d][c] = mu + L.dh2 * bl[d];
   }
 }
@@ -351,13 +353,14 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
     const int i = (int)(q % X.nx);
     const int j = (int)((q / X.nx) % X.ny);
     const int k = (int)(q / ((int64_t)X.nx * X.ny));
-    const int64_t c = pidx(X.px, X.pxy, i, j, k);
+    const Node n = node_at(X.px, X.pxy, i, j, k);
+    const int64_t c = n.c;
     const uint8_t fl = X.flags[c];
     const double* uu[3] = {X.u[0], X.u[1], X.u[2]};  // no address of kernel-parameter members
     if (fl & F_VFREE) {
       double au[3], bt[3];
-      row_A(X, uu, c, fl, au);
-      row_BT(X, X.p, c, fl, bt);
+      row_A(X, uu, n, fl, au);
+      row_BT(X, X.p, n, fl, bt);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const double r = X.f[d][c] - au[d] - bt[d];
@@ -369,7 +372,7 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
       for (int d = 0; d < 3; ++d) E.f[d][c] = 0.f;
     }
     if (fl & F_ACT) {
-      const double r = X.g[c] - row_B(X, uu, c, fl) + row_C(X, X.p, c, fl);
+      const double r = X.g[c] - row_B(X, uu, n, fl) + row_C(X, X.p, n, fl);
       E.g[c] = (float)r;
       v[0] += r * r;
     } else {
@@ -462,13 +465,14 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
     const int i = (int)(q % X.nx);
     const int j = (int)((q / X.nx) % X.ny);
     const int k = (int)(q / ((int64_t)X.nx * X.ny));
-    const int64_t c = pidx(X.px, X.pxy, i, j, k);
+    const Node n = node_at(X.px, X.pxy, i, j, k);
+    const int64_t c = n.c;
     const uint8_t fl = X.flags[c];
     double r[4];
     if (!(fl & F_IRR)) {
-      const GNb<int64_t> gu[3] = {gnb(Q.u[0], c, X.px, X.pxy), gnb(Q.u[1], c, X.px, X.pxy),
-                                  gnb(Q.u[2], c, X.px, X.pxy)};
-      const GNb<int64_t> gp = gnb(Q.p, c, X.px, X.pxy);
+      const GNb<int64_t> gu[3] = {gnb(Q.u[0], n, X.px, X.pxy), gnb(Q.u[1], n, X.px, X.pxy),
+                                  gnb(Q.u[2], n, X.px, X.pxy)};
+      const GNb<int64_t> gp = gnb(Q.p, n, X.px, X.pxy);
       if (fl & F_VFREE) {
         int64_t ibt[3];
         div12_all(diff7v<int64_t>(gp), ibt);
@@ -490,9 +494,9 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
         r[3] = 0.0;
       }
     } else {
-      const GNb<double> u[3] = {gnb(X.u[0], c, X.px, X.pxy), gnb(X.u[1], c, X.px, X.pxy),
-                                gnb(X.u[2], c, X.px, X.pxy)};
-      node_residual_v(X, c, fl, u, gnb(X.p, c, X.px, X.pxy), r);
+      const GNb<double> u[3] = {gnb(X.u[0], n, X.px, X.pxy), gnb(X.u[1], n, X.px, X.pxy),
+                                gnb(X.u[2], n, X.px, X.pxy)};
+      node_residual_v(X, c, fl, u, gnb(X.p, n, X.px, X.pxy), r);
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {

@@ -9,11 +9,12 @@ namespace hhg {
 
 // RU = F - B^T P (velocity nodes).
 template <class T>
-__device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, int64_t c) {
+__device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, const Node& n) {
+  const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
   if (!(fl & F_VFREE)) return;
   T bt[3];
-  row_BT(L, L.p, c, fl, bt);
+  row_BT(L, L.p, n, fl, bt);
 #pragma unroll
   for (int d = 0; d < 3; ++d) L.r[d][c] = L.f[d][c] - bt[d];
 }
@@ -61,9 +62,9 @@ __device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, c
 }
 
 template <bool SPEC, class T>
-__device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
-  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
-  node_vel_gs_v<SPEC>(L, c, u, inv6nuh);
+__device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, const Node& n, T inv6nuh) {
+  const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
+  node_vel_gs_v<SPEC>(L, n.c, u, inv6nuh);
 }
 
 // Regular-node velocity update with f - B^T p formed at the node.
@@ -110,32 +111,34 @@ __device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t 
 }
 
 template <bool SPEC, class T>
-__device__ __forceinline__ void node_vel_gs_rhs(const LevelDev<T>& L, int64_t c, T inv6nuh) {
-  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
-  node_vel_gs_rhs_v<SPEC>(L, c, u, gnb(L.p, c, L.px, L.pxy), inv6nuh);
+__device__ __forceinline__ void node_vel_gs_rhs(const LevelDev<T>& L, const Node& n, T inv6nuh) {
+  const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
+  node_vel_gs_rhs_v<SPEC>(L, n.c, u, gnb(L.p, n, L.px, L.pxy), inv6nuh);
 }
 
 // RP = B U - G (pressure nodes).
 template <class T>
-__device__ __forceinline__ void node_pres_rhs(const LevelDev<T>& L, int64_t c) {
+__device__ __forceinline__ void node_pres_rhs(const LevelDev<T>& L, const Node& n) {
+  const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
   if (!(fl & F_ACT)) return;
   const T* uu[3] = {L.u[0], L.u[1], L.u[2]};
-  L.rp[c] = row_B(L, uu, c, fl) - L.g[c];
+  L.rp[c] = row_B(L, uu, n, fl) - L.g[c];
 }
 
 // p <- p + omega (RP - C p) / C_ii  (forward SOR sweep from zero, Sec. 3.5).
 template <class T>
-__device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, int64_t c, T omega_over_6c) {
+__device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, const Node& n, T omega_over_6c) {
+  const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
   if (!(fl & F_ACT)) return;
   const T pc = L.p[c];
   if (!(fl & F_IRR)) {
-    const T cp = L.c * ((T)6 * pc - nb6(L.p, c, L.px, L.pxy));
+    const T cp = L.c * ((T)6 * pc - nb6(L.p, n, L.px, L.pxy));
     L.p[c] = pc + omega_over_6c * (L.rp[c] - cp);
   } else {
     T dg, of;
-    irr_lap_parts(L, L.p, c, dg, of);
+    irr_lap_parts(L, L.p, n, dg, of);
     const T cp = L.c * (dg * pc + of);
     L.p[c] = pc + L.omega * (L.rp[c] - cp) / (L.c * dg);
   }
@@ -184,9 +187,9 @@ __device__ __forceinline__ void node_pres_gs_rhs_v(const LevelDev<T>& L, int64_t
 }
 
 template <bool SPEC, class T>
-__device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, int64_t c, T omega_over_6c) {
-  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
-  node_pres_gs_rhs_v<SPEC>(L, c, u, gnb(L.p, c, L.px, L.pxy), omega_over_6c);
+__device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, const Node& n, T omega_over_6c) {
+  const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
+  node_pres_gs_rhs_v<SPEC>(L, n.c, u, gnb(L.p, n, L.px, L.pxy), omega_over_6c);
 }
 
 // (RU, RP) = (F, G) - K (U, P) at one node, returned in r[0..3]; zero for
@@ -209,11 +212,12 @@ __device__ __forceinline__ void node_residual_v(const LevelDev<T>& L, int64_t c,
 }
 
 template <class T>
-__device__ __forceinline__ void node_residual(const LevelDev<T>& L, int64_t c) {
+__device__ __forceinline__ void node_residual(const LevelDev<T>& L, const Node& n) {
+  const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
-  const GNb<T> u[3] = {gnb(L.u[0], c, L.px, L.pxy), gnb(L.u[1], c, L.px, L.pxy), gnb(L.u[2], c, L.px, L.pxy)};
+  const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
   T r[4];
-  node_residual_v(L, c, fl, u, gnb(L.p, c, L.px, L.pxy), r);
+  node_residual_v(L, c, fl, u, gnb(L.p, n, L.px, L.pxy), r);
 #pragma unroll
   for (int d = 0; d < 3; ++d) L.r[d][c] = r[d];
   L.rp[c] = r[3];
@@ -227,18 +231,22 @@ template <class T>
 __device__ __forceinline__ void node_restrict(const LevelDev<T>& Lf, const LevelDev<T>& Lc, int i, int j, int k) {
   const int64_t cc = pidx(Lc.px, Lc.pxy, i, j, k);
   const uint8_t fl = Lc.flags[cc];
-  const int64_t cf = pidx(Lf.px, Lf.pxy, 2 * i, 2 * j, 2 * k);
-  const int64_t a = 1, b = Lf.px, e = Lf.pxy;
-  const int64_t off[7] = {a, b, e, a + b, b + e, a + e, a + b + e};
+  const Node nf = node_at(Lf.px, Lf.pxy, 2 * i, 2 * j, 2 * k);
   T s[4];
   const T* src[4] = {Lf.r[0], Lf.r[1], Lf.r[2], Lf.rp};
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const T* x = src[q];
+    const GNb<T> x = gnb(src[q], nf, Lf.px, Lf.pxy);
+    // the 14 Kuhn neighbours: +-(e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3)
     T acc = 0;
-#pragma unroll
-    for (int o = 0; o < 7; ++o) acc += x[cf + off[o]] + x[cf - off[o]];
-    s[q] = x[cf] + (T)0.5 * acc;
+    acc += x(1, 0, 0) + x(-1, 0, 0);
+    acc += x(0, 1, 0) + x(0, -1, 0);
+    acc += x(0, 0, 1) + x(0, 0, -1);
+    acc += x(1, 1, 0) + x(-1, -1, 0);
+    acc += x(0, 1, 1) + x(0, -1, -1);
+    acc += x(1, 0, 1) + x(-1, 0, -1);
+    acc += x(1, 1, 1) + x(-1, -1, -1);
+    s[q] = x(0, 0, 0) + (T)0.5 * acc;
   }
   const bool vf = fl & F_VFREE, ac = fl & F_ACT;
 #pragma unroll

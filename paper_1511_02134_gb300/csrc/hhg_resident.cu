@@ -42,9 +42,23 @@ __host__ __device__ inline uint32_t align16(uint64_t x) { return (uint32_t)((x +
 template <class T>
 struct DNb {
   T* const* row;
-  int z, xy, px;
-  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const { return row[z + dz][xy + dx + px * dy]; }
+  int z, xy, dxm, dxp, px;
+  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const {
+    return row[z + dz][xy + (dx < 0 ? dxm : (dx > 0 ? dxp : 0)) + px * dy];
+  }
 };
+
+// In-plane position of node (i, j) of a level and the steps to its
+// x-neighbours (rows grouped by x mod 4, hhg_common.h).
+struct InPlane {
+  int xy, dxm, dxp;
+};
+
+template <class T>
+__device__ __forceinline__ InPlane in_plane(const LevelDev<T>& L, int i, int j) {
+  return InPlane{(int)(L.px * (j + 1) + row_pos(i + 1, L.px)), (int)row_step_minus(i + 1, L.px),
+                 (int)row_step_plus(i + 1, L.px)};
+}
 
 template <class T>
 struct Res {
@@ -60,7 +74,7 @@ struct Res {
     return reinterpret_cast<E*>(table(q)[f * (S.lv[q].nz + 2) + z]);
   }
   // The level with its field pointers at padded plane z (node plane z - 1):
-  // node (i, j) of that plane is entry (j + 1) px + (i + 1).
+  // node (i, j) of that plane is entry in_plane(L, i, j).xy.
   __device__ __forceinline__ LevelDev<T> at_plane(int q, int z) const {
     LevelDev<T> L = S.lv[q];
     L.wt = reinterpret_cast<const T*>(sm + S.wts[q]);
@@ -75,9 +89,9 @@ struct Res {
     L.cls = row_ptr<const uint16_t>(q, 9, z);
     return L;
   }
-  __device__ __forceinline__ DNb<T> view(int q, int f, int z, int xy) const {
+  __device__ __forceinline__ DNb<T> view(int q, int f, int z, const InPlane& at) const {
     void* const* t = table(q) + f * (S.lv[q].nz + 2);
-    return DNb<T>{reinterpret_cast<T* const*>(t), z, xy, (int)S.lv[q].px};
+    return DNb<T>{reinterpret_cast<T* const*>(t), z, at.xy, at.dxm, at.dxp, (int)S.lv[q].px};
   }
 };
 
@@ -207,9 +221,10 @@ __device__ void r_colour(const Res<T>& R, int q, int colour, int what) {
     const int i = ((colour - j - k) & 3) + 4 * tq;
     if (i >= L.nx) continue;
     const LevelDev<T> Ln = R.at_plane(q, k + 1);
-    const int c = (j + 1) * (int)L.px + (i + 1);
-    const DNb<T> u[3] = {R.view(q, 0, k + 1, c), R.view(q, 1, k + 1, c), R.view(q, 2, k + 1, c)};
-    const DNb<T> p = R.view(q, 3, k + 1, c);
+    const InPlane at = in_plane(L, i, j);
+    const int c = at.xy;
+    const DNb<T> u[3] = {R.view(q, 0, k + 1, at), R.view(q, 1, k + 1, at), R.view(q, 2, k + 1, at)};
+    const DNb<T> p = R.view(q, 3, k + 1, at);
     if (what != 1) node_vel_gs_rhs_v<true>(Ln, c, u, p, S.inv6nuh[q]);
     if (what != 0) node_pres_gs_rhs_v<true>(Ln, c, u, p, S.omc[q]);
   }
@@ -234,10 +249,11 @@ __device__ __forceinline__ void r_residual_at(const Res<T>& R, int q, int i, int
     return;
   }
   const LevelDev<T> Ln = R.at_plane(q, k + 1);
-  const int c = (j + 1) * (int)L.px + (i + 1);
+  const InPlane at = in_plane(L, i, j);
+  const int c = at.xy;
   const uint8_t fl = Ln.flags[c];
-  const DNb<T> u[3] = {R.view(q, 0, k + 1, c), R.view(q, 1, k + 1, c), R.view(q, 2, k + 1, c)};
-  node_residual_v(Ln, c, fl, u, R.view(q, 3, k + 1, c), r);
+  const DNb<T> u[3] = {R.view(q, 0, k + 1, at), R.view(q, 1, k + 1, at), R.view(q, 2, k + 1, at)};
+  node_residual_v(Ln, c, fl, u, R.view(q, 3, k + 1, at), r);
 }
 
 // (F, G) of level q - 1 = P^T (residual of level q), (U, P) of level q - 1 = 0,
@@ -286,7 +302,7 @@ __device__ void r_restrict(const Res<T>& R, int q) {
     int64_t cc;
     if (resident) {
       C = R.at_plane(q - 1, K + 1);
-      cc = (J + 1) * Lc.px + (I + 1);
+      cc = in_plane(Lc, I, J).xy;
     } else {
       C = Lc;
       cc = pidx(Lc.px, Lc.pxy, I, J, K);
@@ -319,7 +335,7 @@ __device__ void r_prolong(const Res<T>& R, int q) {
     const int j = (t / Lf.nx) % Lf.ny;
     const int k = k0 + t / (Lf.nx * Lf.ny);
     const LevelDev<T> F = R.at_plane(q, k + 1);
-    const int cf = (j + 1) * (int)Lf.px + (i + 1);
+    const int cf = in_plane(Lf, i, j).xy;
     const uint8_t fl = F.flags[cf];
     if (!(fl & F_ACT)) continue;
     const int a = i & 1, b = j & 1, e = k & 1;
@@ -338,8 +354,8 @@ __device__ void r_prolong(const Res<T>& R, int q) {
       cu1[1] = B.u[1];
       cu1[2] = B.u[2];
       cu1[3] = B.p;
-      c0 = (J + 1) * Lc.px + (I + 1);
-      c1 = (J + b + 1) * Lc.px + (I + a + 1);
+      c0 = in_plane(Lc, I, J).xy;
+      c1 = in_plane(Lc, I + a, J + b).xy;
     } else {
       cu0[0] = cu1[0] = Lc.u[0];
       cu0[1] = cu1[1] = Lc.u[1];

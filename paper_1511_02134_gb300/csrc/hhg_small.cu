@@ -32,7 +32,7 @@ __device__ void b_vel_rhs(const Team& tm, const LevelDev<T>& L) {
   for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) {
     int i, j, k;
     decode3(L, q, i, j, k);
-    node_vel_rhs(L, pidx(L.px, L.pxy, i, j, k));
+    node_vel_rhs(L, node_at(L.px, L.pxy, i, j, k));
   }
   tm.sync();
 }
@@ -43,7 +43,7 @@ __device__ void b_residual(const Team& tm, const LevelDev<T>& L) {
   for (int q = (int)tm.rank(); q < n; q += (int)tm.size()) {
     int i, j, k;
     decode3(L, q, i, j, k);
-    node_residual(L, pidx(L.px, L.pxy, i, j, k));
+    node_residual(L, node_at(L.px, L.pxy, i, j, k));
   }
   tm.sync();
 }
@@ -63,7 +63,7 @@ __device__ void b_colour(const Team& tm, const LevelDev<T>& L, int colour, int w
     const int k = q / (nq * L.ny);
     const int i = ((colour - j - k) & 3) + 4 * t;
     if (i >= L.nx) continue;
-    const int64_t c = pidx(L.px, L.pxy, i, j, k);
+    const Node c = node_at(L.px, L.pxy, i, j, k);
     if (what != 1) {
       if (sizeof(T) == 4)
         node_vel_gs_rhs<true>(L, c, inv6nuh);

@@ -31,8 +31,13 @@ namespace hhg {
 
 namespace {
 
-constexpr int TX = 64, TY = 8;     // tile of interior nodes; TX a multiple of 4
-constexpr int BX = TX + 4;         // box width: TX + 2 halo nodes, rounded up to 16 bytes of FP32
+constexpr int TX = 64, TY = 8;     // tile of interior nodes; TX a multiple of 64
+// The rows of the padded arrays are grouped by x mod 4 (hhg_common.h), so a
+// tile row with its halo, padded x in [x0, x0 + TX + 1], is 4 runs of
+// TX / 4 + 1 positions, one per residue.  The box takes BQ positions of each
+// of the 4 residues (BQ = TX/4 + 1 rounded up to 16 bytes of FP32).
+constexpr int BQ = 20;
+constexpr int BX = 4 * BQ;         // staged entries per tile row
 constexpr int BY = TY + 2;         // box height with the halo rows
 constexpr int SLOTS = 4;           // ring of staged planes
 constexpr int TT = (TX / 4) * TY;  // threads: one per node of the colour in a tile plane
@@ -57,11 +62,15 @@ __host__ __device__ constexpr size_t tile_smem() {
 }
 
 // Shared-memory view over three consecutive staged planes of one field.
+// Staged row entry of padded x q: (q mod 4) BQ + (q div 4 - x0 / 4).
 template <class T>
 struct SNb {
   const T* pl[3];  // planes k-1, k, k+1
-  int c;           // xi + BX * yi of the centre node
-  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const { return pl[dz + 1][c + dx + BX * dy]; }
+  int yb;          // BX * yi of the centre node's row
+  int xo[3];       // row entries of padded x q-1, q, q+1
+  __device__ __forceinline__ T operator()(int dx, int dy, int dz) const {
+    return pl[dz + 1][yb + BX * dy + xo[dx + 1]];
+  }
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -89,11 +98,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, int t, int r, int y, int z,
+                                            uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];" ::"r"(smem_addr(dst)),
-      "l"(map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(t), "r"(r), "r"(y), "r"(z), "r"(smem_addr(bar))
       : "memory");
 }
 
@@ -108,7 +118,7 @@ __device__ __forceinline__ void issue_plane(const TileMaps& tm, unsigned char* s
   mbar_expect(&bar[s], (uint32_t)(NF * BX * BY * sizeof(T)));
 #pragma unroll
   for (int f = 0; f < NF; ++f)
-    tma_load_3d(sm + (size_t)(s * NF + f) * plane_bytes<T>(), &tm.m[f], x0, y0, k0 + q, &bar[s]);
+    tma_load_4d(sm + (size_t)(s * NF + f) * plane_bytes<T>(), &tm.m[f], x0 / 4, 0, y0, k0 + q, &bar[s]);
 }
 
 template <class T, int MODE>
@@ -150,20 +160,24 @@ __global__ void __launch_bounds__(TT) k_colour_tma(const __grid_constant__ TileM
     const int i = x0 + 4 * q4 + ((colour - j - k) & 3);
     if (i < L.nx && j < L.ny) {
       const int64_t c = pidx(L.px, L.pxy, i, j, k);
-      const int sc = (i - x0 + 1) + BX * (yq + 1);
+      const int qx = i + 1, tb = x0 / 4;
+      auto entry = [&](int qq) { return (qq & 3) * BQ + (qq >> 2) - tb; };
       const T* pl[3];
 #pragma unroll
       for (int r = 0; r < 3; ++r)
         pl[r] = reinterpret_cast<const T*>(sm + (size_t)((q + r) % SLOTS) * NF * plane_bytes<T>());
+      const int yb = BX * (yq + 1), xo0 = entry(qx - 1), xo1 = entry(qx), xo2 = entry(qx + 1);
       SNb<T> u[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) u[d] = SNb<T>{{pl[0] + d * FS, pl[1] + d * FS, pl[2] + d * FS}, sc};
+      for (int d = 0; d < 3; ++d)
+        u[d] = SNb<T>{{pl[0] + d * FS, pl[1] + d * FS, pl[2] + d * FS}, yb, {xo0, xo1, xo2}};
+      const SNb<T> pv{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, yb, {xo0, xo1, xo2}};
       if (MODE == 0)
-        node_vel_gs_rhs_v<false>(L, c, u, SNb<T>{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, sc}, wfac);
+        node_vel_gs_rhs_v<false>(L, c, u, pv, wfac);
       else if (MODE == 1)
         node_vel_gs_v<false>(L, c, u, wfac);
       else
-        node_pres_gs_rhs_v<false>(L, c, u, SNb<T>{{pl[0] + 3 * FS, pl[1] + 3 * FS, pl[2] + 3 * FS}, sc}, wfac);
+        node_pres_gs_rhs_v<false>(L, c, u, pv, wfac);
     }
     __syncthreads();
     // the slot of plane q is free: stage the next plane into it
@@ -200,8 +214,9 @@ using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, 
 
 }  // namespace
 
-// Tensor maps of u_0, u_1, u_2, p of a level: 3-D over the padded array
-// (px, py, pz), box (BX, BY, 1), zero fill outside the array.
+// Tensor maps of u_0, u_1, u_2, p of a level: 4-D over the padded array
+// (px / 4 positions, 4 residues, py, pz), box (BQ, 4, BY, 1), zero fill
+// outside the array.
 template <class T>
 int make_tile_maps(const LevelDev<T>& L, TileMaps& out, std::string& err) {
   static EncodeTiled encode = nullptr;
@@ -217,17 +232,18 @@ int make_tile_maps(const LevelDev<T>& L, TileMaps& out, std::string& err) {
     encode = reinterpret_cast<EncodeTiled>(fn);
   }
   const T* f[4] = {L.u[0], L.u[1], L.u[2], L.p};
-  const cuuint64_t dims[3] = {(cuuint64_t)L.px, (cuuint64_t)(L.pxy / L.px), (cuuint64_t)(L.nalloc / L.pxy)};
-  const cuuint64_t strides[2] = {(cuuint64_t)L.px * sizeof(T), (cuuint64_t)L.pxy * sizeof(T)};
-  const cuuint32_t box[3] = {BX, BY, 1};
-  const cuuint32_t estr[3] = {1, 1, 1};
+  const cuuint64_t dims[4] = {(cuuint64_t)(L.px / 4), 4, (cuuint64_t)(L.pxy / L.px), (cuuint64_t)(L.nalloc / L.pxy)};
+  const cuuint64_t strides[3] = {(cuuint64_t)(L.px / 4) * sizeof(T), (cuuint64_t)L.px * sizeof(T),
+                                 (cuuint64_t)L.pxy * sizeof(T)};
+  const cuuint32_t box[4] = {BQ, 4, BY, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
   for (int q = 0; q < 4; ++q) {
-    if (((uintptr_t)f[q] & 15) || (strides[0] & 15) || (strides[1] & 15)) {
+    if (((uintptr_t)f[q] & 15) || (strides[0] & 15) || (strides[1] & 15) || (strides[2] & 15)) {
       err = "field not aligned for tensor copies";
       return HHG_EINVAL;
     }
     const CUresult r = encode(&out.m[q], sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                              3, (void*)f[q], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                              4, (void*)f[q], dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
