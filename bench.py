@@ -38,7 +38,7 @@ TOL = 1e-8
 # capture of `bench.py --roofline-only` at that level (cold caches: ncu
 # flushes them before each pass); None where no capture of the current kernel
 # exists.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {7: 47069440 + 84736}
 
 
 def _peaks():
