@@ -211,8 +211,8 @@ constexpr int64_t RES_MAX_NODES = 1 << 16;  // default cap on the top level's la
 constexpr unsigned RES_CTAS_FP32 = 8;
 constexpr unsigned RES_CTAS_FP64 = 16;
 constexpr int RES_MAX_CTAS = 16;
-constexpr int RES_FIELDS = 8;
-constexpr int RES_TAB_FIELDS = 10;
+constexpr int RES_FIELDS = 12;
+constexpr int RES_TAB_FIELDS = 14;
 template <class T>
 struct ResidentCycle {
   unsigned nblocks;

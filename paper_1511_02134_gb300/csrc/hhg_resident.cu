@@ -16,8 +16,7 @@
 // (hhg_node_ops.cuh): the node's own fields are reached through a LevelDev
 // whose field pointers point at the node's plane, its neighbours through
 // plane-pointer tables, the boundary-class rows from a copy of the level's
-// table in shared memory.  The residual is evaluated inside the restriction
-// (the 15 fine nodes of each coarse node), so no residual fields are stored.
+// table in shared memory.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -85,8 +84,11 @@ struct Res {
     }
     L.p = row_ptr<T>(q, 3, z);
     L.g = row_ptr<T>(q, 7, z);
-    L.flags = row_ptr<const uint8_t>(q, 8, z);
-    L.cls = row_ptr<const uint16_t>(q, 9, z);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.r[d] = row_ptr<T>(q, 8 + d, z);
+    L.rp = row_ptr<T>(q, 11, z);
+    L.flags = row_ptr<const uint8_t>(q, RES_FIELDS, z);
+    L.cls = row_ptr<const uint16_t>(q, RES_FIELDS + 1, z);
     return L;
   }
   __device__ __forceinline__ DNb<T> view(int q, int f, int z, const InPlane& at) const {
@@ -137,7 +139,7 @@ __device__ void r_setup(const Res<T>& R) {
         unsigned char* loc;
         if (f < RES_FIELDS)
           loc = base + sizeof(T) * (f * fb + lp * plane);
-        else if (f == 8)
+        else if (f == RES_FIELDS)
           loc = base + sizeof(T) * RES_FIELDS * fb + lp * plane;
         else
           loc = base + align16(sizeof(T) * RES_FIELDS * fb + fb) + 2 * lp * plane;
@@ -240,30 +242,41 @@ __device__ void r_uzawa(const Res<T>& R, int q) {
   for (int c = 1; c < 4; ++c) r_colour(R, q, c, 1);
 }
 
-// Residual of level q at fine node (i, j, k) (zero outside the lattice).
+// (RU, RP) of level q on this CTA's planes (node_residual).
 template <class T>
-__device__ __forceinline__ void r_residual_at(const Res<T>& R, int q, int i, int j, int k, T r[4]) {
-  const LevelDev<T>& L = R.S.lv[q];
-  if (i < 0 || j < 0 || k < 0 || i >= L.nx || j >= L.ny || k >= L.nz) {
-    r[0] = r[1] = r[2] = r[3] = (T)0;
-    return;
+__device__ void r_residual(const Res<T>& R, int q) {
+  const ResidentCycle<T>& S = R.S;
+  const LevelDev<T>& L = S.lv[q];
+  const int k0 = S.kb[q][R.rank], k1 = S.kb[q][R.rank + 1];
+  const int n = (k1 - k0) * L.ny * L.nx;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int i = t % L.nx;
+    const int j = (t / L.nx) % L.ny;
+    const int k = k0 + t / (L.nx * L.ny);
+    const LevelDev<T> Ln = R.at_plane(q, k + 1);
+    const InPlane at = in_plane(L, i, j);
+    const int c = at.xy;
+    const uint8_t fl = Ln.flags[c];
+    const DNb<T> u[3] = {R.view(q, 0, k + 1, at), R.view(q, 1, k + 1, at), R.view(q, 2, k + 1, at)};
+    T r[4];
+    node_residual_v(Ln, c, fl, u, R.view(q, 3, k + 1, at), r);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Ln.r[d][c] = r[d];
+    Ln.rp[c] = r[3];
   }
-  const LevelDev<T> Ln = R.at_plane(q, k + 1);
-  const InPlane at = in_plane(L, i, j);
-  const int c = at.xy;
-  const uint8_t fl = Ln.flags[c];
-  const DNb<T> u[3] = {R.view(q, 0, k + 1, at), R.view(q, 1, k + 1, at), R.view(q, 2, k + 1, at)};
-  node_residual_v(Ln, c, fl, u, R.view(q, 3, k + 1, at), r);
 }
 
-// (F, G) of level q - 1 = P^T (residual of level q), (U, P) of level q - 1 = 0,
-// the arithmetic of node_restrict with the residual evaluated at the 15 fine
-// nodes.  The coarse level is resident (its nodes on this CTA's planes) or
-// the coarsest level in global memory (its nodes shared by the team).
+// (F, G) of level q - 1 = P^T (RU, RP) of level q, (U, P) of level q - 1 = 0
+// (node_restrict).  The coarse level is resident (its nodes on this CTA's
+// planes) or the coarsest level in global memory (its nodes shared by the
+// team).
 template <class T>
 __device__ void r_restrict(const Res<T>& R, int q) {
   const ResidentCycle<T>& S = R.S;
   cluster_sync();  // the fine level's last phase may have run on the first CTA alone
+  r_residual(R, q);
+  cluster_sync();
+  const LevelDev<T>& Lf = S.lv[q];
   const LevelDev<T>& Lc = S.lv[q - 1];
   const bool resident = q - 1 >= 1;
   int k0, k1, t0, ts;
@@ -279,25 +292,26 @@ __device__ void r_restrict(const Res<T>& R, int q) {
     ts = S.nblocks * blockDim.x;
   }
   const int n = (k1 - k0) * Lc.ny * Lc.nx;
-  // Kuhn directions e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3
-  const int ox[7] = {1, 0, 0, 1, 0, 1, 1}, oy[7] = {0, 1, 0, 1, 1, 0, 1}, oz[7] = {0, 0, 1, 0, 1, 1, 1};
   for (int t = t0; t < n; t += ts) {
     const int I = t % Lc.nx;
     const int J = (t / Lc.nx) % Lc.ny;
     const int K = k0 + t / (Lc.nx * Lc.ny);
-    T r0[4], acc[4] = {0, 0, 0, 0};
-    r_residual_at(R, q, 2 * I, 2 * J, 2 * K, r0);
-#pragma unroll
-    for (int o = 0; o < 7; ++o) {
-      T rp[4], rm[4];
-      r_residual_at(R, q, 2 * I + ox[o], 2 * J + oy[o], 2 * K + oz[o], rp);
-      r_residual_at(R, q, 2 * I - ox[o], 2 * J - oy[o], 2 * K - oz[o], rm);
-#pragma unroll
-      for (int w = 0; w < 4; ++w) acc[w] += rp[w] + rm[w];
-    }
+    const InPlane at = in_plane(Lf, 2 * I, 2 * J);
     T s[4];
 #pragma unroll
-    for (int w = 0; w < 4; ++w) s[w] = r0[w] + (T)0.5 * acc[w];
+    for (int w = 0; w < 4; ++w) {
+      const DNb<T> x = R.view(q, 8 + w, 2 * K + 1, at);
+      // the 14 Kuhn neighbours: +-(e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3)
+      T acc = 0;
+      acc += x(1, 0, 0) + x(-1, 0, 0);
+      acc += x(0, 1, 0) + x(0, -1, 0);
+      acc += x(0, 0, 1) + x(0, 0, -1);
+      acc += x(1, 1, 0) + x(-1, -1, 0);
+      acc += x(0, 1, 1) + x(0, -1, -1);
+      acc += x(1, 0, 1) + x(-1, 0, -1);
+      acc += x(1, 1, 1) + x(-1, -1, -1);
+      s[w] = x(0, 0, 0) + (T)0.5 * acc;
+    }
     LevelDev<T> C;
     int64_t cc;
     if (resident) {
@@ -382,7 +396,9 @@ __device__ void r_coarse(const Res<T>& R) {
   const ResidentCycle<T>& S = R.S;
   cluster_sync();
   if (coarse_fits_block(S.cs)) {
-    if (R.rank == 0) coarse::minres_team(Team{1}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
+    if (R.rank == 0) {
+      coarse::minres_team(Team{1}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
+    }
   } else {
     coarse::minres_team(Team{S.nblocks}, S.cs, S.lv[0], S.scratch, S.prm, S.info);
   }
