@@ -385,29 +385,32 @@ void enq_cycle64(hhg_mesh* M) {
   M->launches += 3;
 }
 
-// FP32+IR cycle body: correction V-cycle in FP32 from zero on the FP32
-// residual, x += e in FP64, projection in FP64, FP64 residual -> FP32 rhs.
 // FP64 residual of the finest FP64 iterate into the FP32 right-hand side,
-// its squared norm into d_scalars[0].
-void enq_ir_residual(hhg_mesh* M) {
+// its squared norm into d_scalars[0] (have_max: the update left the
+// iterate's maxima for the fixed-point evaluation).
+void enq_ir_residual(hhg_mesh* M, bool have_max) {
   LevelHost& H = M->lv[M->finest];
   if (M->opt.ir_fixed_point) {
-    launch_ir_residual_fx(H.d64, M->fx, H.d32, M->d_fxmax, M->d_partial, M->d_scalars, M->stream);
-    M->launches += 4;
+    launch_ir_residual_fx(H.d64, M->fx, H.d32, M->d_fxmax, have_max, M->d_partial, M->d_scalars, M->stream);
+    M->launches += have_max ? 3 : 4;
   } else {
     launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
     M->launches += 2;
   }
 }
 
+// FP32+IR cycle body: correction V-cycle in FP32 from zero on the FP32
+// residual, x += e in FP64, FP64 residual -> FP32 right-hand side.  On a
+// mesh without outflow the residual does not change under constant shifts
+// of the pressure (B^T 1 = 0, C 1 = 0), so the mean projection is applied
+// once, to the final iterate (do_solve).
 void enq_cycle32(hhg_mesh* M) {
   LevelHost& H = M->lv[M->finest];
   launch_zero<float>(H.d32, 0, M->stream);
   enq_vcycle<float>(M, M->finest);
-  launch_ir_update(H.d64, H.d32, M->stream);
+  launch_ir_update(H.d64, H.d32, M->opt.ir_fixed_point ? M->d_fxmax : nullptr, M->stream);
   M->launches += 1;
-  if (!M->macro.has_outflow) enq_project<double>(M, M->finest);
-  enq_ir_residual(M);
+  enq_ir_residual(M, M->opt.ir_fixed_point != 0);
 }
 
 // Reads the error word copied with the scalar block: a tiled sweep whose
@@ -458,7 +461,7 @@ int residual_norm2(hhg_mesh* M, int mode, double* norm2) {
     launch_residual_norm2<double>(H.d64, M->d_partial, M->d_scalars, M->stream);
     M->launches += 3;
   } else {
-    enq_ir_residual(M);
+    enq_ir_residual(M, false);
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
@@ -517,6 +520,10 @@ int do_solve(hhg_mesh* M, double tol, int max_cycles, int mode, hhg_stats* st) {
     if (s.status == HHG_OK && rel > tol) s.status = HHG_EMAXIT;
   } else if (!std::isfinite(r0)) {
     s.status = HHG_EDIVERGED;
+  }
+  if (mode == HHG_MODE_FP32_IR && !M->macro.has_outflow) {
+    enq_project<double>(M, M->finest);
+    CK(cudaGetLastError());
   }
   s.cycles = cycles;
   s.rel_residual = rel;
@@ -770,7 +777,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     }
     if ((rc = dalloc(M, (void**)&M->d_stage, sizeof(double) * 3 * (size_t)H.sh.n()))) return bail(rc);
   }
-  if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * REDUCE_BLOCKS))) return bail(rc);
+  if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * std::max(REDUCE_BLOCKS, IR_BLOCKS)))) return bail(rc);
   if ((rc = dalloc(M, (void**)&M->d_scalars, sizeof(double) * 16))) return bail(rc);
   cudaMemset(M->d_scalars, 0, sizeof(double) * 16);
   if ((e = cudaMallocHost((void**)&M->h_scalars, sizeof(double) * 16)) != cudaSuccess) {

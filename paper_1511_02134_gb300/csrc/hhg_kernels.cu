@@ -509,14 +509,36 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
   block_reduce_store<1>(v, partial);
 }
 
-__global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
+// x += e; with mx, also the per-field |x| maxima of the new iterate (as in
+// k_ir_absmax, mx zeroed before).
+__global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E, unsigned long long* mx) {
   pdl_enter();
+  __shared__ double sh[4][32];
+  double m[4] = {0.0, 0.0, 0.0, 0.0};
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
-    X.u[0][q] += (double)E.u[0][q];
-    X.u[1][q] += (double)E.u[1][q];
-    X.u[2][q] += (double)E.u[2][q];
-    X.p[q] += (double)E.p[q];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const double v = X.u[d][q] + (double)E.u[d][q];
+      X.u[d][q] = v;
+      m[d] = fmax(m[d], fabs(v));
+    }
+    const double v = X.p[q] + (double)E.p[q];
+    X.p[q] = v;
+    m[3] = fmax(m[3], fabs(v));
+  }
+  if (!mx) return;
+#pragma unroll
+  for (int w = 0; w < 4; ++w) {
+    double x = m[w];
+    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) sh[w][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double x = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) x = fmax(x, sh[threadIdx.x][q]);
+    atomicMax(&mx[threadIdx.x], (unsigned long long)__double_as_longlong(x));
   }
 }
 
@@ -703,16 +725,19 @@ void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, dou
   launch_k(k_final_sum<1>, 1, 32, s, partial, REDUCE_BLOCKS, out);
 }
 void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e,
-                           unsigned long long* mx, double* partial, double* out, cudaStream_t s) {
-  cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned long long), s);
-  launch_k(k_ir_absmax, REDUCE_BLOCKS, REDUCE_THREADS, s, x, mx);
+                           unsigned long long* mx, bool have_max, double* partial, double* out, cudaStream_t s) {
+  if (!have_max) {
+    cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned long long), s);
+    launch_k(k_ir_absmax, IR_BLOCKS, REDUCE_THREADS, s, x, mx);
+  }
   launch_k(k_ir_quantize, flat_blocks(x.nalloc), 256, s, x, q, (const unsigned long long*)mx);
-  launch_k(k_ir_residual_fx, REDUCE_BLOCKS, REDUCE_THREADS, s, x, q, e, (const unsigned long long*)mx, partial);
-  launch_k(k_final_sum<1>, 1, 32, s, (const double*)partial, REDUCE_BLOCKS, out);
+  launch_k(k_ir_residual_fx, IR_BLOCKS, REDUCE_THREADS, s, x, q, e, (const unsigned long long*)mx, partial);
+  launch_k(k_final_sum<1>, 1, 32, s, (const double*)partial, IR_BLOCKS, out);
 }
 
-void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
-  launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e);
+void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, unsigned long long* mx, cudaStream_t s) {
+  if (mx) cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned long long), s);
+  launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e, mx);
 }
 void launch_scatter(const LevelDev<double>& L, const double* src, int ncomp, double* const* dst, uint8_t mask,
                     cudaStream_t s) {

@@ -86,16 +86,21 @@ void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStr
 // squared norm partials; and x += e.
 void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
                         cudaStream_t s);
-void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s);
+// x += e in FP64; with mx (not null), also the per-field |x| maxima of the
+// new iterate for the fixed-point residual (mx zeroed first).
+void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, unsigned long long* mx, cudaStream_t s);
 // The same residual with the regular-node stencils evaluated exactly in
 // 64-bit fixed point (hhg_kernels.cu): per-field |x| maxima into mx[0..4)
-// (zeroed first), quantization into q, residual, norm into out[0].
+// (zeroed first; skipped when have_max, i.e. launch_ir_update left them),
+// quantization into q, residual, norm into out[0].  IR_BLOCKS blocks: the
+// partial-sum buffer holds that many per value.
+constexpr int IR_BLOCKS = 1216;
 struct FxIterate {
   int64_t* u[3];
   int64_t* p;
 };
 void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e,
-                           unsigned long long* mx, double* partial, double* out, cudaStream_t s);
+                           unsigned long long* mx, bool have_max, double* partial, double* out, cudaStream_t s);
 
 // Layout conversion between contiguous (n, 3)/(n,) arrays and padded fields.
 // mask: nodes whose value is kept (others get 0); 0 = keep all.
