@@ -275,13 +275,15 @@ __global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1
     for (int d = 0; d < 3; ++d) L.f[d][c] = 0.0;
   }
   if (fl & F_ACT) {
-    // g = delta h_T^2 sum_d B_d^T f_d - sum_d B_d u_D,d
+    // g = delta h_T^2 sum_d B_d^T f_d - sum_d B_d u_D,d (component d of B^T
+    // applied to f_d only)
+    const double* w = row_of(L, c, fl);
     double gs = 0.0;
-#pragma unroll 1
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
-      double bt[3];
-      row_BT(L, fn[d], n, fl, bt);
-      gs += bt[d];
+      const GNb<double> v = gnb(fn[d], n, L.px, L.pxy);
+      gs += irr ? L.h2 * st15v<double>(v, w + W_BT + 15 * d)
+                : (-L.h2 * (1.0 / 12.0)) * div12(diff7v<double>(v), d);
     }
     L.g[c] = L.dh2 * gs - row_B(L, ud, n, fl);
   } else {
