@@ -103,6 +103,10 @@ typedef struct hhg_options {
                                 latency-bound levels); 0 = default (2^20), -1 = never */
   int32_t colour_block_z;    /* planes per thread block of the colour kernels (1, 2 or 4; 0 =
                                 default: 2 on levels of at least 2^22 lattice nodes, else 1) */
+  int32_t resident_node_lists; /* cluster-resident levels (fuse_coarse_levels 2): 1 runs each
+                                velocity / pressure colour phase over per-CTA lists of its
+                                regular nodes and then its boundary nodes; 0 = default (1),
+                                -1 = over all lattice positions of the colour with flag tests */
 } hhg_options;
 
 /* Per-solve statistics. */

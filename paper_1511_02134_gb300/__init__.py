@@ -49,7 +49,7 @@ class Options(ctypes.Structure):
                 ("fuse_coarse_levels", ctypes.c_int32), ("fuse_max_nodes", ctypes.c_int32),
                 ("team_blocks", ctypes.c_int32), ("tile_min_nodes", ctypes.c_int32),
                 ("ir_fixed_point", ctypes.c_int32), ("spec_max_nodes", ctypes.c_int32),
-                ("colour_block_z", ctypes.c_int32)]
+                ("colour_block_z", ctypes.c_int32), ("resident_node_lists", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):

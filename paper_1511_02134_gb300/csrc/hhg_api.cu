@@ -35,6 +35,8 @@ struct LevelHost {
   bool tiled = false;  // colour sweeps on shared-memory tiles
   int kz = 4;          // planes per CTA of the tiled sweeps
   TileMaps tm64{}, tm32{};
+  int32_t* d_list = nullptr;         // node lists of the cluster-resident cycle (ResidentCycle::lists)
+  int32_t loff[RES_LISTS + 1] = {};  // their offsets
   double* mem64 = nullptr;
   float* mem32 = nullptr;
   LevelDev<double> d64{};
@@ -313,6 +315,40 @@ void enq_small_cycle(hhg_mesh* M) {
   M->launches += 1;
 }
 
+// Node lists of a level for the cluster-resident cycle: list 8 kind + 2 colour
+// + boundary holds the velocity (kind 0, F_VFREE) or pressure (kind 1, F_ACT)
+// nodes of colour (i + j + k) mod 4, regular (boundary 0) or F_IRR
+// (boundary 1), as (k << 20) | (j << 10) | i in lattice order.  The fused
+// colour-0 phase walks the pressure lists, so the lists are built only where
+// every velocity node is active and every regular active node carries a
+// velocity (a Dirichlet or outflow node lies on the domain boundary, F_IRR).
+int build_node_lists(hhg_mesh* M, LevelHost& H) {
+  const LevelShape& sh = H.sh;
+  if (sh.nx >= 1024 || sh.ny >= 1024 || sh.nz >= 2048) return HHG_OK;
+  std::vector<std::vector<int32_t>> lists(RES_LISTS);
+  for (int k = 0; k < sh.nz; ++k)
+    for (int j = 0; j < sh.ny; ++j)
+      for (int i = 0; i < sh.nx; ++i) {
+        const uint8_t f = H.flags[i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k)];
+        if ((f & F_VFREE) && !(f & F_ACT)) return HHG_OK;
+        if ((f & F_ACT) && !(f & F_IRR) && !(f & F_VFREE)) return HHG_OK;
+        const int32_t e = (k << 20) | (j << 10) | i;
+        const int b = 2 * ((i + j + k) & 3) + ((f & F_IRR) ? 1 : 0);
+        if (f & F_VFREE) lists[b].push_back(e);
+        if (f & F_ACT) lists[8 + b].push_back(e);
+      }
+  std::vector<int32_t> all;
+  for (int l = 0; l < RES_LISTS; ++l) {
+    H.loff[l] = (int32_t)all.size();
+    all.insert(all.end(), lists[l].begin(), lists[l].end());
+  }
+  H.loff[RES_LISTS] = (int32_t)all.size();
+  int rc = dalloc(M, (void**)&H.d_list, sizeof(int32_t) * std::max<size_t>(all.size(), 1));
+  if (rc) return rc;
+  CK(cudaMemcpy(H.d_list, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice));
+  return HHG_OK;
+}
+
 template <class T>
 void fill_resident(hhg_mesh* M, ResidentCycle<T>& S, int top) {
   std::memset(&S, 0, sizeof(S));
@@ -327,6 +363,11 @@ void fill_resident(hhg_mesh* M, ResidentCycle<T>& S, int top) {
     S.nu_post[q] = nu_steps<T>(M, l, false);
     S.inv6nuh[q] = (T)(1.0 / (6.0 * (double)S.lv[q].nuh));
     S.omc[q] = (T)((double)S.lv[q].omega / (6.0 * (double)S.lv[q].c));
+  }
+  for (int q = 1; q <= S.nres; ++q) {
+    const LevelHost& H = M->lv[M->coarsest + q];
+    S.lists[q] = H.d_list;
+    std::memcpy(S.loff[q], H.loff, sizeof(H.loff));
   }
   S.cs = M->coarse_sys;
   S.scratch = M->d_coarse;
@@ -565,6 +606,7 @@ void release(hhg_mesh* M) {
     cudaFree(H.d_cls);
     cudaFree(H.d_wt64);
     cudaFree(H.d_wt32);
+    cudaFree(H.d_list);
     cudaFree(H.mem64);
     cudaFree(H.mem32);
   }
@@ -863,6 +905,9 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   // the shared memory of one cluster (and has at most fuse_max_nodes nodes)
   if (o.fuse_coarse_levels == 2) {
     const int64_t lim = o.fuse_max_nodes > 0 ? o.fuse_max_nodes : RES_MAX_NODES;
+    if (o.resident_node_lists >= 0)
+      for (int l = M->coarsest + 1; l <= std::min(finest, M->coarsest + RES_MAX_LEVELS); ++l)
+        if (M->lv[l].sh.n() <= lim && (rc = build_node_lists(M, M->lv[l]))) return bail(rc);
     for (int pr = 0; pr < 2; ++pr) {
       M->res_nb[pr] = pr ? prepare_resident<float>(M->res_smem[pr]) : prepare_resident<double>(M->res_smem[pr]);
       const unsigned want = o.team_blocks > 0 ? (unsigned)o.team_blocks : (pr ? RES_CTAS_FP32 : RES_CTAS_FP64);

@@ -216,6 +216,7 @@ constexpr int64_t RES_MAX_NODES = 1 << 16;  // default cap on the top level's la
 constexpr unsigned RES_CTAS_FP32 = 8;
 constexpr unsigned RES_CTAS_FP64 = 16;
 constexpr int RES_MAX_CTAS = 16;
+constexpr int RES_LISTS = 16;
 constexpr int RES_FIELDS = 12;
 constexpr int RES_TAB_FIELDS = 14;
 template <class T>
@@ -236,6 +237,15 @@ struct ResidentCycle {
   uint32_t blk[RES_MAX_LEVELS + 1];
   uint32_t zero;
   uint32_t smem;
+  // Node lists of level q (RES_LISTS of them, list l = 8 kind + 2 colour +
+  // boundary, with kind 0 velocity (F_VFREE) / 1 pressure (F_ACT) and
+  // boundary 0 regular / 1 F_IRR): entries (k << 20) | (j << 10) | i in
+  // lattice order (sorted by k), list l at lists[q][loff[q][l] .. loff[q][l + 1]).
+  // (null: the level's colour phases test flags at every lattice position).
+  const int32_t* lists[RES_MAX_LEVELS + 1];
+  int32_t loff[RES_MAX_LEVELS + 1][RES_LISTS + 1];
+  uint32_t lst[RES_MAX_LEVELS + 1];  // byte offset of the CTA's copy of its part of the lists
+  uint32_t lofs;  // byte offset of the per-level offsets of that copy and of its sources
   CoarseSys cs;
   double* scratch;
   CoarseParams prm;

@@ -78,6 +78,20 @@ __device__ __forceinline__ void vel_rhs_regular(const LevelDev<T>& L, int64_t c,
   for (int d = 0; d < 3; ++d) reg[d] = ((L.f[d][c] - s * dv[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
 }
 
+// Velocity update of a boundary node (class rows) with f - B^T p formed at the node.
+template <class T, class V>
+__device__ __forceinline__ void vel_rhs_irr(const LevelDev<T>& L, int64_t c, const V* u, const V& p) {
+  const T* w = class_row(L, c);
+  T bt[3];
+  row_BT_v(L, p, w, F_IRR, bt);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T dg, of;
+    irr_lap_parts_v<T>(u[d], w, dg, of);
+    L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
+  }
+}
+
 // Same update with the right-hand side f - B^T p formed at the node (p does
 // not change during the velocity sweeps, Sec. 3.3), RU is not touched.
 template <bool SPEC, class T, class V>
@@ -99,15 +113,7 @@ __device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t 
     for (int d = 0; d < 3; ++d) L.u[d][c] = reg[d];
     return;
   }
-  const T* w = class_row(L, c);
-  T bt[3];
-  row_BT_v(L, p, w, fl, bt);
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    T dg, of;
-    irr_lap_parts_v<T>(u[d], w, dg, of);
-    L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
-  }
+  vel_rhs_irr(L, c, u, p);
 }
 
 template <bool SPEC, class T>
@@ -156,6 +162,17 @@ __device__ __forceinline__ T pres_rhs_regular(const LevelDev<T>& L, int64_t c, c
   return pc + omega_over_6c * (rp - cp);
 }
 
+// Pressure update of a boundary node (class rows) with B u - g formed at the node.
+template <class T, class V>
+__device__ __forceinline__ void pres_rhs_irr(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T pc) {
+  const T* w = class_row(L, c);
+  const T rp = row_B_v(L, u, w, F_IRR) - L.g[c];
+  T dg, of;
+  irr_lap_parts_v<T>(p, w, dg, of);
+  const T cp = L.c * (dg * pc + of);
+  L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
+}
+
 // Same update with B u - g formed at the node (u does not change during the
 // pressure sweep), RP is not touched.
 template <bool SPEC, class T, class V>
@@ -178,12 +195,7 @@ __device__ __forceinline__ void node_pres_gs_rhs_v(const LevelDev<T>& L, int64_t
     L.p[c] = reg;
     return;
   }
-  const T* w = class_row(L, c);
-  const T rp = row_B_v(L, u, w, fl) - L.g[c];
-  T dg, of;
-  irr_lap_parts_v<T>(p, w, dg, of);
-  const T cp = L.c * (dg * pc + of);
-  L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
+  pres_rhs_irr(L, c, u, p, pc);
 }
 
 template <bool SPEC, class T>

@@ -91,6 +91,11 @@ struct Res {
     L.cls = row_ptr<const uint16_t>(q, RES_FIELDS + 1, z);
     return L;
   }
+  // Offsets of this CTA's part of list l of level q in its copy (loc(q)[l])
+  // and in the level's list array (loc(q)[RES_LISTS + 1 + l]).
+  __device__ __forceinline__ int* loc(int q) const {
+    return reinterpret_cast<int*>(sm + S.lofs) + q * 2 * (RES_LISTS + 1);
+  }
   __device__ __forceinline__ DNb<T> view(int q, int f, int z, const InPlane& at) const {
     void* const* t = table(q) + f * (S.lv[q].nz + 2);
     return DNb<T>{reinterpret_cast<T* const*>(t), z, at.xy, at.dxm, at.dxp, (int)S.lv[q].px};
@@ -111,6 +116,19 @@ __device__ __forceinline__ void level_sync(const ResidentCycle<T>& S, int q) {
 }
 
 // ---- set-up: plane tables, zero plane, flags / classes, top-level fields ------
+
+// First position in list[a, b) (entries (k << 20) | (j << 10) | i, sorted by
+// k) whose plane k is at least kk.
+__device__ __forceinline__ int first_on_plane(const int32_t* list, int a, int b, int kk) {
+  while (a < b) {
+    const int m = (a + b) >> 1;
+    if ((list[m] >> 20) < kk)
+      a = m + 1;
+    else
+      b = m;
+  }
+  return a;
+}
 
 template <class T>
 __device__ void r_setup(const Res<T>& R) {
@@ -147,6 +165,42 @@ __device__ void r_setup(const Res<T>& R) {
         ptr = r == R.rank ? (void*)loc : cl.map_shared_rank(loc, r);
       }
       tab[e] = ptr;
+    }
+  }
+  // this CTA's part of the node lists: the entries of planes [k0, k1) of
+  // every list (each sorted by plane), found by bisection on the plane
+  if (threadIdx.x < 32) {
+    const int l = threadIdx.x;
+    for (int q = 1; q <= S.nres; ++q) {
+      if (!S.lists[q]) continue;
+      int lo = 0, len = 0;
+      if (l < RES_LISTS) {
+        lo = first_on_plane(S.lists[q], S.loff[q][l], S.loff[q][l + 1], S.kb[q][R.rank]);
+        len = first_on_plane(S.lists[q], lo, S.loff[q][l + 1], S.kb[q][R.rank + 1]) - lo;
+      }
+      int x = len;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (l >= o) x += y;
+      }
+      int* lc = R.loc(q);
+      if (l < RES_LISTS) {
+        lc[l] = x - len;
+        lc[RES_LISTS + 1 + l] = lo;
+      }
+      if (l == RES_LISTS - 1) lc[RES_LISTS] = x;
+    }
+  }
+  __syncthreads();
+  for (int q = 1; q <= S.nres; ++q) {
+    if (!S.lists[q]) continue;
+    const int* lc = R.loc(q);
+    int32_t* dst = reinterpret_cast<int32_t*>(R.sm + S.lst[q]);
+    for (int l = 0; l < RES_LISTS; ++l) {
+      const int n = lc[l + 1] - lc[l];
+      const int32_t* src = S.lists[q] + lc[RES_LISTS + 1 + l];
+      for (int e = threadIdx.x; e < n; e += blockDim.x) dst[lc[l] + e] = src[e];
     }
   }
   // class-row tables of the resident levels
@@ -233,9 +287,58 @@ __device__ void r_colour(const Res<T>& R, int q, int colour, int what) {
   level_sync(S, q);
 }
 
+// The same phase over this CTA's node lists (what = KIND: 0 velocity, 1
+// pressure, 2 both): the regular nodes of the colour, then its boundary
+// nodes, so that a warp takes one update form and no node is skipped.  KIND
+// 2 walks the pressure lists (every velocity node carries a pressure, and
+// every regular node a velocity).
+template <int KIND, class T>
+__device__ void r_colour_list(const Res<T>& R, int q, int colour) {
+  const ResidentCycle<T>& S = R.S;
+  const LevelDev<T>& L = S.lv[q];
+  const int* lc = R.loc(q);
+  const uint32_t* ls = reinterpret_cast<const uint32_t*>(R.sm + S.lst[q]);
+  const int l = 8 * (KIND != 0) + 2 * colour;
+  const int a1 = lc[l + 1], a2 = lc[l + 2];
+  for (int t = lc[l] + threadIdx.x; t < a2; t += blockDim.x) {
+    const uint32_t e = ls[t];
+    const int i = e & 1023, j = (e >> 10) & 1023, k = e >> 20;
+    const LevelDev<T> Ln = R.at_plane(q, k + 1);
+    const InPlane at = in_plane(L, i, j);
+    const int c = at.xy;
+    const DNb<T> u[3] = {R.view(q, 0, k + 1, at), R.view(q, 1, k + 1, at), R.view(q, 2, k + 1, at)};
+    const DNb<T> p = R.view(q, 3, k + 1, at);
+    if (KIND != 1) {
+      if (t < a1) {
+        T reg[3];
+        vel_rhs_regular(Ln, c, u, p, S.inv6nuh[q], reg);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) Ln.u[d][c] = reg[d];
+      } else if (KIND == 0 || (Ln.flags[c] & F_VFREE)) {
+        vel_rhs_irr(Ln, c, u, p);
+      }
+    }
+    if (KIND != 0) {
+      const T pc = p(0, 0, 0);
+      if (t < a1)
+        Ln.p[c] = pres_rhs_regular(Ln, c, u, p, pc, S.omc[q]);
+      else
+        pres_rhs_irr(Ln, c, u, p, pc);
+    }
+  }
+  level_sync(S, q);
+}
+
 template <class T>
 __device__ void r_uzawa(const Res<T>& R, int q) {
   if (R.S.nbq[q] == 1 && R.rank != 0) return;
+  if (R.S.lists[q]) {
+    for (int c = 0; c < 4; ++c) r_colour_list<0>(R, q, c);
+    for (int c = 2; c >= 1; --c) r_colour_list<0>(R, q, c);
+    r_colour_list<2>(R, q, 0);
+    for (int c = 1; c < 4; ++c) r_colour_list<1>(R, q, c);
+    return;
+  }
   for (int c = 0; c < 4; ++c) r_colour(R, q, c, 0);
   for (int c = 2; c >= 1; --c) r_colour(R, q, c, 0);
   r_colour(R, q, 0, 2);
@@ -452,6 +555,13 @@ uint64_t layout_resident(ResidentCycle<T>& S) {
     for (unsigned r = 0; r < nb; ++r) mx = std::max(mx, S.kb[q][r + 1] - S.kb[q][r]);
     S.maxpl[q] = mx;
     zero_bytes = std::max<int64_t>(zero_bytes, (int64_t)L.pxy * (int64_t)std::max<size_t>(sizeof(T), 2));
+  }
+  // node lists: every lattice node is in at most one velocity and one pressure list
+  S.lofs = (uint32_t)off;
+  off = align16(off + sizeof(int) * 2 * (RES_LISTS + 1) * (uint64_t)(S.nres + 1));
+  for (int q = 1; q <= S.nres; ++q) {
+    S.lst[q] = (uint32_t)off;
+    if (S.lists[q]) off = align16(off + sizeof(int32_t) * 2 * (uint64_t)S.maxpl[q] * S.lv[q].nx * S.lv[q].ny);
   }
   S.zero = (uint32_t)off;
   off = align16(off + zero_bytes);

@@ -436,7 +436,8 @@ FUSED = {"block": dict(fuse_coarse_levels=1),
          "cluster16": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=16),
          "cluster4": dict(fuse_coarse_levels=1, fuse_max_nodes=1 << 16, team_blocks=4),
          "resident16": dict(fuse_coarse_levels=2, team_blocks=16),
-         "resident8": dict(fuse_coarse_levels=2, team_blocks=8)}
+         "resident8": dict(fuse_coarse_levels=2, team_blocks=8),
+         "resident8_flagtests": dict(fuse_coarse_levels=2, team_blocks=8, resident_node_lists=-1)}
 
 
 @pytest.mark.parametrize("fused", sorted(FUSED))
