@@ -96,8 +96,11 @@ typedef struct hhg_options {
   int32_t tile_min_nodes;    /* levels of at least this many lattice nodes run the colour sweeps
                                 on shared-memory tiles staged by tensor copies; 0 = default
                                 (never), -1 = never */
-  int32_t ir_fixed_point;    /* FP32+IR mode: 1 (default) evaluates the FP64 refinement residual's
-                                regular-node stencils exactly in 64-bit fixed point, 0 in FP64 */
+  int32_t ir_fixed_point;    /* FP32+IR mode: 1 (default) keeps the refined iterate in 64-bit
+                                fixed point (per-field power-of-two scale, updated in integer
+                                arithmetic) and evaluates the FP64 refinement residual's
+                                regular-node stencils exactly on it; 0: FP64 iterate and
+                                residual */
   int32_t spec_max_nodes;    /* levels with fewer lattice nodes evaluate the regular-node update
                                 before reading a node's flags (hides load latency on small,
                                 latency-bound levels); 0 = default (2^20), -1 = never */
@@ -118,6 +121,9 @@ typedef struct hhg_stats {
   double seconds;            /* wall time of the solve (host clock, stream synchronised) */
   int64_t kernel_launches;   /* kernels launched (graph nodes counted per replay) */
   double history[64];        /* relative residual after cycle c (history[0] = 1) */
+  int32_t fx_rescales;       /* FP32+IR fixed point: cycles whose update was redone in FP64
+                                with fresh scales (a correction too large for the scale, or
+                                the iterate's range grown or shrunk past its bounds) */
 } hhg_stats;
 
 typedef struct hhg_mesh hhg_mesh;
@@ -250,13 +256,22 @@ int hhg_level_field(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t fi
                                    (the velocity colours of an FP32 Uzawa step) */
 #define HHG_OP_PRES_SWEEP_F 13  /* forward pressure colour sweep with B U - G formed at each node
                                    (the pressure colours of an Uzawa step) */
+#define HHG_OP_REFINE 14        /* finest level, precision 1: FP64 iterate += FP32 correction and
+                                   the FP64 residual into the FP32 right-hand side (the refinement
+                                   around each FP32 V-cycle) */
+#define HHG_OP_CYCLE 15         /* finest level: one cycle of hhg_solve in that precision (FP64:
+                                   V-cycle, projection, residual norm; FP32: zeroed correction,
+                                   V-cycle, refinement), without the host's convergence test */
 
 /* Run `op` `count` times on `level` in `precision`. */
 int hhg_level_op(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t op, int32_t count);
 
 /* Device time of `reps` back-to-back runs of `op` on `level` (CUDA events on
  * the mesh's stream, after one untimed run); *ms_per_rep receives the mean.
- * The fields are modified exactly as by hhg_level_op.  For measurement. */
+ * The fields are modified as by hhg_level_op, except that HHG_OP_REFINE and
+ * HHG_OP_CYCLE with ir_fixed_point skip the per-step check and recovery of
+ * the fixed-point iterate (hhg_level_op and hhg_solve do both).  For
+ * measurement. */
 int hhg_time_op(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t op, int32_t reps,
                 double* ms_per_rep);
 

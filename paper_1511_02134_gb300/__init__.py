@@ -29,7 +29,7 @@ NODE_ACTIVE, NODE_VFREE, NODE_IRREG, NODE_DIRICHLET, NODE_OUTFLOW = 1, 2, 4, 8, 
 FIELD = {"U": 0, "P": 1, "F": 2, "G": 3, "RU": 4, "RP": 5}
 OP = {"uzawa_step": 0, "vel_forward": 1, "vel_backward": 2, "vel_rhs": 3, "pres_rhs": 4,
       "pres_sweep": 5, "residual": 6, "restrict": 7, "prolong_add": 8, "coarse_solve": 9,
-      "vcycle": 10, "project": 11, "vel_forward_f": 12, "pres_sweep_f": 13}
+      "vcycle": 10, "project": 11, "vel_forward_f": 12, "pres_sweep_f": 13, "refine": 14, "cycle": 15}
 ERRORS = {0: "ok", -1: "HHG_EINVAL", -2: "HHG_EMESH", -3: "HHG_ENOMEM", -4: "HHG_EDIVERGED",
           -5: "HHG_EMAXIT", -6: "HHG_ECUDA", -7: "HHG_ESTATE"}
 
@@ -55,7 +55,7 @@ class Options(ctypes.Structure):
 class _Stats(ctypes.Structure):
     _fields_ = [("cycles", ctypes.c_int32), ("status", ctypes.c_int32), ("rel_residual", ctypes.c_double),
                 ("r0", ctypes.c_double), ("seconds", ctypes.c_double), ("kernel_launches", ctypes.c_int64),
-                ("history", ctypes.c_double * 64)]
+                ("history", ctypes.c_double * 64), ("fx_rescales", ctypes.c_int32)]
 
 
 @dataclass
@@ -67,6 +67,7 @@ class Stats:
     seconds: float
     kernel_launches: int
     history: list
+    fx_rescales: int = 0
 
 
 _lib = None
@@ -360,4 +361,4 @@ class Mesh:
 def _stats(st) -> Stats:
     return Stats(cycles=st.cycles, status=st.status, rel_residual=st.rel_residual, r0=st.r0,
                  seconds=st.seconds, kernel_launches=st.kernel_launches,
-                 history=[st.history[i] for i in range(min(st.cycles + 1, 64))])
+                 history=[st.history[i] for i in range(min(st.cycles + 1, 64))], fx_rescales=st.fx_rescales)

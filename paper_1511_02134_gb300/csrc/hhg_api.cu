@@ -79,17 +79,23 @@ struct hhg_mesh {
   double* d_partial = nullptr;
   double* d_scalars = nullptr;  // [0] norm2, [1..2] moments, [3..4] g-mean, [5..7] coarse info
   double* h_scalars = nullptr;  // pinned mirror
-  unsigned long long* d_fxmax = nullptr;  // per-field |x| maxima of the fixed-point residual
+  unsigned long long* d_fxmax = nullptr;  // fixed-point state: FxState's mx, maxq and exp (12 words)
   FxIterate fx{};                          // fixed-point finest iterate (FP32+IR mode)
   int64_t* d_fx = nullptr;
+  int64_t* d_fx_irr = nullptr;  // F_IRR nodes of the finest level (FxState::irr)
+  int64_t n_fx_irr = 0;
   double* d_coarse = nullptr;  // coarse-solve scratch
   CoarseSys coarse_sys{};       // compact coarsest-level system (device arrays)
   void* d_coarse_sys = nullptr;  // one allocation holding its arrays
   double* d_backup = nullptr;  // 8 finest FP64 fields (adjoint)
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int64_t graph_launches[2] = {0, 0};
+  // cycle graphs: FP64, FP32+IR, FP32+IR with the FP64 update (first cycle
+  // from an iterate with an all-zero field)
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  int64_t graph_launches[3] = {0, 0, 0};
+  unsigned long long h_fxmax[4] = {0, 0, 0, 0};  // max |x| per field of the last quantization
   bool rhs_set = false;
   int64_t launches = 0;
+  int64_t fx_recoveries = 0;  // fixed-point cycles redone in FP64 (fx_recover_if_flagged)
   int64_t device_bytes = 0;
   std::string err;
 };
@@ -174,9 +180,25 @@ int ensure32(hhg_mesh* M) {
     if (rc) return rc;
     for (int d = 0; d < 3; ++d) M->fx.u[d] = M->d_fx + (int64_t)d * H.nalloc;
     M->fx.p = M->d_fx + 3 * H.nalloc;
-    if ((rc = dalloc(M, (void**)&M->d_fxmax, 4 * sizeof(unsigned long long)))) return rc;
+    if ((rc = dalloc(M, (void**)&M->d_fxmax, 12 * sizeof(unsigned long long)))) return rc;
+    CK(cudaMemsetAsync(M->d_fxmax, 0, 12 * sizeof(unsigned long long), M->stream));
+    std::vector<int64_t> irr;
+    for (int64_t k = 0; k < H.sh.nz; ++k)
+      for (int64_t j = 0; j < H.sh.ny; ++j)
+        for (int64_t i = 0; i < H.sh.nx; ++i)
+          if (H.flags[i + H.sh.nx * (j + H.sh.ny * k)] & F_IRR) irr.push_back((k << 42) | (j << 21) | i);
+    M->n_fx_irr = (int64_t)irr.size();
+    if ((rc = dalloc(M, (void**)&M->d_fx_irr, sizeof(int64_t) * std::max<size_t>(irr.size(), 1)))) return rc;
+    CK(cudaMemcpy(M->d_fx_irr, irr.data(), sizeof(int64_t) * irr.size(), cudaMemcpyHostToDevice));
   }
   return HHG_OK;
+}
+
+// Fixed-point state: maxima and shifts in d_fxmax, the flag word in the
+// scalar block (read back with the norm after every cycle).
+FxState fx_state(hhg_mesh* M) {
+  return FxState{M->d_fxmax, M->d_fxmax + 4, reinterpret_cast<int*>(M->d_fxmax + 8),
+                 reinterpret_cast<unsigned*>(M->d_scalars + 14), M->d_fx_irr, M->n_fx_irr};
 }
 
 // ---- enqueue helpers (no synchronisation; graph-capturable) -------------------
@@ -426,14 +448,14 @@ void enq_cycle64(hhg_mesh* M) {
   M->launches += 3;
 }
 
-// FP64 residual of the finest FP64 iterate into the FP32 right-hand side,
-// its squared norm into d_scalars[0] (have_max: the update left the
-// iterate's maxima for the fixed-point evaluation).
-void enq_ir_residual(hhg_mesh* M, bool have_max) {
+// FP64 residual of the finest iterate into the FP32 right-hand side, its
+// squared norm into d_scalars[0]; in fixed point, from_update: of the
+// iterate k_fx_update left (checked), else of the FP64 iterate (quantized).
+void enq_ir_residual(hhg_mesh* M, bool from_update) {
   LevelHost& H = M->lv[M->finest];
   if (M->opt.ir_fixed_point) {
-    launch_ir_residual_fx(H.d64, M->fx, H.d32, M->d_fxmax, have_max, M->d_partial, M->d_scalars, M->stream);
-    M->launches += have_max ? 3 : 4;
+    launch_ir_residual_fx(H.d64, M->fx, H.d32, fx_state(M), from_update, M->d_partial, M->d_scalars, M->stream);
+    M->launches += from_update ? 3 : 5;
   } else {
     launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
     M->launches += 2;
@@ -441,17 +463,25 @@ void enq_ir_residual(hhg_mesh* M, bool have_max) {
 }
 
 // FP32+IR cycle body: correction V-cycle in FP32 from zero on the FP32
-// residual, x += e in FP64, FP64 residual -> FP32 right-hand side.  On a
+// residual, x += e (in fixed point: Q += round(e 2^s)), FP64 residual ->
+// FP32 right-hand side.  On a
 // mesh without outflow the residual does not change under constant shifts
 // of the pressure (B^T 1 = 0, C 1 = 0), so the mean projection is applied
 // once, to the final iterate (do_solve).
-void enq_cycle32(hhg_mesh* M) {
+void enq_cycle32(hhg_mesh* M, bool fp64_update = false) {
   LevelHost& H = M->lv[M->finest];
   launch_zero<float>(H.d32, 0, M->stream);
   enq_vcycle<float>(M, M->finest);
-  launch_ir_update(H.d64, H.d32, M->opt.ir_fixed_point ? M->d_fxmax : nullptr, M->stream);
-  M->launches += 1;
-  enq_ir_residual(M, M->opt.ir_fixed_point != 0);
+  if (M->opt.ir_fixed_point && !fp64_update) {
+    launch_fx_update(M->fx, H.d32, fx_state(M), H.nalloc, M->stream);
+    M->launches += 1;
+    enq_ir_residual(M, true);
+  } else {
+    // FP64 update; in fixed point the iterate is then quantized afresh
+    launch_ir_update(H.d64, H.d32, M->stream);
+    M->launches += 1;
+    enq_ir_residual(M, false);
+  }
 }
 
 // Reads the error word copied with the scalar block: a tiled sweep whose
@@ -462,35 +492,68 @@ int tile_status(hhg_mesh* M) {
   return HHG_OK;
 }
 
-int run_cycle(hhg_mesh* M, int mode, double* norm2) {
+// After a fixed-point cycle whose update or residual check raised a flag
+// (h_scalars just read back): the FP64 iterate is rebuilt as the iterate
+// before the update plus the correction in FP64, requantized with fresh
+// shifts, and its residual and norm recomputed (h_scalars refreshed).
+int fx_recover_if_flagged(hhg_mesh* M) {
+  const unsigned w = *reinterpret_cast<const unsigned*>(M->h_scalars + 14);
+  if (!w) return HHG_OK;
+  LevelHost& H = M->lv[M->finest];
+  const FxState st = fx_state(M);
+  launch_fx_to_fp64(H.d64, M->fx, H.d32, st, true, M->stream);
+  enq_ir_residual(M, false);  // clears the flag
+  M->launches += 1;
+  CK(cudaGetLastError());
+  CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  M->fx_recoveries += 1;
+  return HHG_OK;
+}
+
+// The FP64 iterate from the fixed-point one (end of an FP32+IR solve).
+void fx_materialize(hhg_mesh* M) {
+  LevelHost& H = M->lv[M->finest];
+  launch_fx_to_fp64(H.d64, M->fx, H.d32, fx_state(M), false, M->stream);
+  M->launches += 1;
+}
+
+// One solver cycle; fp64_update: an FP32+IR cycle whose update is done in
+// FP64 (the fixed-point iterate then requantized).
+int run_cycle(hhg_mesh* M, int mode, double* norm2, bool fp64_update = false) {
+  const int gi = mode == 0 ? 0 : (fp64_update && M->opt.ir_fixed_point ? 2 : 1);
   if (M->opt.use_graphs) {
-    if (!M->graph[mode]) {
+    if (!M->graph[gi]) {
       cudaGraph_t g;
       const int64_t before = M->launches;
       CK(cudaStreamBeginCapture(M->stream, cudaStreamCaptureModeThreadLocal));
       if (mode == 0)
         enq_cycle64(M);
       else
-        enq_cycle32(M);
+        enq_cycle32(M, gi == 2);
       cudaError_t e = cudaStreamEndCapture(M->stream, &g);
       if (e != cudaSuccess) return cuda_fail(M, e, "graph capture");
-      M->graph_launches[mode] = M->launches - before;
+      M->graph_launches[gi] = M->launches - before;
       M->launches = before;
-      e = cudaGraphInstantiate(&M->graph[mode], g, 0);
+      e = cudaGraphInstantiate(&M->graph[gi], g, 0);
       cudaGraphDestroy(g);
       if (e != cudaSuccess) return cuda_fail(M, e, "graph instantiate");
     }
-    CK(cudaGraphLaunch(M->graph[mode], M->stream));
-    M->launches += M->graph_launches[mode];
+    CK(cudaGraphLaunch(M->graph[gi], M->stream));
+    M->launches += M->graph_launches[gi];
   } else {
     if (mode == 0)
       enq_cycle64(M);
     else
-      enq_cycle32(M);
+      enq_cycle32(M, gi == 2);
     CK(cudaGetLastError());
   }
   CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
   CK(cudaStreamSynchronize(M->stream));
+  if (mode == 1 && M->opt.ir_fixed_point) {
+    int rc = fx_recover_if_flagged(M);
+    if (rc) return rc;
+  }
   *norm2 = M->h_scalars[0];
   return tile_status(M);
 }
@@ -503,6 +566,8 @@ int residual_norm2(hhg_mesh* M, int mode, double* norm2) {
     M->launches += 3;
   } else {
     enq_ir_residual(M, false);
+    if (M->opt.ir_fixed_point)
+      CK(cudaMemcpyAsync(M->h_fxmax, M->d_fxmax, sizeof(M->h_fxmax), cudaMemcpyDeviceToHost, M->stream));
   }
   CK(cudaGetLastError());
   CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
@@ -534,7 +599,7 @@ int do_solve(hhg_mesh* M, double tol, int max_cycles, int mode, hhg_stats* st) {
     int rc = ensure32(M);
     if (rc) return rc;
   }
-  const int64_t l0 = M->launches;
+  const int64_t l0 = M->launches, x0 = M->fx_recoveries;
   double r2;
   int rc = residual_norm2(M, mode, &r2);
   if (rc) return rc;
@@ -546,8 +611,14 @@ int do_solve(hhg_mesh* M, double tol, int max_cycles, int mode, hhg_stats* st) {
   double rel = 1.0;
   int cycles = 0;
   if (r0 > 0.0 && std::isfinite(r0)) {
+    // fixed point: a field that is zero throughout has no scale for its first
+    // correction, so that cycle updates in FP64 (it would be refused and redone)
+    // (the velocity components share one scale: k_ir_quantize)
+    const bool fp64_first = mode == HHG_MODE_FP32_IR && M->opt.ir_fixed_point &&
+                            (std::max(std::max(M->h_fxmax[0], M->h_fxmax[1]), M->h_fxmax[2]) == 0 ||
+                             M->h_fxmax[3] == 0);
     while (cycles < max_cycles) {
-      rc = run_cycle(M, mode, &r2);
+      rc = run_cycle(M, mode, &r2, cycles == 0 && fp64_first);
       if (rc) return rc;
       ++cycles;
       rel = std::sqrt(r2) / r0;
@@ -562,6 +633,7 @@ int do_solve(hhg_mesh* M, double tol, int max_cycles, int mode, hhg_stats* st) {
   } else if (!std::isfinite(r0)) {
     s.status = HHG_EDIVERGED;
   }
+  if (mode == HHG_MODE_FP32_IR && M->opt.ir_fixed_point && cycles > 0) fx_materialize(M);
   if (mode == HHG_MODE_FP32_IR && !M->macro.has_outflow) {
     enq_project<double>(M, M->finest);
     CK(cudaGetLastError());
@@ -569,6 +641,7 @@ int do_solve(hhg_mesh* M, double tol, int max_cycles, int mode, hhg_stats* st) {
   s.cycles = cycles;
   s.rel_residual = rel;
   s.kernel_launches = M->launches - l0;
+  s.fx_rescales = (int32_t)(M->fx_recoveries - x0);
   s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st) *st = s;
   if (s.status == HHG_EDIVERGED) return fail(M, HHG_EDIVERGED, "residual diverged");
@@ -620,6 +693,7 @@ void release(hhg_mesh* M) {
   cudaFree(M->d_coarse);
   cudaFree(M->d_fx);
   cudaFree(M->d_fxmax);
+  cudaFree(M->d_fx_irr);
   cudaFree(M->d_coarse_sys);
   cudaFree(M->d_backup);
   if (M->h_scalars) cudaFreeHost(M->h_scalars);
@@ -819,7 +893,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     }
     if ((rc = dalloc(M, (void**)&M->d_stage, sizeof(double) * 3 * (size_t)H.sh.n()))) return bail(rc);
   }
-  if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * std::max(REDUCE_BLOCKS, IR_BLOCKS)))) return bail(rc);
+  if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * std::max(REDUCE_BLOCKS, IR_BLOCKS + IR_IRR_BLOCKS)))) return bail(rc);
   if ((rc = dalloc(M, (void**)&M->d_scalars, sizeof(double) * 16))) return bail(rc);
   cudaMemset(M->d_scalars, 0, sizeof(double) * 16);
   if ((e = cudaMallocHost((void**)&M->h_scalars, sizeof(double) * 16)) != cudaSuccess) {
@@ -1329,10 +1403,21 @@ int hhg_level_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int3
   if ((precision != 0 && precision != 1) || count < 0) return fail(M, HHG_EINVAL, "bad precision or count");
   CK(cudaSetDevice(M->device));
   if (precision == 1 && (rc = ensure32(M))) return rc;
+  // fixed-point refinement: Q from the FP64 iterate first, checked after
+  // every step, and the FP64 iterate written back at the end
+  const bool fx = precision == 1 && M->opt.ir_fixed_point && (op == HHG_OP_REFINE || op == HHG_OP_CYCLE) &&
+                  level == M->finest && count > 0;
+  if (fx) enq_ir_residual(M, false);
   for (int it = 0; it < count; ++it) {
     if ((rc = enqueue_op(M, level, precision, op))) return rc;
     CK(cudaGetLastError());
+    if (fx) {
+      CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
+      CK(cudaStreamSynchronize(M->stream));
+      if ((rc = fx_recover_if_flagged(M))) return rc;
+    }
   }
+  if (fx) fx_materialize(M);
   CK(cudaMemcpyAsync(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost, M->stream));
   CK(cudaStreamSynchronize(M->stream));
   return tile_status(M);
@@ -1344,6 +1429,9 @@ int hhg_time_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32
   if ((precision != 0 && precision != 1) || reps < 1 || !ms) return fail(M, HHG_EINVAL, "bad arguments");
   CK(cudaSetDevice(M->device));
   if (precision == 1 && (rc = ensure32(M))) return rc;
+  const bool fx = precision == 1 && M->opt.ir_fixed_point && (op == HHG_OP_REFINE || op == HHG_OP_CYCLE) &&
+                  level == M->finest;
+  if (fx) enq_ir_residual(M, false);
   if ((rc = enqueue_op(M, level, precision, op))) return rc;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
@@ -1360,6 +1448,7 @@ int hhg_time_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32
   if (rc) return rc;
   if (e != cudaSuccess) return cuda_fail(M, e, "time_op");
   *ms = (double)t / reps;
+  if (fx) fx_materialize(M);
   CK(cudaMemcpy(M->h_scalars, M->d_scalars, sizeof(double) * 16, cudaMemcpyDeviceToHost));
   return tile_status(M);
 }
@@ -1419,6 +1508,19 @@ static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op)
         break;
       case HHG_OP_PROJECT:
         precision ? enq_project<float>(M, level) : enq_project<double>(M, level);
+        break;
+      case HHG_OP_REFINE:
+        if (level != M->finest || !precision) return fail(M, HHG_EINVAL, "refinement runs on the finest level in FP32");
+        if (M->opt.ir_fixed_point)
+          launch_fx_update(M->fx, M->lv[level].d32, fx_state(M), M->lv[level].nalloc, M->stream);
+        else
+          launch_ir_update(M->lv[level].d64, M->lv[level].d32, M->stream);
+        M->launches += 1;
+        enq_ir_residual(M, M->opt.ir_fixed_point != 0);
+        break;
+      case HHG_OP_CYCLE:
+        if (level != M->finest) return fail(M, HHG_EINVAL, "a solver cycle is rooted at the finest level");
+        precision ? enq_cycle32(M) : enq_cycle64(M);
         break;
       default:
         return fail(M, HHG_EINVAL, "unknown op");

@@ -423,20 +423,34 @@ __global__ void k_ir_absmax(LevelDev<double> X, unsigned long long* mx) {
   }
 }
 
-// 2^e with max |x| 2^e < 2^55 (e capped so that 2^e stays finite).
-__device__ __forceinline__ int fx_exponent(unsigned long long bits) {
+// Scale 2^s of a field of the fixed-point iterate from its max |x|: max |x|
+// 2^s < 2^(55 - FX_HEADROOM), s capped so that 2^s stays finite; a zero field
+// gets the largest scale, so that any nonzero correction of it is refused by
+// fx_delta and taken by the host's FP64 path.
+constexpr int FX_HEADROOM = 2;
+constexpr int FX_ZERO_SHIFT = 995;
+__device__ __forceinline__ int fx_shift(unsigned long long bits) {
   const double m = __longlong_as_double((long long)bits);
-  if (!(m > 0.0)) return 0;
+  if (!(m > 0.0)) return FX_ZERO_SHIFT;
   int E;
   frexp(m, &E);  // m < 2^E
-  return 55 - max(E, -940);
+  return 55 - FX_HEADROOM - max(E, -940);
 }
 
-__global__ void k_ir_quantize(LevelDev<double> X, FxIterate Q, const unsigned long long* mx) {
+// Q = round(x 2^s) per field, s = fx_shift(max |x|) written to fexp; the
+// three velocity components share the shift of the largest of them (their
+// stencil sums then combine in integers before one conversion).
+__global__ void k_ir_quantize(LevelDev<double> X, FxIterate Q, const unsigned long long* mx, int* fexp) {
   pdl_enter();
   double s[4];
+  // maxima are FP64 bits of non-negative values: their integer order is theirs
+  const unsigned long long mu = max(max(mx[0], mx[1]), mx[2]);
 #pragma unroll
-  for (int f = 0; f < 4; ++f) s[f] = ldexp(1.0, fx_exponent(mx[f]));
+  for (int f = 0; f < 4; ++f) {
+    const int e = fx_shift(f < 3 ? mu : mx[3]);
+    s[f] = ldexp(1.0, e);
+    if (blockIdx.x == 0 && threadIdx.x == 0) fexp[f] = e;
+  }
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
 #pragma unroll
@@ -445,20 +459,181 @@ __global__ void k_ir_quantize(LevelDev<double> X, FxIterate Q, const unsigned lo
   }
 }
 
-// (F, G) - K (U, P) in FP64 from the fixed-point iterate on regular nodes,
-// FP32 output, and the partial sums of its squared norm.
-__global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float> E, const unsigned long long* mx,
-                                 double* partial) {
+// d = round(e 2^s) (halves away from zero) from the bits of e, in integer
+// arithmetic; false (d = 0) when |d| could reach 2^57 or e is not finite.
+__device__ __forceinline__ bool fx_delta(float e, int s, int64_t& d) {
+  const uint32_t b = __float_as_uint(e);
+  const int ex = (int)((b >> 23) & 255u);
+  uint32_t m = b & 0x7fffffu;
+  d = 0;
+  if (ex == 255) return false;
+  int sh = s - 149;  // e = m 2^(ex - 150) with the leading bit, m 2^-149 without
+  if (ex != 0) {
+    m |= 0x800000u;
+    sh += ex - 1;
+  }
+  if (m == 0) return true;
+  uint64_t a;
+  if (sh >= 0) {
+    if (sh + (32 - __clz(m)) > 57) return false;
+    a = (uint64_t)m << sh;
+  } else {
+    const int r = -sh;
+    if (r > 24) return true;  // m 2^-r < 1/2
+    a = ((uint64_t)m + (1ull << (r - 1))) >> r;
+  }
+  d = (b >> 31) ? -(int64_t)a : (int64_t)a;
+  return true;
+}
+
+// Q += round(e 2^s) on every padded position, max |Q| per field into maxq
+// (zeroed before); a correction fx_delta refuses leaves Q and raises
+// FX_FLAG_REFUSED in *flag.
+__global__ void k_fx_update(FxIterate Q, LevelDev<float> E, const int* fexp, unsigned long long* maxq,
+                            unsigned* flag, int64_t n) {
   pdl_enter();
+  __shared__ unsigned long long sh[4][32];
+  int s[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) s[f] = fexp[f];
+  unsigned long long m[4] = {0, 0, 0, 0};
+  bool refused = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += stride) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      int64_t* q = f < 3 ? Q.u[f] : Q.p;
+      const float e = f < 3 ? E.u[f][c] : E.p[c];
+      int64_t d;
+      if (!fx_delta(e, s[f], d)) {
+        refused = true;
+        continue;
+      }
+      const int64_t v = q[c] + d;
+      q[c] = v;
+      m[f] = max(m[f], (unsigned long long)(v < 0 ? -v : v));
+    }
+  }
+  if (refused) atomicOr(flag, FX_FLAG_REFUSED);
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    unsigned long long x = m[f];
+    for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_down_sync(0xffffffffu, x, o));
+    if ((threadIdx.x & 31) == 0) sh[f][threadIdx.x >> 5] = x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    unsigned long long x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x = max(x, sh[threadIdx.x][w]);
+    atomicMax(&maxq[threadIdx.x], x);
+  }
+}
+
+// FP64 iterate from the fixed-point one: x = Q 2^-s, or (recover) the
+// iterate before the last k_fx_update plus the FP32 correction in FP64,
+// x = (Q - round(e 2^s)) 2^-s + e, with Q untouched where that update
+// refused the correction.
+__global__ void k_fx_to_fp64(LevelDev<double> X, FxIterate Q, LevelDev<float> E, const int* fexp, int recover) {
+  pdl_enter();
+  int s[4];
   double is[4];
 #pragma unroll
-  for (int f = 0; f < 4; ++f) is[f] = ldexp(1.0, -fx_exponent(mx[f]));
-  double kA[3], kB[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    kA[d] = X.nuh * is[d];
-    kB[d] = X.h2 * (1.0 / 12.0) * is[d];
+  for (int f = 0; f < 4; ++f) {
+    s[f] = fexp[f];
+    is[f] = ldexp(1.0, -s[f]);
   }
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < X.nalloc; c += stride) {
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      int64_t q = (f < 3 ? Q.u[f] : Q.p)[c];
+      double v;
+      if (recover) {
+        const float e = f < 3 ? E.u[f][c] : E.p[c];
+        int64_t d;
+        if (fx_delta(e, s[f], d)) q -= d;
+        v = (double)q * is[f] + (double)e;
+      } else {
+        v = (double)q * is[f];
+      }
+      (f < 3 ? X.u[f] : X.p)[c] = v;
+    }
+  }
+}
+
+// Slot of a Kuhn neighbour offset in the class-row order: 0 centre, 1..7
+// +o, 8..14 -o over e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3.
+__host__ __device__ constexpr int kuhn_slot(int dx, int dy, int dz) {
+  return (dx | dy | dz) == 0 ? 0
+                             : (dx && dy && dz ? 7
+                                : dx && dz   ? 6
+                                : dy && dz   ? 5
+                                : dx && dy   ? 4
+                                : dz         ? 3
+                                : dy         ? 2
+                                             : 1) +
+                                   ((dx | dy | dz) < 0 ? 7 : 0);
+}
+static_assert(kuhn_slot(1, 0, 0) == 1 && kuhn_slot(0, 1, 0) == 2 && kuhn_slot(0, 0, 1) == 3 &&
+                  kuhn_slot(1, 1, 0) == 4 && kuhn_slot(0, 1, 1) == 5 && kuhn_slot(1, 0, 1) == 6 &&
+                  kuhn_slot(1, 1, 1) == 7 && kuhn_slot(-1, 0, 0) == 8 && kuhn_slot(0, -1, -1) == 12 &&
+                  kuhn_slot(-1, -1, -1) == 14 && kuhn_slot(0, 0, 0) == 0,
+              "class-row offset order");
+
+// Neighbour view over the 15 values of a node's stencil held in registers.
+struct SlotNb {
+  const double* v;
+  __device__ __forceinline__ double operator()(int dx, int dy, int dz) const { return v[kuhn_slot(dx, dy, dz)]; }
+};
+
+// Loads the 15 stencil values of a fixed-point field at node n as FP64 (q 2^-s).
+__device__ __forceinline__ void fx_gather15(const int64_t* x, const Node& n, int64_t px, int64_t pxy, double sc,
+                                            double v[15]) {
+  const GNb<int64_t> g = gnb(x, n, px, pxy);
+  v[0] = sc * (double)g(0, 0, 0);
+  v[1] = sc * (double)g(1, 0, 0);
+  v[2] = sc * (double)g(0, 1, 0);
+  v[3] = sc * (double)g(0, 0, 1);
+  v[4] = sc * (double)g(1, 1, 0);
+  v[5] = sc * (double)g(0, 1, 1);
+  v[6] = sc * (double)g(1, 0, 1);
+  v[7] = sc * (double)g(1, 1, 1);
+  v[8] = sc * (double)g(-1, 0, 0);
+  v[9] = sc * (double)g(0, -1, 0);
+  v[10] = sc * (double)g(0, 0, -1);
+  v[11] = sc * (double)g(-1, -1, 0);
+  v[12] = sc * (double)g(0, -1, -1);
+  v[13] = sc * (double)g(-1, 0, -1);
+  v[14] = sc * (double)g(-1, -1, -1);
+}
+
+// (F, G) - K (U, P) in FP64 from the fixed-point iterate on regular nodes,
+// FP32 output, and the partial sums of its squared norm.
+// With check, the iterate must have come from k_fx_update: when that update
+// refused a correction, or a field's max |Q| reached 2^55 (the stencil sums
+// could overflow) or fell below 2^45 (too few bits), the kernel raises
+// FX_FLAG_RESCALE and returns without output.
+__device__ __forceinline__ bool fx_iterate_fit(const unsigned long long* maxq, unsigned* flag) {
+  bool ok = *(volatile unsigned*)flag == 0;
+#pragma unroll
+  for (int f = 0; f < 4; ++f) {
+    const unsigned long long m = maxq[f];
+    if (m >= (1ull << 55) || (m != 0 && m < (1ull << 45))) ok = false;
+  }
+  if (!ok && blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flag, FX_FLAG_RESCALE);
+  return ok;
+}
+
+// The regular nodes; boundary nodes (F_IRR) are left to k_ir_residual_fx_irr.
+__global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float> E, const int* fexp,
+                                 const unsigned long long* maxq, unsigned* flag, int check, double* partial) {
+  pdl_enter();
+  if (check && !fx_iterate_fit(maxq, flag)) return;
+  double is[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) is[f] = ldexp(1.0, -fexp[f]);
+  // one shift for the three velocity components (k_ir_quantize)
+  const double kA = X.nuh * is[0], kB = X.h2 * (1.0 / 12.0) * is[0];
   const double kBT = X.h2 * (1.0 / 12.0) * is[3], kC = X.c * is[3];
   double v[1] = {0.0};
   const int64_t n = (int64_t)X.nx * X.ny * X.nz;
@@ -481,24 +656,22 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
           const int64_t ia = 6 * gu[d](0, 0, 0) - nb6v(gu[d]);
-          r[d] = (X.f[d][c] - kA[d] * (double)ia) + kBT * (double)ibt[d];
+          r[d] = (X.f[d][c] - kA * (double)ia) + kBT * (double)ibt[d];
         }
       } else {
         r[0] = r[1] = r[2] = 0.0;
       }
       if (fl & F_ACT) {
         const int64_t ic = 6 * gp(0, 0, 0) - nb6v(gp);
-        double b = 0.0;
-#pragma unroll
-        for (int d = 0; d < 3; ++d) b += kB[d] * (double)div12(diff7v<int64_t>(gu[d]), d);
-        r[3] = (X.g[c] - b) + kC * (double)ic;
+        // 12 B u in integers: |Q| < 2^55 keeps each div12 below 15 2^56
+        const int64_t ib = (div12(diff7v<int64_t>(gu[0]), 0) + div12(diff7v<int64_t>(gu[1]), 1)) +
+                           div12(diff7v<int64_t>(gu[2]), 2);
+        r[3] = (X.g[c] - kB * (double)ib) + kC * (double)ic;
       } else {
         r[3] = 0.0;
       }
     } else {
-      const GNb<double> u[3] = {gnb(X.u[0], n, X.px, X.pxy), gnb(X.u[1], n, X.px, X.pxy),
-                                gnb(X.u[2], n, X.px, X.pxy)};
-      node_residual_v(X, c, fl, u, gnb(X.p, n, X.px, X.pxy), r);
+      continue;
     }
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
@@ -511,36 +684,51 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
   block_reduce_store<1>(v, partial);
 }
 
-// x += e; with mx, also the per-field |x| maxima of the new iterate (as in
-// k_ir_absmax, mx zeroed before).
-__global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E, unsigned long long* mx) {
+// The boundary nodes of k_ir_residual_fx, from the list of their lattice
+// coordinates ((k << 42) | (j << 21) | i): class rows in FP64 on the
+// iterate's values, each neighbour converted once.  Partial norms into
+// partial[0 .. gridDim.x).
+__global__ void k_ir_residual_fx_irr(LevelDev<double> X, FxIterate Q, LevelDev<float> E, const int* fexp,
+                                     const unsigned long long* maxq, unsigned* flag, int check,
+                                     const int64_t* irr, int64_t nirr, double* partial) {
   pdl_enter();
-  __shared__ double sh[4][32];
-  double m[4] = {0.0, 0.0, 0.0, 0.0};
+  if (check && !fx_iterate_fit(maxq, flag)) return;
+  double is[4];
+#pragma unroll
+  for (int f = 0; f < 4; ++f) is[f] = ldexp(1.0, -fexp[f]);
+  double v[1] = {0.0};
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nirr; t += stride) {
+    const int64_t e = irr[t];
+    const Node n = node_at(X.px, X.pxy, (int)(e & 0x1fffff), (int)((e >> 21) & 0x1fffff), (int)(e >> 42));
+    const int64_t c = n.c;
+    const uint8_t fl = X.flags[c];
+    double uv[3][15], pv[15];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) fx_gather15(Q.u[d], n, X.px, X.pxy, is[d], uv[d]);
+    fx_gather15(Q.p, n, X.px, X.pxy, is[3], pv);
+    const SlotNb u[3] = {SlotNb{uv[0]}, SlotNb{uv[1]}, SlotNb{uv[2]}};
+    double r[4];
+    node_residual_v(X, c, fl, u, SlotNb{pv}, r);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      E.f[d][c] = (float)r[d];
+      v[0] += r[d] * r[d];
+    }
+    E.g[c] = (float)r[3];
+    v[0] += r[3] * r[3];
+  }
+  block_reduce_store<1>(v, partial);
+}
+
+// x += e (the FP64 refinement update).
+__global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
+  pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < X.nalloc; q += stride) {
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const double v = X.u[d][q] + (double)E.u[d][q];
-      X.u[d][q] = v;
-      m[d] = fmax(m[d], fabs(v));
-    }
-    const double v = X.p[q] + (double)E.p[q];
-    X.p[q] = v;
-    m[3] = fmax(m[3], fabs(v));
-  }
-  if (!mx) return;
-#pragma unroll
-  for (int w = 0; w < 4; ++w) {
-    double x = m[w];
-    for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_down_sync(0xffffffffu, x, o));
-    if ((threadIdx.x & 31) == 0) sh[w][threadIdx.x >> 5] = x;
-  }
-  __syncthreads();
-  if (threadIdx.x < 4) {
-    double x = 0.0;
-    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) x = fmax(x, sh[threadIdx.x][q]);
-    atomicMax(&mx[threadIdx.x], (unsigned long long)__double_as_longlong(x));
+    for (int d = 0; d < 3; ++d) X.u[d][q] += (double)E.u[d][q];
+    X.p[q] += (double)E.p[q];
   }
 }
 
@@ -726,20 +914,32 @@ void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, dou
   launch_k(k_ir_residual, REDUCE_BLOCKS, REDUCE_THREADS, s, x, e, partial);
   launch_k(k_final_sum<1>, 1, 32, s, partial, REDUCE_BLOCKS, out);
 }
-void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e,
-                           unsigned long long* mx, bool have_max, double* partial, double* out, cudaStream_t s) {
-  if (!have_max) {
-    cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned long long), s);
-    launch_k(k_ir_absmax, IR_BLOCKS, REDUCE_THREADS, s, x, mx);
+void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,
+                           bool from_update, double* partial, double* out, cudaStream_t s) {
+  if (!from_update) {
+    cudaMemsetAsync(st.flag, 0, sizeof(unsigned), s);
+    cudaMemsetAsync(st.mx, 0, 4 * sizeof(unsigned long long), s);
+    launch_k(k_ir_absmax, IR_BLOCKS, REDUCE_THREADS, s, x, st.mx);
+    launch_k(k_ir_quantize, flat_blocks(x.nalloc), 256, s, x, q, (const unsigned long long*)st.mx, st.exp);
   }
-  launch_k(k_ir_quantize, flat_blocks(x.nalloc), 256, s, x, q, (const unsigned long long*)mx);
-  launch_k(k_ir_residual_fx, IR_BLOCKS, REDUCE_THREADS, s, x, q, e, (const unsigned long long*)mx, partial);
-  launch_k(k_final_sum<1>, 1, 32, s, (const double*)partial, IR_BLOCKS, out);
+  launch_k(k_ir_residual_fx, IR_BLOCKS, REDUCE_THREADS, s, x, q, e, (const int*)st.exp,
+           (const unsigned long long*)st.maxq, st.flag, from_update ? 1 : 0, partial);
+  launch_k(k_ir_residual_fx_irr, IR_IRR_BLOCKS, REDUCE_THREADS, s, x, q, e, (const int*)st.exp,
+           (const unsigned long long*)st.maxq, st.flag, from_update ? 1 : 0, (const int64_t*)st.irr, st.nirr,
+           partial + IR_BLOCKS);
+  launch_k(k_final_sum<1>, 1, 32, s, (const double*)partial, IR_BLOCKS + IR_IRR_BLOCKS, out);
+}
+void launch_fx_update(const FxIterate& q, const LevelDev<float>& e, const FxState& st, int64_t nalloc, cudaStream_t s) {
+  cudaMemsetAsync(st.maxq, 0, 4 * sizeof(unsigned long long), s);
+  launch_k(k_fx_update, flat_blocks(nalloc), 256, s, q, e, (const int*)st.exp, st.maxq, st.flag, nalloc);
+}
+void launch_fx_to_fp64(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,
+                       bool recover, cudaStream_t s) {
+  launch_k(k_fx_to_fp64, flat_blocks(x.nalloc), 256, s, x, q, e, (const int*)st.exp, recover ? 1 : 0);
 }
 
-void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, unsigned long long* mx, cudaStream_t s) {
-  if (mx) cudaMemsetAsync(mx, 0, 4 * sizeof(unsigned long long), s);
-  launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e, mx);
+void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
+  launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e);
 }
 void launch_scatter(const LevelDev<double>& L, const double* src, int ncomp, double* const* dst, uint8_t mask,
                     cudaStream_t s) {

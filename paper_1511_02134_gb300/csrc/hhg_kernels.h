@@ -86,21 +86,45 @@ void launch_rhs_transpose(const LevelDev<double>& L, double* const* out, cudaStr
 // squared norm partials; and x += e.
 void launch_ir_residual(const LevelDev<double>& x, const LevelDev<float>& e, double* partial, double* out,
                         cudaStream_t s);
-// x += e in FP64; with mx (not null), also the per-field |x| maxima of the
-// new iterate for the fixed-point residual (mx zeroed first).
-void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, unsigned long long* mx, cudaStream_t s);
-// The same residual with the regular-node stencils evaluated exactly in
-// 64-bit fixed point (hhg_kernels.cu): per-field |x| maxima into mx[0..4)
-// (zeroed first; skipped when have_max, i.e. launch_ir_update left them),
-// quantization into q, residual, norm into out[0].  IR_BLOCKS blocks: the
-// partial-sum buffer holds that many per value.
+// x += e in FP64.
+void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s);
+// Fixed-point iterate of the FP32+IR solve (hhg_kernels.cu): per field
+// Q = x 2^s with an integer per-field shift s, |Q| < 2^55, so that the
+// regular-node stencils of the FP64 residual are exact 64-bit sums.  The
+// cycle updates Q itself (launch_fx_update, no FP64 arithmetic); the FP64
+// iterate x is written from Q at the end of a solve, or rebuilt as
+// old iterate + e in FP64 when a check of the update fails (a correction too
+// large for the shift, |Q| grown to 2^55 or shrunk below 2^45): the host then
+// requantizes x with fresh shifts.  IR_BLOCKS blocks: the partial-sum buffer
+// holds that many per value.
 constexpr int IR_BLOCKS = 1216;
 struct FxIterate {
   int64_t* u[3];
   int64_t* p;
 };
-void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e,
-                           unsigned long long* mx, bool have_max, double* partial, double* out, cudaStream_t s);
+struct FxState {
+  unsigned long long* mx;    // [4] per-field max |x| (FP64 bits), quantization
+  unsigned long long* maxq;  // [4] per-field max |Q| after an update
+  int* exp;                  // [4] shifts s
+  unsigned* flag;            // FX_FLAG_* bits, cleared by the host
+  const int64_t* irr;        // lattice coordinates (k << 42) | (j << 21) | i of the F_IRR nodes
+  int64_t nirr;
+};
+// Blocks of the boundary-node part of the fixed-point residual (its partial
+// sums follow the IR_BLOCKS of the regular part).
+constexpr int IR_IRR_BLOCKS = 304;
+constexpr unsigned FX_FLAG_REFUSED = 1u;  // k_fx_update left a correction out
+constexpr unsigned FX_FLAG_RESCALE = 2u;  // the residual found the iterate unfit for its shifts
+// Residual of the fixed-point iterate into e.f / e.g, norm into out[0].
+// from_update = false: max |x| -> shifts -> Q = round(x 2^s) first;
+// true: Q comes from launch_fx_update and is checked first.
+void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,
+                           bool from_update, double* partial, double* out, cudaStream_t s);
+// Q += round(e 2^s) over the nalloc padded positions.
+void launch_fx_update(const FxIterate& q, const LevelDev<float>& e, const FxState& st, int64_t nalloc, cudaStream_t s);
+// x = Q 2^-s, or (recover) the iterate before the last update + e in FP64.
+void launch_fx_to_fp64(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,
+                       bool recover, cudaStream_t s);
 
 // Layout conversion between contiguous (n, 3)/(n,) arrays and padded fields.
 // mask: nodes whose value is kept (others get 0); 0 = keep all.

@@ -352,6 +352,34 @@ def test_fixed_point_refinement_residual(pkg, name, level, coarsest, mx):
     # evaluations (4.5e-14 absolute seen on the partial mesh)
     np.testing.assert_allclose(s1.history, s0.history, rtol=1e-6, atol=1e-12)
     assert rel_err(u1, u0) < 1e-9 and rel_err(p1, p0) < 1e-8
+    # from a zero iterate the first cycle updates in FP64 (a zero field has
+    # no scale for its correction); no cycle needs its update redone
+    assert s0.fx_rescales == 0 and s1.fx_rescales == 0
+
+
+def test_fixed_point_rescaling(pkg):
+    """The fixed-point iterate's checks: an initial iterate 1e-6 times the
+    solution makes the first correction too large for its scales (the update
+    is redone in FP64 and rescaled), 1.01 times the solution needs no
+    rescaling; both solves follow the FP64-iterate solve."""
+    cube = W.unit_cube()
+    meshes = {fx: pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 4, ir_fixed_point=fx) for fx in (0, 1)}
+    x = meshes[0].node_coords()
+    for m in meshes.values():
+        m.set_rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    us, ps, _ = meshes[0].solve(tol=1e-11, max_cycles=60, mode=pkg.MODE_FP32_IR)
+    for scale, rescales in ((1e-6, 1), (1.01, 0)):
+        outs = {}
+        for fx, m in meshes.items():
+            m.set_initial(scale * us, scale * ps)
+            outs[fx] = m.solve(tol=1e-9, max_cycles=60, mode=pkg.MODE_FP32_IR)
+        (u0, p0, s0), (u1, p1, s1) = outs[0], outs[1]
+        assert s0.status == 0 and s1.status == 0 and s0.cycles == s1.cycles
+        assert s1.fx_rescales == rescales
+        np.testing.assert_allclose(s1.history, s0.history, rtol=1e-6, atol=1e-12)
+        assert rel_err(u1, u0) < 1e-9 and rel_err(p1, p0) < 1e-8
+    for m in meshes.values():
+        m.close()
 
 
 def test_edge_cases(pkg):
