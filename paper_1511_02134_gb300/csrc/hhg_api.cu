@@ -84,6 +84,7 @@ struct hhg_mesh {
   int64_t* d_fx = nullptr;
   int64_t* d_fx_irr = nullptr;  // F_IRR nodes of the finest level (FxState::irr)
   int64_t n_fx_irr = 0;
+  unsigned long long* d_rhs_fx = nullptr;  // right-hand side quantization: maxima [0..8), shifts
   double* d_coarse = nullptr;  // coarse-solve scratch
   CoarseSys coarse_sys{};       // compact coarsest-level system (device arrays)
   void* d_coarse_sys = nullptr;  // one allocation holding its arrays
@@ -182,14 +183,6 @@ int ensure32(hhg_mesh* M) {
     M->fx.p = M->d_fx + 3 * H.nalloc;
     if ((rc = dalloc(M, (void**)&M->d_fxmax, 12 * sizeof(unsigned long long)))) return rc;
     CK(cudaMemsetAsync(M->d_fxmax, 0, 12 * sizeof(unsigned long long), M->stream));
-    std::vector<int64_t> irr;
-    for (int64_t k = 0; k < H.sh.nz; ++k)
-      for (int64_t j = 0; j < H.sh.ny; ++j)
-        for (int64_t i = 0; i < H.sh.nx; ++i)
-          if (H.flags[i + H.sh.nx * (j + H.sh.ny * k)] & F_IRR) irr.push_back((k << 42) | (j << 21) | i);
-    M->n_fx_irr = (int64_t)irr.size();
-    if ((rc = dalloc(M, (void**)&M->d_fx_irr, sizeof(int64_t) * std::max<size_t>(irr.size(), 1)))) return rc;
-    CK(cudaMemcpy(M->d_fx_irr, irr.data(), sizeof(int64_t) * irr.size(), cudaMemcpyHostToDevice));
   }
   return HHG_OK;
 }
@@ -694,6 +687,7 @@ void release(hhg_mesh* M) {
   cudaFree(M->d_fx);
   cudaFree(M->d_fxmax);
   cudaFree(M->d_fx_irr);
+  cudaFree(M->d_rhs_fx);
   cudaFree(M->d_coarse_sys);
   cudaFree(M->d_backup);
   if (M->h_scalars) cudaFreeHost(M->h_scalars);
@@ -896,6 +890,23 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * std::max(REDUCE_BLOCKS, IR_BLOCKS + IR_IRR_BLOCKS)))) return bail(rc);
   if ((rc = dalloc(M, (void**)&M->d_scalars, sizeof(double) * 16))) return bail(rc);
   cudaMemset(M->d_scalars, 0, sizeof(double) * 16);
+  if ((rc = dalloc(M, (void**)&M->d_rhs_fx, sizeof(unsigned long long) * 10))) return bail(rc);
+  {
+    // boundary nodes of the finest level (right-hand side, refinement residual)
+    const LevelHost& H = M->lv[M->finest];
+    std::vector<int64_t> irr;
+    for (int64_t k = 0; k < H.sh.nz; ++k)
+      for (int64_t j = 0; j < H.sh.ny; ++j)
+        for (int64_t i = 0; i < H.sh.nx; ++i)
+          if (H.flags[i + H.sh.nx * (j + H.sh.ny * k)] & F_IRR) irr.push_back((k << 42) | (j << 21) | i);
+    M->n_fx_irr = (int64_t)irr.size();
+    if ((rc = dalloc(M, (void**)&M->d_fx_irr, sizeof(int64_t) * std::max<size_t>(irr.size(), 1)))) return bail(rc);
+    if (!irr.empty() && (e = cudaMemcpy(M->d_fx_irr, irr.data(), sizeof(int64_t) * irr.size(),
+                                         cudaMemcpyHostToDevice)) != cudaSuccess) {
+      M->err = std::string("set-up: ") + cudaGetErrorString(e);
+      return bail(HHG_ECUDA);
+    }
+  }
   if ((e = cudaMallocHost((void**)&M->h_scalars, sizeof(double) * 16)) != cudaSuccess) {
     M->err = cudaGetErrorString(e);
     return bail(HHG_ENOMEM);
@@ -1121,10 +1132,12 @@ int hhg_set_rhs(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet) {
     if (rc) return rc;
     launch_scatter(L, M->d_stage, 3, L.u, F_DIR, M->stream);
   }
-  launch_set_rhs(L, L.r, L.u, M->stream);
+  launch_dirichlet_gather(M->d_dir_pad, M->ndir, L, M->d_dir_val, M->stream);  // before U is quantized
+  launch_set_rhs(L, L.r, L.u, M->d_rhs_fx, reinterpret_cast<int*>(M->d_rhs_fx + 8), M->d_fx_irr, M->n_fx_irr,
+                 M->stream);
   if (!M->macro.has_outflow) launch_remove_mean_g(L, M->d_partial, M->d_scalars + 3, M->stream);
-  launch_dirichlet_gather(M->d_dir_pad, M->ndir, L, M->d_dir_val, M->stream);
-  M->launches += (f_nodal ? 1 : 0) + (u_dirichlet ? 1 : 0) + 1 + (M->macro.has_outflow ? 0 : 3) + (M->ndir ? 1 : 0);
+  M->launches += (f_nodal ? 1 : 0) + (u_dirichlet ? 1 : 0) + 4 + (M->n_fx_irr ? 1 : 0) +
+                 (M->macro.has_outflow ? 0 : 3) + (M->ndir ? 1 : 0);
   launch_zero<double>(L, 0, M->stream);
   launch_zero<double>(L, 2, M->stream);
   CK(cudaGetLastError());

@@ -251,46 +251,6 @@ __device__ __forceinline__ double mass_reg(const double* x, const Node& n, int64
   return h3 * (0.4 * v(0, 0, 0) + 0.05 * ax + fc * (1.0 / 30.0));
 }
 
-__global__ void k_set_rhs(LevelDev<double> L, const double* f0, const double* f1, const double* f2,
-                          const double* d0, const double* d1, const double* d2) {
-  pdl_enter();
-  int i, j, k;
-  if (!full_node(L, i, j, k)) return;
-  const Node n = node_at(L.px, L.pxy, i, j, k);
-  const int64_t c = n.c;
-  const uint8_t fl = L.flags[c];
-  const double* fn[3] = {f0, f1, f2};
-  const double* ud[3] = {d0, d1, d2};
-  const bool irr = fl & F_IRR;
-  if (fl & F_VFREE) {
-    double au[3];
-    row_A(L, ud, n, fl, au);
-#pragma unroll 1
-    for (int d = 0; d < 3; ++d) {
-      const double mf = irr ? irr_mass_row(L, fn[d], n) : mass_reg(fn[d], n, L.px, L.pxy, L.h3);
-      L.f[d][c] = mf - au[d];
-    }
-  } else {
-#pragma unroll
-    for (int d = 0; d < 3; ++d) L.f[d][c] = 0.0;
-  }
-  if (fl & F_ACT) {
-    // g = delta h_T^2 sum_d B_d^T f_d - sum_d B_d u_D,d (component d of B^T
-    // applied to f_d only)
-    const double* w = row_of(L, c, fl);
-    double gs = 0.0;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const GNb<double> v = gnb(fn[d], n, L.px, L.pxy);
-      gs += irr ? L.h2 * st15v<double>(v, w + W_BT + 15 * d)
-                : (-L.h2 * (1.0 / 12.0)) * div12(diff7v<double>(v), d);
-    }
-    L.g[c] = L.dh2 * gs - row_B(L, ud, n, fl);
-  } else {
-    L.g[c] = 0.0;
-  }
-}
-
 __global__ void k_sum_g(LevelDev<double> L, double* partial) {
   pdl_enter();
   double v[2] = {0.0, 0.0};
@@ -721,6 +681,109 @@ __global__ void k_ir_residual_fx_irr(LevelDev<double> X, FxIterate Q, LevelDev<f
   block_reduce_store<1>(v, partial);
 }
 
+// ---- right-hand side in fixed point ------------------------------------------------
+
+// In place: the staged nodal f (a0..a2) and u_D (b0..b2) become int64
+// round(v 2^s), one shift for f and one for u_D from their max |v| (mx[0..3)
+// and mx[4..7)), written to sh[0..2).
+__global__ void k_rhs_quantize(double* a0, double* a1, double* a2, double* b0, double* b1, double* b2,
+                               const unsigned long long* mx, int* sh, int64_t n) {
+  pdl_enter();
+  const int sf = fx_shift(max(max(mx[0], mx[1]), mx[2]));
+  const int su = fx_shift(max(max(mx[4], mx[5]), mx[6]));
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    sh[0] = sf;
+    sh[1] = su;
+  }
+  const double cf = ldexp(1.0, sf), cu = ldexp(1.0, su);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < n; c += stride) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      double* a = k == 0 ? a0 : k == 1 ? a1 : k == 2 ? a2 : k == 3 ? b0 : k == 4 ? b1 : b2;
+      const double v = a[c];
+      reinterpret_cast<int64_t*>(a)[c] = __double2ll_rn(v * (k < 3 ? cf : cu));
+    }
+  }
+}
+
+// f~ = M f - A u_D (velocity nodes), g~ = delta h_T^2 sum_d B_d^T f_d - B u_D
+// (pressure nodes) on the regular nodes from the quantized data: the mass,
+// stiffness and divergence stencils as exact integer sums (60 M_reg / h^3 =
+// 24 centre + 3 axis/body + 2 face diagonals), one conversion per term.
+// Boundary nodes are left to k_set_rhs_irr.
+__global__ void k_set_rhs_fx(LevelDev<double> L, const int64_t* f0, const int64_t* f1, const int64_t* f2,
+                             const int64_t* d0, const int64_t* d1, const int64_t* d2, const int* sh) {
+  pdl_enter();
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const Node n = node_at(L.px, L.pxy, i, j, k);
+  const int64_t c = n.c;
+  const uint8_t fl = L.flags[c];
+  if (fl & F_IRR) return;
+  const double isf = ldexp(1.0, -sh[0]), isu = ldexp(1.0, -sh[1]);
+  const GNb<int64_t> F[3] = {gnb(f0, n, L.px, L.pxy), gnb(f1, n, L.px, L.pxy), gnb(f2, n, L.px, L.pxy)};
+  const GNb<int64_t> U[3] = {gnb(d0, n, L.px, L.pxy), gnb(d1, n, L.px, L.pxy), gnb(d2, n, L.px, L.pxy)};
+  if (fl & F_VFREE) {
+    const double km = L.h3 * (1.0 / 60.0) * isf, ka = L.nuh * isu;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const GNb<int64_t>& v = F[d];
+      const int64_t ax = nb6v(v) + (v(1, 1, 1) + v(-1, -1, -1));
+      const int64_t fc = (v(1, 1, 0) + v(-1, -1, 0)) + (v(0, 1, 1) + v(0, -1, -1)) + (v(1, 0, 1) + v(-1, 0, -1));
+      const int64_t m = 24 * v(0, 0, 0) + 3 * ax + 2 * fc;
+      const int64_t a = 6 * U[d](0, 0, 0) - nb6v(U[d]);
+      L.f[d][c] = km * (double)m - ka * (double)a;
+    }
+  } else {
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.f[d][c] = 0.0;
+  }
+  if (fl & F_ACT) {
+    const int64_t bf = (div12(diff7v<int64_t>(F[0]), 0) + div12(diff7v<int64_t>(F[1]), 1)) +
+                       div12(diff7v<int64_t>(F[2]), 2);
+    const int64_t bu = (div12(diff7v<int64_t>(U[0]), 0) + div12(diff7v<int64_t>(U[1]), 1)) +
+                       div12(diff7v<int64_t>(U[2]), 2);
+    const double k12 = L.h2 * (1.0 / 12.0);
+    L.g[c] = (L.dh2 * (-k12 * isf)) * (double)bf - (k12 * isu) * (double)bu;
+  } else {
+    L.g[c] = 0.0;
+  }
+}
+
+// The boundary nodes (list of lattice coordinates, as k_ir_residual_fx_irr):
+// class rows in FP64 on the dequantized data, component by component.
+__global__ void k_set_rhs_irr(LevelDev<double> L, const int64_t* f0, const int64_t* f1, const int64_t* f2,
+                              const int64_t* d0, const int64_t* d1, const int64_t* d2, const int* sh,
+                              const int64_t* irr, int64_t nirr) {
+  pdl_enter();
+  const double isf = ldexp(1.0, -sh[0]), isu = ldexp(1.0, -sh[1]);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nirr; t += stride) {
+    const int64_t e = irr[t];
+    const Node n = node_at(L.px, L.pxy, (int)(e & 0x1fffff), (int)((e >> 21) & 0x1fffff), (int)(e >> 42));
+    const int64_t c = n.c;
+    const uint8_t fl = L.flags[c];
+    const double* w = class_row(L, c);
+    double gf = 0.0, gu = 0.0;
+#pragma unroll 1
+    for (int d = 0; d < 3; ++d) {
+      double fv[15], uv[15];
+      fx_gather15(d == 0 ? f0 : d == 1 ? f1 : f2, n, L.px, L.pxy, isf, fv);
+      fx_gather15(d == 0 ? d0 : d == 1 ? d1 : d2, n, L.px, L.pxy, isu, uv);
+      const SlotNb fs{fv}, us{uv};
+      if (fl & F_VFREE) L.f[d][c] = L.h3 * st15v<double>(fs, w + W_M) - L.nuh * st15v<double>(us, w + W_LAP);
+      gf += L.h2 * st15v<double>(fs, w + W_BT + 15 * d);
+      gu += st15v<double>(us, w + W_B + 15 * d);
+    }
+    if (!(fl & F_VFREE)) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) L.f[d][c] = 0.0;
+    }
+    L.g[c] = (fl & F_ACT) ? L.dh2 * gf - L.h2 * gu : 0.0;
+  }
+}
+
 // x += e (the FP64 refinement update).
 __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
   pdl_enter();
@@ -898,8 +961,26 @@ void launch_zero(const LevelDev<T>& L, int what, cudaStream_t s) {
   cudaMemsetAsync(base, 0, sizeof(T) * 4 * (size_t)L.nalloc, s);
 }
 
-void launch_set_rhs(const LevelDev<double>& L, const double* const* fnod, const double* const* uD, cudaStream_t s) {
-  launch_k(k_set_rhs, full_grid(L), dim3(FX, FY), s, L, fnod[0], fnod[1], fnod[2], uD[0], uD[1], uD[2]);
+void launch_set_rhs(const LevelDev<double>& L, double* const* fnod, double* const* uD, unsigned long long* mx,
+                    int* sh, const int64_t* irr, int64_t nirr, cudaStream_t s) {
+  cudaMemsetAsync(mx, 0, 8 * sizeof(unsigned long long), s);
+  LevelDev<double> a = L;  // the max |v| kernel reads u[0..3) and p
+  for (int d = 0; d < 3; ++d) a.u[d] = fnod[d];
+  a.p = fnod[0];
+  launch_k(k_ir_absmax, IR_BLOCKS, REDUCE_THREADS, s, a, mx);
+  for (int d = 0; d < 3; ++d) a.u[d] = uD[d];
+  a.p = uD[0];
+  launch_k(k_ir_absmax, IR_BLOCKS, REDUCE_THREADS, s, a, mx + 4);
+  launch_k(k_rhs_quantize, flat_blocks(L.nalloc), 256, s, fnod[0], fnod[1], fnod[2], uD[0], uD[1], uD[2],
+           (const unsigned long long*)mx, sh, L.nalloc);
+  const int64_t* f[3] = {reinterpret_cast<const int64_t*>(fnod[0]), reinterpret_cast<const int64_t*>(fnod[1]),
+                         reinterpret_cast<const int64_t*>(fnod[2])};
+  const int64_t* u[3] = {reinterpret_cast<const int64_t*>(uD[0]), reinterpret_cast<const int64_t*>(uD[1]),
+                         reinterpret_cast<const int64_t*>(uD[2])};
+  launch_k(k_set_rhs_fx, full_grid(L), dim3(FX, FY), s, L, f[0], f[1], f[2], u[0], u[1], u[2], (const int*)sh);
+  if (nirr > 0)
+    launch_k(k_set_rhs_irr, IR_IRR_BLOCKS, REDUCE_THREADS, s, L, f[0], f[1], f[2], u[0], u[1], u[2],
+             (const int*)sh, irr, nirr);
 }
 void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s) {
   launch_k(k_sum_g, REDUCE_BLOCKS, REDUCE_THREADS, s, L, partial);

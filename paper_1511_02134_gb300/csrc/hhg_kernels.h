@@ -74,7 +74,12 @@ template <class T> void launch_zero(const LevelDev<T>& L, int what, cudaStream_t
 
 // Right-hand side of the finest level from staged nodal arrays (padded
 // layout, component planes): fnod[3], uD[3] (uD zero off Dirichlet nodes).
-void launch_set_rhs(const LevelDev<double>& L, const double* const* fnod, const double* const* uD, cudaStream_t s);
+// The arrays are quantized in place to int64 (one power-of-two scale for f,
+// one for u_D, from their max |v| into mx[0..8) and sh[0..2)) and the
+// regular-node stencils summed exactly in integers; the boundary nodes (irr,
+// lattice coordinates as FxState::irr) use their class rows in FP64.
+void launch_set_rhs(const LevelDev<double>& L, double* const* fnod, double* const* uD, unsigned long long* mx,
+                    int* sh, const int64_t* irr, int64_t nirr, cudaStream_t s);
 // G -= mean(G) over active nodes (two passes through partial/out).
 void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s);
 
