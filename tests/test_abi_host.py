@@ -89,3 +89,46 @@ def test_create_mesh_without_gpu_fails_cleanly(pkg):
     with pytest.raises(pkg.HHGError) as e:
         pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 2)
     assert e.value.code == -6
+
+
+def _struct_fields(header, name):
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), header, re.S).group(1)
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    return re.findall(r"^\s*(double|int32_t|int64_t)\s+(\w+)(\[\d+\])?\s*;", body, re.M)
+
+
+def test_binding_mirrors_header(pkg, tmp_path):
+    """The Python binding's op codes and ctypes structs match the C header:
+    names, order, types, and (compiled with the host C compiler) offsets and
+    sizes."""
+    import ctypes
+    import shutil
+    import subprocess
+    header = open(os.path.join(ROOT, "include", "hhg_stokes.h")).read()
+    ops = {m[0].lower(): int(m[1]) for m in re.findall(r"#define HHG_OP_(\w+)\s+(\d+)", header)}
+    assert ops == pkg.OP
+    ctype = {"double": ctypes.c_double, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64}
+    for cname, py in (("hhg_options", pkg.Options), ("hhg_stats", pkg._Stats)):
+        fields = _struct_fields(header, cname)
+        assert [f[1] for f in fields] == [f[0] for f in py._fields_], cname
+        for (ty, nm, arr), (pn, pt) in zip(fields, py._fields_):
+            want = ctype[ty] * int(arr[1:-1]) if arr else ctype[ty]
+            assert ctypes.sizeof(pt) == ctypes.sizeof(want) and getattr(pt, "_type_", pt) == getattr(want, "_type_", want), nm
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "layout.c"
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "hhg_stokes.h"', "int main(void) {"]
+    for cname in ("hhg_options", "hhg_stats"):
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (cname, cname))
+        for _, nm, _ in _struct_fields(header, cname):
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (cname, nm, cname, nm))
+    lines += ["return 0;", "}"]
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.split() for l in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n") if l)
+    for cname, py in (("hhg_options", pkg.Options), ("hhg_stats", pkg._Stats)):
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for pn, _ in py._fields_:
+            assert int(got["%s.%s" % (cname, pn)]) == getattr(py, pn).offset, (cname, pn)
