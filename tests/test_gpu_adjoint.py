@@ -1,4 +1,4 @@
-"""Adjoint gradient on the GPU (SURVEY config: obstacle channel, level 5).
+"""Adjoint gradient on the GPU (obstacle channel, level 5).
 
 J_psi(u) = sum_i psi_i w_i . u_i is the outflow flux weighted by
 psi = y z / 16 (the unweighted flux does not depend on the body force, see
