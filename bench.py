@@ -37,8 +37,10 @@ TOL = 1e-8
 # DRAM bytes (read + write) of one k_vel_colour_rhs<float> launch, from an ncu
 # capture of `bench.py --roofline-only` at that level (cold caches: ncu
 # flushes them before each pass); None where no capture of the current kernel
-# exists.
-TRAFFIC_PER_LAUNCH = {7: 47069440 + 84736}
+# exists.  The level-7 capture (47,154,176 bytes) predates the packed
+# (row, quarter-row slot) thread mapping of the colour kernels, so it is not
+# reported for the current kernel.
+TRAFFIC_PER_LAUNCH = {}
 
 
 def _peaks():

@@ -157,7 +157,8 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     // Uzawa step); no effect measured at level 7
     const int want = M->opt.colour_block_z;
     L.cbz = want == 1 || want == 2 || want == 4 ? want : (H.sh.n() >= ((int64_t)1 << 22) ? 2 : 1);
-    L.cby = 4;
+    L.nq = (int)((H.sh.nx + 3) / 4);
+    L.nq_mul = L.nq == 1 ? 0 : ~0ull / (uint64_t)L.nq + 1;
   };
   set(H.d64);
   set(H.d32);

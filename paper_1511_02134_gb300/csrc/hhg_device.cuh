@@ -45,7 +45,9 @@ struct LevelDev {
   T dh2;                 // delta * h_T^2
   T omega;               // pressure under-relaxation
   int spec;              // colour updates in the speculative node form (small levels)
-  int cby, cbz;          // rows and planes per thread block of the colour kernels
+  int cbz;               // planes per thread block of the colour kernels
+  int nq;                // quarter-row slots per row, (nx + 3) / 4: the colour kernels' packed index
+  uint64_t nq_mul;       // ceil(2^64 / nq) (0 when nq = 1): t / nq = umul64hi(t, nq_mul)
   T* u[3];
   T* p;
   T* f[3];

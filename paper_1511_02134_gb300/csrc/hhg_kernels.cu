@@ -11,17 +11,17 @@ namespace hhg {
 
 namespace {
 
-constexpr int CX = 32;  // colour kernels: quarter-rows per block; rows and planes per level (cby, cbz)
+constexpr int CB = 128;  // colour kernels: packed (row, quarter-row slot) indices per block; planes per level (cbz)
 constexpr int FX = 64, FY = 4;  // full kernels
 
 template <class T>
 dim3 colour_block(const LevelDev<T>& L) {
-  return dim3(CX, L.cby, L.cbz);
+  return dim3(CB, 1, L.cbz);
 }
 template <class T>
 dim3 colour_grid(const LevelDev<T>& L) {
-  const int nq = (L.nx + 3) / 4;
-  return dim3((nq + CX - 1) / CX, (L.ny + L.cby - 1) / L.cby, (L.nz + L.cbz - 1) / L.cbz);
+  const int64_t slots = (int64_t)L.ny * L.nq;
+  return dim3((unsigned)((slots + CB - 1) / CB), (unsigned)((L.nz + L.cbz - 1) / L.cbz), 1);
 }
 template <class T>
 dim3 full_grid(const LevelDev<T>& L) {
@@ -38,11 +38,15 @@ bool spec_level(const LevelDev<T>& L) {
 // Colour-kernel node: returns false if outside the lattice.
 template <class T>
 __device__ __forceinline__ bool colour_node(const LevelDev<T>& L, int colour, int& i, int& j, int& k) {
-  const int t = blockIdx.x * CX + threadIdx.x;
-  j = blockIdx.y * blockDim.y + threadIdx.y;
-  k = blockIdx.z * blockDim.z + threadIdx.z;
-  i = ((colour - j - k) & 3) + 4 * t;
-  return i < L.nx && j < L.ny && k < L.nz;
+  // slot t of plane k: row j = t / nq, quarter-row slot t - j nq (the rows of
+  // a plane packed back to back, so that no warp holds only a row's tail)
+  const uint64_t t = (uint64_t)blockIdx.x * CB + threadIdx.x;
+  k = blockIdx.y * blockDim.z + threadIdx.z;
+  const uint64_t row = L.nq == 1 ? t : __umul64hi(t, L.nq_mul);
+  if (row >= (uint64_t)L.ny) return false;
+  j = (int)row;
+  i = ((colour - j - k) & 3) + 4 * (int)(t - row * (uint64_t)L.nq);
+  return i < L.nx && k < L.nz;
 }
 
 template <class T>
