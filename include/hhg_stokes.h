@@ -278,6 +278,11 @@ int hhg_time_op(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t op, in
 /* Kernels launched by this mesh so far (graph nodes counted per replay). */
 int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count);
 
+/* Allocations (cudaMalloc and pinned cudaMallocHost calls) made for this mesh
+ * so far, including the temporaries of hhg_apply_operator and
+ * hhg_level_field that are freed before those calls return. */
+int hhg_allocations(const hhg_mesh* mesh, int64_t* count);
+
 /* ---- allocation-free coarse-grid solve ---------------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory after set-up: code whose device
@@ -295,7 +300,8 @@ int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count);
  *   space, so do not overlap this call with other calls on the same mesh.
  *   Errors: HHG_EINVAL when the coarsest level needs more than 2^18 scratch
  *   doubles (11 (3 nv + np) + 9 nv for nv free velocity nodes and np
- *   pressure nodes), HHG_ECUDA on CUDA errors.
+ *   pressure nodes), HHG_ECUDA on CUDA errors.  On HHG_EINVAL nothing is
+ *   written: neither the caller's u, p nor the mesh's fields.
  *   The first call on a device looks up the array's device address (one
  *   cudaGetSymbolAddress); make that first call before any stream capture.
  *   Every call shares the one array per device, which keeps the last call's

@@ -111,6 +111,7 @@ def load_library():
         "hhg_lattice_classify": (I32, [P, I64, P, I64, P, I32, P, P]),
         "hhg_time_op": (I32, [P, I32, I32, I32, I32, P]),
         "hhg_kernel_launches": (I32, [P, P]),
+        "hhg_allocations": (I32, [P, P]),
         "hhg_coarse_solve_noalloc": (I32, [P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
@@ -355,6 +356,12 @@ class Mesh:
     def kernel_launches(self) -> int:
         n = ctypes.c_int64()
         self._check(self._lib.hhg_kernel_launches(self._h, ctypes.byref(n)))
+        return n.value
+
+    def allocations(self) -> int:
+        """cudaMalloc / cudaMallocHost calls made for this mesh so far (hhg_allocations)."""
+        n = ctypes.c_int64()
+        self._check(self._lib.hhg_allocations(self._h, ctypes.byref(n)))
         return n.value
 
 

@@ -98,6 +98,7 @@ struct hhg_mesh {
   int64_t launches = 0;
   int64_t fx_recoveries = 0;  // fixed-point cycles redone in FP64 (fx_recover_if_flagged)
   int64_t device_bytes = 0;
+  int64_t allocations = 0;  // cudaMalloc / cudaMallocHost calls made for this mesh, temporaries included
   std::string err;
 };
 
@@ -126,6 +127,7 @@ int dalloc(hhg_mesh* M, void** p, size_t bytes) {
     return fail(M, HHG_ENOMEM, std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes failed");
   }
   M->device_bytes += (int64_t)bytes;
+  M->allocations += 1;
   return HHG_OK;
 }
 
@@ -912,6 +914,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     M->err = cudaGetErrorString(e);
     return bail(HHG_ENOMEM);
   }
+  M->allocations += 1;
   // compact coarsest-level system for the coarse solver
   {
     LevelHost& H = M->lv[M->coarsest];
@@ -1381,6 +1384,12 @@ static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op)
 
 int hhg_coarse_solve_noalloc(hhg_mesh* M, const double* f, const double* g, double* u, double* p) {
   if (!M || !f || !g || !u || !p) return HHG_EINVAL;
+  // size check before anything is staged: a rejected call writes nothing
+  if (coarse_scratch_doubles(M->coarse_sys) > NOALLOC_COARSE_DOUBLES)
+    return fail(M, HHG_EINVAL,
+                "coarsest level needs " + std::to_string(coarse_scratch_doubles(M->coarse_sys)) +
+                    " scratch doubles; the allocation-free coarse solve holds " +
+                    std::to_string(NOALLOC_COARSE_DOUBLES));
   CK(cudaSetDevice(M->device));
   LevelHost& H = M->lv[M->coarsest];
   LevelDev<double>& L = H.d64;
@@ -1470,6 +1479,12 @@ int hhg_time_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op, int32
 int hhg_kernel_launches(const hhg_mesh* mesh, int64_t* count) {
   if (!mesh || !count) return HHG_EINVAL;
   *count = mesh->launches;
+  return HHG_OK;
+}
+
+int hhg_allocations(const hhg_mesh* mesh, int64_t* count) {
+  if (!mesh || !count) return HHG_EINVAL;
+  *count = mesh->allocations;
   return HHG_OK;
 }
 

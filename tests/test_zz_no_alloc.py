@@ -5,7 +5,10 @@ Callers that may not allocate device memory after set-up (fixed arenas,
 framework-owned pools, latency-bound loops) use the allocation-free entry
 point; it must give the same corrected iterate as the regular coarse solve.
 Two calls in a row, with different data, check that the shared scratch array
-carries nothing from one call into the next.  This file is collected last.
+carries nothing from one call into the next, and that neither call allocates:
+the mesh's allocation counter (every cudaMalloc / cudaMallocHost it makes,
+temporaries included) and the device's free memory are unchanged across it.
+A call rejected for size writes nothing.  This file is collected last.
 """
 import numpy as np
 import pytest
@@ -55,11 +58,17 @@ def test_noalloc_matches_coarse_solve(pkg, name, finest, coarsest, mx):
                     coarse_minres_max=mx)
     flags = mesh.node_flags(coarsest)
     vf, act = (flags & 2) > 0, (flags & 1) > 0
+    import torch
     for call, seed in enumerate((1, 2)):
         f, g, u, p = _data(mesh, coarsest, seed)
         ur, pr = _reference(mesh, coarsest, f, g, u, p)
         u2, p2 = u.copy(), p.copy()
+        torch.cuda.synchronize()
+        allocs, free0 = mesh.allocations(), torch.cuda.mem_get_info()[0]
         mesh.coarse_solve_noalloc(f, g, u2, p2)
+        torch.cuda.synchronize()
+        assert mesh.allocations() == allocs, call
+        assert torch.cuda.mem_get_info()[0] == free0, call
         assert _rel(u2[vf], ur[vf]) <= 1e-12, call
         assert _rel(p2[act], pr[act]) <= 1e-12, call
         assert np.all(u2[~vf] == 0) and np.all(p2[~act] == 0)
@@ -70,7 +79,18 @@ def test_noalloc_rejects_large_coarse_level(pkg):
     cube = W.unit_cube()
     mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, coarsest_level=5)
     n = mesh.num_nodes(5)
+    f, g, u, p = _data(mesh, 5, 3)
+    for name, val in (("F", f), ("G", g), ("U", u), ("P", p)):
+        mesh.level_field(5, name, 0, val)
+    before = {name: mesh.level_field(5, name) for name in ("F", "G", "U", "P")}
+    u_in, p_in = np.ones((n, 3)), np.ones(n)
+    allocs = mesh.allocations()
     with pytest.raises(pkg.HHGError) as e:
-        mesh.coarse_solve_noalloc(np.zeros((n, 3)), np.zeros(n), np.zeros((n, 3)), np.zeros(n))
+        mesh.coarse_solve_noalloc(np.zeros((n, 3)), np.zeros(n), u_in, p_in)
     assert e.value.code == -1 and "scratch" in str(e.value)
+    assert mesh.allocations() == allocs
+    # nothing written: neither the caller's arrays nor the mesh's fields
+    assert np.all(u_in == 1.0) and np.all(p_in == 1.0)
+    for name, val in before.items():
+        assert np.array_equal(mesh.level_field(5, name), val), name
     mesh.close()
