@@ -1,28 +1,31 @@
 """Benchmark: Stokes DoF solved per second to a 1e-8 relative residual.
 
-Workload (default): unit cube of 6 Kuhn tetrahedra refined to level 7
-(129^3 nodes, 8,291,838 free DoFs), manufactured smooth solution (Sec. 5),
+Workload (default): unit cube of 6 Kuhn tetrahedra refined to level 9
+(513^3 nodes, 535,291,902 free DoFs), manufactured smooth solution (Sec. 5),
 viscosity 1, Dirichlet velocity, zero-mean pressure; all-at-once Uzawa
 multigrid V_var(3,3) from a zero initial guess.  One step = set the
 right-hand side from device-resident nodal inputs + solve to 1e-8 in the
 FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
-timed the same way and reported beside it.
+timed the same way and reported beside it, and the same pair is reported for
+the level-7 cube (8,291,838 free DoFs) under "level7".
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
-bounded sample of the same workload (the oracle cannot hold level 7 in
-seconds); with torchrun, ranks > 0 of the reference arm exit at once.
+bounded sample of the same workload (the oracle cannot hold level 9); with
+torchrun, ranks > 0 of the reference arm exit at once.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
+import platform
 import subprocess
 import sys
 import threading
 import time
 
-# the CPU oracle is timed single-threaded; fix the BLAS pools before numpy loads
+# the CPU oracle is timed single-threaded per process; fix the BLAS pools before numpy loads
 for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
     os.environ.setdefault(_v, "1")
 
@@ -32,15 +35,17 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Stokes DoF solved/s to 1e-8 rel. residual, FP32+refine vs FP64; HBM % of peak"
-LEVEL = 7
+LEVEL = 9
+EXTRA_LEVEL = 7
 TOL = 1e-8
-# DRAM bytes (read + write) of one k_vel_colour_rhs<float> launch, from an ncu
-# capture of `bench.py --roofline-only` at that level (cold caches: ncu
-# flushes them before each pass); None where no capture of the current kernel
-# exists.  The level-7 capture (47,154,176 bytes) predates the packed
-# (row, quarter-row slot) thread mapping of the colour kernels, so it is not
-# reported for the current kernel.
-TRAFFIC_PER_LAUNCH = {}
+ORACLE_LEVEL = 5
+# DRAM bytes (read + write) of one launch of the roofline kernel, per lattice
+# node of the level, from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of that kernel on the level-8 cube (17 M nodes, a
+# few GB on the device: the fields are far larger than L2), scaled to the
+# bench level by its node count; None where no capture of the current kernel
+# exists.
+TRAFFIC_BYTES_PER_NODE = {}
 
 
 def _peaks():
@@ -130,115 +135,182 @@ def _barrier(world: int):
 def _inputs(mesh):
     import workloads as W
     x = mesh.node_coords()
-    return W.manufactured_forcing(x), W.manufactured_velocity(x)
+    f, ud = W.manufactured_forcing(x), W.manufactured_velocity(x)
+    del x
+    return f, ud
+
+
+class LevelBench:
+    """One cube level: the mesh, device-resident inputs and the timed steps."""
+
+    def __init__(self, pkg, level, stream, flush, world):
+        import torch
+
+        import workloads as W
+        self.pkg, self.level, self.stream, self.flush, self.world = pkg, level, stream, flush, world
+        macro = W.unit_cube()
+        self.mesh = pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, stream=stream.cuda_stream)
+        nv, npn = self.mesh.num_dofs()
+        self.dofs = 3 * nv + npn
+        self.n = self.mesh.num_nodes()
+        self.f_host, self.ud_host = _inputs(self.mesh)
+        self.f_dev = torch.from_numpy(self.f_host).cuda()
+        self.ud_dev = torch.from_numpy(self.ud_host).cuda()
+
+    def step(self, mode, u_out=None, p_out=None):
+        self.mesh.set_rhs(self.f_dev, self.ud_dev)
+        want = u_out is not None
+        _, _, st = self.mesh.solve(tol=TOL, max_cycles=50, mode=mode, u_out=u_out, p_out=p_out,
+                                   want_solution=want)
+        if st.status != 0:
+            raise RuntimeError(f"solve did not converge: {st}")
+        return st
+
+    def timed(self, mode, steps, warmup):
+        import torch
+        for _ in range(warmup):
+            self.step(mode)
+        total_ms, cycles, launches = 0.0, [], 0
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        _barrier(self.world)
+        torch.cuda.synchronize()
+        for _ in range(steps):
+            with torch.cuda.stream(self.stream):
+                self.flush.fill_(1.0)  # evict L2 between timed steps (not timed)
+            self.stream.synchronize()
+            k0 = self.mesh.kernel_launches()
+            e0.record(self.stream)
+            st = self.step(mode)
+            e1.record(self.stream)
+            e1.synchronize()
+            launches += self.mesh.kernel_launches() - k0
+            total_ms += e0.elapsed_time(e1)
+            cycles.append(st.cycles)
+        torch.cuda.synchronize()
+        _barrier(self.world)
+        return _max_over_ranks(total_ms, self.world), cycles, launches
+
+    def pair(self, steps, warmup, steps64, clocks=None):
+        """FP32+IR (headline) and FP64, device-timed."""
+        pkg = self.pkg
+        if clocks:
+            clocks.start()
+        ms32, cyc32, launches32 = self.timed(pkg.MODE_FP32_IR, steps, warmup)
+        clk = clocks.stop() if clocks else None
+        ms64, cyc64, _ = self.timed(pkg.MODE_FP64, steps64, 1)
+        v32 = self.world * self.dofs * steps / (ms32 / 1e3)
+        v64 = self.world * self.dofs * steps64 / (ms64 / 1e3)
+        return {"value": v32, "ms_per_step": ms32 / steps, "cycles": cyc32, "launches": launches32,
+                "fp64": {"value": v64, "ms_per_step": ms64 / steps64, "cycles": cyc64, "dtype": "f64"},
+                "speedup_fp32ir_vs_fp64": v32 / v64, "clocks": clk}
+
+    def e2e(self, steps):
+        """The same metric end to end through the C ABI: pinned host inputs in,
+        solution out, host<->device copies inside the timed region."""
+        import torch
+        f_pin = torch.from_numpy(self.f_host).pin_memory()
+        ud_pin = torch.from_numpy(self.ud_host).pin_memory()
+        u_pin = torch.empty((self.n, 3), dtype=torch.float64).pin_memory()
+        p_pin = torch.empty((self.n,), dtype=torch.float64).pin_memory()
+        ms = 0.0
+        for _ in range(steps):
+            self.stream.synchronize()
+            t0 = time.perf_counter()
+            self.mesh.set_rhs(f_pin, ud_pin)
+            self.mesh.solve(tol=TOL, max_cycles=50, mode=self.pkg.MODE_FP32_IR, u_out=u_pin, p_out=p_pin)
+            ms += (time.perf_counter() - t0) * 1e3
+        ms = _max_over_ranks(ms, self.world)
+        del f_pin, ud_pin, u_pin, p_pin
+        return {"value": self.world * self.dofs * steps / (ms / 1e3), "unit": "DoF/s",
+                "h2d_bytes_per_step": int(2 * 3 * self.n * 8), "d2h_bytes_per_step": int(4 * self.n * 8)}
+
+    def error_vs_fp64(self):
+        """Relative max-norm difference of the FP32+IR solution (to 1e-8) from
+        an FP64 solve to 1e-12 on the same device (the FP64 path matches the
+        oracle's iterates and solutions at the levels the oracle can hold)."""
+        import torch
+        pkg = self.pkg
+        u32 = torch.empty((self.n, 3), dtype=torch.float64, device="cuda")
+        p32 = torch.empty((self.n,), dtype=torch.float64, device="cuda")
+        self.step(pkg.MODE_FP32_IR, u32, p32)
+        u64 = torch.empty_like(u32)
+        p64 = torch.empty_like(p32)
+        self.mesh.set_rhs(self.f_dev, self.ud_dev)
+        _, _, st = self.mesh.solve(tol=1e-12, max_cycles=60, mode=pkg.MODE_FP64, u_out=u64, p_out=p64)
+        eu = float((u32 - u64).abs().max() / u64.abs().max())
+        ep = float((p32 - p64).abs().max() / p64.abs().max())
+        del u32, p32, u64, p64
+        return {"u": eu, "p": ep, "against": f"FP64 solve to 1e-12 ({st.cycles} cycles) on the same GPU",
+                "norm": "max |x - x_ref| / max |x_ref| over all nodes"}
+
+    def close(self):
+        self.mesh.close()
 
 
 def run_gpu(args):
     import torch
 
     import paper_1511_02134_gb300 as pkg
-    import workloads as W
 
     world, rank, local = _dist()
+    if rank == 0 and not args.no_cpu:
+        # the oracle's process pool starts before any GPU call (spawned workers)
+        cpu = cpu_baseline(args.cpu_seconds)
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     pkg.load_library()
     stream = torch.cuda.Stream()
-    macro = W.unit_cube()
-    mesh = pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, args.level, stream=stream.cuda_stream)
-    nv, npn = mesh.num_dofs()
-    dofs = 3 * nv + npn
-    f_host, ud_host = _inputs(mesh)
-    f_dev = torch.from_numpy(f_host).cuda()
-    ud_dev = torch.from_numpy(ud_host).cuda()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
 
-    def step(mode):
-        mesh.set_rhs(f_dev, ud_dev)
-        _, _, st = mesh.solve(tol=TOL, max_cycles=50, mode=mode, want_solution=False)
-        if st.status != 0:
-            raise RuntimeError(f"solve did not converge: {st}")
-        return st
-
-    def timed(mode, steps, warmup):
-        for _ in range(warmup):
-            step(mode)
-        total_ms, cycles, launches = 0.0, [], 0
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        _barrier(world)
-        torch.cuda.synchronize()
-        for _ in range(steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(1.0)  # evict L2 between timed steps (not timed)
-            stream.synchronize()
-            k0 = mesh.kernel_launches()
-            e0.record(stream)
-            st = step(mode)
-            e1.record(stream)
-            e1.synchronize()
-            launches += mesh.kernel_launches() - k0
-            total_ms += e0.elapsed_time(e1)
-            cycles.append(st.cycles)
-        torch.cuda.synchronize()
-        _barrier(world)
-        return total_ms, cycles, launches, st
-
-    clocks = ClockSampler(local)
-    clocks.start()
-    ms32, cyc32, launches32, st32 = timed(pkg.MODE_FP32_IR, args.steps, args.warmup)
-    clk = clocks.stop()
-    ms64, cyc64, launches64, st64 = timed(pkg.MODE_FP64, max(1, args.steps // 2), max(1, args.warmup // 3))
-
-    ms32_max = _max_over_ranks(ms32, world)
-    ms64_max = _max_over_ranks(ms64, world)
-    n64 = max(1, args.steps // 2)
-    value = world * dofs * args.steps / (ms32_max / 1e3)
-    value64 = world * dofs * n64 / (ms64_max / 1e3)
-
-    # ---- end to end through the C ABI with pinned host buffers ----
-    f_pin = torch.from_numpy(f_host).pin_memory()
-    ud_pin = torch.from_numpy(ud_host).pin_memory()
-    n = mesh.num_nodes()
-    u_pin = torch.empty((n, 3), dtype=torch.float64).pin_memory()
-    p_pin = torch.empty((n,), dtype=torch.float64).pin_memory()
-    e2e_ms = 0.0
-    for _ in range(args.steps):
-        stream.synchronize()
-        t0 = time.perf_counter()
-        mesh.set_rhs(f_pin, ud_pin)
-        mesh.solve(tol=TOL, max_cycles=50, mode=pkg.MODE_FP32_IR, u_out=u_pin, p_out=p_pin)
-        e2e_ms += (time.perf_counter() - t0) * 1e3
-    e2e_ms = _max_over_ranks(e2e_ms, world)
-    e2e = {"value": world * dofs * args.steps / (e2e_ms / 1e3), "unit": "DoF/s",
-           "h2d_bytes_per_step": int(2 * 3 * n * 8), "d2h_bytes_per_step": int(4 * n * 8)}
-
-    roofline = measure_roofline(mesh, args.level, stream, flush)
+    steps64 = max(1, args.steps // 4)
+    head = LevelBench(pkg, args.level, stream, flush, world)
+    res = head.pair(args.steps, args.warmup, steps64, clocks=ClockSampler(local))
+    e2e = head.e2e(max(1, args.steps // 4))
+    err = head.error_vs_fp64()
+    roofline = measure_roofline(head.mesh, args.level, stream, flush)
+    dofs = head.dofs
+    head.close()
+    del head
+    extra = None
+    if args.extra_level and args.extra_level != args.level:
+        lb = LevelBench(pkg, args.extra_level, stream, flush, world)
+        r7 = lb.pair(args.steps, args.warmup, max(1, args.steps // 2))
+        extra = {"free_dofs": lb.dofs, "value": r7["value"], "ms_per_step": r7["ms_per_step"],
+                 "cycles": r7["cycles"][:1], "fp64": {k: r7["fp64"][k] for k in ("value", "ms_per_step")},
+                 "speedup_fp32ir_vs_fp64": r7["speedup_fp32ir_vs_fp64"],
+                 "roofline": measure_roofline(lb.mesh, args.extra_level, stream, flush, bound="l2")}
+        extra["fp64"]["cycles"] = r7["fp64"]["cycles"][:1]
+        lb.close()
 
     out = {
-        "metric": METRIC, "value": value, "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms32_max / args.steps, "higher_is_better": True,
+        "metric": METRIC, "value": res["value"], "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 V-cycle + f64 refinement", "data": "synthetic",
         "config": {"workload": f"unit cube, 6 Kuhn tetrahedra, level {args.level} ({dofs} free DoFs), manufactured "
                                "solution, V_var(3,3) from zero to 1e-8", "level": args.level, "free_dofs": dofs,
-                   "mode": "FP32 V-cycle inside FP64 iterative refinement", "l2": "flushed (256 MB write) "
-                   "between timed steps", "parallelism": "replicas" if world > 1 else "single GPU"},
-        "cycles": cyc32, "fp64": {"value": value64, "ms_per_step": ms64_max / n64, "cycles": cyc64,
-                                  "dtype": "f64"},
-        "speedup_fp32ir_vs_fp64": value / value64,
-        "roofline": roofline, "clocks": clk, "e2e": e2e, "gpu_launches": launches32,
+                   "mode": "FP32 V-cycle inside FP64 iterative refinement", "l2": "inputs larger than L2, and "
+                   "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else
+                   "single GPU"},
+        "cycles": res["cycles"], "fp64": res["fp64"], "speedup_fp32ir_vs_fp64": res["speedup_fp32ir_vs_fp64"],
+        "err_vs_oracle": err, "roofline": roofline, "clocks": res["clocks"], "e2e": e2e,
+        "gpu_launches": res["launches"],
     }
+    if extra:
+        out[f"level{args.extra_level}"] = extra
     if rank == 0:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        if not args.no_cpu:
+            out["cpu_baseline"] = cpu
         print(json.dumps(out))
-    mesh.close()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
 
 
-def measure_roofline(mesh, lvl, stream, flush):
+# ---- roofline of the dominant kernel ------------------------------------------------------------
+
+def measure_roofline(mesh, lvl, stream, flush, bound="hbm"):
     """Roofline of the dominant kernel of the FP32 path: the velocity colour
     sweep with f - B^T p formed at each node (k_vel_colour_rhs<float>) on the
     finest level, timed with CUDA events on the mesh's stream (hhg_time_op).
@@ -247,7 +319,7 @@ def measure_roofline(mesh, lvl, stream, flush):
     node; one colour launch carries a quarter of that."""
     import torch
     peak, peak_kind = _peaks()
-    reps = 20
+    reps = 10
     with torch.cuda.stream(stream):
         flush.fill_(1.0)
     stream.synchronize()
@@ -256,15 +328,16 @@ def measure_roofline(mesh, lvl, stream, flush):
     nodes = mesh.num_nodes(lvl)
     alg_bytes = nodes * (2 * 3 * 4 + 3 * 4 + 4 + 1) / 4.0
     achieved = alg_bytes / (ms_launch / 1e3) / 1e9
-    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": TRAFFIC_PER_LAUNCH.get(lvl),
+    tb = TRAFFIC_BYTES_PER_NODE.get("k_vel_colour_rhs")
+    return {"bound": bound, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None if tb is None else round(tb * nodes),
             "kernel": "k_vel_colour_rhs<float> (level %d)" % lvl, "peak_kind": peak_kind,
             "ms_per_launch": ms_launch, "alg_bytes_per_launch": alg_bytes}
 
 
 def roofline_only(args):
-    """Set up the bench workload, run one FP32+IR solve and print the roofline
-    measurement alone (the command the kernel profiles are taken with)."""
+    """Set up the workload of --level, run one FP32+IR solve and print the
+    roofline measurement alone (the command the kernel profiles are taken with)."""
     import torch
     import paper_1511_02134_gb300 as pkg
     import workloads as W
@@ -274,20 +347,41 @@ def roofline_only(args):
     mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, args.level, stream=stream.cuda_stream)
     x = mesh.node_coords()
     mesh.set_rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    del x
     mesh.solve(tol=TOL, max_cycles=50, mode=pkg.MODE_FP32_IR, want_solution=False)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
     print(json.dumps(measure_roofline(mesh, args.level, stream, flush)))
     mesh.close()
 
 
-def _oracle_sample(level: int, seconds: float):
-    """Time the CPU oracle's FP64 solve (as it stands) on the cube at `level`."""
+# ---- CPU oracle -----------------------------------------------------------------------------------
+
+def _cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def _oracle_problem(level: int):
     import workloads as W
     from oracle import multigrid as MG
     H = MG.build_hierarchy(W.unit_cube(), level)
     L = H.levels[level]
     x = L.mesh.xyz
     f, g = L.rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    return H, L, f, g
+
+
+def _oracle_sample(level: int, seconds: float, problem=None):
+    """Time the CPU oracle's FP64 solve (as it stands) on the cube at `level`
+    until `seconds` of solve time have passed (at least one solve)."""
+    from oracle import multigrid as MG
+    H, L, f, g = problem or _oracle_problem(level)
     t_solve, runs, cycles = 0.0, 0, 0
     while t_solve < seconds or runs == 0:
         t0 = time.perf_counter()
@@ -298,23 +392,41 @@ def _oracle_sample(level: int, seconds: float):
     return L.n_dofs * runs / t_solve, runs, cycles, L.n_dofs
 
 
-def cpu_baseline(seconds: float, level: int = 5):
+def _oracle_worker(args):
+    level, seconds = args
+    return _oracle_sample(level, seconds)
+
+
+def cpu_baseline(seconds: float, level: int = ORACLE_LEVEL):
+    """The oracle on one core, and on all cores as independent solves (one
+    spawned process per core, aggregate DoF/s)."""
     v, runs, cycles, dofs = _oracle_sample(level, seconds)
+    cores = os.cpu_count() or 1
+    v_all, procs = None, 1
+    if cores > 1:
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(cores) as pool:
+            outs = pool.map(_oracle_worker, [(level, seconds / 2)] * cores)
+        v_all, procs = float(sum(o[0] for o in outs)), cores
     return {"value": v, "unit": "DoF/s", "cores": 1, "kind": "oracle",
             "sample": f"unit cube level {level} ({dofs} free DoFs), FP64 V_var(3,3) to 1e-8, {runs} solves "
-                      f"x {cycles} cycles, numpy/scipy single thread; setup excluded"}
+                      f"x {cycles} cycles, numpy/scipy single thread; setup excluded",
+            "all_cores": {"value": v_all, "unit": "DoF/s", "cores": procs,
+                          "sample": "the same solve in one process per core, aggregate throughput"},
+            "host": {"nproc": cores, "cpu_model": _cpu_model(), "machine": platform.machine()}}
 
 
 def run_reference(args):
     world, rank, _ = _dist()
     if rank != 0:
         return
-    level = 5
+    level = ORACLE_LEVEL
+    problem = _oracle_problem(level)
     per = []
     for _ in range(args.warmup):
-        _oracle_sample(level, 0.0)
+        _oracle_sample(level, 0.0, problem)
     for _ in range(args.steps):
-        v, runs, cycles, dofs = _oracle_sample(level, 0.0)
+        v, runs, cycles, dofs = _oracle_sample(level, 0.0, problem)
         per.append(v)
     value = float(np.mean(per))
     sample = (f"unit cube level {level} ({dofs} free DoFs) instead of level {args.level}: FP64 V_var(3,3) to 1e-8 "
@@ -324,7 +436,8 @@ def run_reference(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"unit cube, 6 Kuhn tetrahedra, level {args.level}, manufactured solution "
                                   "(oracle on a bounded sample)", "level": level},
-           "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": "DoF/s", "cores": 1, "kind": "oracle", "sample": sample,
+                            "host": {"nproc": os.cpu_count(), "cpu_model": _cpu_model()}},
            "e2e": {"value": value, "unit": "DoF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -336,7 +449,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--level", type=int, default=LEVEL)
-    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--extra-level", type=int, default=EXTRA_LEVEL,
+                    help="second cube level reported beside the headline (0: none)")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--roofline-only", action="store_true",
                     help="print only the roofline measurement of the dominant kernel")
     args = ap.parse_args()

@@ -1,14 +1,20 @@
 """GPU parity: every step of the CUDA path against the CPU oracle, element by
 element, on the same seeded inputs, through the C ABI.
 
-Tolerances: FP64 single operations agree to 1e-12 relative to the field's
-maximum (rounding order differs: factored stencils vs assembled rows);
-whole cycles to 1e-10 (1e-9 where the coarse MINRES runs 30+ iterations:
-its recurrence amplifies the rounding-order differences of dot products);
-converged solutions to 1e-10.  FP32 steps agree with
-the FP64 oracle to 1e-5 relative (single-precision rounding of ~30
-dependent operations), and FP32+IR solutions reach the FP64 residual
-tolerance.
+Tolerances (element-wise, relative to the field's maximum):
+  * FP64 single operations: 1e-12 (rounding order differs: factored stencils
+    vs assembled rows);
+  * FP64 whole cycles: 1e-12 where the coarse MINRES runs at most 5
+    iterations, 1e-9 where it runs 30+ (its Lanczos recurrence amplifies the
+    rounding-order differences of dot products); converged solutions 1e-10;
+  * FP32 steps against the FP64 oracle: TOL32 = 1e-5.  A node update sums
+    about 20 terms bounded by the field maximum, so one update carries at
+    most ~20 u = 1.2e-6 relative error (u = 2^-24), plus the rounding of the
+    FP32 inputs (6e-8); the smoother contracts, so a few dependent colour
+    phases, a V-cycle included, stay below 1e-5;
+  * FP32+IR solutions: within 10x (plus a floor) of the error the FP64 oracle
+    itself makes when stopped at the same relative residual, both measured
+    against the oracle solved to 1e-13 ("equal accuracy").
 """
 import numpy as np
 import pytest
@@ -21,6 +27,7 @@ from tests.helpers import (lattice_index, macro_by_name, nodal_to_lattice, p_fro
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
+TOL32 = 1e-5
 
 
 @pytest.fixture(scope="module")
@@ -114,15 +121,20 @@ def test_set_rhs(pkg, name, level):
 
 # ---- smoother pieces, transfers, coarse solve ---------------------------------------------
 
-@pytest.mark.parametrize("tiles,spec", [(-1, 0), (-1, -1), (1, 0)])
+KERNEL_FORMS = [(-1, 0, 0), (-1, -1, 1), (-1, -1, 2), (-1, -1, 4), (-1, 0, 4), (1, 0, 0)]
+
+
+@pytest.mark.parametrize("tiles,spec,cbz", KERNEL_FORMS)
 @pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3)])
-def test_smoother_pieces(pkg, name, level, tiles, spec):
+def test_smoother_pieces(pkg, name, level, tiles, spec, cbz):
     """Smoother steps against the oracle, with the colour sweeps run by the
     grid kernels (tiles = -1) in the speculative node form of small levels
     (spec = 0, the default here) or the flags-first form of large levels
-    (spec = -1), and by the shared-memory tile kernels (tiles = 1: every
-    level tiled, ragged tiles included)."""
-    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), tile_min_nodes=tiles, spec_max_nodes=spec)
+    (spec = -1), with 1, 2 or 4 planes per colour block (cbz; 0 = the
+    level's default), and by the shared-memory tile kernels (tiles = 1:
+    every level tiled, ragged tiles included)."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), tile_min_nodes=tiles, spec_max_nodes=spec,
+                           colour_block_z=cbz)
     L = H.levels[level]
     dims = mesh.dims()
     st = _random_state(H, level, 7)
@@ -178,6 +190,102 @@ def test_smoother_pieces(pkg, name, level, tiles, spec):
     ru, rp = L.residual(u, p, f, g)
     assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU")), ru) < 1e-11
     assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP")), rp) < 1e-11
+
+
+@pytest.mark.parametrize("cbz", [1, 2])
+@pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
+def test_fp32_steps_match_oracle(pkg, name, level, cbz):
+    """Every FP32 kernel of the V-cycle against the FP64 oracle on the same
+    seeded state (written into the FP32 hierarchy, i.e. rounded once):
+    forward velocity sweep and pressure sweep with their right-hand sides
+    formed at each node, whole Uzawa steps, residual, restriction,
+    prolongation and a whole V-cycle rooted at the finest level."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=level - 2, coarse_minres_max=5, spec_max_nodes=-1,
+                           colour_block_z=cbz)
+    L = H.levels[level]
+    dims = mesh.dims()
+    st = _random_state(H, level, 13)
+    # sweeps with the right-hand sides formed at the node
+    _load(mesh, H, level, st, precision=1)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(level, "vel_forward_f", precision=1)
+    ru = np.stack([f[d] - L.BT[d] @ p for d in range(3)])
+    for d in range(3):
+        MG._gs_sweep(L.A, L.A_diag, u[d], ru[d], H.colours_u[level], (0, 1, 2, 3))
+    gu, _ = _read_up(mesh, H, level, precision=1)
+    assert rel_err(gu, u) < TOL32
+    mesh.level_op(level, "pres_sweep_f", precision=1)
+    rp = sum(L.B[d] @ u[d] for d in range(3)) - g
+    MG._gs_sweep(L.C, L.C_diag, p, rp, H.colours_p[level], (0, 1, 2, 3), relax=H.opt.omega)
+    _, gp = _read_up(mesh, H, level, precision=1)
+    assert rel_err(gp, p) < TOL32
+    # whole Uzawa steps, then the residual
+    _load(mesh, H, level, st, precision=1)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(level, "uzawa_step", precision=1, count=2)
+    for _ in range(2):
+        MG.uzawa_step(H, level, u, p, f, g)
+    gu, gp = _read_up(mesh, H, level, precision=1)
+    assert rel_err(gu, u) < TOL32 and rel_err(gp, p) < TOL32
+    mesh.level_op(level, "residual", precision=1)
+    ru, rp = L.residual(u, p, f, g)
+    assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU", 1)), ru) < TOL32
+    assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP", 1)), rp) < TOL32
+    # restriction of that residual, prolongation of a random coarse correction
+    Lc = H.levels[level - 1]
+    dc = mesh.dims(level - 1)
+    mesh.level_op(level, "restrict", precision=1)
+    ru32 = u_from_lattice(L, dims, mesh.level_field(level, "RU", 1))
+    rp32 = p_from_lattice(L, dims, mesh.level_field(level, "RP", 1))
+    fc = np.stack([H.Pu[level].T @ ru32[d] for d in range(3)])
+    assert rel_err(u_from_lattice(Lc, dc, mesh.level_field(level - 1, "F", 1)), fc) < TOL32
+    assert rel_err(p_from_lattice(Lc, dc, mesh.level_field(level - 1, "G", 1)), H.P[level].T @ rp32) < TOL32
+    rng = np.random.default_rng(14)
+    uc, pc = rng.standard_normal((3, Lc.n_u)), rng.standard_normal(Lc.n_p)
+    mesh.level_field(level - 1, "U", 1, u_to_lattice(Lc, dc, uc))
+    mesh.level_field(level - 1, "P", 1, p_to_lattice(Lc, dc, pc))
+    gu0, gp0 = _read_up(mesh, H, level, precision=1)
+    mesh.level_op(level, "prolong_add", precision=1)
+    gu, gp = _read_up(mesh, H, level, precision=1)
+    assert rel_err(gu, gu0 + np.stack([H.Pu[level] @ uc[d] for d in range(3)])) < TOL32
+    assert rel_err(gp, gp0 + H.P[level] @ pc) < TOL32
+    # a whole FP32 V-cycle (coarse solve in FP64 on the FP32 residual)
+    _load(mesh, H, level, st, precision=1)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(level, "vcycle", precision=1)
+    MG.vcycle(H, level, u, p, f, g)
+    gu, gp = _read_up(mesh, H, level, precision=1)
+    assert rel_err(gu, u) < TOL32 and _p_err(L, gp, p) < TOL32
+    mesh.close()
+
+
+def test_level6_large_level_kernels_match_oracle(pkg):
+    """The colour kernels in the form the bench uses on levels of 2^22 nodes
+    and more (flags-first node form, two planes per colour block), on a
+    level large enough to span many blocks with ragged edges (65^3 nodes):
+    FP64 Uzawa steps and a V-cycle against the oracle, and FP32 Uzawa steps."""
+    macro, mesh, H = _pair(pkg, "cube", 6, coarsest=2, spec_max_nodes=-1, colour_block_z=2)
+    L = H.levels[6]
+    st = _random_state(H, 6, 23)
+    _load(mesh, H, 6, st)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(6, "uzawa_step", count=2)
+    for _ in range(2):
+        MG.uzawa_step(H, 6, u, p, f, g)
+    gu, gp = _read_up(mesh, H, 6)
+    assert rel_err(gu, u) < TOL64 and rel_err(gp, p) < TOL64
+    mesh.level_op(6, "vcycle")
+    MG.vcycle(H, 6, u, p, f, g)
+    gu, gp = _read_up(mesh, H, 6)
+    assert rel_err(gu, u) < TOL64 and _p_err(L, gp, p) < TOL64
+    _load(mesh, H, 6, st, precision=1)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(6, "uzawa_step", precision=1, count=2)
+    for _ in range(2):
+        MG.uzawa_step(H, 6, u, p, f, g)
+    gu, gp = _read_up(mesh, H, 6, precision=1)
+    assert rel_err(gu, u) < TOL32 and rel_err(gp, p) < TOL32
+    mesh.close()
 
 
 @pytest.mark.parametrize("name,level", [("cube", 5), ("channel", 3), ("partial", 4)])
@@ -251,17 +359,17 @@ def test_coarse_solve(pkg, name, level, mx):
 
 # ---- cycles and solves ------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tiles,spec", [(-1, 0), (-1, -1), (1, 0)])
+@pytest.mark.parametrize("tiles,spec,cbz", KERNEL_FORMS)
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 3, 2, 5), ("cube", 5, 2, 5), ("channel", 2, 1, 200),
                                                     ("partial", 3, 1, 30)])
-def test_vcycle_iterates(pkg, name, level, coarsest, mx, tiles, spec):
+def test_vcycle_iterates(pkg, name, level, coarsest, mx, tiles, spec, cbz):
     macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles,
-                           spec_max_nodes=spec)
+                           spec_max_nodes=spec, colour_block_z=cbz)
     L = H.levels[level]
     st = _random_state(H, level, 9)
     _load(mesh, H, level, st)
     u, p, f, g = (a.copy() for a in st)
-    tol = 1e-10 if mx <= 5 else 1e-9
+    tol = TOL64 if mx <= 5 else 1e-9
     for cyc in range(2):
         mesh.level_op(level, "vcycle")
         MG.vcycle(H, level, u, p, f, g)
@@ -301,9 +409,11 @@ def test_fp64_solve_matches_oracle(pkg, name, level, coarsest, mx):
 @pytest.mark.parametrize("tiles", [0, 1])
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 5, 2, 5), ("channel", 3, 1, 200)])
 def test_fp32_ir_solve(pkg, name, level, coarsest, mx, tiles):
-    """FP32 V-cycles inside FP64 refinement reach the FP64 tolerance; the
-    solution differs from the FP64 solution by far less than it differs from
-    the exact discrete solution at that tolerance."""
+    """FP32 V-cycles inside FP64 refinement reach the FP64 tolerance, and the
+    solution's error against the oracle (solved to 1e-13) is within 10x of
+    the error the FP64 oracle itself makes when stopped at the same relative
+    residual (plus a floor of 1e-9 for u, 1e-7 for p, relative to the field
+    maxima).  The GPU FP64 solve is checked the same way."""
     macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles)
     L = H.levels[level]
     dims = mesh.dims()
@@ -313,16 +423,22 @@ def test_fp32_ir_solve(pkg, name, level, coarsest, mx, tiles):
         fn, ud = W.manufactured_forcing(x), W.manufactured_velocity(x)
     else:
         fn, ud = np.zeros_like(x), W.channel_inflow(x)
-    mesh.set_rhs(fn, ud)
-    u32, p32, s32 = mesh.solve(tol=1e-8, max_cycles=40, mode=pkg.MODE_FP32_IR)
-    assert s32.status == 0 and s32.rel_residual <= 1e-8
-    mesh.set_rhs(fn, ud)
-    u64, p64, s64 = mesh.solve(tol=1e-12, max_cycles=60, mode=pkg.MODE_FP64)
-    assert s64.rel_residual <= 1e-12
-    # error of the FP32+IR solution w.r.t. the (nearly) exact discrete solution
-    eu = rel_err(u32[lat], u64[lat])
-    ep = rel_err(p32[lat], p64[lat])
-    assert eu < 1e-6 and ep < 1e-4, (eu, ep)
+    f, g = L.rhs(fn[lat], ud[lat])
+    tight = MG.solve(H, f, g, tol=1e-13, max_cycles=80)
+    loose = MG.solve(H, f, g, tol=1e-8, max_cycles=40)
+    ut = L.scatter(tight.u, ud[lat])
+    eu64 = rel_err(L.scatter(loose.u, ud[lat]), ut)
+    ep64 = rel_err(loose.p, tight.p)
+    for mode in (pkg.MODE_FP32_IR, pkg.MODE_FP64):
+        mesh.set_rhs(fn, ud)
+        u, p, st = mesh.solve(tol=1e-8, max_cycles=40, mode=mode)
+        assert st.status == 0 and st.rel_residual <= 1e-8
+        eu = rel_err(u[lat], ut)
+        ep = rel_err(p[lat], tight.p)
+        print(name, level, "mode", mode, "cycles", st.cycles, "oracle", loose.cycles, "err u", eu, "vs", eu64,
+              "err p", ep, "vs", ep64)
+        assert eu <= 10 * eu64 + 1e-9, (eu, eu64)
+        assert ep <= 10 * ep64 + 1e-7, (ep, ep64)
 
 
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 5, 2, 5), ("channel", 3, 1, 200), ("partial", 4, 1, 30)])
