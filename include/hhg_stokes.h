@@ -93,9 +93,10 @@ typedef struct hhg_options {
   int32_t team_blocks;       /* CTAs of the fused kernel's thread-block cluster (1 = one block,
                                 at most 16); 0 = default (1 for mode 1; for mode 2, 8 in FP32
                                 and 16 in FP64) */
-  int32_t tile_min_nodes;    /* levels of at least this many lattice nodes run the colour sweeps
-                                on shared-memory tiles staged by tensor copies; 0 = default
-                                (never), -1 = never */
+  int32_t fused_min_nodes;   /* FP32 Uzawa steps on levels of at least this many lattice nodes
+                                run as three colour-fused passes (a z-march over (x, y) tiles
+                                staged into shared memory by tensor copies, several colour
+                                phases per pass); 0 = default (2^24), -1 = never */
   int32_t ir_fixed_point;    /* FP32+IR mode: 1 (default) keeps the refined iterate in 64-bit
                                 fixed point (per-field power-of-two scale, updated in integer
                                 arithmetic) and evaluates the FP64 refinement residual's
@@ -110,6 +111,10 @@ typedef struct hhg_options {
                                 velocity / pressure colour phase over per-CTA lists of its
                                 regular nodes and then its boundary nodes; 0 = default (1),
                                 -1 = over all lattice positions of the colour with flag tests */
+  int32_t fused_tile_rows;   /* rows (y) per tile of the fused passes; 0 = chosen per level and
+                                pass (most nodes per staged row at the fewest CTA waves) */
+  int64_t wait_poll_limit;   /* tests of one mbarrier wait of the fused passes before the pass
+                                gives up and reports HHG_ECUDA; 0 = default (2^20) */
 } hhg_options;
 
 /* Per-solve statistics. */
@@ -262,6 +267,11 @@ int hhg_level_field(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t fi
 #define HHG_OP_CYCLE 15         /* finest level: one cycle of hhg_solve in that precision (FP64:
                                    V-cycle, projection, residual norm; FP32: zeroed correction,
                                    V-cycle, refinement), without the host's convergence test */
+#define HHG_OP_FUSED_PASS0 16   /* precision 1, a level with fused passes: pass 0 alone (velocity
+                                   colours 0 1 2 3 from (U, P) into RU) */
+#define HHG_OP_FUSED_PASS1 17   /* pass 1 alone (velocity colours 2 1, velocity + pressure colour
+                                   0, from (RU, P) into (U, RP)) */
+#define HHG_OP_FUSED_PASS2 18   /* pass 2 alone (pressure colours 1 2 3 from (U, RP) into P) */
 
 /* Run `op` `count` times on `level` in `precision`. */
 int hhg_level_op(hhg_mesh* mesh, int32_t level, int32_t precision, int32_t op, int32_t count);

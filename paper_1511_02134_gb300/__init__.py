@@ -29,7 +29,8 @@ NODE_ACTIVE, NODE_VFREE, NODE_IRREG, NODE_DIRICHLET, NODE_OUTFLOW = 1, 2, 4, 8, 
 FIELD = {"U": 0, "P": 1, "F": 2, "G": 3, "RU": 4, "RP": 5}
 OP = {"uzawa_step": 0, "vel_forward": 1, "vel_backward": 2, "vel_rhs": 3, "pres_rhs": 4,
       "pres_sweep": 5, "residual": 6, "restrict": 7, "prolong_add": 8, "coarse_solve": 9,
-      "vcycle": 10, "project": 11, "vel_forward_f": 12, "pres_sweep_f": 13, "refine": 14, "cycle": 15}
+      "vcycle": 10, "project": 11, "vel_forward_f": 12, "pres_sweep_f": 13, "refine": 14, "cycle": 15,
+      "fused_pass0": 16, "fused_pass1": 17, "fused_pass2": 18}
 ERRORS = {0: "ok", -1: "HHG_EINVAL", -2: "HHG_EMESH", -3: "HHG_ENOMEM", -4: "HHG_EDIVERGED",
           -5: "HHG_EMAXIT", -6: "HHG_ECUDA", -7: "HHG_ESTATE"}
 
@@ -47,9 +48,10 @@ class Options(ctypes.Structure):
                 ("coarse_minres_rtol", ctypes.c_double), ("coarse_cg_max", ctypes.c_int32),
                 ("coarse_cg_rtol", ctypes.c_double), ("use_graphs", ctypes.c_int32),
                 ("fuse_coarse_levels", ctypes.c_int32), ("fuse_max_nodes", ctypes.c_int32),
-                ("team_blocks", ctypes.c_int32), ("tile_min_nodes", ctypes.c_int32),
+                ("team_blocks", ctypes.c_int32), ("fused_min_nodes", ctypes.c_int32),
                 ("ir_fixed_point", ctypes.c_int32), ("spec_max_nodes", ctypes.c_int32),
-                ("colour_block_z", ctypes.c_int32), ("resident_node_lists", ctypes.c_int32)]
+                ("colour_block_z", ctypes.c_int32), ("resident_node_lists", ctypes.c_int32),
+                ("fused_tile_rows", ctypes.c_int32), ("wait_poll_limit", ctypes.c_int64)]
 
 
 class _Stats(ctypes.Structure):

@@ -16,7 +16,7 @@ SRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT, "libhhg_stokes.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hhg_api.cu", "hhg_kernels.cu", "hhg_coarse.cu", "hhg_small.cu", "hhg_tiled.cu", "hhg_resident.cu", "hhg_lattice.cpp", "hhg_coarse_csr.cpp"]
+SOURCES = ["hhg_api.cu", "hhg_kernels.cu", "hhg_coarse.cu", "hhg_small.cu", "hhg_fused.cu", "hhg_resident.cu", "hhg_lattice.cpp", "hhg_coarse_csr.cpp"]
 
 
 def _nvcc() -> str:

@@ -32,9 +32,8 @@ struct LevelHost {
   float* d_wt32 = nullptr;
   int n_classes = 0;
   int64_t n_vel = 0, n_pres = 0;
-  bool tiled = false;  // colour sweeps on shared-memory tiles
-  int kz = 4;          // planes per CTA of the tiled sweeps
-  TileMaps tm64{}, tm32{};
+  bool fused = false;  // FP32 Uzawa steps as the three colour-fused passes (hhg_fused.cu)
+  FusedPlan fz{};
   int32_t* d_list = nullptr;         // node lists of the cluster-resident cycle (ResidentCycle::lists)
   int32_t loff[RES_LISTS + 1] = {};  // their offsets
   double* mem64 = nullptr;
@@ -95,6 +94,7 @@ struct hhg_mesh {
   int64_t graph_launches[3] = {0, 0, 0};
   unsigned long long h_fxmax[4] = {0, 0, 0, 0};  // max |x| per field of the last quantization
   bool rhs_set = false;
+  bool broken = false;  // a fused pass could not drain its copies (tile_status)
   int64_t launches = 0;
   int64_t fx_recoveries = 0;  // fixed-point cycles redone in FP64 (fx_recover_if_flagged)
   int64_t device_bytes = 0;
@@ -176,7 +176,9 @@ int ensure32(hhg_mesh* M) {
     if (rc) return rc;
     CK(cudaMemsetAsync(H.mem32, 0, sizeof(float) * 12 * (size_t)H.nalloc, M->stream));
     bind_fields(H.d32, H.mem32, H.nalloc);
-    if (H.tiled && (rc = make_tile_maps<float>(H.d32, H.tm32, M->err))) return rc;
+    const int64_t lim = M->opt.fused_min_nodes != 0 ? M->opt.fused_min_nodes : FUSED_MIN_NODES;
+    H.fused = lim > 0 && H.sh.n() >= lim;
+    if (H.fused && (rc = plan_fused(H.d32, M->opt.fused_tile_rows, H.fz, M->err))) return rc;
   }
   if (M->opt.ir_fixed_point && !M->d_fx) {
     const LevelHost& H = M->lv[M->finest];
@@ -206,24 +208,12 @@ LevelDev<double>& view<double>(hhg_mesh* M, int l) { return M->lv[l].d64; }
 template <>
 LevelDev<float>& view<float>(hhg_mesh* M, int l) { return M->lv[l].d32; }
 
-template <class T>
-const TileMaps& maps(hhg_mesh* M, int l);
-template <>
-const TileMaps& maps<double>(hhg_mesh* M, int l) { return M->lv[l].tm64; }
-template <>
-const TileMaps& maps<float>(hhg_mesh* M, int l) { return M->lv[l].tm32; }
-
-// Error word of the tiled kernels (the last slot of the scalar block).
+// Error word of the fused passes (the last slot of the scalar block).
 unsigned* err_word(hhg_mesh* M) { return reinterpret_cast<unsigned*>(M->d_scalars + 15); }
 
 template <class T>
 void enq_vel_sweep(hhg_mesh* M, int l, bool forward) {
-  for (int q = 0; q < 4; ++q) {
-    const int colour = forward ? q : 3 - q;
-    M->lv[l].tiled
-        ? launch_vel_colour_ru_tile<T>(maps<T>(M, l), view<T>(M, l), colour, M->lv[l].kz, err_word(M), M->stream)
-        : launch_vel_colour<T>(view<T>(M, l), colour, M->stream);
-  }
+  for (int q = 0; q < 4; ++q) launch_vel_colour<T>(view<T>(M, l), forward ? q : 3 - q, M->stream);
   M->launches += 4;
 }
 
@@ -239,18 +229,14 @@ void enq_pres_sweep(hhg_mesh* M, int l) {
 template <class T>
 void enq_vel_sweep_f(hhg_mesh* M, int l) {
   const LevelDev<T>& L = view<T>(M, l);
-  for (int q = 0; q < 4; ++q)
-    M->lv[l].tiled ? launch_vel_colour_tile<T>(maps<T>(M, l), L, q, M->lv[l].kz, err_word(M), M->stream)
-                   : launch_vel_colour_rhs<T>(L, q, M->stream);
+  for (int q = 0; q < 4; ++q) launch_vel_colour_rhs<T>(L, q, M->stream);
   M->launches += 4;
 }
 
 template <class T>
 void enq_pres_sweep_f(hhg_mesh* M, int l) {
   const LevelDev<T>& L = view<T>(M, l);
-  for (int q = 0; q < 4; ++q)
-    M->lv[l].tiled ? launch_pres_colour_tile<T>(maps<T>(M, l), L, q, M->lv[l].kz, err_word(M), M->stream)
-                   : launch_pres_colour_rhs<T>(L, q, M->stream);
+  for (int q = 0; q < 4; ++q) launch_pres_colour_rhs<T>(L, q, M->stream);
   M->launches += 4;
 }
 
@@ -263,27 +249,28 @@ void enq_pres_sweep_f(hhg_mesh* M, int l) {
 // pressure colours form B u - g at each node (every node is updated once).
 // The last velocity colour and the first pressure colour share a launch
 // (k_vel_pres_colour0): 10 launches per step.
+// The three colour-fused passes of an FP32 Uzawa step (hhg_fused.cu); kind
+// -1 runs all three.
+void enq_uzawa_fused(hhg_mesh* M, int l, int kind = -1) {
+  const long long polls = M->opt.wait_poll_limit > 0 ? M->opt.wait_poll_limit : FUSED_WAIT_POLLS;
+  for (int k = 0; k < 3; ++k)
+    if (kind < 0 || kind == k) {
+      launch_uzawa_pass(M->lv[l].fz, view<float>(M, l), k, err_word(M), polls, M->stream);
+      M->launches += 1;
+    }
+}
+
 template <class T>
 void enq_uzawa(hhg_mesh* M, int l) {
   const LevelDev<T>& L = view<T>(M, l);
-  const bool tiled = M->lv[l].tiled;
-  const TileMaps& tm = maps<T>(M, l);
-  const int kz = M->lv[l].kz;
-  unsigned* err = err_word(M);
   const bool ru = sizeof(T) != 4;
+  if (!ru && M->lv[l].fused) {
+    enq_uzawa_fused(M, l);
+    return;
+  }
   if (ru) {
     launch_vel_rhs<T>(L, M->stream);
     M->launches += 1;
-  }
-  if (tiled) {
-    for (int q = 0; q < 7; ++q) {
-      const int colour = q < 4 ? q : 6 - q;
-      ru ? launch_vel_colour_ru_tile<T>(tm, L, colour, kz, err, M->stream)
-         : launch_vel_colour_tile<T>(tm, L, colour, kz, err, M->stream);
-    }
-    for (int q = 0; q < 4; ++q) launch_pres_colour_tile<T>(tm, L, q, kz, err, M->stream);
-    M->launches += 11;
-    return;
   }
   // velocity colours 0 1 2 3 2 1, then backward colour 0 with pressure colour 0, then pressure 1 2 3
   for (int q = 0; q < 6; ++q) {
@@ -480,12 +467,24 @@ void enq_cycle32(hhg_mesh* M, bool fp64_update = false) {
   }
 }
 
-// Reads the error word copied with the scalar block: a tiled sweep whose
-// tensor copy did not complete in time leaves HHG_TILE_TIMEOUT there.
+// Reads the error word copied with the scalar block: a fused pass whose
+// tensor copy did not complete in time leaves HHG_TILE_TIMEOUT there (the
+// word is cleared for the next call; the level's fields are then
+// undefined), HHG_TILE_DRAIN_TIMEOUT if the CTA could not even wait for its
+// copies to land (the mesh is marked failed: every later call returns
+// HHG_ECUDA).
 int tile_status(hhg_mesh* M) {
+  if (M->broken) return fail(M, HHG_ECUDA, "a fused pass could not drain its tensor copies; destroy the mesh");
   const unsigned w = *reinterpret_cast<const unsigned*>(M->h_scalars + 15);
-  if (w == HHG_TILE_TIMEOUT) return fail(M, HHG_ECUDA, "a tiled colour sweep gave up waiting for its tensor copies");
-  return HHG_OK;
+  if (!w) return HHG_OK;
+  CK(cudaMemsetAsync(err_word(M), 0, sizeof(unsigned), M->stream));
+  CK(cudaStreamSynchronize(M->stream));
+  *reinterpret_cast<unsigned*>(M->h_scalars + 15) = 0;
+  if (w == HHG_TILE_DRAIN_TIMEOUT) {
+    M->broken = true;
+    return fail(M, HHG_ECUDA, "a fused pass could not drain its tensor copies; destroy the mesh");
+  }
+  return fail(M, HHG_ECUDA, "a fused colour pass gave up waiting for its tensor copies");
 }
 
 // After a fixed-point cycle whose update or residual check raised a flag
@@ -972,16 +971,8 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   }
   if ((rc = dalloc(M, (void**)&M->d_coarse, sizeof(double) * (size_t)std::max<int64_t>(1, coarse_scratch_doubles(M->coarse_sys)))))
     return bail(rc);
-  // colour sweeps on shared-memory tiles on the large levels
-  prepare_tiled();
-  for (int l = M->coarsest; l <= finest; ++l) {
-    LevelHost& H = M->lv[l];
-    const int64_t lim = o.tile_min_nodes != 0 ? o.tile_min_nodes : TILE_MIN_NODES;
-    H.tiled = lim > 0 && H.sh.n() >= lim;
-    // long runs of planes where the level streams from HBM, short ones (more CTAs) below
-    H.kz = H.sh.n() >= (int64_t)1 << 24 ? 16 : 4;
-    if (H.tiled && (rc = make_tile_maps<double>(H.d64, H.tm64, M->err))) return bail(rc);
-  }
+  // colour-fused FP32 passes on the large levels (planned when the FP32 fields are allocated)
+  prepare_fused();
   // cluster kernels (fused coarse levels, coarse solve)
   prepare_coarse_solve();
   {
@@ -1550,6 +1541,12 @@ static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op)
       case HHG_OP_CYCLE:
         if (level != M->finest) return fail(M, HHG_EINVAL, "a solver cycle is rooted at the finest level");
         precision ? enq_cycle32(M) : enq_cycle64(M);
+        break;
+      case HHG_OP_FUSED_PASS0:
+      case HHG_OP_FUSED_PASS1:
+      case HHG_OP_FUSED_PASS2:
+        if (!precision || !M->lv[level].fused) return fail(M, HHG_EINVAL, "the level has no fused FP32 passes");
+        enq_uzawa_fused(M, level, op - HHG_OP_FUSED_PASS0);
         break;
       default:
         return fail(M, HHG_EINVAL, "unknown op");

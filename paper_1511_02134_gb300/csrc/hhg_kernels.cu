@@ -12,6 +12,7 @@ namespace hhg {
 namespace {
 
 constexpr int CB = 128;  // colour kernels: packed (row, quarter-row slot) indices per block; planes per level (cbz)
+// (blocks of CB x cbz threads, cbz <= 4: the colour kernels are compiled for 4 CB threads per block)
 constexpr int FX = 64, FY = 4;  // full kernels
 
 template <class T>
@@ -72,7 +73,7 @@ __global__ void k_vel_rhs(LevelDev<T> L) {
 // Gauss-Seidel update of the velocity nodes of one colour.  SPEC: the
 // speculative node form of small levels (hhg_node_ops.cuh).
 template <class T, bool SPEC>
-__global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
+__global__ void __launch_bounds__(CB * 4) k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
@@ -80,7 +81,7 @@ __global__ void k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
 }
 
 template <class T, bool SPEC>
-__global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
+__global__ void __launch_bounds__(CB * 4) k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
@@ -97,7 +98,7 @@ __global__ void k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
 // RU: the velocity right-hand side is read from RU (FP64 path) instead of
 // being formed at the node.
 template <class T, bool RU, bool SPEC>
-__global__ void k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
+__global__ void __launch_bounds__(CB * 4) k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, 0, i, j, k)) return;
@@ -110,7 +111,7 @@ __global__ void k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
 }
 
 template <class T, bool SPEC>
-__global__ void k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
+__global__ void __launch_bounds__(CB * 4) k_pres_colour_rhs(LevelDev<T> L, int colour, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
@@ -128,7 +129,7 @@ __global__ void k_pres_rhs(LevelDev<T> L) {
 
 // Under-relaxed Gauss-Seidel on C for the pressure nodes of one colour.
 template <class T>
-__global__ void k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
+__global__ void __launch_bounds__(CB * 4) k_pres_colour(LevelDev<T> L, int colour, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;

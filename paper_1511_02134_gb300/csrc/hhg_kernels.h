@@ -22,37 +22,54 @@ template <class T> void launch_pres_colour_rhs(const LevelDev<T>& L, int colour,
 // Backward velocity colour 0 and pressure colour 0 in one launch (the
 // velocity right-hand side read from RU when ru, else formed at the node).
 template <class T> void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s);
-// The same colour sweeps on shared-memory tiles staged by tensor copies
-// (hhg_tiled.cu): f - B^T p at the node, stored RU, and B u - g at the node.
-// TileMaps holds the tensor maps of u_0, u_1, u_2, p of one level and
-// precision (make_tile_maps); kz is the run of planes per CTA.  A CTA whose
-// bounded wait for a copy runs out writes HHG_TILE_TIMEOUT to *err and stops.
-// prepare_tiled() sets the kernels' shared-memory limits (once per device).
+// Colour-fused FP32 Uzawa step (hhg_fused.cu): three passes over a level,
+// each a z-march of CTAs over (x, y) tiles with F colour phases per march
+// step on planes staged into a shared-memory ring by tensor copies:
+//   kind 0: velocity colours 0 1 2 3, (U, P) -> RU;
+//   kind 1: velocity colours 2 1, then velocity + pressure colour 0,
+//           (RU, P) -> (U, RP);
+//   kind 2: pressure colours 1 2 3, (U, RP) -> P.
+// TileMaps holds the tensor maps of the four staged input fields of one pass.
+// A CTA whose bounded wait for a copy runs out writes HHG_TILE_TIMEOUT to
+// *err and stops after its copies have landed (HHG_TILE_DRAIN_TIMEOUT if
+// even that bounded wait runs out).
 struct TileMaps {
   CUtensorMap m[4];
 };
 constexpr unsigned HHG_TILE_TIMEOUT = 0x7117u;
-template <class T> int make_tile_maps(const LevelDev<T>& L, TileMaps& out, std::string& err);
-template <class T>
-void launch_vel_colour_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
-                            cudaStream_t s);
-template <class T>
-void launch_vel_colour_ru_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
-                               cudaStream_t s);
-template <class T>
-void launch_pres_colour_tile(const TileMaps& tm, const LevelDev<T>& L, int colour, int kz, unsigned* err,
-                             cudaStream_t s);
-void prepare_tiled();
+constexpr unsigned HHG_TILE_DRAIN_TIMEOUT = 0x7118u;
+constexpr int FUSED_MAX_THREADS = 640;
+constexpr long long FUSED_WAIT_POLLS = 1ll << 20;  // default bound of one mbarrier wait
+// Default of hhg_options.fused_min_nodes: levels of at least this many
+// lattice nodes run the fused passes (they stream from HBM; smaller levels
+// sit in L2 and have too few tiles to fill the GPU).
+constexpr int64_t FUSED_MIN_NODES = (int64_t)1 << 24;
+struct FusedArgs {
+  int by, ty;      // staged rows (ty + 2 F) and the tile's rows
+  int fstride;     // floats between staged fields in shared memory
+  long long polls; // bound of one mbarrier wait
+  unsigned* err;   // error word
+  float* out_u[3]; // output velocity (kinds 0, 1)
+  float* out_p;    // output pressure (kinds 1, 2)
+};
+struct FusedPlan {
+  int ntx;                          // tiles in x (64 nodes each, the first 67)
+  int ty[3], by[3], nty[3];         // per kind: tile rows, staged rows, tiles in y
+  TileMaps maps[3];                 // per kind: maps of its input fields
+};
+int fused_tiles_x(int nx);
+// Tile heights (ty_override > 0 forces one) and tensor maps of a level's FP32
+// fields; call after the FP32 fields are allocated.
+int plan_fused(const LevelDev<float>& L, int ty_override, FusedPlan& P, std::string& err);
+void launch_uzawa_pass(const FusedPlan& P, const LevelDev<float>& L, int kind, unsigned* err, long long polls,
+                       cudaStream_t s);
+// Shared-memory limits of the pass kernels (once per device).
+void prepare_fused();
 // Default of hhg_options.spec_max_nodes: levels below 2^20 lattice nodes are
 // latency bound and use the speculative node form of the colour updates
 // (hhg_node_ops.cuh).  Measured on GB300: a level-5 FP32 Uzawa step 37.9 ->
 // 28.2 us, level 6 60 -> 49 us, while level 7 went 170 -> 191 us.
 constexpr int64_t SPEC_MAX_NODES = 1 << 20;
-// Default of hhg_options.tile_min_nodes: off.  Measured on GB300, the tile
-// kernels move the same bytes per colour launch as the grid kernels (the
-// own-node reads of f and the writes of u stay strided) and run 25% slower.
-constexpr int64_t TILE_MIN_NODES = -1;
-
 // Residual (RU, RP) = (F, G) - K (U, P); zero on nodes without unknowns.
 template <class T> void launch_residual(const LevelDev<T>& L, cudaStream_t s);
 

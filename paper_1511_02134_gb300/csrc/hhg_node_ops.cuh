@@ -67,29 +67,48 @@ __device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, const Node& n,
   node_vel_gs_v<SPEC>(L, n.c, u, inv6nuh);
 }
 
-// Regular-node velocity update with f - B^T p formed at the node.
+// New velocity of a regular node from its right-hand side f (3 values) and
+// f - B^T p formed at the node: the node's own old value does not enter.
 template <class T, class V>
-__device__ __forceinline__ void vel_rhs_regular(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T inv6nuh,
-                                                T reg[3]) {
+__device__ __forceinline__ void vel_regular_value(const LevelDev<T>& L, const T* f, const V* u, const V& p,
+                                                  T inv6nuh, T reg[3]) {
   T dv[3];
   div12_all(diff7v<T>(p), dv);
   const T s = -L.h2 * (T)(1.0 / 12.0);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) reg[d] = ((L.f[d][c] - s * dv[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
+  for (int d = 0; d < 3; ++d) reg[d] = ((f[d] - s * dv[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
 }
 
-// Velocity update of a boundary node (class rows) with f - B^T p formed at the node.
+// New velocity of a boundary node from its class row w.
 template <class T, class V>
-__device__ __forceinline__ void vel_rhs_irr(const LevelDev<T>& L, int64_t c, const V* u, const V& p) {
-  const T* w = class_row(L, c);
+__device__ __forceinline__ void vel_irr_value(const LevelDev<T>& L, const T* w, const T* f, const V* u, const V& p,
+                                              T out[3]) {
   T bt[3];
   row_BT_v(L, p, w, F_IRR, bt);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     T dg, of;
     irr_lap_parts_v<T>(u[d], w, dg, of);
-    L.u[d][c] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
+    out[d] = ((f[d] - bt[d]) - L.nuh * of) / (L.nuh * dg);
   }
+}
+
+// Regular-node velocity update with f - B^T p formed at the node.
+template <class T, class V>
+__device__ __forceinline__ void vel_rhs_regular(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T inv6nuh,
+                                                T reg[3]) {
+  const T f[3] = {L.f[0][c], L.f[1][c], L.f[2][c]};
+  vel_regular_value(L, f, u, p, inv6nuh, reg);
+}
+
+// Velocity update of a boundary node (class rows) with f - B^T p formed at the node.
+template <class T, class V>
+__device__ __forceinline__ void vel_rhs_irr(const LevelDev<T>& L, int64_t c, const V* u, const V& p) {
+  const T f[3] = {L.f[0][c], L.f[1][c], L.f[2][c]};
+  T out[3];
+  vel_irr_value(L, class_row(L, c), f, u, p, out);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) L.u[d][c] = out[d];
 }
 
 // Same update with the right-hand side f - B^T p formed at the node (p does
@@ -150,27 +169,40 @@ __device__ __forceinline__ void node_pres_gs(const LevelDev<T>& L, const Node& n
   }
 }
 
+// New pressure of a regular node from its right-hand side g, B u - g formed at
+// the node, and its old value pc.
+template <class T, class V>
+__device__ __forceinline__ T pres_regular_value(const LevelDev<T>& L, T g, const V* u, const V& p, T pc,
+                                                T omega_over_6c) {
+  const T d0 = div12(diff7v<T>(u[0]), 0);
+  const T d1 = div12(diff7v<T>(u[1]), 1);
+  const T d2 = div12(diff7v<T>(u[2]), 2);
+  const T rp = L.h2 * (T)(1.0 / 12.0) * ((d0 + d1) + d2) - g;
+  const T cp = L.c * ((T)6 * pc - nb6v(p));
+  return pc + omega_over_6c * (rp - cp);
+}
+
+// New pressure of a boundary node from its class row w.
+template <class T, class V>
+__device__ __forceinline__ T pres_irr_value(const LevelDev<T>& L, const T* w, T g, const V* u, const V& p, T pc) {
+  const T rp = row_B_v(L, u, w, F_IRR) - g;
+  T dg, of;
+  irr_lap_parts_v<T>(p, w, dg, of);
+  const T cp = L.c * (dg * pc + of);
+  return pc + L.omega * (rp - cp) / (L.c * dg);
+}
+
 // Regular-node pressure update with B u - g formed at the node.
 template <class T, class V>
 __device__ __forceinline__ T pres_rhs_regular(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T pc,
                                               T omega_over_6c) {
-  const T d0 = div12(diff7v<T>(u[0]), 0);
-  const T d1 = div12(diff7v<T>(u[1]), 1);
-  const T d2 = div12(diff7v<T>(u[2]), 2);
-  const T rp = L.h2 * (T)(1.0 / 12.0) * ((d0 + d1) + d2) - L.g[c];
-  const T cp = L.c * ((T)6 * pc - nb6v(p));
-  return pc + omega_over_6c * (rp - cp);
+  return pres_regular_value(L, L.g[c], u, p, pc, omega_over_6c);
 }
 
 // Pressure update of a boundary node (class rows) with B u - g formed at the node.
 template <class T, class V>
 __device__ __forceinline__ void pres_rhs_irr(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T pc) {
-  const T* w = class_row(L, c);
-  const T rp = row_B_v(L, u, w, F_IRR) - L.g[c];
-  T dg, of;
-  irr_lap_parts_v<T>(p, w, dg, of);
-  const T cp = L.c * (dg * pc + of);
-  L.p[c] = pc + L.omega * (rp - cp) / (L.c * dg);
+  L.p[c] = pres_irr_value(L, class_row(L, c), L.g[c], u, p, pc);
 }
 
 // Same update with B u - g formed at the node (u does not change during the

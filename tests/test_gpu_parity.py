@@ -121,20 +121,17 @@ def test_set_rhs(pkg, name, level):
 
 # ---- smoother pieces, transfers, coarse solve ---------------------------------------------
 
-KERNEL_FORMS = [(-1, 0, 0), (-1, -1, 1), (-1, -1, 2), (-1, -1, 4), (-1, 0, 4), (1, 0, 0)]
+KERNEL_FORMS = [(0, 0), (-1, 1), (-1, 2), (-1, 4), (0, 4)]
 
 
-@pytest.mark.parametrize("tiles,spec,cbz", KERNEL_FORMS)
+@pytest.mark.parametrize("spec,cbz", KERNEL_FORMS)
 @pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3)])
-def test_smoother_pieces(pkg, name, level, tiles, spec, cbz):
+def test_smoother_pieces(pkg, name, level, spec, cbz):
     """Smoother steps against the oracle, with the colour sweeps run by the
-    grid kernels (tiles = -1) in the speculative node form of small levels
-    (spec = 0, the default here) or the flags-first form of large levels
-    (spec = -1), with 1, 2 or 4 planes per colour block (cbz; 0 = the
-    level's default), and by the shared-memory tile kernels (tiles = 1:
-    every level tiled, ragged tiles included)."""
-    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), tile_min_nodes=tiles, spec_max_nodes=spec,
-                           colour_block_z=cbz)
+    grid kernels in the speculative node form of small levels (spec = 0, the
+    default here) or the flags-first form of large levels (spec = -1), with
+    1, 2 or 4 planes per colour block (cbz; 0 = the level's default)."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level), spec_max_nodes=spec, colour_block_z=cbz)
     L = H.levels[level]
     dims = mesh.dims()
     st = _random_state(H, level, 7)
@@ -192,16 +189,17 @@ def test_smoother_pieces(pkg, name, level, tiles, spec, cbz):
     assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP")), rp) < 1e-11
 
 
-@pytest.mark.parametrize("cbz", [1, 2])
+@pytest.mark.parametrize("cbz,fused", [(1, -1), (2, -1), (1, 1)])
 @pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
-def test_fp32_steps_match_oracle(pkg, name, level, cbz):
+def test_fp32_steps_match_oracle(pkg, name, level, cbz, fused):
     """Every FP32 kernel of the V-cycle against the FP64 oracle on the same
     seeded state (written into the FP32 hierarchy, i.e. rounded once):
     forward velocity sweep and pressure sweep with their right-hand sides
     formed at each node, whole Uzawa steps, residual, restriction,
-    prolongation and a whole V-cycle rooted at the finest level."""
+    prolongation and a whole V-cycle rooted at the finest level.  fused = 1
+    runs every level's Uzawa steps as the three colour-fused passes."""
     macro, mesh, H = _pair(pkg, name, level, coarsest=level - 2, coarse_minres_max=5, spec_max_nodes=-1,
-                           colour_block_z=cbz)
+                           colour_block_z=cbz, fused_min_nodes=fused)
     L = H.levels[level]
     dims = mesh.dims()
     st = _random_state(H, level, 13)
@@ -288,27 +286,75 @@ def test_level6_large_level_kernels_match_oracle(pkg):
     mesh.close()
 
 
+@pytest.mark.parametrize("rows", [0, 1, 3])
 @pytest.mark.parametrize("name,level", [("cube", 5), ("channel", 3), ("partial", 4)])
-def test_tiled_sweeps_match_grid_kernels(pkg, name, level):
-    """The shared-memory tile kernels evaluate the same per-node expressions
-    as the grid kernels: Uzawa steps agree to rounding in FP64 and FP32
-    (both read the same neighbour values; only the compiler's contraction
-    of the expressions into fused multiply-adds may differ)."""
+def test_fused_passes_match_grid_kernels_and_oracle(pkg, name, level, rows):
+    """The colour-fused FP32 passes (every level fused; rows = tile rows, 0 =
+    the per-level choice, 1 and 3 give many ragged tiles) evaluate the same
+    per-node expressions as the per-colour grid kernels: Uzawa steps agree to
+    FP32 rounding (only the compiler's contraction into fused multiply-adds
+    may differ) and with the FP64 oracle at TOL32; each pass alone moves its
+    fields as documented (pass 0 leaves U, P and writes RU)."""
     macro = macro_by_name(name)
     H = MG.build_hierarchy(macro, level, coarsest=level - 1)
+    L = H.levels[level]
+    dims_mesh = [pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=level - 1,
+                          fused_min_nodes=fz, fused_tile_rows=rows) for fz in (-1, 1)]
     st = _random_state(H, level, 17)
-    meshes = [pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=level - 1,
-                       tile_min_nodes=t) for t in (-1, 1)]
-    for prec, tol in ((0, 1e-14), (1, 1e-6)):
-        outs = []
-        for mesh in meshes:
-            _load(mesh, H, level, st, precision=prec)
-            mesh.level_op(level, "uzawa_step", precision=prec, count=2)
-            outs.append(_read_up(mesh, H, level, precision=prec))
-        assert rel_err(outs[1][0], outs[0][0]) < tol, prec
-        assert rel_err(outs[1][1], outs[0][1]) < tol, prec
-    for mesh in meshes:
+    outs = []
+    for mesh in dims_mesh:
+        _load(mesh, H, level, st, precision=1)
+        mesh.level_op(level, "uzawa_step", precision=1, count=2)
+        outs.append(_read_up(mesh, H, level, precision=1))
+    assert rel_err(outs[1][0], outs[0][0]) < 1e-6
+    assert rel_err(outs[1][1], outs[0][1]) < 1e-6
+    u, p, f, g = (a.copy() for a in st)
+    for _ in range(2):
+        MG.uzawa_step(H, level, u, p, f, g)
+    assert rel_err(outs[1][0], u) < TOL32 and rel_err(outs[1][1], p) < TOL32
+    # pass 0 alone: the forward velocity sweep lands in RU, U and P untouched
+    mesh = dims_mesh[1]
+    dims = mesh.dims()
+    _load(mesh, H, level, st, precision=1)
+    u0, p0 = _read_up(mesh, H, level, precision=1)
+    mesh.level_op(level, "fused_pass0", precision=1)
+    u, p, f, g = (a.copy() for a in st)
+    ru = np.stack([f[d] - L.BT[d] @ p for d in range(3)])
+    for d in range(3):
+        MG._gs_sweep(L.A, L.A_diag, u[d], ru[d], H.colours_u[level], (0, 1, 2, 3))
+    assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU", 1)), u) < TOL32
+    gu, gp = _read_up(mesh, H, level, precision=1)
+    assert np.array_equal(gu, u0) and np.array_equal(gp, p0)
+    for mesh in dims_mesh:
         mesh.close()
+
+
+def test_fused_pass_wait_timeout(pkg):
+    """A fused pass whose bounded mbarrier wait runs out (a poll limit of one
+    test, while its valid tensor copies are still in flight) reports
+    HHG_ECUDA without faulting: its CTAs wait for their copies to land and
+    return.  The error word is cleared: the next call on the same mesh that
+    runs no fused pass succeeds, and a mesh with the default limit still
+    matches the grid kernels."""
+    cube = W.unit_cube()
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, fused_min_nodes=1, wait_poll_limit=1)
+    H = MG.build_hierarchy(cube, 5, coarsest=4)
+    st = _random_state(H, 5, 31)
+    _load(mesh, H, 5, st, precision=1)
+    with pytest.raises(pkg.HHGError) as e:
+        mesh.level_op(5, "uzawa_step", precision=1)
+    assert e.value.code == -6 and "gave up waiting" in str(e.value)
+    mesh.level_op(5, "uzawa_step", precision=0)   # grid kernels: no stale error
+    good = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, fused_min_nodes=1)
+    ref = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, fused_min_nodes=-1)
+    outs = []
+    for m in (good, ref):
+        _load(m, H, 5, st, precision=1)
+        m.level_op(5, "uzawa_step", precision=1)
+        outs.append(_read_up(m, H, 5, precision=1))
+    assert rel_err(outs[0][0], outs[1][0]) < 1e-6 and rel_err(outs[0][1], outs[1][1]) < 1e-6
+    for m in (mesh, good, ref):
+        m.close()
 
 
 @pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
@@ -359,12 +405,12 @@ def test_coarse_solve(pkg, name, level, mx):
 
 # ---- cycles and solves ------------------------------------------------------------------------
 
-@pytest.mark.parametrize("tiles,spec,cbz", KERNEL_FORMS)
+@pytest.mark.parametrize("spec,cbz", KERNEL_FORMS)
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 3, 2, 5), ("cube", 5, 2, 5), ("channel", 2, 1, 200),
                                                     ("partial", 3, 1, 30)])
-def test_vcycle_iterates(pkg, name, level, coarsest, mx, tiles, spec, cbz):
-    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles,
-                           spec_max_nodes=spec, colour_block_z=cbz)
+def test_vcycle_iterates(pkg, name, level, coarsest, mx, spec, cbz):
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, spec_max_nodes=spec,
+                           colour_block_z=cbz)
     L = H.levels[level]
     st = _random_state(H, level, 9)
     _load(mesh, H, level, st)
@@ -406,15 +452,15 @@ def test_fp64_solve_matches_oracle(pkg, name, level, coarsest, mx):
         assert abs(np.dot(m, p[lat])) < 1e-12 * np.abs(p).max()
 
 
-@pytest.mark.parametrize("tiles", [0, 1])
+@pytest.mark.parametrize("fused", [0, 1])
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 5, 2, 5), ("channel", 3, 1, 200)])
-def test_fp32_ir_solve(pkg, name, level, coarsest, mx, tiles):
+def test_fp32_ir_solve(pkg, name, level, coarsest, mx, fused):
     """FP32 V-cycles inside FP64 refinement reach the FP64 tolerance, and the
     solution's error against the oracle (solved to 1e-13) is within 10x of
     the error the FP64 oracle itself makes when stopped at the same relative
     residual (plus a floor of 1e-9 for u, 1e-7 for p, relative to the field
     maxima).  The GPU FP64 solve is checked the same way."""
-    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, tile_min_nodes=tiles)
+    macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, fused_min_nodes=fused)
     L = H.levels[level]
     dims = mesh.dims()
     x = mesh.node_coords()
