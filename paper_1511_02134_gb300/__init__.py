@@ -51,7 +51,8 @@ class Options(ctypes.Structure):
                 ("team_blocks", ctypes.c_int32), ("fused_min_nodes", ctypes.c_int32),
                 ("ir_fixed_point", ctypes.c_int32), ("spec_max_nodes", ctypes.c_int32),
                 ("colour_block_z", ctypes.c_int32), ("resident_node_lists", ctypes.c_int32),
-                ("fused_tile_rows", ctypes.c_int32), ("wait_poll_limit", ctypes.c_int64)]
+                ("fused_tile_rows", ctypes.c_int32), ("wait_poll_limit", ctypes.c_int64),
+                ("fused_wait_test", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):

@@ -255,7 +255,8 @@ void enq_uzawa_fused(hhg_mesh* M, int l, int kind = -1) {
   const long long polls = M->opt.wait_poll_limit > 0 ? M->opt.wait_poll_limit : FUSED_WAIT_POLLS;
   for (int k = 0; k < 3; ++k)
     if (kind < 0 || kind == k) {
-      launch_uzawa_pass(M->lv[l].fz, view<float>(M, l), k, err_word(M), polls, M->stream);
+      launch_uzawa_pass(M->lv[l].fz, view<float>(M, l), k, err_word(M), polls, M->opt.fused_wait_test ? 16 : 0,
+                        M->stream);
       M->launches += 1;
     }
 }

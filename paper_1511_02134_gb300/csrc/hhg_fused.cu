@@ -111,7 +111,9 @@ __global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
   auto issue = [&](int zp) {  // padded plane zp into its slot (thread 0)
     const int s = zp % NS;
     fence_proxy_async_smem();
-    mbar_expect(&bar[s], slot_bytes);
+    // (a.extra_tx: tests announce more bytes than plane 0 delivers, so that
+    // the first wait runs out while the real copies land)
+    mbar_expect(&bar[s], slot_bytes + (zp == 0 ? (uint32_t)a.extra_tx : 0u));
 #pragma unroll
     for (int f = 0; f < 4; ++f) tma_load_4d(field(s, f), &tm.m[f], P0, 0, jb + 1, zp, &bar[s]);
   };
@@ -171,6 +173,7 @@ __global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
         // a copy did not land in time: report it, and let every copy still in
         // flight land before the CTA's shared memory is released
         atomicExch(a.err, (unsigned)HHG_TILE_TIMEOUT);
+        if (a.extra_tx && waited == 0) mbar_complete_tx(&bar[0], (uint32_t)a.extra_tx);
         bool drained = true;
         for (int w = waited; w < issued && drained; ++w)
           drained = mbar_wait(&bar[w % NS], (uint32_t)((w / NS) & 1), FUSED_DRAIN_POLLS);
@@ -352,13 +355,15 @@ int plan_fused(const LevelDev<float>& L, int ty_override, FusedPlan& P, std::str
 }
 
 template <int KIND>
-static void launch_pass(const FusedPlan& P, const LevelDev<float>& L, unsigned* err, long long polls, cudaStream_t s) {
+static void launch_pass(const FusedPlan& P, const LevelDev<float>& L, unsigned* err, long long polls, int extra_tx,
+                        cudaStream_t s) {
   constexpr int F = pass_phases<KIND>();
   FusedArgs a{};
   a.by = P.by[KIND];
   a.ty = P.ty[KIND];
   a.fstride = (int)pass_fstride(a.by);
   a.polls = polls;
+  a.extra_tx = extra_tx;
   a.err = err;
   for (int d = 0; d < 3; ++d) a.out_u[d] = KIND == 0 ? L.r[d] : L.u[d];
   a.out_p = KIND == 1 ? L.rp : L.p;
@@ -378,13 +383,13 @@ static void launch_pass(const FusedPlan& P, const LevelDev<float>& L, unsigned* 
 }
 
 void launch_uzawa_pass(const FusedPlan& P, const LevelDev<float>& L, int kind, unsigned* err, long long polls,
-                       cudaStream_t s) {
+                       int extra_tx, cudaStream_t s) {
   if (kind == 0)
-    launch_pass<0>(P, L, err, polls, s);
+    launch_pass<0>(P, L, err, polls, extra_tx, s);
   else if (kind == 1)
-    launch_pass<1>(P, L, err, polls, s);
+    launch_pass<1>(P, L, err, polls, extra_tx, s);
   else
-    launch_pass<2>(P, L, err, polls, s);
+    launch_pass<2>(P, L, err, polls, extra_tx, s);
 }
 
 void prepare_fused() {

@@ -48,6 +48,7 @@ struct FusedArgs {
   int by, ty;      // staged rows (ty + 2 F) and the tile's rows
   int fstride;     // floats between staged fields in shared memory
   long long polls; // bound of one mbarrier wait
+  int extra_tx;    // tests: bytes announced beyond what the first staged plane delivers
   unsigned* err;   // error word
   float* out_u[3]; // output velocity (kinds 0, 1)
   float* out_p;    // output pressure (kinds 1, 2)
@@ -62,7 +63,7 @@ int fused_tiles_x(int nx);
 // fields; call after the FP32 fields are allocated.
 int plan_fused(const LevelDev<float>& L, int ty_override, FusedPlan& P, std::string& err);
 void launch_uzawa_pass(const FusedPlan& P, const LevelDev<float>& L, int kind, unsigned* err, long long polls,
-                       cudaStream_t s);
+                       int extra_tx, cudaStream_t s);
 // Shared-memory limits of the pass kernels (once per device).
 void prepare_fused();
 // Default of hhg_options.spec_max_nodes: levels below 2^20 lattice nodes are

@@ -25,6 +25,12 @@ __device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
+// Counts `bytes` of the current phase's announced transaction as delivered
+// (used to withdraw bytes announced in excess).
+__device__ __forceinline__ void mbar_complete_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.complete_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+
 // Bounded wait for the phase with the given parity; false if it did not
 // complete within `polls` tests.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long polls) {

@@ -330,14 +330,16 @@ def test_fused_passes_match_grid_kernels_and_oracle(pkg, name, level, rows):
 
 
 def test_fused_pass_wait_timeout(pkg):
-    """A fused pass whose bounded mbarrier wait runs out (a poll limit of one
-    test, while its valid tensor copies are still in flight) reports
-    HHG_ECUDA without faulting: its CTAs wait for their copies to land and
-    return.  The error word is cleared: the next call on the same mesh that
-    runs no fused pass succeeds, and a mesh with the default limit still
-    matches the grid kernels."""
+    """A fused pass whose bounded mbarrier wait runs out reports HHG_ECUDA
+    without faulting.  The test option announces 16 bytes more than the first
+    staged plane delivers, so that wait cannot complete (1024 polls); the CTA
+    withdraws the excess, waits for its valid copies to land and returns.  The
+    error word is cleared: the next call on the same mesh that runs no fused
+    pass succeeds, and a mesh without the option still matches the grid
+    kernels."""
     cube = W.unit_cube()
-    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, fused_min_nodes=1, wait_poll_limit=1)
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, 5, fused_min_nodes=1, wait_poll_limit=1024,
+                    fused_wait_test=1)
     H = MG.build_hierarchy(cube, 5, coarsest=4)
     st = _random_state(H, 5, 31)
     _load(mesh, H, 5, st, precision=1)
