@@ -129,7 +129,10 @@ __global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
     for (; issued < 4 && issued <= last_zp; ++issued) issue(issued);
   issued = min(4, last_zp + 1);
 
-  // the node of phase q on march step s, and its centre data
+  // the node of phase q on march step s, and its centre data.  The loads
+  // depend on the node's indices only (never on loaded values), so a march
+  // step issues all of the next step's loads back to back and first uses
+  // them one step later.
   auto fetch = [&](int s, int q, Centre& cd) {
     cd.fl = 0;
     const int k = s - q;
@@ -140,17 +143,15 @@ __global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
     const int i = 4 * (P0 + pb) + rho - 1;
     if (i < 0 || i >= L.nx || i < x_lo - d || i >= x_hi + d) return;
     const int64_t c = pad_index(L.px, L.pxy, i, j, k);
-    const uint8_t fl = __ldg(L.flags + c);
     const int w = phase_work<KIND>(q);
-    if (!(fl & (w == 2 ? F_ACT : (w == 1 ? (F_ACT | F_VFREE) : F_VFREE)))) return;
-    cd.fl = fl;
     cd.c = c;
+    cd.fl = __ldg(L.flags + c);
     if (w != 2) {
 #pragma unroll
       for (int dd = 0; dd < 3; ++dd) cd.f[dd] = __ldg(L.f[dd] + c);
     }
     if (w != 0) cd.g = __ldg(L.g + c);
-    cd.cls = (fl & F_IRR) ? __ldg(L.cls + c) : (uint16_t)0;
+    cd.cls = __ldg(L.cls + c);
   };
 
   Centre cur[F], nxt[F];
@@ -185,7 +186,8 @@ __global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
 #pragma unroll
     for (int q = 0; q < F; ++q) {
       const Centre& cd = cur[q];
-      if (cd.fl) {
+      const int work = phase_work<KIND>(q);
+      if (cd.fl & (work == 2 ? F_ACT : (work == 1 ? (F_ACT | F_VFREE) : F_VFREE))) {
         const int k = s - q;
         const int rho = (phase_colour<KIND>(q) - j - k + 1) & 3;
         float* pl[3][4];
@@ -200,7 +202,6 @@ __global__ void __launch_bounds__(FUSED_MAX_THREADS, 1)
                              RingNb{{pl[0][2], pl[1][2], pl[2][2]}, {e[0], e[1], e[2]}}};
         const RingNb p{{pl[0][3], pl[1][3], pl[2][3]}, {e[0], e[1], e[2]}};
         const float* w = (cd.fl & F_IRR) ? L.wt + (int64_t)W_STRIDE * cd.cls : nullptr;
-        const int work = phase_work<KIND>(q);
         if (work != 2 && (cd.fl & F_VFREE)) {
           float nu[3];
           if (!(cd.fl & F_IRR))
