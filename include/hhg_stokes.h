@@ -96,7 +96,8 @@ typedef struct hhg_options {
   int32_t fused_min_nodes;   /* FP32 Uzawa steps on levels of at least this many lattice nodes
                                 run as three colour-fused passes (a z-march over (x, y) tiles
                                 staged into shared memory by tensor copies, several colour
-                                phases per pass); 0 = default (2^24), -1 = never */
+                                phases per pass); 0 = default (never: slower than the
+                                per-colour launches on GB300), -1 = never */
   int32_t ir_fixed_point;    /* FP32+IR mode: 1 (default) keeps the refined iterate in 64-bit
                                 fixed point (per-field power-of-two scale, updated in integer
                                 arithmetic) and evaluates the FP64 refinement residual's

@@ -40,10 +40,13 @@ constexpr unsigned HHG_TILE_TIMEOUT = 0x7117u;
 constexpr unsigned HHG_TILE_DRAIN_TIMEOUT = 0x7118u;
 constexpr int FUSED_MAX_THREADS = 640;
 constexpr long long FUSED_WAIT_POLLS = 1ll << 20;  // default bound of one mbarrier wait
-// Default of hhg_options.fused_min_nodes: levels of at least this many
-// lattice nodes run the fused passes (they stream from HBM; smaller levels
-// sit in L2 and have too few tiles to fill the GPU).
-constexpr int64_t FUSED_MIN_NODES = (int64_t)1 << 24;
+// Default of hhg_options.fused_min_nodes: never.  Measured on GB300 (cube,
+// FP32 Uzawa step): level 9 12.0 ms fused against 6.8 ms with the colour
+// launches, level 8 2.4 against 1.0 ms.  The passes move 1.1x their
+// algorithmic DRAM bytes but are bound on the SM side: one CTA per SM (its
+// plane ring fills the shared memory), a few hundred node updates per colour
+// phase between barriers, about 30 shared-memory loads per update.
+constexpr int64_t FUSED_MIN_NODES = -1;
 struct FusedArgs {
   int by, ty;      // staged rows (ty + 2 F) and the tile's rows
   int fstride;     // floats between staged fields in shared memory
