@@ -45,7 +45,7 @@ ORACLE_LEVEL = 5
 # few GB on the device: the fields are far larger than L2), scaled to the
 # bench level by its node count; None where no capture of the current kernel
 # exists.
-TRAFFIC_BYTES_PER_NODE = {}
+TRAFFIC_BYTES_PER_NODE = {"k_vel_colour_rhs": (296033536 + 43298560) / 257 ** 3}  # 19.99 B: 339.3 MB / 257^3
 
 
 def _peaks():

@@ -186,9 +186,12 @@ def uzawa_step(H: Hierarchy, l: int, u, p, f, g):
     return u, p
 
 
-def smoothing_steps(H: Hierarchy, l: int, pre: bool = True) -> int:
-    base = H.opt.nu_pre if pre else H.opt.nu_post
-    return base + H.opt.var_increment * (H.finest - l)
+def smoothing_steps(H: Hierarchy, l: int, pre: bool = True, root: int | None = None, nu: int | None = None) -> int:
+    """nu_l = nu + var_increment (root - l) on level l of a V_var(nu, nu) cycle
+    rooted at level `root` (default: the finest level, nu: the options' nu_pre
+    / nu_post); Sec. 3.5 for the solver cycle, Sec. 5 for the cycles of FMG."""
+    base = (H.opt.nu_pre if pre else H.opt.nu_post) if nu is None else nu
+    return base + H.opt.var_increment * ((H.finest if root is None else root) - l)
 
 
 # --- coarse grid ------------------------------------------------------------
@@ -219,8 +222,9 @@ def coarse_solve(H: Hierarchy, f, g, history=None):
 
 # --- cycle and solve ----------------------------------------------------------
 
-def vcycle(H: Hierarchy, l: int, u, p, f, g):
-    """One V_var cycle on level l, in place on (u, p)."""
+def vcycle(H: Hierarchy, l: int, u, p, f, g, root: int | None = None, nu: int | None = None):
+    """One V_var cycle on level l, in place on (u, p); smoothing counts as in
+    smoothing_steps (root defaults to the finest level)."""
     if l == H.coarsest:
         # correction from the residual equation (inside a cycle u = p = 0 here)
         ru, rp = H.levels[l].residual(u, p, f, g)
@@ -229,7 +233,7 @@ def vcycle(H: Hierarchy, l: int, u, p, f, g):
         p += cp
         return u, p
     L = H.levels[l]
-    for _ in range(smoothing_steps(H, l, True)):
+    for _ in range(smoothing_steps(H, l, True, root, nu)):
         uzawa_step(H, l, u, p, f, g)
     ru, rp = L.residual(u, p, f, g)
     H.count(l, "A", 1)
@@ -241,11 +245,11 @@ def vcycle(H: Hierarchy, l: int, u, p, f, g):
     gc = P.T @ rp
     uc = np.zeros((3, Lc.n_u))
     pc = np.zeros(Lc.n_p)
-    vcycle(H, l - 1, uc, pc, fc, gc)
+    vcycle(H, l - 1, uc, pc, fc, gc, root, nu)
     for d in range(3):
         u[d] += Pu @ uc[d]
     p += P @ pc
-    for _ in range(smoothing_steps(H, l, False)):
+    for _ in range(smoothing_steps(H, l, False, root, nu)):
         uzawa_step(H, l, u, p, f, g)
     return u, p
 
@@ -281,3 +285,49 @@ def solve(H: Hierarchy, f, g, u0=None, p0=None, tol: float = 1e-8, max_cycles: i
         if rel <= tol:
             break
     return SolveResult(u, p, cycles, hist, its)
+
+
+# --- full multigrid (Sec. 5) ------------------------------------------------------
+
+def fmg(H: Hierarchy, rhs: dict, dirichlet: dict, cycles: int = 1, nu: int = 2) -> SolveResult:
+    """Full multigrid with `cycles` V_var(nu, nu) cycles per level (Sec. 5,
+    Fig. "FMG": one cycle per level for "FMG V", two for "FMG 2V").
+
+    rhs[l] = (f_l, g_l): the right-hand side rediscretised on level l;
+    dirichlet[l]: (n_l, 3) nodal Dirichlet data of level l (None = 0).
+    Starting from zero (Sec. 5), the coarsest level is solved by the coarse
+    solver, and on every finer level l the iterate starts from the P1
+    interpolant of the coarser level's whole velocity (Dirichlet values
+    included) and pressure, followed by `cycles` V-cycles rooted at l with
+    nu + var_increment (l - k) smoothing steps on level k; the pressure is
+    projected to sum m p = 0 after each cycle on pure-Dirichlet meshes."""
+    c = H.coarsest
+    Lc = H.levels[c]
+    u = np.zeros((3, Lc.n_u))
+    p = np.zeros(Lc.n_p)
+    f, g = rhs[c]
+    vcycle(H, c, u, p, f, g)
+    p = Lc.project_pressure(p)
+    n_cycles = 0
+    for l in range(c + 1, H.finest + 1):
+        L, Lk = H.levels[l], H.levels[l - 1]
+        full = Lk.scatter(u, dirichlet.get(l - 1))
+        u = np.stack([(H.P[l] @ full[:, d])[L.free] for d in range(3)])
+        p = H.P[l] @ p
+        f, g = rhs[l]
+        for _ in range(cycles):
+            vcycle(H, l, u, p, f, g, root=l, nu=nu)
+            p = L.project_pressure(p)
+            n_cycles += 1
+    Lf = H.levels[H.finest]
+    f, g = rhs[H.finest]
+    r0 = Lf.norm(f, g)
+    rel = Lf.norm(*Lf.residual(u, p, f, g)) / r0 if r0 > 0 else 0.0
+    return SolveResult(u, p, n_cycles, [1.0, rel], [])
+
+
+def h_norm(L: StokesLevel, u, p) -> float:
+    """Mesh-dependent norm of Sec. 5: (||u||_2^2 + h^2 ||p||_2^2)^(1/2) over the
+    free velocity values and all pressure values of level L."""
+    h = L.mesh.h
+    return float(np.sqrt(np.sum(np.asarray(u) ** 2) + h * h * np.sum(np.asarray(p) ** 2)))

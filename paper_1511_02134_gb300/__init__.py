@@ -107,6 +107,7 @@ def load_library():
         "hhg_vcycle": (I32, [P, I32, P]),
         "hhg_solve": (I32, [P, D, I32, I32, P, P, P]),
         "hhg_get_solution": (I32, [P, P, P]),
+        "hhg_fmg_solve": (I32, [P, P, P, I32, I32, P, P, P]),
         "hhg_apply_operator": (I32, [P, I32, P, P, P, P]),
         "hhg_adjoint_gradient": (I32, [P, P, P, D, I32, I32, P, P]),
         "hhg_level_field": (I32, [P, I32, I32, I32, I32, P]),
@@ -294,6 +295,22 @@ class Mesh:
         st = _Stats()
         rc = self._lib.hhg_solve(self._h, tol, max_cycles, mode, _ptr(u_out), _ptr(p_out), ctypes.byref(st))
         self._check(rc, allow=(-5,))
+        return u_out, p_out, _stats(st)
+
+    def fmg_solve(self, f_nodal=None, u_dirichlet=None, cycles=1, nu=2, u_out=None, p_out=None,
+                  want_solution=True):
+        """Full multigrid with `cycles` V_var(nu, nu) cycles per level (hhg_fmg_solve);
+        returns (u, p, stats), u/p None when want_solution is False."""
+        n = self.num_nodes()
+        f = _as_f64(f_nodal, (n, 3))
+        d = _as_f64(u_dirichlet, (n, 3))
+        if want_solution and u_out is None:
+            u_out = np.zeros((n, 3))
+        if want_solution and p_out is None:
+            p_out = np.zeros(n)
+        st = _Stats()
+        self._check(self._lib.hhg_fmg_solve(self._h, _ptr(f), _ptr(d), cycles, nu, _ptr(u_out), _ptr(p_out),
+                                            ctypes.byref(st)))
         return u_out, p_out, _stats(st)
 
     def get_solution(self, u_out=None, p_out=None):

@@ -34,6 +34,12 @@ struct LevelHost {
   int64_t n_vel = 0, n_pres = 0;
   bool fused = false;  // FP32 Uzawa steps as the three colour-fused passes (hhg_fused.cu)
   FusedPlan fz{};
+  int64_t ndir = 0;                  // Dirichlet nodes of the level: lattice and padded indices, values
+  int64_t* d_dir_lat = nullptr;
+  int64_t* d_dir_pad = nullptr;
+  double* d_dir_val = nullptr;
+  int64_t nirr = 0;                  // F_IRR nodes of the level, (k << 42) | (j << 21) | i
+  int64_t* d_irr = nullptr;
   int32_t* d_list = nullptr;         // node lists of the cluster-resident cycle (ResidentCycle::lists)
   int32_t loff[RES_LISTS + 1] = {};  // their offsets
   double* mem64 = nullptr;
@@ -70,7 +76,7 @@ struct hhg_mesh {
   unsigned small_cluster[2] = {1, 8};  // CTAs of the fused team, FP64 / FP32
   std::vector<LevelHost> lv;
   uint8_t* d_mmask = nullptr;
-  int64_t ndir = 0;
+  int64_t ndir = 0;               // the finest level's Dirichlet list (aliases of lv[finest]'s)
   int64_t* d_dir_lat = nullptr;
   int64_t* d_dir_pad = nullptr;
   double* d_dir_val = nullptr;
@@ -81,7 +87,7 @@ struct hhg_mesh {
   unsigned long long* d_fxmax = nullptr;  // fixed-point state: FxState's mx, maxq and exp (12 words)
   FxIterate fx{};                          // fixed-point finest iterate (FP32+IR mode)
   int64_t* d_fx = nullptr;
-  int64_t* d_fx_irr = nullptr;  // F_IRR nodes of the finest level (FxState::irr)
+  int64_t* d_fx_irr = nullptr;  // F_IRR nodes of the finest level (FxState::irr; alias of lv[finest].d_irr)
   int64_t n_fx_irr = 0;
   unsigned long long* d_rhs_fx = nullptr;  // right-hand side quantization: maxima [0..8), shifts
   double* d_coarse = nullptr;  // coarse-solve scratch
@@ -97,6 +103,8 @@ struct hhg_mesh {
   bool broken = false;  // a fused pass could not drain its copies (tile_status)
   int64_t launches = 0;
   int64_t fx_recoveries = 0;  // fixed-point cycles redone in FP64 (fx_recover_if_flagged)
+  int vroot = -1;             // root level of the V-cycles being enqueued (-1: the finest)
+  int vnu = -1;               // their smoothing steps on the root level (-1: nu_pre / nu_post)
   int64_t device_bytes = 0;
   int64_t allocations = 0;  // cudaMalloc / cudaMallocHost calls made for this mesh, temporaries included
   std::string err;
@@ -290,9 +298,13 @@ void enq_coarse(hhg_mesh* M) {
   M->launches += 1;
 }
 
+// Smoothing steps on level l of a V_var cycle rooted at M->vroot (Sec. 3.5;
+// Sec. 5 for the cycles of FMG, rooted below the finest level).
 template <class T>
 int nu_steps(hhg_mesh* M, int l, bool pre) {
-  return (pre ? M->opt.nu_pre : M->opt.nu_post) + M->opt.var_increment * (M->finest - l);
+  const int base = M->vnu >= 0 ? M->vnu : (pre ? M->opt.nu_pre : M->opt.nu_post);
+  const int root = M->vroot >= 0 ? M->vroot : M->finest;
+  return base + M->opt.var_increment * (root - l);
 }
 
 template <class T>
@@ -676,20 +688,20 @@ void release(hhg_mesh* M) {
     cudaFree(H.d_wt64);
     cudaFree(H.d_wt32);
     cudaFree(H.d_list);
+    cudaFree(H.d_dir_lat);
+    cudaFree(H.d_dir_pad);
+    cudaFree(H.d_dir_val);
+    cudaFree(H.d_irr);
     cudaFree(H.mem64);
     cudaFree(H.mem32);
   }
   cudaFree(M->d_mmask);
-  cudaFree(M->d_dir_lat);
-  cudaFree(M->d_dir_pad);
-  cudaFree(M->d_dir_val);
   cudaFree(M->d_stage);
   cudaFree(M->d_partial);
   cudaFree(M->d_scalars);
   cudaFree(M->d_coarse);
   cudaFree(M->d_fx);
   cudaFree(M->d_fxmax);
-  cudaFree(M->d_fx_irr);
   cudaFree(M->d_rhs_fx);
   cudaFree(M->d_coarse_sys);
   cudaFree(M->d_backup);
@@ -866,50 +878,52 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     bind_fields(H.d64, H.mem64, H.nalloc);
     fill_coefs(M, H);
   }
-  // Dirichlet nodes of the finest level (compact list)
+  // Dirichlet nodes and boundary (F_IRR) nodes of every level (compact lists)
+  for (int l = M->coarsest; l <= finest; ++l) {
+    LevelHost& H = M->lv[l];
+    std::vector<int64_t> lat, pad, irr;
+    for (int64_t k = 0; k < H.sh.nz; ++k)
+      for (int64_t j = 0; j < H.sh.ny; ++j)
+        for (int64_t i = 0; i < H.sh.nx; ++i) {
+          const int64_t q = i + H.sh.nx * (j + H.sh.ny * k);
+          const uint8_t f = H.flags[q];
+          if ((f & F_DIR) && (f & F_ACT)) {
+            lat.push_back(q);
+            pad.push_back(pad_index(H.px, H.px * H.py, (int)i, (int)j, (int)k));
+          }
+          if (f & F_IRR) irr.push_back((k << 42) | (j << 21) | i);
+        }
+    H.ndir = (int64_t)lat.size();
+    if (H.ndir) {
+      if ((rc = dalloc(M, (void**)&H.d_dir_lat, sizeof(int64_t) * lat.size()))) return bail(rc);
+      if ((rc = dalloc(M, (void**)&H.d_dir_pad, sizeof(int64_t) * pad.size()))) return bail(rc);
+      if ((rc = dalloc(M, (void**)&H.d_dir_val, sizeof(double) * 3 * lat.size()))) return bail(rc);
+      cudaMemcpy(H.d_dir_lat, lat.data(), sizeof(int64_t) * lat.size(), cudaMemcpyHostToDevice);
+      cudaMemcpy(H.d_dir_pad, pad.data(), sizeof(int64_t) * pad.size(), cudaMemcpyHostToDevice);
+      cudaMemset(H.d_dir_val, 0, sizeof(double) * 3 * lat.size());
+    }
+    H.nirr = (int64_t)irr.size();
+    if ((rc = dalloc(M, (void**)&H.d_irr, sizeof(int64_t) * std::max<size_t>(irr.size(), 1)))) return bail(rc);
+    if (!irr.empty() &&
+        (e = cudaMemcpy(H.d_irr, irr.data(), sizeof(int64_t) * irr.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      M->err = std::string("set-up: ") + cudaGetErrorString(e);
+      return bail(HHG_ECUDA);
+    }
+  }
   {
     LevelHost& H = M->lv[finest];
-    std::vector<int64_t> lat, pad;
-    for (int k = 0; k < H.sh.nz; ++k)
-      for (int j = 0; j < H.sh.ny; ++j)
-        for (int i = 0; i < H.sh.nx; ++i) {
-          const int64_t q = i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k);
-          if ((H.flags[q] & F_DIR) && (H.flags[q] & F_ACT)) {
-            lat.push_back(q);
-            pad.push_back(pad_index(H.px, H.px * H.py, i, j, k));
-          }
-        }
-    M->ndir = (int64_t)lat.size();
-    if (M->ndir) {
-      if ((rc = dalloc(M, (void**)&M->d_dir_lat, sizeof(int64_t) * lat.size()))) return bail(rc);
-      if ((rc = dalloc(M, (void**)&M->d_dir_pad, sizeof(int64_t) * pad.size()))) return bail(rc);
-      if ((rc = dalloc(M, (void**)&M->d_dir_val, sizeof(double) * 3 * lat.size()))) return bail(rc);
-      cudaMemcpy(M->d_dir_lat, lat.data(), sizeof(int64_t) * lat.size(), cudaMemcpyHostToDevice);
-      cudaMemcpy(M->d_dir_pad, pad.data(), sizeof(int64_t) * pad.size(), cudaMemcpyHostToDevice);
-      cudaMemset(M->d_dir_val, 0, sizeof(double) * 3 * lat.size());
-    }
+    M->ndir = H.ndir;
+    M->d_dir_lat = H.d_dir_lat;
+    M->d_dir_pad = H.d_dir_pad;
+    M->d_dir_val = H.d_dir_val;
+    M->n_fx_irr = H.nirr;
+    M->d_fx_irr = H.d_irr;
     if ((rc = dalloc(M, (void**)&M->d_stage, sizeof(double) * 3 * (size_t)H.sh.n()))) return bail(rc);
   }
   if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * std::max(REDUCE_BLOCKS, IR_BLOCKS + IR_IRR_BLOCKS)))) return bail(rc);
   if ((rc = dalloc(M, (void**)&M->d_scalars, sizeof(double) * 16))) return bail(rc);
   cudaMemset(M->d_scalars, 0, sizeof(double) * 16);
   if ((rc = dalloc(M, (void**)&M->d_rhs_fx, sizeof(unsigned long long) * 10))) return bail(rc);
-  {
-    // boundary nodes of the finest level (right-hand side, refinement residual)
-    const LevelHost& H = M->lv[M->finest];
-    std::vector<int64_t> irr;
-    for (int64_t k = 0; k < H.sh.nz; ++k)
-      for (int64_t j = 0; j < H.sh.ny; ++j)
-        for (int64_t i = 0; i < H.sh.nx; ++i)
-          if (H.flags[i + H.sh.nx * (j + H.sh.ny * k)] & F_IRR) irr.push_back((k << 42) | (j << 21) | i);
-    M->n_fx_irr = (int64_t)irr.size();
-    if ((rc = dalloc(M, (void**)&M->d_fx_irr, sizeof(int64_t) * std::max<size_t>(irr.size(), 1)))) return bail(rc);
-    if (!irr.empty() && (e = cudaMemcpy(M->d_fx_irr, irr.data(), sizeof(int64_t) * irr.size(),
-                                         cudaMemcpyHostToDevice)) != cudaSuccess) {
-      M->err = std::string("set-up: ") + cudaGetErrorString(e);
-      return bail(HHG_ECUDA);
-    }
-  }
   if ((e = cudaMallocHost((void**)&M->h_scalars, sizeof(double) * 16)) != cudaSuccess) {
     M->err = cudaGetErrorString(e);
     return bail(HHG_ENOMEM);
@@ -1193,6 +1207,91 @@ int hhg_solve(hhg_mesh* M, double tol, int32_t max_cycles, int32_t mode, double*
   if (rc != HHG_OK && rc != HHG_EMAXIT) return rc;
   int rc2 = gather_solution(M, u_out, p_out);
   return rc2 ? rc2 : rc;
+}
+
+int hhg_fmg_solve(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet, int32_t cycles, int32_t nu,
+                  double* u_out, double* p_out, hhg_stats* stats) {
+  if (!M || cycles < 0 || nu < 0) return HHG_EINVAL;
+  CK(cudaSetDevice(M->device));
+  auto t0 = std::chrono::steady_clock::now();
+  const int64_t l0 = M->launches;
+  LevelHost& Fh = M->lv[M->finest];
+  LevelDev<double>& Lf = Fh.d64;
+  const int64_t n = Fh.sh.n();
+  for (int l = M->coarsest; l <= M->finest; ++l) {
+    launch_zero<double>(M->lv[l].d64, 0, M->stream);
+    launch_zero<double>(M->lv[l].d64, 2, M->stream);
+  }
+  // nodal data staged as hhg_set_rhs does: body force in RU, Dirichlet data in U
+  if (f_nodal) {
+    int rc = stage_in(M, f_nodal, 3 * n);
+    if (rc) return rc;
+    launch_scatter(Lf, M->d_stage, 3, Lf.r, F_ACT, M->stream);
+  }
+  if (u_dirichlet) {
+    int rc = stage_in(M, u_dirichlet, 3 * n);
+    if (rc) return rc;
+    launch_scatter(Lf, M->d_stage, 3, Lf.u, F_DIR, M->stream);
+  }
+  // right-hand side rediscretised on every level (Sec. 2.1 forms with the
+  // data at that level's nodes); the finest level's staged data, the source
+  // of the coarser levels', is quantized last
+  for (int l = M->coarsest; l <= M->finest; ++l) {
+    LevelHost& H = M->lv[l];
+    LevelDev<double>& L = H.d64;
+    if (l < M->finest) launch_inject(Lf, L, 1 << (M->finest - l), M->stream);
+    launch_dirichlet_gather(H.d_dir_pad, H.ndir, L, H.d_dir_val, M->stream);
+    launch_set_rhs(L, L.r, L.u, M->d_rhs_fx, reinterpret_cast<int*>(M->d_rhs_fx + 8), H.d_irr, H.nirr, M->stream);
+    if (!M->macro.has_outflow) launch_remove_mean_g(L, M->d_partial, M->d_scalars + 3, M->stream);
+    launch_zero<double>(L, 0, M->stream);
+    launch_zero<double>(L, 2, M->stream);
+    M->launches += (l < M->finest ? 1 : 0) + (H.ndir ? 1 : 0) + 4 + (H.nirr ? 1 : 0) +
+                   (M->macro.has_outflow ? 0 : 3);
+  }
+  M->launches += (f_nodal ? 1 : 0) + (u_dirichlet ? 1 : 0);
+  M->rhs_set = true;
+  double r2;
+  int rc = residual_norm2(M, 0, &r2);  // of the zero iterate: ||f~||
+  if (rc) return rc;
+  const double r0 = std::sqrt(r2);
+  // coarsest level: the coarse solver from zero; then, level by level, the P1
+  // interpolant of the coarser solution (its Dirichlet values included) and
+  // `cycles` V_var(nu, nu) cycles rooted at the level (Sec. 5)
+  M->vnu = nu;
+  M->vroot = M->coarsest;
+  enq_vcycle<double>(M, M->coarsest);
+  if (!M->macro.has_outflow) enq_project<double>(M, M->coarsest);
+  int ncyc = 0;
+  for (int l = M->coarsest + 1; l <= M->finest; ++l) {
+    LevelHost& C = M->lv[l - 1];
+    launch_dirichlet_scatter(C.d_dir_pad, C.ndir, C.d_dir_val, C.d64, M->stream);
+    launch_prolong_add<double>(M->lv[l].d64, C.d64, M->stream);
+    M->launches += (C.ndir ? 1 : 0) + 1;
+    M->vroot = l;
+    for (int c = 0; c < cycles; ++c, ++ncyc) {
+      enq_vcycle<double>(M, l);
+      if (!M->macro.has_outflow) enq_project<double>(M, l);
+    }
+  }
+  M->vroot = -1;
+  M->vnu = -1;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(M, e, "fmg");
+  rc = residual_norm2(M, 0, &r2);
+  if (rc) return rc;
+  hhg_stats s{};
+  s.cycles = ncyc;
+  s.status = HHG_OK;
+  s.r0 = r0;
+  s.rel_residual = r0 > 0 ? std::sqrt(r2) / r0 : 0.0;
+  s.history[0] = 1.0;
+  s.history[1] = s.rel_residual;
+  if (!std::isfinite(s.rel_residual)) s.status = HHG_EDIVERGED;
+  s.kernel_launches = M->launches - l0;
+  s.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = s;
+  if (s.status == HHG_EDIVERGED) return fail(M, HHG_EDIVERGED, "FMG diverged");
+  return gather_solution(M, u_out, p_out);
 }
 
 int hhg_get_solution(hhg_mesh* M, double* u_out, double* p_out) {

@@ -845,6 +845,36 @@ __global__ void k_dirichlet_gather(const int64_t* pad, int64_t ndir, const doubl
   val[3 * q + 2] = u2[c];
 }
 
+// Nodal data of a coarser level taken at its nodes from the finest level's
+// padded arrays (node (i, j, k) of the coarse level is node (s i, s j, s k) of
+// the finest): body force into RU on active nodes, Dirichlet data into U on
+// Dirichlet nodes, zero elsewhere (the layout hhg_set_rhs stages).
+__global__ void k_inject(LevelDev<double> Lf, LevelDev<double> Lc, int s) {
+  pdl_enter();
+  int i, j, k;
+  if (!full_node(Lc, i, j, k)) return;
+  const int64_t cc = pidx(Lc.px, Lc.pxy, i, j, k);
+  const int64_t cf = pidx(Lf.px, Lf.pxy, s * i, s * j, s * k);
+  const uint8_t fl = Lc.flags[cc];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    Lc.r[d][cc] = (fl & F_ACT) ? Lf.r[d][cf] : 0.0;
+    Lc.u[d][cc] = (fl & F_DIR) ? Lf.u[d][cf] : 0.0;
+  }
+}
+
+// U at the listed (padded) Dirichlet nodes = their values (3 per node).
+__global__ void k_dirichlet_scatter(const int64_t* pad, int64_t ndir, const double* val, double* u0, double* u1,
+                                    double* u2) {
+  pdl_enter();
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= ndir) return;
+  const int64_t c = pad[q];
+  u0[c] = val[3 * q + 0];
+  u1[c] = val[3 * q + 1];
+  u2[c] = val[3 * q + 2];
+}
+
 __global__ void k_scale(double* x, int64_t n, double a) {
   pdl_enter();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -1048,6 +1078,14 @@ void launch_dirichlet_gather(const int64_t* pad, int64_t ndir, const LevelDev<do
   launch_k(k_dirichlet_gather, (unsigned)((ndir + 255) / 256), 256, s, pad, ndir, L.u[0], L.u[1], L.u[2], val);
 }
 void launch_scale(double* x, int64_t n, double a, cudaStream_t s) { launch_k(k_scale, flat_blocks(n), 256, s, x, n, a); }
+void launch_inject(const LevelDev<double>& fine, const LevelDev<double>& coarse, int stride, cudaStream_t s) {
+  launch_k(k_inject, full_grid(coarse), dim3(FX, FY), s, fine, coarse, stride);
+}
+void launch_dirichlet_scatter(const int64_t* pad, int64_t ndir, const double* val, const LevelDev<double>& L,
+                              cudaStream_t s) {
+  if (ndir == 0) return;
+  launch_k(k_dirichlet_scatter, (unsigned)((ndir + 255) / 256), 256, s, pad, ndir, val, L.u[0], L.u[1], L.u[2]);
+}
 void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s) {
   launch_k(k_cast, flat_blocks(n), 256, s, src, dst, n);
 }

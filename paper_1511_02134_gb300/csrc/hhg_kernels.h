@@ -165,6 +165,13 @@ void launch_dirichlet_fill(const int64_t* idx, const double* val, int64_t ndir, 
 void launch_dirichlet_gather(const int64_t* pad, int64_t ndir, const LevelDev<double>& L, double* val,
                              cudaStream_t s);
 void launch_cast_field(const double* src, float* dst, int64_t n, cudaStream_t s);
+// Coarse level's RU (body force, active nodes) and U (Dirichlet data,
+// Dirichlet nodes) from the finest level's, node (i, j, k) taken from
+// (stride i, stride j, stride k) of the finest.
+void launch_inject(const LevelDev<double>& fine, const LevelDev<double>& coarse, int stride, cudaStream_t s);
+// U at the listed padded indices = val (3 per entry): the inverse of launch_dirichlet_gather.
+void launch_dirichlet_scatter(const int64_t* pad, int64_t ndir, const double* val, const LevelDev<double>& L,
+                              cudaStream_t s);
 void launch_scale(double* x, int64_t n, double a, cudaStream_t s);
 
 // Coarse-grid solver (hhg_coarse.cu): (U, P) += PMINRES correction of the
