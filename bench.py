@@ -7,7 +7,8 @@ multigrid V_var(3,3) from a zero initial guess.  One step = set the
 right-hand side from device-resident nodal inputs + solve to 1e-8 in the
 FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
-the level-7 cube (8,291,838 free DoFs) under "level7".
+the level-7 cube (8,291,838 free DoFs) under "level7".  "fmg" times full
+multigrid (Sec. 5) on the headline level, with its error ratio gamma.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload (the oracle cannot hold level 9); with
@@ -224,13 +225,20 @@ class LevelBench:
         return {"value": self.world * self.dofs * steps / (ms / 1e3), "unit": "DoF/s",
                 "h2d_bytes_per_step": int(2 * 3 * self.n * 8), "d2h_bytes_per_step": int(4 * self.n * 8)}
 
-    def error_vs_fp64(self):
-        """Difference of the FP32+IR solution (to 1e-8) from an FP64 solve to
-        1e-12 on the same device (the FP64 path matches the oracle's iterates
-        and solutions at the levels the oracle can hold), beside the
-        difference the plain FP64 solve stopped at the same 1e-8 shows: the
-        stopping rule, not the precision, sets the pressure error."""
+    def accuracy(self, fmg_reps=3):
+        """Errors and FMG, against an FP64 solve to 1e-12 on the same device (the
+        FP64 path matches the oracle's iterates and solutions at the levels the
+        oracle can hold):
+          * err_vs_oracle: the FP32+IR solution (to 1e-8) beside the plain FP64
+            solve stopped at the same 1e-8 -- the stopping rule, not the
+            precision, sets the pressure error;
+          * fmg: full multigrid with one and two V_var(2,2) cycles per level
+            (Sec. 5), device time, and gamma = ||I u - u~||_h / ||I u - u_h||_h
+            with the mesh-dependent norm of Sec. 5 (I: nodal interpolant of the
+            manufactured solution, u~ the FMG result, u_h the discrete solution)."""
         import torch
+
+        import workloads as W
         pkg = self.pkg
 
         def solve(mode, tol):
@@ -253,8 +261,42 @@ class LevelBench:
             out[name] = {"u": err(u, u_ref), "p": err(p, p_ref), "cycles": st.cycles,
                          "rel_residual": st.rel_residual}
             del u, p
+        # FMG and gamma_l
+        flags = torch.from_numpy(self.mesh.node_flags()).cuda()
+        vf = (flags & 2) > 0
+        act = (flags & 1) > 0
+        x = self.mesh.node_coords()
+        ip = torch.from_numpy(W.manufactured_pressure(x)).cuda()
+        del x
+        h = 1.0 / (1 << self.level)
+        iu = self.ud_dev
+
+        def hnorm2(u, p):
+            return float((iu[vf] - u[vf]).square().sum() + h * h * (ip[act] - p[act]).square().sum())
+
+        disc = hnorm2(u_ref, p_ref)
+        fmg = {"discretisation_error_h": disc ** 0.5}
+        for cycles, mode in ((1, pkg.MODE_FP64), (2, pkg.MODE_FP64), (1, pkg.MODE_FP32_IR), (2, pkg.MODE_FP32_IR)):
+            u = torch.empty_like(u_ref)
+            p = torch.empty_like(p_ref)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            best = None
+            for _ in range(fmg_reps):
+                torch.cuda.synchronize()
+                e0.record(self.stream)
+                _, _, st = self.mesh.fmg_solve(self.f_dev, self.ud_dev, cycles=cycles, nu=2, mode=mode, u_out=u,
+                                               p_out=p)
+                e1.record(self.stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            fmg[("V22" if cycles == 1 else "2V22") + ("_fp64" if mode == pkg.MODE_FP64 else "_fp32ir")] = {
+                "ms": best, "value": self.world * self.dofs / (best / 1e3), "unit": "DoF/s",
+                "gamma": (hnorm2(u, p) / disc) ** 0.5, "rel_residual": st.rel_residual, "cycles": st.cycles}
+            del u, p
+        out_fmg = fmg
         del u_ref, p_ref
-        return out
+        return out, out_fmg
 
     def close(self):
         self.mesh.close()
@@ -281,7 +323,7 @@ def run_gpu(args):
     head = LevelBench(pkg, args.level, stream, flush, world)
     res = head.pair(args.steps, args.warmup, steps64, clocks=ClockSampler(local))
     e2e = head.e2e(max(1, args.steps // 4))
-    err = head.error_vs_fp64()
+    err, fmg = head.accuracy()
     roofline = measure_roofline(head.mesh, args.level, stream, flush)
     dofs = head.dofs
     head.close()
@@ -307,7 +349,7 @@ def run_gpu(args):
                    "flushed (256 MB write) between timed steps", "parallelism": "replicas" if world > 1 else
                    "single GPU"},
         "cycles": res["cycles"], "fp64": res["fp64"], "speedup_fp32ir_vs_fp64": res["speedup_fp32ir_vs_fp64"],
-        "err_vs_oracle": err, "roofline": roofline, "clocks": res["clocks"], "e2e": e2e,
+        "err_vs_oracle": err, "fmg": fmg, "roofline": roofline, "clocks": res["clocks"], "e2e": e2e,
         "gpu_launches": res["launches"],
     }
     if extra:

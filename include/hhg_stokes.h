@@ -224,17 +224,20 @@ int hhg_solve(hhg_mesh* mesh, double tol, int32_t max_cycles, int32_t mode,
  * that level's nodes.  Starting from zero, the coarsest level is solved by
  * the coarse solver; on every finer level l the iterate starts from the P1
  * interpolant of level l-1's velocity (its Dirichlet values included) and
- * pressure and runs `cycles` FP64 V_var(nu, nu) cycles rooted at l
+ * pressure and runs `cycles` V_var(nu, nu) cycles rooted at l
  * (nu + var_increment (l - k) smoothing steps on level k), each followed by
  * the pressure-mean projection on meshes without outflow.  The paper's FMG
  * V_var(2,2) is cycles = 1, nu = 2, its "2V" variant cycles = 2.
+ *   mode: HHG_MODE_FP64, or HHG_MODE_FP32_IR (each cycle an FP32 correction
+ *   cycle on the level's FP64 residual, the update in FP64; the coarsest
+ *   level is solved in FP64 either way).
  *   f_nodal, u_dirichlet: (n, 3) or NULL (= 0), finest lattice order.
  *   u_out, p_out: as hhg_solve (may be NULL); stats (may be NULL): cycles =
  *   V-cycles run, rel_residual = ||K x - f~|| / ||f~|| of the result.
  * The finest iterate stays on the device: hhg_solve may continue from it.
  * Overwrites the right-hand sides and iterates of every level. */
 int hhg_fmg_solve(hhg_mesh* mesh, const double* f_nodal, const double* u_dirichlet, int32_t cycles, int32_t nu,
-                  double* u_out, double* p_out, hhg_stats* stats);
+                  int32_t mode, double* u_out, double* p_out, hhg_stats* stats);
 
 /* Current iterate as nodal fields (Dirichlet values included in u). */
 int hhg_get_solution(hhg_mesh* mesh, double* u_out, double* p_out);

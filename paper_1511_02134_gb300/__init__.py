@@ -107,7 +107,7 @@ def load_library():
         "hhg_vcycle": (I32, [P, I32, P]),
         "hhg_solve": (I32, [P, D, I32, I32, P, P, P]),
         "hhg_get_solution": (I32, [P, P, P]),
-        "hhg_fmg_solve": (I32, [P, P, P, I32, I32, P, P, P]),
+        "hhg_fmg_solve": (I32, [P, P, P, I32, I32, I32, P, P, P]),
         "hhg_apply_operator": (I32, [P, I32, P, P, P, P]),
         "hhg_adjoint_gradient": (I32, [P, P, P, D, I32, I32, P, P]),
         "hhg_level_field": (I32, [P, I32, I32, I32, I32, P]),
@@ -297,7 +297,7 @@ class Mesh:
         self._check(rc, allow=(-5,))
         return u_out, p_out, _stats(st)
 
-    def fmg_solve(self, f_nodal=None, u_dirichlet=None, cycles=1, nu=2, u_out=None, p_out=None,
+    def fmg_solve(self, f_nodal=None, u_dirichlet=None, cycles=1, nu=2, mode=MODE_FP64, u_out=None, p_out=None,
                   want_solution=True):
         """Full multigrid with `cycles` V_var(nu, nu) cycles per level (hhg_fmg_solve);
         returns (u, p, stats), u/p None when want_solution is False."""
@@ -309,7 +309,7 @@ class Mesh:
         if want_solution and p_out is None:
             p_out = np.zeros(n)
         st = _Stats()
-        self._check(self._lib.hhg_fmg_solve(self._h, _ptr(f), _ptr(d), cycles, nu, _ptr(u_out), _ptr(p_out),
+        self._check(self._lib.hhg_fmg_solve(self._h, _ptr(f), _ptr(d), cycles, nu, mode, _ptr(u_out), _ptr(p_out),
                                             ctypes.byref(st)))
         return u_out, p_out, _stats(st)
 

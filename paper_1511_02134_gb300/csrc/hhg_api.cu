@@ -1210,9 +1210,13 @@ int hhg_solve(hhg_mesh* M, double tol, int32_t max_cycles, int32_t mode, double*
 }
 
 int hhg_fmg_solve(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet, int32_t cycles, int32_t nu,
-                  double* u_out, double* p_out, hhg_stats* stats) {
-  if (!M || cycles < 0 || nu < 0) return HHG_EINVAL;
+                  int32_t mode, double* u_out, double* p_out, hhg_stats* stats) {
+  if (!M || cycles < 0 || nu < 0 || (mode != HHG_MODE_FP64 && mode != HHG_MODE_FP32_IR)) return HHG_EINVAL;
   CK(cudaSetDevice(M->device));
+  if (mode == HHG_MODE_FP32_IR) {
+    int rc = ensure32(M);
+    if (rc) return rc;
+  }
   auto t0 = std::chrono::steady_clock::now();
   const int64_t l0 = M->launches;
   LevelHost& Fh = M->lv[M->finest];
@@ -1268,8 +1272,18 @@ int hhg_fmg_solve(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet,
     launch_prolong_add<double>(M->lv[l].d64, C.d64, M->stream);
     M->launches += (C.ndir ? 1 : 0) + 1;
     M->vroot = l;
+    LevelHost& H = M->lv[l];
     for (int c = 0; c < cycles; ++c, ++ncyc) {
-      enq_vcycle<double>(M, l);
+      if (mode == HHG_MODE_FP64) {
+        enq_vcycle<double>(M, l);
+      } else {
+        // FP32 correction cycle from zero on the FP64 residual, FP64 update
+        launch_zero<float>(H.d32, 0, M->stream);
+        launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
+        enq_vcycle<float>(M, l);
+        launch_ir_update(H.d64, H.d32, M->stream);
+        M->launches += 3;
+      }
       if (!M->macro.has_outflow) enq_project<double>(M, l);
     }
   }
