@@ -8,7 +8,8 @@ right-hand side from device-resident nodal inputs + solve to 1e-8 in the
 FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
 the level-7 cube (8,291,838 free DoFs) under "level7".  "fmg" times full
-multigrid (Sec. 5) on the headline level, with its error ratio gamma.
+multigrid (Sec. 5) on the headline level, with its error ratio gamma;
+"channel_level6" times the obstacle channel (2.7e8 free DoFs) FP32+IR solve.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload (the oracle cannot hold level 9); with
@@ -328,6 +329,7 @@ def run_gpu(args):
     dofs = head.dofs
     head.close()
     del head
+    channel = channel_solve(pkg, args.channel_level, stream) if args.channel_level else None
     extra = None
     if args.extra_level and args.extra_level != args.level:
         lb = LevelBench(pkg, args.extra_level, stream, flush, world)
@@ -354,6 +356,8 @@ def run_gpu(args):
     }
     if extra:
         out[f"level{args.extra_level}"] = extra
+    if channel:
+        out[f"channel_level{args.channel_level}"] = channel
     if rank == 0:
         if not args.no_cpu:
             out["cpu_baseline"] = cpu
@@ -361,6 +365,39 @@ def run_gpu(args):
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def channel_solve(pkg, level, stream, reps=3):
+    """Obstacle channel (16 x 4 x 4 unit cubes, 6 seeded obstacles, inflow of
+    peak 1, do-nothing outflow; the stand-in for the sphere bed of Sec. 6) at
+    `level`, FP32+IR to 1e-8 from zero; coarsest level 1 with the
+    tolerance-driven coarse MINRES (relative 5e-3, at most 300 iterations,
+    Sec. 3.7).  Best of `reps` device-timed set_rhs + solve steps."""
+    import torch
+
+    import workloads as W
+    ch = W.obstacle_channel()
+    mesh = pkg.Mesh(ch.vertices, ch.tets, ch.bc_flags, level, coarsest_level=1, coarse_minres_max=300,
+                    coarse_minres_rtol=5e-3, stream=stream.cuda_stream)
+    x = mesh.node_coords()
+    ud = torch.from_numpy(W.channel_inflow(x)).cuda()
+    del x
+    dofs = mesh.free_dofs()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best, st = None, None
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        mesh.set_rhs(None, ud)
+        _, _, st = mesh.solve(tol=TOL, max_cycles=60, mode=pkg.MODE_FP32_IR, want_solution=False)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    mesh.close()
+    return {"free_dofs": dofs, "ms_per_step": best, "value": dofs / (best / 1e3), "unit": "DoF/s",
+            "cycles": st.cycles, "rel_residual": st.rel_residual, "status": st.status,
+            "config": "16x4x4 channel, 6 obstacle cubes, coarsest level 1, coarse MINRES 5e-3 / 300"}
 
 
 # ---- roofline of the dominant kernel ------------------------------------------------------------
@@ -506,6 +543,8 @@ def main():
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--extra-level", type=int, default=EXTRA_LEVEL,
                     help="second cube level reported beside the headline (0: none)")
+    ap.add_argument("--channel-level", type=int, default=6,
+                    help="obstacle channel level reported beside the headline (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--roofline-only", action="store_true",
