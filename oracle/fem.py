@@ -6,6 +6,9 @@ variational problem in Sec. 2.1 (bilinear forms a_1, b, c_l and linear forms
 f, g_l), with P1 hat functions phi_i whose gradients are constant per element:
 
   A[i,j]   = a_1(phi_j, phi_i) = nu * int grad phi_i . grad phi_j        (Laplace form)
+  A2[a][b][i,j] = a_2(phi_j e_b, phi_i e_a) = 2 nu int D(phi_j e_b) : D(phi_i e_a)
+           = nu int (delta_ab grad phi_i . grad phi_j + d_b phi_i d_a phi_j)   (D form,
+             D(u) = (grad u + grad u^T) / 2; expanding D : D gives the two terms)
   B_d[i,j] = b(phi_j e_d, phi_i) = - int phi_i  d_d phi_j                 (rows: pressure)
   C[i,j]   = c_l(phi_i, phi_j) = sum_T delta h_T^2 int_T grad phi_i . grad phi_j,
              h_T = |T|^(1/3), delta = 1/12                                 (Sec. 2.1)
@@ -39,6 +42,7 @@ class Operators:
     m: np.ndarray    # lumped mass
     G: list          # [G_0, G_1, G_2]
     w_out: np.ndarray  # (n, 3): int over outflow faces of phi_i * n  (outflow functional)
+    A2: list = None   # [[A2[a][b]]]: the D-form velocity blocks (row component a, column component b)
 
 
 def element_geometry(xyz: np.ndarray, tets: np.ndarray):
@@ -85,4 +89,10 @@ def assemble(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0) -> O
         for c in range(3):
             contrib = np.repeat((area / 3.0)[:, None] * mesh.outflow_normals[:, c][:, None], 3, axis=1)
             w[:, c] = np.bincount(mesh.outflow_tris.ravel(), weights=contrib.ravel(), minlength=n)
-    return Operators(A=A, B=B, C=C, M=M, m=m, G=G, w_out=w)
+    # D form: nu int (delta_ab grad phi_m . grad phi_n + d_b phi_m d_a phi_n), m test (row), n trial (column)
+    A2 = [[None] * 3 for _ in range(3)]
+    for a in range(3):
+        for b in range(3):
+            Kab = vol[:, None, None] * (grads[:, :, None, b] * grads[:, None, :, a])
+            A2[a][b] = _assemble(mesh.tets, nu * ((K if a == b else 0.0) + Kab), n)
+    return Operators(A=A, B=B, C=C, M=M, m=m, G=G, w_out=w, A2=A2)

@@ -11,7 +11,9 @@ Follows the paper's best solver (UMG, Tab. "settings" of Sec. 3.7):
     in-place update p_i <- p_i + omega (B u - g - C p)_i / C_ii;
   * variable V-cycle: nu_l = 3 + 2 (L - l) pre- and post-smoothing steps on
     level l (Sec. 3.5), residual, restriction, recursion, prolongation;
-  * coarsest level: block-preconditioned MINRES (oracle.krylov, Sec. 3.7);
+  * coarsest level: block-preconditioned MINRES (oracle.krylov, Sec. 3.7),
+    CG on the velocity block (per component for A_1, on the coupled A_2 in the
+    D form) and the lumped mass on the pressure;
   * outer loop: stop when ||K x_k - f~|| / ||K x_0 - f~|| <= eps (Sec. 3.6);
     pure-Dirichlet problems project the pressure to sum m_i p_i = 0 after
     every cycle (K (0, 1) = 0, so the residual is unaffected).
@@ -136,11 +138,11 @@ class Hierarchy:
 
 
 def build_hierarchy(macro, finest: int, coarsest: int = 2, nu: float = 1.0, delta: float = 1.0 / 12.0,
-                    opt: Options | None = None) -> Hierarchy:
+                    opt: Options | None = None, form: str = "laplace") -> Hierarchy:
     levels = {}
     for l in range(coarsest, finest + 1):
         mesh = refine(macro.vertices, macro.tets, macro.bc_flags, l, spacing=macro.spacing)
-        levels[l] = build_level(mesh, nu=nu, delta=delta)
+        levels[l] = build_level(mesh, nu=nu, delta=delta, form=form)
     H = Hierarchy(levels=levels, coarsest=coarsest, finest=finest, opt=opt or Options())
     for l in range(coarsest, finest + 1):
         L = levels[l]
@@ -167,10 +169,40 @@ def _gs_sweep(Amat, diag, x, rhs, colour_rows, order, relax=1.0):
     return x
 
 
+def _block_gs_sweep(L: StokesLevel, u, rhs, colour_rows, order):
+    """Colour-ordered block Gauss-Seidel on the D-form A2: for each colour,
+    the velocity of its nodes (3 components each) becomes
+    u_c += D_c^-1 (rhs - A2 u)_c, D_c the nodes' 3 x 3 diagonal blocks of A2
+    solved exactly.  Nodes of one colour are not coupled, so this equals a
+    node-by-node block Gauss-Seidel in colour order."""
+    for c in order:
+        rows = colour_rows[c]
+        if len(rows) == 0:
+            continue
+        r = (rhs - L.apply_A(u))[:, rows]                      # (3, nc)
+        delta = np.linalg.solve(L.A2_node[rows], r.T[:, :, None])[:, :, 0]
+        u[:, rows] += delta.T
+    return u
+
+
 def uzawa_step(H: Hierarchy, l: int, u, p, f, g):
-    """One inexact Uzawa smoothing step (Sec. 3.3) in place on (u, p)."""
+    """One inexact Uzawa smoothing step (Sec. 3.3) in place on (u, p).
+    Velocity: SHGS, a forward and a backward colour Gauss-Seidel sweep on A
+    with the right-hand side f - B^T p_k; in the D form (Sec. 2.1) on the
+    coupled A2 with the 3 x 3 node blocks solved exactly (for the Laplace
+    form these blocks are diagonal and the sweep is the component-wise one)."""
     L = H.levels[l]
     cu = H.colours_u[l]
+    if L.form == "D":
+        H.count(l, "A", 2)
+        H.count(l, "B", 2)
+        H.count(l, "C", 1)
+        rhs = np.stack([f[d] - L.BT[d] @ p for d in range(3)])
+        _block_gs_sweep(L, u, rhs, cu, (0, 1, 2, 3))
+        _block_gs_sweep(L, u, rhs, cu, (3, 2, 1, 0))
+        rhs_p = sum(L.B[d] @ u[d] for d in range(3)) - g
+        _gs_sweep(L.C, L.C_diag, p, rhs_p, H.colours_p[l], (0, 1, 2, 3), relax=H.opt.omega)
+        return u, p
     # operator applications in the counting of Sec. 4.2: the SHGS sweep pair
     # applies A twice, B^T p and B u are one B application each, the
     # pressure sweep applies C once
@@ -212,7 +244,10 @@ def coarse_solve(H: Hierarchy, f, g, history=None):
 
     def apply_Pinv(x):
         u, p = split(x)
-        zu = np.stack([krylov.cg(lambda v: L.A @ v, u[d], o.coarse_cg_max, o.coarse_cg_rtol) for d in range(3)])
+        if L.form == "D":
+            zu = krylov.cg(lambda v: L.A2 @ v, u.ravel(), o.coarse_cg_max, o.coarse_cg_rtol)
+        else:
+            zu = np.stack([krylov.cg(lambda v: L.A @ v, u[d], o.coarse_cg_max, o.coarse_cg_rtol) for d in range(3)])
         return np.concatenate([zu.ravel(), p / L.m])
 
     b = np.concatenate([f.ravel(), g])

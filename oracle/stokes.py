@@ -1,7 +1,8 @@
 """Oracle: the discrete Stokes system on one level (test infrastructure).
 
 Builds the block system of Sec. 3 (the linear system with matrix
-K = [A B^T; B -C] and right-hand side (f, g)) from the assembled operators of
+K = [A B^T; B -C] and right-hand side (f, g); A = A_1 per component in the
+Laplace form, the coupled A_2 in the D form, Sec. 2.1) from the assembled operators of
 oracle.fem, with the Dirichlet velocity nodes eliminated (Sec. 2.1: the
 velocity space carries the boundary condition, the pressure is free at every
 node).  Vectors are kept as u: (3, n_u) over the free velocity nodes and
@@ -41,6 +42,9 @@ class StokesLevel:
     C_diag: np.ndarray
     m: np.ndarray           # lumped pressure mass
     pure_dirichlet: bool
+    form: str = "laplace"   # "laplace" (a_1) or "D" (a_2, Sec. 2.1)
+    A2: sp.csr_matrix = None  # D form: the coupled velocity block over (u_0, u_1, u_2) of the free nodes
+    A2_node: np.ndarray = None  # D form: (n_u, 3, 3) diagonal node blocks of A2
 
     @property
     def n_u(self) -> int:
@@ -55,9 +59,16 @@ class StokesLevel:
         return 3 * self.n_u + self.n_p
 
     # --- the operator K and the residual (Sec. 3) --------------------------
+    def apply_A(self, u: np.ndarray) -> np.ndarray:
+        """The velocity block: A u_d per component (Laplace form) or A2 u (D form)."""
+        if self.form == "D":
+            return (self.A2 @ np.asarray(u).ravel()).reshape(3, self.n_u)
+        return np.stack([self.A @ u[d] for d in range(3)])
+
     def apply(self, u: np.ndarray, p: np.ndarray):
-        """K (u, p) = (A u_d + B_d^T p,  sum_d B_d u_d - C p)."""
-        ru = np.stack([self.A @ u[d] + self.BT[d] @ p for d in range(3)])
+        """K (u, p) = (A u + B^T p,  sum_d B_d u_d - C p)."""
+        au = self.apply_A(u)
+        ru = np.stack([au[d] + self.BT[d] @ p for d in range(3)])
         rp = sum(self.B[d] @ u[d] for d in range(3)) - self.C @ p
         return ru, rp
 
@@ -88,7 +99,11 @@ class StokesLevel:
             uD = np.asarray(u_dirichlet, float)
             for d in range(3):
                 vd = uD[self.dir, d]
-                fu[d] -= self.ops.A[self.free][:, self.dir] @ vd
+                if self.form == "D":
+                    for a in range(3):
+                        fu[a] -= self.ops.A2[a][d][self.free][:, self.dir] @ vd
+                else:
+                    fu[d] -= self.ops.A[self.free][:, self.dir] @ vd
                 g = g - self.ops.B[d][:, self.dir] @ vd
         if self.pure_dirichlet:
             g = g - g.mean()
@@ -103,27 +118,40 @@ class StokesLevel:
         return out
 
 
-def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0) -> StokesLevel:
+def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, form: str = "laplace") -> StokesLevel:
     ops = fem.assemble(mesh, nu=nu, delta=delta)
     free = np.where(mesh.free_velocity)[0]
     dirn = np.where(~mesh.free_velocity)[0]
     A = ops.A[free][:, free].tocsr()
     B = [ops.B[d][:, free].tocsr() for d in range(3)]
+    A2, A2_node = None, None
+    if form == "D":
+        A2 = sp.bmat([[ops.A2[a][b][free][:, free] for b in range(3)] for a in range(3)], format="csr")
+        A2_node = np.stack([np.stack([ops.A2[a][b].diagonal()[free] for b in range(3)], axis=1)
+                            for a in range(3)], axis=1)
+    elif form != "laplace":
+        raise ValueError(form)
     return StokesLevel(mesh=mesh, ops=ops, free=free, dir=dirn, A=A, A_diag=A.diagonal().copy(),
                        B=B, BT=[b.T.tocsr() for b in B], C=ops.C, C_diag=ops.C.diagonal().copy(),
-                       m=ops.m, pure_dirichlet=not mesh.has_outflow)
+                       m=ops.m, pure_dirichlet=not mesh.has_outflow, form=form, A2=A2, A2_node=A2_node)
 
 
-def build_from_macro(macro, level: int, nu: float = 1.0, delta: float = 1.0 / 12.0) -> StokesLevel:
+def build_from_macro(macro, level: int, nu: float = 1.0, delta: float = 1.0 / 12.0,
+                     form: str = "laplace") -> StokesLevel:
     mesh = refine(macro.vertices, macro.tets, macro.bc_flags, level, spacing=macro.spacing)
-    return build_level(mesh, nu=nu, delta=delta)
+    return build_level(mesh, nu=nu, delta=delta, form=form)
 
 
 def full_matrix(L: StokesLevel) -> sp.csr_matrix:
     """K as one sparse matrix, unknown order (u_0, u_1, u_2, p)."""
     Z = [[None] * 4 for _ in range(4)]
+    n = L.n_u
     for d in range(3):
-        Z[d][d] = L.A
+        if L.form == "D":
+            for e in range(3):
+                Z[d][e] = L.A2[d * n:(d + 1) * n, e * n:(e + 1) * n]
+        else:
+            Z[d][d] = L.A
         Z[d][3] = L.BT[d]
         Z[3][d] = L.B[d]
     Z[3][3] = -L.C
