@@ -4,6 +4,8 @@
 // Colour kernels update the nodes with (i + j + k) mod 4 == colour; these
 // are not coupled by the 15-point pattern of the operator, so one launch per
 // colour performs the Gauss-Seidel sweep in colour order.
+#include <type_traits>
+
 #include "hhg_kernels.h"
 #include "hhg_node_ops.cuh"
 
@@ -116,6 +118,123 @@ __global__ void __launch_bounds__(CB * 4) k_pres_colour_rhs(LevelDev<T> L, int c
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
   node_pres_gs_rhs<SPEC>(L, node_at(L.px, L.pxy, i, j, k), omega_over_6c);
+}
+
+// ---- FP32 colour kernels with two nodes per thread -------------------------------
+// On rows grouped by x mod 4, the nodes of one colour sit at consecutive
+// positions of one residue group.  A thread takes the two nodes at positions
+// 2p, 2p + 1 (8-byte aligned: row pitches are multiples of 16 entries), and
+// every neighbour pair it reads lies at two consecutive positions too; the
+// pairs of its y and z neighbours and of its x neighbours in the adjacent
+// residue groups are aligned, except the x - 1 pair of residue 0 and the
+// x + 1 pair of residue 3, read as two values.  Where both nodes take the
+// closed-form update (regular, with the unknown), the thread evaluates the
+// per-node expressions of hhg_node_ops.cuh on the pair (half the load
+// instructions, twice the bytes per load); otherwise each node runs the
+// per-node body.
+
+struct F2 {
+  float x, y;
+  __device__ __forceinline__ F2() {}
+  __device__ __forceinline__ F2(float s) : x(s), y(s) {}
+  __device__ __forceinline__ F2(float a, float b) : x(a), y(b) {}
+};
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ F2 operator*(F2 a, F2 b) { return F2(a.x * b.x, a.y * b.y); }
+
+// Pair view centred on the node pair at entry c (first node).
+struct PairNb {
+  const float* x;
+  int64_t c, dxm, dxp, px, pxy;
+  bool am, ap;  // the x - 1 / x + 1 pair is 8-byte aligned
+  __device__ __forceinline__ F2 operator()(int dx, int dy, int dz) const {
+    const int64_t e = c + (dx < 0 ? dxm : (dx > 0 ? dxp : 0)) + px * dy + pxy * dz;
+    if ((dx < 0 && !am) || (dx > 0 && !ap)) return F2(x[e], x[e + 1]);
+    const float2 v = *reinterpret_cast<const float2*>(x + e);
+    return F2(v.x, v.y);
+  }
+};
+
+__device__ __forceinline__ F2 load2(const float* x, int64_t c) {
+  const float2 v = *reinterpret_cast<const float2*>(x + c);
+  return F2(v.x, v.y);
+}
+__device__ __forceinline__ void store2(float* x, int64_t c, F2 v) {
+  *reinterpret_cast<float2*>(x + c) = make_float2(v.x, v.y);
+}
+
+// KIND 0: velocity colour with f - B^T p formed at the node; 1: pressure
+// colour with B u - g formed at the node; 2: velocity colour 0 then pressure
+// colour 0 (the last velocity and first pressure colour of a step).
+template <int KIND>
+__global__ void __launch_bounds__(CB * 4) k_colour_pair(LevelDev<float> L, int colour, float inv6nuh, float omc) {
+  pdl_enter();
+  const uint64_t t = (uint64_t)blockIdx.x * CB + threadIdx.x;
+  const int k = blockIdx.y * blockDim.z + threadIdx.z;
+  const uint64_t row = L.nq2 == 1 ? t : __umul64hi(t, L.nq2_mul);
+  if (row >= (uint64_t)L.ny || k >= L.nz) return;
+  const int j = (int)row;
+  const int pp = (int)(t - row * (uint64_t)L.nq2);
+  const int rho = (colour - j - k) & 3;             // i mod 4 of the colour's nodes in this row
+  const int i0 = 4 * (2 * pp - ((rho + 1) >> 2)) + rho;  // at padded position 2 pp
+  const int i1 = i0 + 4;
+  const bool in0 = i0 >= 0 && i0 < L.nx, in1 = i1 < L.nx;
+  if (!in0 && !in1) return;
+  const int r = (rho + 1) & 3;                       // residue of padded x = i + 1
+  const int64_t c0 = (int64_t)r * (L.px >> 2) + 2 * pp + L.px * (j + 1) + L.pxy * (k + 1);
+  const uint8_t fl0 = in0 ? L.flags[c0] : (uint8_t)0, fl1 = in1 ? L.flags[c0 + 1] : (uint8_t)0;
+  const uint8_t need = KIND == 1 ? F_ACT : (KIND == 2 ? (F_ACT | F_VFREE) : F_VFREE);
+  const bool fast = ((fl0 & need) == need) && ((fl1 & need) == need) && !((fl0 | fl1) & F_IRR);
+  if (!fast) {
+#pragma unroll 1
+    for (int q = 0; q < 2; ++q) {
+      const int i = q ? i1 : i0;
+      if (!(q ? in1 : in0)) continue;
+      const Node n = node_at(L.px, L.pxy, i, j, k);
+      if (KIND == 0) node_vel_gs_rhs<false>(L, n, inv6nuh);
+      if (KIND == 1) node_pres_gs_rhs<false>(L, n, omc);
+      if (KIND == 2) {
+        node_vel_gs_rhs<false>(L, n, inv6nuh);
+        node_pres_gs_rhs<false>(L, n, omc);
+      }
+    }
+    return;
+  }
+  const int64_t dxm = row_step_minus(i0 + 1, L.px), dxp = row_step_plus(i0 + 1, L.px);
+  const bool am = r != 0, ap = r != 3;
+  const PairNb u[3] = {PairNb{L.u[0], c0, dxm, dxp, L.px, L.pxy, am, ap},
+                       PairNb{L.u[1], c0, dxm, dxp, L.px, L.pxy, am, ap},
+                       PairNb{L.u[2], c0, dxm, dxp, L.px, L.pxy, am, ap}};
+  const PairNb p{L.p, c0, dxm, dxp, L.px, L.pxy, am, ap};
+  if (KIND != 1) {
+    // the closed-form velocity update (vel_regular_value) on the pair
+    F2 dv[3];
+    div12_all(diff7v<F2>(p), dv);
+    const F2 s = F2(-L.h2 * (1.0f / 12.0f));
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const F2 v = ((load2(L.f[d], c0) - s * dv[d]) + F2(L.nuh) * nb6v(u[d])) * F2(inv6nuh);
+      store2(L.u[d], c0, v);
+    }
+  }
+  if (KIND != 0) {
+    // the closed-form pressure update (pres_regular_value) on the pair; the
+    // pair's own velocities are not among the neighbours read
+    const F2 d0 = div12(diff7v<F2>(u[0]), 0);
+    const F2 d1 = div12(diff7v<F2>(u[1]), 1);
+    const F2 d2 = div12(diff7v<F2>(u[2]), 2);
+    const F2 pc = load2(L.p, c0);
+    const F2 rp = F2(L.h2 * (1.0f / 12.0f)) * ((d0 + d1) + d2) - load2(L.g, c0);
+    const F2 cp = F2(L.c) * (F2(6.0f) * pc - nb6v(p));
+    store2(L.p, c0, pc + F2(omc) * (rp - cp));
+  }
+}
+
+template <class T>
+dim3 pair_grid(const LevelDev<T>& L) {
+  const int64_t slots = (int64_t)L.ny * L.nq2;
+  return dim3((unsigned)((slots + CB - 1) / CB), (unsigned)((L.nz + L.cbz - 1) / L.cbz), 1);
 }
 
 // RP = B U - G on pressure nodes.
@@ -927,6 +1046,12 @@ void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
 template <class T>
 void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.pairs) {
+      launch_k(k_colour_pair<0>, pair_grid(L), colour_block(L), s, L, colour, inv, 0.0f);
+      return;
+    }
+  }
   if (spec_level(L))
     launch_k(k_vel_colour_rhs<T, true>, colour_grid(L), colour_block(L), s, L, colour, inv);
   else
@@ -937,6 +1062,12 @@ void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
   const bool sp = spec_level(L);
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.pairs && !ru) {
+      launch_k(k_colour_pair<2>, pair_grid(L), colour_block(L), s, L, 0, inv, w);
+      return;
+    }
+  }
   if (ru && sp)
     launch_k(k_vel_pres_colour0<T, true, true>, colour_grid(L), colour_block(L), s, L, inv, w);
   else if (ru)
@@ -950,6 +1081,12 @@ void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
 template <class T>
 void launch_pres_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T w = (T)((double)L.omega / (6.0 * (double)L.c));
+  if constexpr (std::is_same<T, float>::value) {
+    if (L.pairs) {
+      launch_k(k_colour_pair<1>, pair_grid(L), colour_block(L), s, L, colour, 0.0f, w);
+      return;
+    }
+  }
   if (spec_level(L))
     launch_k(k_pres_colour_rhs<T, true>, colour_grid(L), colour_block(L), s, L, colour, w);
   else
