@@ -116,9 +116,10 @@ typedef struct hhg_options {
                                 pass (most nodes per staged row at the fewest CTA waves) */
   int64_t wait_poll_limit;   /* tests of one mbarrier wait of the fused passes before the pass
                                 gives up and reports HHG_ECUDA; 0 = default (2^20) */
-  int32_t colour_pairs;      /* FP32 colour kernels of the levels in the flags-first form (see
+  int32_t colour_pairs;      /* 1: FP32 colour kernels of the levels in the flags-first form (see
                                 spec_max_nodes) update two neighbouring nodes of the colour per
-                                thread with 8-byte loads: 0 = default (on), -1 = off */
+                                thread with 8-byte loads; 0 = default (off: slower on GB300,
+                                the kernels are bound by the loads in flight), -1 = off */
   int32_t fused_wait_test;   /* tests only: 1 makes each fused pass announce 16 bytes more than its
                                 first staged plane delivers, so that its first wait runs out (the
                                 pass then withdraws them, waits for its copies to land and reports

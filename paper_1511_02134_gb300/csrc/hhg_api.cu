@@ -169,8 +169,13 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     L.cbz = want == 1 || want == 2 || want == 4 ? want : (H.sh.n() >= ((int64_t)1 << 22) ? 2 : 1);
     L.nq = (int)((H.sh.nx + 3) / 4);
     L.nq_mul = L.nq == 1 ? 0 : ~0ull / (uint64_t)L.nq + 1;
-    // two nodes per thread in the FP32 colour kernels of the flags-first (large) levels
-    L.pairs = sizeof(T) == 4 && M->opt.colour_pairs >= 0 && !L.spec;
+    // two nodes per thread in the FP32 colour kernels of the flags-first (large)
+    // levels: an option, off by default (measured on GB300, level-9 FP32 Uzawa
+    // step 9.30 ms with pairs against 6.70 ms without: the colour kernels are
+    // bound by the loads in flight, and the pair kernels' 64 registers and the
+    // unaligned x-neighbour pairs of two residues in four cost more than the
+    // halved load count saves)
+    L.pairs = sizeof(T) == 4 && M->opt.colour_pairs > 0 && !L.spec;
     L.nq2 = L.nq / 2 + 1;
     L.nq2_mul = L.nq2 == 1 ? 0 : ~0ull / (uint64_t)L.nq2 + 1;
   };

@@ -189,7 +189,7 @@ def test_smoother_pieces(pkg, name, level, spec, cbz):
     assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP")), rp) < 1e-11
 
 
-@pytest.mark.parametrize("cbz,fused,pairs", [(1, -1, 0), (2, -1, 0), (2, -1, -1), (1, 1, 0)])
+@pytest.mark.parametrize("cbz,fused,pairs", [(1, -1, 0), (2, -1, 0), (2, -1, 1), (1, 1, 0)])
 @pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
 def test_fp32_steps_match_oracle(pkg, name, level, cbz, fused, pairs):
     """Every FP32 kernel of the V-cycle against the FP64 oracle on the same
@@ -197,8 +197,8 @@ def test_fp32_steps_match_oracle(pkg, name, level, cbz, fused, pairs):
     forward velocity sweep and pressure sweep with their right-hand sides
     formed at each node, whole Uzawa steps, residual, restriction,
     prolongation and a whole V-cycle rooted at the finest level.  fused = 1
-    runs every level's Uzawa steps as the three colour-fused passes; pairs = 0
-    (default) has the colour kernels update two nodes per thread, -1 one."""
+    runs every level's Uzawa steps as the three colour-fused passes; pairs = 1
+    has the colour kernels update two nodes per thread (0: the default, one)."""
     macro, mesh, H = _pair(pkg, name, level, coarsest=level - 2, coarse_minres_max=5, spec_max_nodes=-1,
                            colour_block_z=cbz, fused_min_nodes=fused, colour_pairs=pairs)
     L = H.levels[level]
