@@ -116,6 +116,11 @@ typedef struct hhg_options {
                                 pass (most nodes per staged row at the fewest CTA waves) */
   int64_t wait_poll_limit;   /* tests of one mbarrier wait of the fused passes before the pass
                                 gives up and reports HHG_ECUDA; 0 = default (2^20) */
+  int32_t operator_form;     /* velocity block of the discretisation (Sec. 2.1): 0 = Laplace form
+                                a_1 (default), 1 = D form a_2(u, v) = 2 nu <D(u), D(v)> (the
+                                velocity smoother then updates the three components of a node
+                                at once with its 3 x 3 block; the FP32+IR mode keeps its iterate
+                                and refinement residual in FP64) */
   int32_t colour_pairs;      /* 1: FP32 colour kernels of the levels in the flags-first form (see
                                 spec_max_nodes) update two neighbouring nodes of the colour per
                                 thread with 8-byte loads; 0 = default (off: slower on GB300,

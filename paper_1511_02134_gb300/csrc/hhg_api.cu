@@ -30,6 +30,8 @@ struct LevelHost {
   uint16_t* d_cls = nullptr;   // padded stencil class of boundary nodes
   double* d_wt64 = nullptr;    // class row tables
   float* d_wt32 = nullptr;
+  double* d_wt2_64 = nullptr;  // D form: velocity-block row tables (W2_STRIDE per class)
+  float* d_wt2_32 = nullptr;
   int n_classes = 0;
   int64_t n_vel = 0, n_pres = 0;
   bool fused = false;  // FP32 Uzawa steps as the three colour-fused passes (hhg_fused.cu)
@@ -183,6 +185,8 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
   set(H.d32);
   H.d64.wt = H.d_wt64;
   H.d32.wt = H.d_wt32;
+  H.d64.wt2 = H.d_wt2_64;
+  H.d32.wt2 = H.d_wt2_32;
 }
 
 int ensure32(hhg_mesh* M) {
@@ -696,6 +700,8 @@ void release(hhg_mesh* M) {
     cudaFree(H.d_cls);
     cudaFree(H.d_wt64);
     cudaFree(H.d_wt32);
+    cudaFree(H.d_wt2_64);
+    cudaFree(H.d_wt2_32);
     cudaFree(H.d_list);
     cudaFree(H.d_dir_lat);
     cudaFree(H.d_dir_pad);
@@ -790,6 +796,20 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     g_create_error = "invalid level or option";
     return HHG_EINVAL;
   }
+  if (o.operator_form != 0 && o.operator_form != 1) {
+    g_create_error = "operator_form must be 0 (Laplace) or 1 (D)";
+    return HHG_EINVAL;
+  }
+  if (o.operator_form == 1) {
+    // the cluster-resident and fused levels, the fused and pair colour
+    // kernels and the fixed-point refinement residual evaluate the Laplace
+    // form's closed-form stencils: the D form runs the per-level kernels with
+    // its class rows and the FP64 refinement residual
+    o.fuse_coarse_levels = 0;
+    o.ir_fixed_point = 0;
+    o.fused_min_nodes = -1;
+    o.colour_pairs = -1;
+  }
   hhg_mesh* M = new hhg_mesh();
   M->opt = o;
   M->finest = finest;
@@ -856,11 +876,25 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     {
       std::vector<uint16_t> cls;
       std::vector<double> table;
+      std::vector<uint32_t> patterns;
       std::string cerr;
-      stencil_classes(M->macro, l, H.flags.data(), cls, table, H.n_classes, cerr);
+      stencil_classes(M->macro, l, H.flags.data(), cls, table, H.n_classes, cerr, &patterns);
       if (!cerr.empty()) {
         M->err = cerr;
         return bail(HHG_EMESH);
+      }
+      if (o.operator_form == 1) {
+        std::vector<double> table2;
+        stencil_classes_d(patterns, table2);
+        std::vector<float> table2_32(table2.begin(), table2.end());
+        if ((rc = dalloc(M, (void**)&H.d_wt2_64, sizeof(double) * table2.size()))) return bail(rc);
+        if ((rc = dalloc(M, (void**)&H.d_wt2_32, sizeof(float) * table2.size()))) return bail(rc);
+        if (cudaMemcpy(H.d_wt2_64, table2.data(), sizeof(double) * table2.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(H.d_wt2_32, table2_32.data(), sizeof(float) * table2.size(), cudaMemcpyHostToDevice) !=
+                cudaSuccess) {
+          M->err = "upload of the D-form stencil tables failed";
+          return bail(HHG_ECUDA);
+        }
       }
       std::vector<uint16_t> pcls(H.nalloc, 0);
       for (int k = 0; k < H.sh.nz; ++k)
@@ -942,14 +976,16 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
   {
     LevelHost& H = M->lv[M->coarsest];
     std::vector<uint16_t> cls;
-    std::vector<double> table;
+    std::vector<double> table, table2;
+    std::vector<uint32_t> patterns;
     std::string cerr;
     int ncls = 0;
-    stencil_classes(M->macro, H.level, H.flags.data(), cls, table, ncls, cerr);
+    stencil_classes(M->macro, H.level, H.flags.data(), cls, table, ncls, cerr, &patterns);
+    if (o.operator_form == 1) stencil_classes_d(patterns, table2);
     CoarseMatrix cm;
     if (cerr.empty() &&
         (rc = assemble_coarse(H.sh, H.px, H.px * H.py, H.flags.data(), cls.data(), table.data(), H.d64.nuh, H.d64.c,
-                              H.d64.h2, H.d64.h3, cm, cerr))) {
+                              H.d64.h2, H.d64.h3, cm, cerr, o.operator_form == 1 ? table2.data() : nullptr))) {
       M->err = cerr;
       return bail(rc);
     }
@@ -979,6 +1015,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     CoarseSys& S = M->coarse_sys;
     S.nv = cm.nv;
     S.np = cm.np;
+    S.coupled = cm.coupled;
     S.kval = put_d(cm.kval);
     S.aval = put_d(cm.aval);
     S.mass = put_d(cm.mass);
@@ -1154,6 +1191,10 @@ int hhg_set_rhs(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet) {
   launch_dirichlet_gather(M->d_dir_pad, M->ndir, L, M->d_dir_val, M->stream);  // before U is quantized
   launch_set_rhs(L, L.r, L.u, M->d_rhs_fx, reinterpret_cast<int*>(M->d_rhs_fx + 8), M->d_fx_irr, M->n_fx_irr,
                  M->stream);
+  if (L.wt2) {
+    launch_lift_d(L, L.u, reinterpret_cast<const int*>(M->d_rhs_fx + 8), M->stream);
+    M->launches += 1;
+  }
   if (!M->macro.has_outflow) launch_remove_mean_g(L, M->d_partial, M->d_scalars + 3, M->stream);
   M->launches += (f_nodal ? 1 : 0) + (u_dirichlet ? 1 : 0) + 4 + (M->n_fx_irr ? 1 : 0) +
                  (M->macro.has_outflow ? 0 : 3) + (M->ndir ? 1 : 0);
@@ -1255,6 +1296,10 @@ int hhg_fmg_solve(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet,
     if (l < M->finest) launch_inject(Lf, L, 1 << (M->finest - l), M->stream);
     launch_dirichlet_gather(H.d_dir_pad, H.ndir, L, H.d_dir_val, M->stream);
     launch_set_rhs(L, L.r, L.u, M->d_rhs_fx, reinterpret_cast<int*>(M->d_rhs_fx + 8), H.d_irr, H.nirr, M->stream);
+    if (L.wt2) {
+      launch_lift_d(L, L.u, reinterpret_cast<const int*>(M->d_rhs_fx + 8), M->stream);
+      M->launches += 1;
+    }
     if (!M->macro.has_outflow) launch_remove_mean_g(L, M->d_partial, M->d_scalars + 3, M->stream);
     launch_zero<double>(L, 0, M->stream);
     launch_zero<double>(L, 2, M->stream);

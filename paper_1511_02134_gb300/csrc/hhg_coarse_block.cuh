@@ -127,6 +127,49 @@ __device__ inline int cg3(const Ctx& C, const double* b, double* x, double* cg, 
   return its;
 }
 
+// x = CG(A, b) from zero on the coupled D-form velocity block (3 nv rows of
+// A in CSR) over the team, same stopping rule; cg: 9 nv scratch.
+__device__ inline int cg_coupled(const Ctx& C, const double* b, double* x, double* cg, int max_it, double rtol) {
+  const int n = 3 * C.S.nv;
+  double* R = cg;
+  double* D = cg + n;
+  double* Q = cg + 2 * n;
+  double rr = 0.0;
+  for (int q = (int)C.T.rank(); q < n; q += (int)C.T.size()) {
+    x[q] = 0.0;
+    R[q] = b[q];
+    D[q] = b[q];
+    rr += b[q] * b[q];
+  }
+  rr = team_sum1(C.T, rr);
+  const double stop = rtol * rtol * rr;
+  int it = 0;
+  for (; it < max_it; ++it) {
+    if (rr <= stop || rr == 0.0) break;
+    double dq = 0.0;
+    for (int q = (int)C.T.rank(); q < n; q += (int)C.T.size()) {
+      const double aq = csr_row(C.S.aptr, C.S.acol, C.S.aval, q, D);
+      Q[q] = aq;
+      dq += D[q] * aq;
+    }
+    dq = team_sum1(C.T, dq);
+    if (dq == 0.0) break;
+    const double alpha = rr / dq;
+    double rn = 0.0;
+    for (int q = (int)C.T.rank(); q < n; q += (int)C.T.size()) {
+      x[q] += alpha * D[q];
+      R[q] -= alpha * Q[q];
+      rn += R[q] * R[q];
+    }
+    rn = team_sum1(C.T, rn);
+    const double beta = rn / rr;
+    for (int q = (int)C.T.rank(); q < n; q += (int)C.T.size()) D[q] = R[q] + beta * D[q];
+    C.T.sync();
+    rr = rn;
+  }
+  return it;
+}
+
 // ---- warp-level CG: the three velocity blocks are solved concurrently ------
 
 // Sum over the warp, the same value in every lane (shuffle tree, lane 0 broadcast).
@@ -191,8 +234,10 @@ __device__ inline int precond(const Ctx& C, const double* v, double* z, double* 
   int its = 0;
   const int nv = C.S.nv;
   const int warp = threadIdx.x >> 5;
-  const bool par = C.T.nblocks == 1 && blockDim.x >= 96 && nv <= WARP_CG_MAX_NV;
-  if (par) {
+  const bool par = !C.S.coupled && C.T.nblocks == 1 && blockDim.x >= 96 && nv <= WARP_CG_MAX_NV;
+  if (C.S.coupled) {
+    its = cg_coupled(C, v, z, cg, cg_max, cg_rtol);
+  } else if (par) {
     if (warp < 3) {
       const int n = cg_warp(C.S, v + warp * nv, z + warp * nv, cg + 3 * warp * nv, cg + (3 * warp + 1) * nv,
                             cg + (3 * warp + 2) * nv, cg_max, cg_rtol);

@@ -53,7 +53,7 @@ Rows rows_of(uint16_t cls, const double* table) {
 
 int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t* flags, const uint16_t* cls,
                     const double* table, double nuh, double c, double h2, double h3, CoarseMatrix& out,
-                    std::string& err) {
+                    std::string& err, const double* table2) {
   out = CoarseMatrix{};
   const int64_t n = sh.n();
   const int64_t nalloc = pxy * (sh.nz + 2);
@@ -104,10 +104,20 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
   for (int d = 0; d < 3; ++d)
     for (int32_t r = 0; r < nv; ++r) {
       const int64_t pc = out.vidx[r];
-      const Rows w = rows_of(cls[lat_of[pc]], table);
-      for (int o = 0; o < 15; ++o) {
-        const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
-        if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], nuh * w.lap[o]);
+      const uint16_t cl = cls[lat_of[pc]];
+      const Rows w = rows_of(cl, table);
+      if (table2) {
+        const double* w2 = table2 + (size_t)cl * W2_STRIDE;
+        for (int b = 0; b < 3; ++b)
+          for (int o = 0; o < 15; ++o) {
+            const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
+            if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)b * nv + iv[nb], nuh * w2[15 * (3 * d + b) + o]);
+          }
+      } else {
+        for (int o = 0; o < 15; ++o) {
+          const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
+          if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], nuh * w.lap[o]);
+        }
       }
       for (int o = 0; o < 15; ++o) {
         const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
@@ -139,9 +149,23 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
     out.kptr.push_back((int32_t)nnz);
     out.mass.push_back(h3 * w.lump);
   }
-  // scalar A
+  // A: the coupled D-form block (3 nv rows), or the scalar Laplacian
   nnz = 0;
   out.aptr.push_back(0);
+  if (table2) {
+    out.coupled = 1;
+    for (int d = 0; d < 3; ++d)
+      for (int32_t r = 0; r < nv; ++r) {
+        const double* w2 = table2 + (size_t)cls[lat_of[out.vidx[r]]] * W2_STRIDE;
+        for (int b = 0; b < 3; ++b)
+          for (int o = 0; o < 15; ++o) {
+            const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
+            if (iv[nb] >= 0) push(out.acol, out.aval, (int64_t)b * nv + iv[nb], nuh * w2[15 * (3 * d + b) + o]);
+          }
+        out.aptr.push_back((int32_t)nnz);
+      }
+    return HHG_OK;
+  }
   for (int32_t r = 0; r < nv; ++r) {
     const int64_t pc = out.vidx[r];
     const Rows w = rows_of(cls[lat_of[pc]], table);

@@ -48,6 +48,12 @@ HHG_HD int64_t row_step_plus(int64_t q, int64_t px) { return (q & 3) == 3 ? 1 - 
 // centre, +o then -o over the Kuhn directions e1, e2, e3, e1+e2, e2+e3,
 // e1+e3, e1+e2+e3), lumped mass.
 constexpr int W_LAP = 0, W_B = 15, W_BT = 60, W_M = 105, W_LUMP = 120, W_STRIDE = 128;
+// Rows of the D-operator velocity block (Sec. 2.1, a_2) of one class (unit
+// lattice spacing): block (a, b) = row component a, column component b at
+// [15 (3 a + b), +15) in the same offset order, then the inverse of the
+// 3 x 3 centre block (row-major) at W2_DINV.  Class 0 holds the rows of the
+// nodes with all 24 incident tetrahedra.
+constexpr int W2_DINV = 135, W2_STRIDE = 144;
 
 // Kuhn path index of the axis permutation (a, b, c), lexicographic order:
 // (0,1,2)=0 (0,2,1)=1 (1,0,2)=2 (1,2,0)=3 (2,0,1)=4 (2,1,0)=5

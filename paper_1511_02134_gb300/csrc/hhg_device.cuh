@@ -38,6 +38,8 @@ struct LevelDev {
   const uint8_t* mmask;  // macro cell masks
   const uint16_t* cls;   // padded stencil class of F_IRR nodes
   const T* wt;           // class table, W_STRIDE weights per class
+  const T* wt2;          // D form (Sec. 2.1, a_2): rows of the velocity block, W2_STRIDE per class
+                         // (class 0: full-star nodes); null in the Laplace form
   T nuh;                 // nu * h
   T c;                   // delta * h_T^2 * h
   T h2;                  // h^2
@@ -223,6 +225,38 @@ __device__ __forceinline__ void irr_B_scalar(const LevelDev<T>& L, const T* x, c
   for (int d = 0; d < 3; ++d) out[d] = L.h2 * st15v<T>(v, w + W_B + 15 * d);
 }
 
+// --- D form (a_2): the coupled velocity block from its class rows ------------
+
+template <class T>
+__device__ __forceinline__ const T* d_row(const LevelDev<T>& L, int64_t c) {
+  return L.wt2 + (int64_t)W2_STRIDE * L.cls[c];
+}
+
+// (A2 u)_a at the node for a = 0, 1, 2 (times nu h).
+template <class T, class V>
+__device__ __forceinline__ void row_A2_v(const LevelDev<T>& L, const V* u, const T* w2, T out[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    out[a] = L.nuh * ((st15v<T>(u[0], w2 + 15 * (3 * a)) + st15v<T>(u[1], w2 + 15 * (3 * a + 1))) +
+                      st15v<T>(u[2], w2 + 15 * (3 * a + 2)));
+}
+
+// Node-block Gauss-Seidel update: the node's three components solve
+// D (u_new) = r - (off-centre part of A2 u), D the 3 x 3 centre block.
+template <class T, class V>
+__device__ __forceinline__ void vel_block_value(const LevelDev<T>& L, const T* w2, const T r[3], const V* u,
+                                                T out[3]) {
+  T s[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    s[a] = r[a] - L.nuh * ((st14v<T>(u[0], w2 + 15 * (3 * a), (T)0) + st14v<T>(u[1], w2 + 15 * (3 * a + 1), (T)0)) +
+                           st14v<T>(u[2], w2 + 15 * (3 * a + 2), (T)0));
+  const T* di = w2 + W2_DINV;
+  const T inv = (T)1 / L.nuh;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[a] = inv * ((di[3 * a] * s[0] + di[3 * a + 1] * s[1]) + di[3 * a + 2] * s[2]);
+}
+
 // --- full rows of the Stokes operator ----------------------------------------
 // View forms take the class row w of the node (used when fl has F_IRR).
 
@@ -282,7 +316,10 @@ __device__ __forceinline__ const T* row_of(const LevelDev<T>& L, int64_t c, uint
 template <class T>
 __device__ __forceinline__ void row_A(const LevelDev<T>& L, const T* const* u, const Node& n, uint8_t fl, T out[3]) {
   const GNb<T> v[3] = {gnb(u[0], n, L.px, L.pxy), gnb(u[1], n, L.px, L.pxy), gnb(u[2], n, L.px, L.pxy)};
-  row_A_v(L, v, row_of(L, n.c, fl), fl, out);
+  if (L.wt2)
+    row_A2_v(L, v, d_row(L, n.c), out);
+  else
+    row_A_v(L, v, row_of(L, n.c, fl), fl, out);
 }
 
 template <class T>

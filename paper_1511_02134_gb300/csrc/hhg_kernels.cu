@@ -908,6 +908,29 @@ __global__ void k_set_rhs_irr(LevelDev<double> L, const int64_t* f0, const int64
   }
 }
 
+// D form: f_a += nu h (A1 u_D)_a - nu h (A2 u_D)_a on velocity nodes, from the
+// quantized staged u_D (the values launch_set_rhs lifted with).
+__global__ void k_lift_d(LevelDev<double> L, const int64_t* d0, const int64_t* d1, const int64_t* d2,
+                         const int* sh) {
+  pdl_enter();
+  int i, j, k;
+  if (!full_node(L, i, j, k)) return;
+  const Node n = node_at(L.px, L.pxy, i, j, k);
+  const uint8_t fl = L.flags[n.c];
+  if (!(fl & F_VFREE)) return;
+  const double isu = ldexp(1.0, -sh[1]);
+  double uv[3][15];
+  fx_gather15(d0, n, L.px, L.pxy, isu, uv[0]);
+  fx_gather15(d1, n, L.px, L.pxy, isu, uv[1]);
+  fx_gather15(d2, n, L.px, L.pxy, isu, uv[2]);
+  const SlotNb u[3] = {SlotNb{uv[0]}, SlotNb{uv[1]}, SlotNb{uv[2]}};
+  double a2[3], a1[3];
+  row_A2_v(L, u, d_row(L, n.c), a2);
+  row_A_v(L, u, row_of(L, n.c, fl), fl, a1);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) L.f[d][n.c] += a1[d] - a2[d];
+}
+
 // x += e (the FP64 refinement update).
 __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
   pdl_enter();
@@ -1153,6 +1176,10 @@ void launch_set_rhs(const LevelDev<double>& L, double* const* fnod, double* cons
   if (nirr > 0)
     launch_k(k_set_rhs_irr, IR_IRR_BLOCKS, REDUCE_THREADS, s, L, f[0], f[1], f[2], u[0], u[1], u[2],
              (const int*)sh, irr, nirr);
+}
+void launch_lift_d(const LevelDev<double>& L, double* const* uD, const int* sh, cudaStream_t s) {
+  launch_k(k_lift_d, full_grid(L), dim3(FX, FY), s, L, reinterpret_cast<const int64_t*>(uD[0]),
+           reinterpret_cast<const int64_t*>(uD[1]), reinterpret_cast<const int64_t*>(uD[2]), sh);
 }
 void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s) {
   launch_k(k_sum_g, REDUCE_BLOCKS, REDUCE_THREADS, s, L, partial);

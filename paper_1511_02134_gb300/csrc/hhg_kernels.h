@@ -101,6 +101,10 @@ template <class T> void launch_zero(const LevelDev<T>& L, int what, cudaStream_t
 // lattice coordinates as FxState::irr) use their class rows in FP64.
 void launch_set_rhs(const LevelDev<double>& L, double* const* fnod, double* const* uD, unsigned long long* mx,
                     int* sh, const int64_t* irr, int64_t nirr, cudaStream_t s);
+// D form: the Dirichlet lift of launch_set_rhs (its staged, quantized u_D
+// and shifts) used A_1 per component; this adds A_1 u_D and subtracts
+// A_2 u_D on the velocity nodes.
+void launch_lift_d(const LevelDev<double>& L, double* const* uD, const int* sh, cudaStream_t s);
 // G -= mean(G) over active nodes (two passes through partial/out).
 void launch_remove_mean_g(const LevelDev<double>& L, double* partial, double* out, cudaStream_t s);
 
@@ -179,6 +183,7 @@ void launch_scale(double* x, int64_t n, double a, cudaStream_t s);
 // CoarseSys is the device view of the assembled CoarseMatrix (hhg_lattice.h).
 struct CoarseSys {
   int32_t nv, np;         // velocity unknowns per component, pressure unknowns
+  int32_t coupled;        // D form: A is the coupled 3 nv x 3 nv velocity block
   const int32_t* vidx;    // padded lattice index of each velocity unknown's node
   const int32_t* pidx;    // padded lattice index of each pressure unknown's node
   const int32_t* kptr;    // K in CSR, 3 nv + np rows

@@ -337,15 +337,75 @@ void class_rows(uint32_t pattern, double* w) {
   }
 }
 
+// D-operator rows of one class: per active tetrahedron, with the centre the
+// local vertex m and neighbour n, a_2(phi_n e_b, phi_m e_a) =
+// nu int (delta_ab grad l_m . grad l_n + d_b l_m d_a l_n) = nu |T| (delta_ab
+// g_m . g_n + g_m[b] g_n[a]), |T| = 1/6 at unit spacing; then the centre
+// block's inverse.
+void class_rows_d(uint32_t pattern, double* w) {
+  std::fill(w, w + W2_STRIDE, 0.0);
+  int bit = 0;
+  for (int q = 0; q < 8; ++q) {
+    const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+    for (int s = 0; s < 6; ++s) {
+      const int m = corner_local(s, qx, qy, qz);
+      if (m < 0) continue;
+      const bool active = (pattern >> bit) & 1u;
+      ++bit;
+      if (!active) continue;
+      const int a[3] = {path_axis(s, 0), path_axis(s, 1), path_axis(s, 2)};
+      int idx[4];
+      int p[3] = {0, 0, 0};
+      for (int n = 0; n < 4; ++n) {
+        if (n > 0) p[a[n - 1]] += 1;
+        idx[n] = offset_index(p[0] - qx, p[1] - qy, p[2] - qz);
+      }
+      double g[4][3] = {};
+      g[0][a[0]] = -1;
+      g[1][a[0]] += 1;
+      g[1][a[1]] -= 1;
+      g[2][a[1]] += 1;
+      g[2][a[2]] -= 1;
+      g[3][a[2]] = 1;
+      for (int n = 0; n < 4; ++n) {
+        const double gg = g[m][0] * g[n][0] + g[m][1] * g[n][1] + g[m][2] * g[n][2];
+        for (int ra = 0; ra < 3; ++ra)
+          for (int cb = 0; cb < 3; ++cb)
+            w[15 * (3 * ra + cb) + idx[n]] += ((ra == cb ? gg : 0.0) + g[m][cb] * g[n][ra]) / 6.0;
+      }
+    }
+  }
+  // inverse of the centre block by cofactors (it is symmetric positive definite
+  // whenever the node has an active tetrahedron)
+  double D[3][3];
+  for (int ra = 0; ra < 3; ++ra)
+    for (int cb = 0; cb < 3; ++cb) D[ra][cb] = w[15 * (3 * ra + cb)];
+  const double det = D[0][0] * (D[1][1] * D[2][2] - D[1][2] * D[2][1]) -
+                     D[0][1] * (D[1][0] * D[2][2] - D[1][2] * D[2][0]) +
+                     D[0][2] * (D[1][0] * D[2][1] - D[1][1] * D[2][0]);
+  if (det == 0.0) return;
+  for (int ra = 0; ra < 3; ++ra)
+    for (int cb = 0; cb < 3; ++cb) {
+      const int r1 = (cb + 1) % 3, r2 = (cb + 2) % 3, c1 = (ra + 1) % 3, c2 = (ra + 2) % 3;
+      w[W2_DINV + 3 * ra + cb] = (D[r1][c1] * D[r2][c2] - D[r1][c2] * D[r2][c1]) / det;
+    }
+}
+
 }  // namespace
 
+void stencil_classes_d(const std::vector<uint32_t>& patterns, std::vector<double>& table2) {
+  table2.assign(patterns.size() * W2_STRIDE, 0.0);
+  for (size_t c = 0; c < patterns.size(); ++c) class_rows_d(patterns[c], table2.data() + c * W2_STRIDE);
+}
+
 void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
-                     std::vector<double>& table, int& n_classes, std::string& err) {
+                     std::vector<double>& table, int& n_classes, std::string& err, std::vector<uint32_t>* patterns) {
   const LevelShape sh = level_shape(m, level);
   cls.assign((size_t)sh.n(), 0);
   table.assign(W_STRIDE, 0.0);  // class 0: regular nodes (rows not stored)
   std::unordered_map<uint32_t, uint16_t> ids;
   n_classes = 0;
+  if (patterns) patterns->assign(1, FULL_STAR_PATTERN);
   for (int k = 0; k < sh.nz; ++k)
     for (int j = 0; j < sh.ny; ++j)
       for (int i = 0; i < sh.nx; ++i) {
@@ -371,6 +431,7 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
           it = ids.emplace(pattern, (uint16_t)n_classes).first;
           table.resize((size_t)(n_classes + 1) * W_STRIDE);
           class_rows(pattern, table.data() + (size_t)n_classes * W_STRIDE);
+          if (patterns) patterns->push_back(pattern);
         }
         cls[q] = it->second;
       }

@@ -63,8 +63,15 @@ int active_incident(const MacroLattice& m, int level, int i, int j, int k);
 // Offsets of the 15-point pattern: 0 = centre, 1..7 = +o, 8..14 = -o over the
 // Kuhn directions o = e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3.
 extern const int STENCIL_OFFSETS[15][3];
+// patterns (optional) receives the set of active incident tetrahedra of each
+// class (bit per (cell corner, Kuhn path) pair; class 0: all 24).
+constexpr uint32_t FULL_STAR_PATTERN = (1u << 24) - 1;
 void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
-                     std::vector<double>& table, int& n_classes, std::string& err);
+                     std::vector<double>& table, int& n_classes, std::string& err,
+                     std::vector<uint32_t>* patterns = nullptr);
+// D-operator row tables (W2_STRIDE doubles per class, hhg_common.h) of the
+// classes with the given patterns.
+void stencil_classes_d(const std::vector<uint32_t>& patterns, std::vector<double>& table2);
 
 }  // namespace hhg
 
@@ -81,6 +88,7 @@ namespace hhg {
 // Zero weights are not stored.
 struct CoarseMatrix {
   int32_t nv = 0, np = 0;
+  int32_t coupled = 0;  // D form: A is the coupled 3 nv x 3 nv velocity block (rows d nv + r)
   std::vector<int32_t> vidx, pidx;  // padded lattice index of each velocity / pressure unknown
   std::vector<int32_t> kptr, kcol;
   std::vector<double> kval;
@@ -92,8 +100,10 @@ struct CoarseMatrix {
 // flags and cls in lattice order (x fastest); table as from stencil_classes;
 // px, pxy the padded strides of the level's fields (ghost frame of one node).
 // Returns 0, or HHG_EINVAL when the matrix would not fit 32-bit indices.
+// table2 (D form, else null): the D-operator rows per class; the velocity
+// block of K and A are then the coupled a_2 rows.
 int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t* flags, const uint16_t* cls,
                     const double* table, double nuh, double c, double h2, double h3, CoarseMatrix& out,
-                    std::string& err);
+                    std::string& err, const double* table2 = nullptr);
 
 }  // namespace hhg

@@ -29,9 +29,19 @@ __device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, const Node& n
 // first.  Both store the same values.  u, p are neighbour views centred on
 // the node (global arrays, a shared-memory tile, or plane-pointer tables).
 
-// u_d <- u_d + (RU_d - (A u_d)) / A_ii  (one node of the current colour).
+// u_d <- u_d + (RU_d - (A u_d)) / A_ii  (one node of the current colour);
+// in the D form the node's three components at once with its 3 x 3 block.
 template <bool SPEC, class T, class V>
 __device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, const V* u, T inv6nuh) {
+  if (L.wt2) {
+    if (!(L.flags[c] & F_VFREE)) return;
+    const T r[3] = {L.r[0][c], L.r[1][c], L.r[2][c]};
+    T out[3];
+    vel_block_value(L, d_row(L, c), r, u, out);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.u[d][c] = out[d];
+    return;
+  }
   T reg[3];
   uint8_t fl;
   if (SPEC) {
@@ -116,6 +126,18 @@ __device__ __forceinline__ void vel_rhs_irr(const LevelDev<T>& L, int64_t c, con
 template <bool SPEC, class T, class V>
 __device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t c, const V* u, const V& p,
                                                   T inv6nuh) {
+  if (L.wt2) {
+    const uint8_t fl = L.flags[c];
+    if (!(fl & F_VFREE)) return;
+    T bt[3];
+    row_BT_v(L, p, row_of(L, c, fl), fl, bt);
+    const T r[3] = {L.f[0][c] - bt[0], L.f[1][c] - bt[1], L.f[2][c] - bt[2]};
+    T out[3];
+    vel_block_value(L, d_row(L, c), r, u, out);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.u[d][c] = out[d];
+    return;
+  }
   T reg[3];
   uint8_t fl;
   if (SPEC) {
@@ -244,7 +266,10 @@ __device__ __forceinline__ void node_residual_v(const LevelDev<T>& L, int64_t c,
   const T* w = row_of(L, c, fl);
   if (fl & F_VFREE) {
     T au[3], bt[3];
-    row_A_v(L, u, w, fl, au);
+    if (L.wt2)
+      row_A2_v(L, u, d_row(L, c), au);
+    else
+      row_A_v(L, u, w, fl, au);
     row_BT_v(L, p, w, fl, bt);
 #pragma unroll
     for (int d = 0; d < 3; ++d) r[d] = L.f[d][c] - au[d] - bt[d];
