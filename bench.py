@@ -9,7 +9,8 @@ FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
 the level-7 cube (8,291,838 free DoFs) under "level7".  "fmg" times full
 multigrid (Sec. 5) on the headline level, with its error ratio gamma;
-"channel_level6" times the obstacle channel (2.7e8 free DoFs) FP32+IR solve.
+"channel_level6" times the obstacle channel (2.7e8 free DoFs) FP32+IR solve;
+"dform_level7" the D-operator formulation beside the Laplace form.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
 bounded sample of the same workload (the oracle cannot hold level 9); with
@@ -330,6 +331,7 @@ def run_gpu(args):
     head.close()
     del head
     channel = channel_solve(pkg, args.channel_level, stream) if args.channel_level else None
+    dform = dform_solve(pkg, args.dform_level, stream) if args.dform_level else None
     extra = None
     if args.extra_level and args.extra_level != args.level:
         lb = LevelBench(pkg, args.extra_level, stream, flush, world)
@@ -358,6 +360,8 @@ def run_gpu(args):
         out[f"level{args.extra_level}"] = extra
     if channel:
         out[f"channel_level{args.channel_level}"] = channel
+    if dform:
+        out[f"dform_level{args.dform_level}"] = dform
     if rank == 0:
         if not args.no_cpu:
             out["cpu_baseline"] = cpu
@@ -398,6 +402,44 @@ def channel_solve(pkg, level, stream, reps=3):
     return {"free_dofs": dofs, "ms_per_step": best, "value": dofs / (best / 1e3), "unit": "DoF/s",
             "cycles": st.cycles, "rel_residual": st.rel_residual, "status": st.status,
             "config": "16x4x4 channel, 6 obstacle cubes, coarsest level 1, coarse MINRES 5e-3 / 300"}
+
+
+def dform_solve(pkg, level, stream, reps=3):
+    """The unit cube in the D-operator formulation (Sec. 2.1, a_2) beside the
+    Laplace form, FP64 and FP32+IR to 1e-8, manufactured solution: best of
+    `reps` device-timed set_rhs + solve steps each, and the D / Laplace time
+    ratio (the paper's serial ratio for UMG is 2.10 at its level 5, Tab.
+    "itertime_D_ser")."""
+    import torch
+
+    import workloads as W
+    cube = W.unit_cube()
+    out = {}
+    for form in (0, 1):
+        mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, level, operator_form=form,
+                        stream=stream.cuda_stream)
+        f, ud = _inputs(mesh)
+        f, ud = torch.from_numpy(f).cuda(), torch.from_numpy(ud).cuda()
+        dofs = mesh.free_dofs()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for mode, key in ((pkg.MODE_FP64, "fp64"), (pkg.MODE_FP32_IR, "fp32ir")):
+            best, st = None, None
+            for _ in range(reps + 1):
+                torch.cuda.synchronize()
+                e0.record(stream)
+                mesh.set_rhs(f, ud)
+                _, _, st = mesh.solve(tol=TOL, max_cycles=60, mode=mode, want_solution=False)
+                e1.record(stream)
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            out[("laplace_" if form == 0 else "dform_") + key] = {
+                "ms_per_step": best, "value": dofs / (best / 1e3), "unit": "DoF/s", "cycles": st.cycles}
+        mesh.close()
+    out["free_dofs"] = dofs
+    out["time_ratio_d_over_laplace"] = {k: out["dform_" + k]["ms_per_step"] / out["laplace_" + k]["ms_per_step"]
+                                        for k in ("fp64", "fp32ir")}
+    return out
 
 
 # ---- roofline of the dominant kernel ------------------------------------------------------------
@@ -545,6 +587,8 @@ def main():
                     help="second cube level reported beside the headline (0: none)")
     ap.add_argument("--channel-level", type=int, default=6,
                     help="obstacle channel level reported beside the headline (0: none)")
+    ap.add_argument("--dform-level", type=int, default=7,
+                    help="cube level of the D-operator comparison (0: none)")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--roofline-only", action="store_true",
