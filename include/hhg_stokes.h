@@ -65,7 +65,8 @@ extern "C" {
 /* Node flag bits returned by hhg_node_flags. */
 #define HHG_NODE_ACTIVE 1   /* carries a pressure unknown */
 #define HHG_NODE_VFREE 2    /* carries velocity unknowns */
-#define HHG_NODE_IRREG 4    /* near the boundary: some incident tetrahedra are missing */
+#define HHG_NODE_IRREG 4    /* near the boundary: some incident tetrahedra are missing (or the
+                               mesh is an affine lattice: every active node) */
 #define HHG_NODE_DIRICHLET 8
 #define HHG_NODE_OUTFLOW 16
 
@@ -154,10 +155,16 @@ void hhg_default_options(hhg_options* opt);
  * device (Sec. 2.1 refinement, Sec. 3.4 primitives).
  *   macro_vertices: nv x 3 doubles; macro_tets: nt x 4 int32 vertex ids
  *   (0-based); bc_flags: nt x 4 bytes (HHG_BC_*), may be NULL (all AUTO).
- *   Every tetrahedron must be a Kuhn tetrahedron of a cell of an
- *   axis-aligned lattice of spacing H, with its vertices listed along the
- *   path o, o+H e_a, o+H(e_a+e_b), o+H(1,1,1) or along the reverse path:
- *   the order defines the regular refinement.  Otherwise HHG_EMESH.
+ *   Every tetrahedron must be a Kuhn tetrahedron of a cell of a lattice,
+ *   with its vertices listed along the path o, o+H e_a, o+H(e_a+e_b),
+ *   o+H(1,1,1) or along the reverse path: the order defines the regular
+ *   refinement.  The lattice is axis-aligned with spacing H when the first
+ *   tetrahedron's edges v1-v0, v2-v1, v3-v2 are axis-aligned of one length;
+ *   otherwise it is the affine lattice spanned by those three edges (a
+ *   sheared or stretched cube, for example), on which every node takes the
+ *   stencil rows of its class (HHG_NODE_IRREG set on every active node)
+ *   and nodal arrays cover the bounding box in lattice coordinates.
+ *   Otherwise HHG_EMESH.
  *   finest_level >= coarsest_level >= 0, finest_level <= 12.
  *   opt may be NULL (defaults).  cuda_stream: a cudaStream_t or NULL.
  *   On success *out owns all device memory of the hierarchy. */
@@ -187,7 +194,7 @@ int hhg_num_nodes(const hhg_mesh* mesh, int32_t level, int64_t* n);
 int hhg_num_dofs(const hhg_mesh* mesh, int32_t level, int64_t* n_velocity_nodes,
                  int64_t* n_pressure_nodes);
 
-/* Node coordinates of `level`, (n, 3) doubles. */
+/* Node coordinates of `level`, (n, 3) doubles: origin + h basis (i, j, k). */
 int hhg_node_coords(const hhg_mesh* mesh, int32_t level, double* xyz);
 
 /* Node flags (HHG_NODE_* bits) of `level`, n bytes. */

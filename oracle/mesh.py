@@ -82,12 +82,15 @@ def _reference_simplices(N: int, lut: np.ndarray) -> np.ndarray:
     return simp
 
 
-def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0) -> RefinedMesh:
+def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0, basis=None) -> RefinedMesh:
     """Refine the macro mesh ``level`` times (N = 2**level intervals per macro edge).
 
     vertices: (nv, 3) integer-valued coordinates; tets: (nt, 4) vertex ids in
     refinement order; bc_flags: (nt, 4) per face opposite local vertex f,
-    0 = interior/Dirichlet-by-default, 1 = Dirichlet, 2 = do-nothing outflow.
+    0 = interior/Dirichlet-by-default, 1 = Dirichlet, 2 = do-nothing outflow;
+    basis (3, 3): lattice axes as columns when the macro mesh is the affine
+    image of a lattice (default: the coordinate axes) -- used only to derive
+    the lattice coordinates of the nodes (for the colouring).
     """
     V = np.asarray(vertices, dtype=np.float64)
     T = np.asarray(tets, dtype=np.int64)
@@ -161,8 +164,10 @@ def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0) -> Refine
                        on_dirichlet=on_dir, on_outflow=on_out & ~on_dir,
                        outflow_tris=out_tris, outflow_normals=out_normals)
     # lattice coordinates (only meaningful when the macro mesh lives on a lattice of spacing H)
-    origin = V.min(axis=0)
-    ijk_f = (xyz - origin[None, :]) / h
+    Binv = np.eye(3) if basis is None else np.linalg.inv(np.asarray(basis, float))
+    lat = xyz @ Binv.T
+    origin = lat.min(axis=0)
+    ijk_f = (lat - origin[None, :]) / h
     ijk = np.rint(ijk_f).astype(np.int64)
     if np.allclose(ijk_f, ijk, rtol=0, atol=1e-9):
         mesh.ijk = ijk

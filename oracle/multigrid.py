@@ -141,7 +141,8 @@ def build_hierarchy(macro, finest: int, coarsest: int = 2, nu: float = 1.0, delt
                     opt: Options | None = None, form: str = "laplace") -> Hierarchy:
     levels = {}
     for l in range(coarsest, finest + 1):
-        mesh = refine(macro.vertices, macro.tets, macro.bc_flags, l, spacing=macro.spacing)
+        mesh = refine(macro.vertices, macro.tets, macro.bc_flags, l, spacing=macro.spacing,
+                      basis=getattr(macro, "basis", None))
         levels[l] = build_level(mesh, nu=nu, delta=delta, form=form)
     H = Hierarchy(levels=levels, coarsest=coarsest, finest=finest, opt=opt or Options())
     for l in range(coarsest, finest + 1):

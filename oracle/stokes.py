@@ -138,7 +138,8 @@ def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, f
 
 def build_from_macro(macro, level: int, nu: float = 1.0, delta: float = 1.0 / 12.0,
                      form: str = "laplace") -> StokesLevel:
-    mesh = refine(macro.vertices, macro.tets, macro.bc_flags, level, spacing=macro.spacing)
+    mesh = refine(macro.vertices, macro.tets, macro.bc_flags, level, spacing=macro.spacing,
+                  basis=getattr(macro, "basis", None))
     return build_level(mesh, nu=nu, delta=delta, form=form)
 
 

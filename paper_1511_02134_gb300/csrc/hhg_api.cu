@@ -855,7 +855,8 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     H.pz = H.sh.nz + 2;
     H.nalloc = H.px * H.py * H.pz;
     H.h = M->macro.H / (double)(1 << l);
-    H.hT2 = std::pow(H.h * H.h * H.h / 6.0, 2.0 / 3.0);
+    // h_T = |T|^(1/3), |T| = det h^3 / 6 (det = 1 on axis-aligned lattices)
+    H.hT2 = std::pow(M->macro.det * H.h * H.h * H.h / 6.0, 2.0 / 3.0);
     H.flags.resize(H.sh.n());
     classify_nodes(M->macro, l, H.flags.data());
     std::vector<uint8_t> padded(H.nalloc, 0);
@@ -885,7 +886,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
       }
       if (o.operator_form == 1) {
         std::vector<double> table2;
-        stencil_classes_d(patterns, table2);
+        stencil_classes_d(M->macro, patterns, table2);
         std::vector<float> table2_32(table2.begin(), table2.end());
         if ((rc = dalloc(M, (void**)&H.d_wt2_64, sizeof(double) * table2.size()))) return bail(rc);
         if ((rc = dalloc(M, (void**)&H.d_wt2_32, sizeof(float) * table2.size()))) return bail(rc);
@@ -981,7 +982,7 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     std::string cerr;
     int ncls = 0;
     stencil_classes(M->macro, H.level, H.flags.data(), cls, table, ncls, cerr, &patterns);
-    if (o.operator_form == 1) stencil_classes_d(patterns, table2);
+    if (o.operator_form == 1) stencil_classes_d(M->macro, patterns, table2);
     CoarseMatrix cm;
     if (cerr.empty() &&
         (rc = assemble_coarse(H.sh, H.px, H.px * H.py, H.flags.data(), cls.data(), table.data(), H.d64.nuh, H.d64.c,
@@ -1135,9 +1136,12 @@ int hhg_node_coords(const hhg_mesh* mesh, int32_t level, double* xyz) {
     for (int j = 0; j < H.sh.ny; ++j)
       for (int i = 0; i < H.sh.nx; ++i) {
         const int64_t q = i + (int64_t)H.sh.nx * (j + (int64_t)H.sh.ny * k);
-        tmp[3 * q + 0] = M->macro.origin[0] + i * H.h;
-        tmp[3 * q + 1] = M->macro.origin[1] + j * H.h;
-        tmp[3 * q + 2] = M->macro.origin[2] + k * H.h;
+        const double* B0 = M->macro.basis[0];
+        const double* B1 = M->macro.basis[1];
+        const double* B2 = M->macro.basis[2];
+        tmp[3 * q + 0] = M->macro.origin[0] + H.h * (B0[0] * i + B0[1] * j + B0[2] * k);
+        tmp[3 * q + 1] = M->macro.origin[1] + H.h * (B1[0] * i + B1[1] * j + B1[2] * k);
+        tmp[3 * q + 2] = M->macro.origin[2] + H.h * (B2[0] * i + B2[1] * j + B2[2] * k);
       }
   CK(cudaMemcpy(xyz, tmp.data(), sizeof(double) * tmp.size(), cudaMemcpyDefault));
   return HHG_OK;

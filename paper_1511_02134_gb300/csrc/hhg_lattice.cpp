@@ -47,32 +47,77 @@ int build_macro_lattice(const double* V, int64_t nv, const int32_t* T, int64_t n
       return HHG_EINVAL;
     }
   }
-  // spacing from the first edge of the first tetrahedron
-  double e[3];
-  for (int a = 0; a < 3; ++a) e[a] = V[3 * T[1] + a] - V[3 * T[0] + a];
-  const double H = std::sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
-  if (!(H > 0) || !std::isfinite(H)) {
+  // lattice axes from the first tetrahedron: its edges v1 - v0, v2 - v1,
+  // v3 - v2; axis-aligned edges of one length give the identity basis with
+  // that spacing, anything else the affine lattice of those edge vectors
+  double E[3][3];  // E[a][c]: component a of edge c
+  for (int c = 0; c < 3; ++c)
+    for (int a = 0; a < 3; ++a) E[a][c] = V[3 * T[c + 1] + a] - V[3 * T[c] + a];
+  double len[3];
+  bool aligned = true;
+  for (int c = 0; c < 3; ++c) {
+    len[c] = std::sqrt(E[0][c] * E[0][c] + E[1][c] * E[1][c] + E[2][c] * E[2][c]);
+    int nzc = 0;
+    for (int a = 0; a < 3; ++a) nzc += E[a][c] != 0.0;
+    aligned = aligned && nzc == 1;
+  }
+  const double H = aligned ? len[0] : 1.0;
+  if (!(len[0] > 0) || !std::isfinite(len[0])) {
     err = "degenerate first edge";
     return HHG_EMESH;
   }
+  aligned = aligned && std::fabs(len[1] - H) <= 1e-12 * H && std::fabs(len[2] - H) <= 1e-12 * H;
+  double Bi[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // lattice coordinates per physical unit (x H for aligned)
+  if (!aligned) {
+    const double det = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+                       E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+                       E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+    if (!(std::fabs(det) > 1e-12 * len[0] * len[1] * len[2]) || !std::isfinite(det)) {
+      err = "degenerate first tetrahedron";
+      return HHG_EMESH;
+    }
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        const int r1 = (c + 1) % 3, r2 = (c + 2) % 3, c1 = (r + 1) % 3, c2 = (r + 2) % 3;
+        Bi[r][c] = (E[r1][c1] * E[r2][c2] - E[r1][c2] * E[r2][c1]) / det;
+      }
+    out.affine = true;
+    out.det = std::fabs(det);
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) {
+        out.basis[r][c] = E[r][c];
+        out.basis_inv_t[r][c] = Bi[c][r];
+      }
+  }
+  // lattice coordinates of the vertices: Bi (v - v0) / H, integers
+  const double* v0 = V + 3 * T[0];
+  std::vector<std::array<double, 3>> xi(nv);
   double lo[3] = {INFINITY, INFINITY, INFINITY};
-  for (int64_t t = 0; t < nt * 4; ++t)
-    for (int a = 0; a < 3; ++a) lo[a] = std::min(lo[a], V[3 * T[t] + a]);
-  std::vector<Key3> L(nv, Key3{0, 0, 0});
   std::vector<char> used(nv, 0);
   for (int64_t t = 0; t < nt * 4; ++t) used[T[t]] = 1;
   for (int64_t v = 0; v < nv; ++v) {
     if (!used[v]) continue;
     for (int a = 0; a < 3; ++a) {
-      const double x = (V[3 * v + a] - lo[a]) / H;
+      double x = 0.0;
+      for (int c = 0; c < 3; ++c) x += Bi[a][c] * (V[3 * v + c] - v0[c]);
+      xi[v][a] = x / H;
+      lo[a] = std::min(lo[a], xi[v][a]);
+    }
+  }
+  std::vector<Key3> L(nv, Key3{0, 0, 0});
+  for (int64_t v = 0; v < nv; ++v) {
+    if (!used[v]) continue;
+    for (int a = 0; a < 3; ++a) {
+      const double x = xi[v][a] - std::nearbyint(lo[a]);
       const double r = std::nearbyint(x);
       if (!std::isfinite(x) || std::fabs(x - r) > 1e-9 * std::max(1.0, std::fabs(x))) {
-        err = "macro vertex not on the lattice of the first edge's spacing";
+        err = "macro vertex not on the lattice of the first tetrahedron's edges";
         return HHG_EMESH;
       }
       L[v][a] = (int64_t)r;
     }
   }
+  for (int a = 0; a < 3; ++a) lo[a] = std::nearbyint(lo[a]);
   int64_t hi[3] = {0, 0, 0};
   for (int64_t v = 0; v < nv; ++v)
     if (used[v])
@@ -82,7 +127,12 @@ int build_macro_lattice(const double* V, int64_t nv, const int32_t* T, int64_t n
     return HHG_EMESH;
   }
   out.H = H;
-  for (int a = 0; a < 3; ++a) out.origin[a] = lo[a];
+  // physical position of lattice point 0: v0 + H basis lo
+  for (int a = 0; a < 3; ++a) {
+    double x = v0[a];
+    for (int c = 0; c < 3; ++c) x += H * out.basis[a][c] * lo[c];
+    out.origin[a] = x;
+  }
   out.mx = (int)hi[0];
   out.my = (int)hi[1];
   out.mz = (int)hi[2];
@@ -168,20 +218,32 @@ int build_macro_lattice(const double* V, int64_t nv, const int32_t* T, int64_t n
       }
     bf.flag = code == HHG_BC_OUTFLOW ? 2 : 1;
     if (bf.flag == 2) out.has_outflow = true;
-    double u[3], w[3], n[3];
+    // physical edge vectors of the face (H basis times the lattice differences)
+    auto phys = [&](const int64_t* d, double* x) {
+      for (int a = 0; a < 3; ++a) {
+        x[a] = 0.0;
+        for (int c = 0; c < 3; ++c) x[a] += H * out.basis[a][c] * (double)d[c];
+      }
+    };
+    int64_t du[3], dw[3], dq[3];
     for (int a = 0; a < 3; ++a) {
-      u[a] = (double)(bf.v[1][a] - bf.v[0][a]);
-      w[a] = (double)(bf.v[2][a] - bf.v[0][a]);
+      du[a] = bf.v[1][a] - bf.v[0][a];
+      dw[a] = bf.v[2][a] - bf.v[0][a];
+      dq[a] = L[T[4 * t + f]][a] - bf.v[0][a];
     }
+    double u[3], w[3], q[3], n[3];
+    phys(du, u);
+    phys(dw, w);
+    phys(dq, q);
     n[0] = u[1] * w[2] - u[2] * w[1];
     n[1] = u[2] * w[0] - u[0] * w[2];
     n[2] = u[0] * w[1] - u[1] * w[0];
     const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
     double to_opp = 0;
-    for (int a = 0; a < 3; ++a) to_opp += n[a] * (double)(L[T[4 * t + f]][a] - bf.v[0][a]);
+    for (int a = 0; a < 3; ++a) to_opp += n[a] * q[a];
     const double sgn = to_opp > 0 ? -1.0 : 1.0;
     for (int a = 0; a < 3; ++a) bf.normal[a] = sgn * n[a] / nn;
-    bf.area = 0.5 * nn * H * H;
+    bf.area = 0.5 * nn;
     out.bfaces.push_back(bf);
   }
   return HHG_OK;
@@ -246,7 +308,8 @@ void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
           }
           uint8_t f = 0;
           if (count > 0) f |= F_ACT;
-          if (count > 0 && count < 24) f |= F_IRR;
+          // affine lattices: the closed-form rows of the axis-aligned lattice do not apply
+          if (count > 0 && (count < 24 || m.affine)) f |= F_IRR;
           flags[i + sh.nx * j + nxy * k] = f;
         }
       }
@@ -294,8 +357,17 @@ int offset_index(int dx, int dy, int dz) {
 // o, o+e_a0, o+e_a0+e_a1, o+(1,1,1) with o = node - q; the unit barycentric
 // gradients are g0 = -e_a0, g1 = e_a0 - e_a1, g2 = e_a1 - e_a2, g3 = e_a2;
 // |T| = 1/6 at unit spacing.
-void class_rows(uint32_t pattern, double* w) {
+// Gradients of the barycentric functions in physical directions per lattice
+// step: basis^-T g (the identity on axis-aligned lattices); volume factor det.
+void geo_grads(const MacroLattice& m, const double g[4][3], double gp[4][3]) {
+  for (int n = 0; n < 4; ++n)
+    for (int a = 0; a < 3; ++a)
+      gp[n][a] = m.basis_inv_t[a][0] * g[n][0] + m.basis_inv_t[a][1] * g[n][1] + m.basis_inv_t[a][2] * g[n][2];
+}
+
+void class_rows(const MacroLattice& mac, uint32_t pattern, double* w) {
   std::fill(w, w + W_STRIDE, 0.0);
+  const double vol = mac.det;  // 6 |T| at unit lattice spacing
   int bit = 0;
   for (int q = 0; q < 8; ++q) {
     const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
@@ -323,16 +395,18 @@ void class_rows(uint32_t pattern, double* w) {
       g[2][a[1]] += 1;
       g[2][a[2]] -= 1;
       g[3][a[2]] = 1;
+      double gp[4][3];
+      geo_grads(mac, g, gp);
       for (int n = 0; n < 4; ++n) {
-        w[W_LAP + idx[n]] += kuhn_stiff6(m, n) / 6.0;
+        w[W_LAP + idx[n]] += vol * (gp[m][0] * gp[n][0] + gp[m][1] * gp[n][1] + gp[m][2] * gp[n][2]) / 6.0;
         for (int d = 0; d < 3; ++d) {
-          w[W_B + 15 * d + idx[n]] += -g[n][d] / 24.0;
-          w[W_BT + 15 * d + idx[n]] += -g[m][d] / 24.0;
+          w[W_B + 15 * d + idx[n]] += -vol * gp[n][d] / 24.0;
+          w[W_BT + 15 * d + idx[n]] += -vol * gp[m][d] / 24.0;
         }
-        w[W_M + idx[n]] += 1.0 / 120.0;
+        w[W_M + idx[n]] += vol / 120.0;
       }
-      w[W_M + 0] += 1.0 / 120.0;
-      w[W_LUMP] += 1.0 / 24.0;
+      w[W_M + 0] += vol / 120.0;
+      w[W_LUMP] += vol / 24.0;
     }
   }
 }
@@ -342,8 +416,9 @@ void class_rows(uint32_t pattern, double* w) {
 // nu int (delta_ab grad l_m . grad l_n + d_b l_m d_a l_n) = nu |T| (delta_ab
 // g_m . g_n + g_m[b] g_n[a]), |T| = 1/6 at unit spacing; then the centre
 // block's inverse.
-void class_rows_d(uint32_t pattern, double* w) {
+void class_rows_d(const MacroLattice& mac, uint32_t pattern, double* w) {
   std::fill(w, w + W2_STRIDE, 0.0);
+  const double vol = mac.det;
   int bit = 0;
   for (int q = 0; q < 8; ++q) {
     const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
@@ -367,11 +442,13 @@ void class_rows_d(uint32_t pattern, double* w) {
       g[2][a[1]] += 1;
       g[2][a[2]] -= 1;
       g[3][a[2]] = 1;
+      double gp[4][3];
+      geo_grads(mac, g, gp);
       for (int n = 0; n < 4; ++n) {
-        const double gg = g[m][0] * g[n][0] + g[m][1] * g[n][1] + g[m][2] * g[n][2];
+        const double gg = gp[m][0] * gp[n][0] + gp[m][1] * gp[n][1] + gp[m][2] * gp[n][2];
         for (int ra = 0; ra < 3; ++ra)
           for (int cb = 0; cb < 3; ++cb)
-            w[15 * (3 * ra + cb) + idx[n]] += ((ra == cb ? gg : 0.0) + g[m][cb] * g[n][ra]) / 6.0;
+            w[15 * (3 * ra + cb) + idx[n]] += vol * ((ra == cb ? gg : 0.0) + gp[m][cb] * gp[n][ra]) / 6.0;
       }
     }
   }
@@ -393,9 +470,9 @@ void class_rows_d(uint32_t pattern, double* w) {
 
 }  // namespace
 
-void stencil_classes_d(const std::vector<uint32_t>& patterns, std::vector<double>& table2) {
+void stencil_classes_d(const MacroLattice& m, const std::vector<uint32_t>& patterns, std::vector<double>& table2) {
   table2.assign(patterns.size() * W2_STRIDE, 0.0);
-  for (size_t c = 0; c < patterns.size(); ++c) class_rows_d(patterns[c], table2.data() + c * W2_STRIDE);
+  for (size_t c = 0; c < patterns.size(); ++c) class_rows_d(m, patterns[c], table2.data() + c * W2_STRIDE);
 }
 
 void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
@@ -430,7 +507,7 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
           ++n_classes;
           it = ids.emplace(pattern, (uint16_t)n_classes).first;
           table.resize((size_t)(n_classes + 1) * W_STRIDE);
-          class_rows(pattern, table.data() + (size_t)n_classes * W_STRIDE);
+          class_rows(m, pattern, table.data() + (size_t)n_classes * W_STRIDE);
           if (patterns) patterns->push_back(pattern);
         }
         cls[q] = it->second;

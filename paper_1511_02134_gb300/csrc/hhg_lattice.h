@@ -19,6 +19,14 @@ struct BoundaryFace {
 struct MacroLattice {
   double origin[3] = {0, 0, 0};
   double H = 1.0;                    // macro cell edge length
+  // Lattice axes: a lattice point xi (integer at macro vertices) sits at
+  // origin + H * basis * xi.  The identity for axis-aligned meshes; for the
+  // affine image of a Kuhn lattice (affine = true) the first tetrahedron's
+  // edge vectors with H = 1, and every node then takes its class rows.
+  double basis[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+  double basis_inv_t[3][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}};  // basis^-T
+  double det = 1.0;                  // |det basis|: volume factor of the lattice cells
+  bool affine = false;
   int mx = 0, my = 0, mz = 0;        // macro cells per axis
   std::vector<uint8_t> mask;         // per macro cell: bit s = Kuhn path s present
   std::vector<BoundaryFace> bfaces;  // faces of the macro mesh boundary
@@ -71,7 +79,7 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
                      std::vector<uint32_t>* patterns = nullptr);
 // D-operator row tables (W2_STRIDE doubles per class, hhg_common.h) of the
 // classes with the given patterns.
-void stencil_classes_d(const std::vector<uint32_t>& patterns, std::vector<double>& table2);
+void stencil_classes_d(const MacroLattice& m, const std::vector<uint32_t>& patterns, std::vector<double>& table2);
 
 }  // namespace hhg
 

@@ -52,6 +52,8 @@ def macro_by_name(name):
         return W.unit_cube()
     if name == "channel":
         return W.obstacle_channel()
+    if name == "sheared":
+        return W.sheared_cube()
     if name == "partial":
         # two unit cubes with two Kuhn tetrahedra removed and one listed along
         # its reversed path: partially filled macro cells, irregular rows inside

@@ -32,12 +32,14 @@ def test_exports_every_declared_symbol(pkg):
         assert hasattr(lib, name), name
 
 
-@pytest.mark.parametrize("name,levels", [("cube", (0, 1, 2, 3)), ("channel", (0, 1, 2)), ("partial", (1, 2, 3))])
+@pytest.mark.parametrize("name,levels", [("cube", (0, 1, 2, 3)), ("channel", (0, 1, 2)), ("partial", (1, 2, 3)),
+                                         ("sheared", (1, 2, 3))])
 def test_classification_matches_oracle(pkg, name, levels):
     macro = macro_by_name(name)
+    affine = macro.basis is not None
     for lev in levels:
         dims, fl = pkg.lattice_classify(macro.vertices, macro.tets, macro.bc_flags, lev)
-        r = M.refine(macro.vertices, macro.tets, macro.bc_flags, lev)
+        r = M.refine(macro.vertices, macro.tets, macro.bc_flags, lev, basis=macro.basis)
         lat = r.ijk[:, 0] + dims[0] * (r.ijk[:, 1] + dims[1] * r.ijk[:, 2])
         act = np.zeros(len(fl), bool)
         act[lat] = True
@@ -45,7 +47,7 @@ def test_classification_matches_oracle(pkg, name, levels):
         vf[lat[r.free_velocity]] = True
         cnt = np.bincount(r.tets.ravel(), minlength=r.n_nodes)
         irr = np.zeros(len(fl), bool)
-        irr[lat[cnt < 24]] = True
+        irr[lat[(cnt < 24) | affine]] = True   # affine lattices: every active node takes class rows
         out = np.zeros(len(fl), bool)
         out[lat[r.on_outflow]] = True
         assert np.array_equal(act, (fl & pkg.NODE_ACTIVE) > 0)

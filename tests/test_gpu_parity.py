@@ -86,7 +86,7 @@ def _read_up(mesh, H, l, precision=0):
 # ---- operator and right-hand side ---------------------------------------------------
 
 @pytest.mark.parametrize("name,level", [("cube", 2), ("cube", 4), ("cube", 5), ("channel", 1), ("channel", 2),
-                                        ("partial", 3)])
+                                        ("partial", 3), ("sheared", 3)])
 def test_apply_operator(pkg, name, level):
     macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level))
     L = H.levels[level]
@@ -103,7 +103,7 @@ def test_apply_operator(pkg, name, level):
     assert np.all(kp[mask] == 0) and np.all(ku[mask] == 0)
 
 
-@pytest.mark.parametrize("name,level", [("cube", 3), ("cube", 5), ("channel", 2), ("partial", 3)])
+@pytest.mark.parametrize("name,level", [("cube", 3), ("cube", 5), ("channel", 2), ("partial", 3), ("sheared", 3)])
 def test_set_rhs(pkg, name, level):
     macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level))
     L = H.levels[level]
@@ -112,6 +112,8 @@ def test_set_rhs(pkg, name, level):
     rng = np.random.default_rng(3)
     fn = rng.standard_normal(x.shape)
     ud = W.manufactured_velocity(x) if name != "channel" else W.channel_inflow(x)
+    if name == "sheared":
+        np.testing.assert_allclose(x, macro.lattice_coords(level), atol=1e-14)
     mesh.set_rhs(fn, ud)
     lat = lattice_index(L, dims)
     f, g = L.rhs(fn[lat], ud[lat])
@@ -125,7 +127,7 @@ KERNEL_FORMS = [(0, 0), (-1, 1), (-1, 2), (-1, 4), (0, 4)]
 
 
 @pytest.mark.parametrize("spec,cbz", KERNEL_FORMS)
-@pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3)])
+@pytest.mark.parametrize("name,level", [("cube", 3), ("channel", 2), ("partial", 3), ("sheared", 3)])
 def test_smoother_pieces(pkg, name, level, spec, cbz):
     """Smoother steps against the oracle, with the colour sweeps run by the
     grid kernels in the speculative node form of small levels (spec = 0, the
@@ -360,7 +362,7 @@ def test_fused_pass_wait_timeout(pkg):
         m.close()
 
 
-@pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3)])
+@pytest.mark.parametrize("name,level", [("cube", 4), ("channel", 2), ("partial", 3), ("sheared", 3)])
 def test_transfers(pkg, name, level):
     macro, mesh, H = _pair(pkg, name, level, coarsest=level - 1)
     Lf, Lc = H.levels[level], H.levels[level - 1]
@@ -410,7 +412,7 @@ def test_coarse_solve(pkg, name, level, mx):
 
 @pytest.mark.parametrize("spec,cbz", KERNEL_FORMS)
 @pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 3, 2, 5), ("cube", 5, 2, 5), ("channel", 2, 1, 200),
-                                                    ("partial", 3, 1, 30)])
+                                                    ("partial", 3, 1, 30), ("sheared", 4, 2, 5)])
 def test_vcycle_iterates(pkg, name, level, coarsest, mx, spec, cbz):
     macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx, spec_max_nodes=spec,
                            colour_block_z=cbz)
@@ -428,14 +430,15 @@ def test_vcycle_iterates(pkg, name, level, coarsest, mx, spec, cbz):
         assert _p_err(L, gp, p) < tol, cyc
 
 
-@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 4, 2, 5), ("cube", 5, 2, 5), ("channel", 3, 1, 200)])
+@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 4, 2, 5), ("cube", 5, 2, 5), ("channel", 3, 1, 200),
+                                                    ("sheared", 4, 2, 5)])
 def test_fp64_solve_matches_oracle(pkg, name, level, coarsest, mx):
     macro, mesh, H = _pair(pkg, name, level, coarsest=coarsest, coarse_minres_max=mx)
     L = H.levels[level]
     dims = mesh.dims()
     x = mesh.node_coords()
     lat = lattice_index(L, dims)
-    if name == "cube":
+    if name in ("cube", "sheared"):
         fn, ud = W.manufactured_forcing(x), W.manufactured_velocity(x)
     else:
         fn, ud = np.zeros_like(x), W.channel_inflow(x)
@@ -450,7 +453,7 @@ def test_fp64_solve_matches_oracle(pkg, name, level, coarsest, mx):
     uo = L.scatter(ref.u, ud[lat])
     assert rel_err(u[lat], uo) < 1e-10
     assert rel_err(p[lat], ref.p) < 1e-10
-    if name == "cube":
+    if name in ("cube", "sheared"):
         m = L.m
         assert abs(np.dot(m, p[lat])) < 1e-12 * np.abs(p).max()
 

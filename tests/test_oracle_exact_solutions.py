@@ -162,3 +162,22 @@ def test_backward_colour_sweep_equals_sequential_gs():
         for i in np.where(col == c)[0][::-1]:
             y[i] += (rhs[i] - Ad[i] @ y) / Ad[i, i]
     np.testing.assert_allclose(x, y, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("form", ["laplace", "D"])
+def test_exact_states_on_sheared_cube(form):
+    """The hydrostatic and linear-flow states are exact on any mesh, here the
+    sheared cube (tetrahedra not aligned with the axes), in both forms."""
+    L = S.build_from_macro(W.sheared_cube(), 2, form=form)
+    x = L.mesh.xyz
+    G = np.array([[0.5, 1.2, -0.3], [0.7, -1.5, 0.4], [-0.9, 0.2, 1.0]])
+    u_lin = x @ G.T + np.array([0.1, -0.2, 0.3])
+    grad = np.array([-1.1, 0.8, 0.5])
+    f, g = L.rhs(np.broadcast_to(grad, x.shape).copy(), u_lin)
+    phi = x @ grad
+    p_ref = phi - np.dot(L.m, phi) / L.m.sum()
+    ru, rp = L.residual(u_lin[L.free].T, p_ref, f, g)
+    scale = max(np.abs(f).max(), np.abs(g).max())
+    assert np.abs(ru).max() <= 1e-13 * scale and np.abs(rp).max() <= 1e-13 * scale
+    H = MG.build_hierarchy(W.sheared_cube(), 2)
+    assert MG.colouring_is_valid(H.levels[2])

@@ -51,18 +51,21 @@ class MacroMesh:
     spacing: float         # macro cell edge length H
     origin: np.ndarray     # (3,) float64
     removed: tuple = ()    # removed cells (obstacles), as (i, j, k)
+    basis: np.ndarray = None  # (3, 3) lattice axes as columns (None: the identity)
 
     def lattice_dims(self, level: int) -> tuple:
         n = 1 << level
         return tuple(c * n + 1 for c in self.cells)
 
     def lattice_coords(self, level: int) -> np.ndarray:
-        """(n_nodes, 3) coordinates of the bounding-box lattice, x fastest."""
+        """(n_nodes, 3) coordinates of the bounding-box lattice, x fastest:
+        origin + h basis (i, j, k)."""
         nx, ny, nz = self.lattice_dims(level)
         h = self.spacing / (1 << level)
         k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
         ijk = np.stack([i.ravel(), j.ravel(), k.ravel()], axis=1).astype(np.float64)
-        return self.origin[None, :] + ijk * h
+        B = np.eye(3) if self.basis is None else np.asarray(self.basis, float)
+        return self.origin[None, :] + (ijk * h) @ B.T
 
 
 def _box_vertex_id(i, j, k, nx, ny):
@@ -118,6 +121,19 @@ def box_of_cubes(nx: int, ny: int, nz: int, removed=(), outflow_x_max: bool = Fa
 def unit_cube() -> MacroMesh:
     """The unit cube as 6 Kuhn tetrahedra, all boundary faces Dirichlet."""
     return box_of_cubes(1, 1, 1)
+
+
+SHEAR = np.array([[1.0, 1.0, 0.0], [0.0, 1.0, 0.0], [0.0, 0.0, 1.0]])
+
+
+def sheared_cube() -> MacroMesh:
+    """The unit cube's 6 Kuhn tetrahedra under the integer shear x' = x + y:
+    a parallelepiped of integer-vertex tetrahedra that are not aligned with
+    the coordinate axes (the lattice axes are the columns of SHEAR)."""
+    m = box_of_cubes(1, 1, 1)
+    m.vertices = m.vertices @ SHEAR.T
+    m.basis = SHEAR.copy()
+    return m
 
 
 def channel_obstacles(seed: int = 0, nx: int = 16, ny: int = 4, nz: int = 4, fraction: float = 0.1):
