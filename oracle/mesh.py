@@ -25,6 +25,7 @@ import numpy as np
 
 _BC_DIRICHLET_CODES = (0, 1)
 _BC_OUTFLOW = 2
+_BC_SLIP = 3
 
 
 @dataclass
@@ -41,6 +42,7 @@ class RefinedMesh:
     outflow_tris: np.ndarray  # (nF, 3) node ids of fine triangles on outflow faces
     outflow_normals: np.ndarray  # (nF, 3) outward unit normals of those triangles
     ijk: np.ndarray = field(default=None)  # (n, 3) lattice coordinates, if a lattice
+    on_slip: np.ndarray = field(default=None)  # (n,) bool, free-slip node (on a slip face, on no Dirichlet face)
 
     @property
     def n_nodes(self) -> int:
@@ -87,7 +89,8 @@ def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0, basis=Non
 
     vertices: (nv, 3) integer-valued coordinates; tets: (nt, 4) vertex ids in
     refinement order; bc_flags: (nt, 4) per face opposite local vertex f,
-    0 = interior/Dirichlet-by-default, 1 = Dirichlet, 2 = do-nothing outflow;
+    0 = interior/Dirichlet-by-default, 1 = Dirichlet, 2 = do-nothing outflow,
+    3 = free slip (Sec. 6.1; Dirichlet wins on shared edges and corners);
     basis (3, 3): lattice axes as columns when the macro mesh is the affine
     image of a lattice (default: the coordinate axes) -- used only to derive
     the lattice coordinates of the nodes (for the colouring).
@@ -124,6 +127,7 @@ def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0, basis=Non
     n = len(uniq)
     on_dir = np.zeros(n, bool)
     on_out = np.zeros(n, bool)
+    on_slip = np.zeros(n, bool)
     out_tris, out_normals = [], []
     simp_local_faces = [[m for m in range(4) if m != f] for f in range(4)]
     for t in range(len(T)):
@@ -150,6 +154,8 @@ def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0, basis=Non
                     out_normals.append(np.repeat(nrm[None], int(sel.sum()), axis=0))
             elif F[t, f] in _BC_DIRICHLET_CODES:
                 on_dir[ids] = True
+            elif F[t, f] == _BC_SLIP:
+                on_slip[ids] = True
             else:
                 raise ValueError(f"unknown boundary flag {F[t, f]}")
     if out_tris:
@@ -162,7 +168,7 @@ def refine(vertices, tets, bc_flags, level: int, spacing: float = 1.0, basis=Non
     h = spacing / N
     mesh = RefinedMesh(level=level, N=N, h=h, xyz=xyz, key=uniq, tets=fine, tet_parent=parent,
                        on_dirichlet=on_dir, on_outflow=on_out & ~on_dir,
-                       outflow_tris=out_tris, outflow_normals=out_normals)
+                       outflow_tris=out_tris, outflow_normals=out_normals, on_slip=on_slip & ~on_dir)
     # lattice coordinates (only meaningful when the macro mesh lives on a lattice of spacing H)
     Binv = np.eye(3) if basis is None else np.linalg.inv(np.asarray(basis, float))
     lat = xyz @ Binv.T

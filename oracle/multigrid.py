@@ -29,7 +29,13 @@ be reproduced without its source):
     R = P^T, for velocity and pressure alike; the velocity transfers act on
     free nodes only (a coarse Dirichlet node carries no correction);
   * coarse operators are rediscretised on every level (c_l is level
-    dependent, Sec. 2.1), not Galerkin products.
+    dependent, Sec. 2.1), not Galerkin products;
+  * free slip (Sec. 6.1, oracle.stokes): the smoother works on the coupled
+    velocity block Pi A Pi + (I - Pi) with its 3 x 3 node blocks (the update
+    of a slip node is the tangential part of its unconstrained update); the
+    restricted residual is projected with the coarse normals and the
+    prolongated correction with the fine normals, so every level's iterate
+    stays tangential at its own slip nodes.
 """
 from __future__ import annotations
 
@@ -171,17 +177,17 @@ def _gs_sweep(Amat, diag, x, rhs, colour_rows, order, relax=1.0):
 
 
 def _block_gs_sweep(L: StokesLevel, u, rhs, colour_rows, order):
-    """Colour-ordered block Gauss-Seidel on the D-form A2: for each colour,
-    the velocity of its nodes (3 components each) becomes
-    u_c += D_c^-1 (rhs - A2 u)_c, D_c the nodes' 3 x 3 diagonal blocks of A2
-    solved exactly.  Nodes of one colour are not coupled, so this equals a
-    node-by-node block Gauss-Seidel in colour order."""
+    """Colour-ordered block Gauss-Seidel on the coupled velocity block Kv (the
+    D-form A2, free slip): for each colour, the velocity of its nodes (3
+    components each) becomes u_c += D_c^-1 (rhs - Kv u)_c, D_c the nodes'
+    3 x 3 diagonal blocks of Kv solved exactly.  Nodes of one colour are not
+    coupled, so this equals a node-by-node block Gauss-Seidel in colour order."""
     for c in order:
         rows = colour_rows[c]
         if len(rows) == 0:
             continue
         r = (rhs - L.apply_A(u))[:, rows]                      # (3, nc)
-        delta = np.linalg.solve(L.A2_node[rows], r.T[:, :, None])[:, :, 0]
+        delta = np.linalg.solve(L.Kv_node[rows], r.T[:, :, None])[:, :, 0]
         u[:, rows] += delta.T
     return u
 
@@ -194,14 +200,15 @@ def uzawa_step(H: Hierarchy, l: int, u, p, f, g):
     form these blocks are diagonal and the sweep is the component-wise one)."""
     L = H.levels[l]
     cu = H.colours_u[l]
-    if L.form == "D":
+    if L.coupled:
         H.count(l, "A", 2)
         H.count(l, "B", 2)
         H.count(l, "C", 1)
-        rhs = np.stack([f[d] - L.BT[d] @ p for d in range(3)])
+        rhs = L.proj(np.stack([f[d] - L.BT[d] @ p for d in range(3)]))
         _block_gs_sweep(L, u, rhs, cu, (0, 1, 2, 3))
         _block_gs_sweep(L, u, rhs, cu, (3, 2, 1, 0))
-        rhs_p = sum(L.B[d] @ u[d] for d in range(3)) - g
+        up = L.proj(u)
+        rhs_p = sum(L.B[d] @ up[d] for d in range(3)) - g
         _gs_sweep(L.C, L.C_diag, p, rhs_p, H.colours_p[l], (0, 1, 2, 3), relax=H.opt.omega)
         return u, p
     # operator applications in the counting of Sec. 4.2: the SHGS sweep pair
@@ -245,8 +252,8 @@ def coarse_solve(H: Hierarchy, f, g, history=None):
 
     def apply_Pinv(x):
         u, p = split(x)
-        if L.form == "D":
-            zu = krylov.cg(lambda v: L.A2 @ v, u.ravel(), o.coarse_cg_max, o.coarse_cg_rtol)
+        if L.coupled:
+            zu = krylov.cg(lambda v: L.Kv @ v, u.ravel(), o.coarse_cg_max, o.coarse_cg_rtol)
         else:
             zu = np.stack([krylov.cg(lambda v: L.A @ v, u[d], o.coarse_cg_max, o.coarse_cg_rtol) for d in range(3)])
         return np.concatenate([zu.ravel(), p / L.m])
@@ -277,13 +284,12 @@ def vcycle(H: Hierarchy, l: int, u, p, f, g, root: int | None = None, nu: int | 
     H.count(l, "C", 1)
     Pu, P = H.Pu[l], H.P[l]
     Lc = H.levels[l - 1]
-    fc = np.stack([Pu.T @ ru[d] for d in range(3)])
+    fc = Lc.proj(np.stack([Pu.T @ ru[d] for d in range(3)]))
     gc = P.T @ rp
     uc = np.zeros((3, Lc.n_u))
     pc = np.zeros(Lc.n_p)
     vcycle(H, l - 1, uc, pc, fc, gc, root, nu)
-    for d in range(3):
-        u[d] += Pu @ uc[d]
+    u += L.proj(np.stack([Pu @ uc[d] for d in range(3)]))
     p += P @ pc
     for _ in range(smoothing_steps(H, l, False, root, nu)):
         uzawa_step(H, l, u, p, f, g)
@@ -348,7 +354,7 @@ def fmg(H: Hierarchy, rhs: dict, dirichlet: dict, cycles: int = 1, nu: int = 2) 
     for l in range(c + 1, H.finest + 1):
         L, Lk = H.levels[l], H.levels[l - 1]
         full = Lk.scatter(u, dirichlet.get(l - 1))
-        u = np.stack([(H.P[l] @ full[:, d])[L.free] for d in range(3)])
+        u = L.proj(np.stack([(H.P[l] @ full[:, d])[L.free] for d in range(3)]))
         p = H.P[l] @ p
         f, g = rhs[l]
         for _ in range(cycles):

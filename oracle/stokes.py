@@ -16,6 +16,21 @@ Readings where the paper is silent:
   * pure-Dirichlet problems: g is projected onto the range of K by removing
     its Euclidean mean (the null vector of K is (0, 1)), and the pressure is
     normalised by sum_i m_i p_i = 0 (the discrete L^2_0 condition, Sec. 2).
+
+Free slip (Sec. 6.1): u . n_i = 0 at a free-slip node i, with the
+mass-conservative normal n_i = <grad phi_i, 1> / |<grad phi_i, 1>| (taken
+from B^T 1, whose entries are -<grad phi_i, 1>), and the tangential stress
+condition imposed point-wise by testing the momentum rows only in the
+tangent plane.  With Pi the projector I - n_i n_i^T at slip nodes (identity
+elsewhere) the system solved is
+    [Pi A Pi + (I - Pi)   Pi B^T] [u]   [Pi f]
+    [B Pi                 -C    ] [p] = [g   ]
+whose velocity block is the identity in the normal directions, so their
+solution is u . n_i = 0.  Where <grad phi_i, 1> = 0 (two free-slip faces
+back to back, e.g. obstacles that touch along an edge) there is no normal
+and the node carries no constraint (Pi_i = I); its flux term is zero anyway.  Since Pi_i B^T 1 = 0 at slip nodes, the constant
+pressure stays in the kernel of a slip-and-Dirichlet problem, and the flux
+through slip faces vanishes exactly (the mass-conservation property).
 """
 from __future__ import annotations
 
@@ -45,6 +60,14 @@ class StokesLevel:
     form: str = "laplace"   # "laplace" (a_1) or "D" (a_2, Sec. 2.1)
     A2: sp.csr_matrix = None  # D form: the coupled velocity block over (u_0, u_1, u_2) of the free nodes
     A2_node: np.ndarray = None  # D form: (n_u, 3, 3) diagonal node blocks of A2
+    slip: np.ndarray = None     # positions (within free) of the free-slip velocity nodes
+    normals: np.ndarray = None  # (n_slip, 3) mass-conservative unit normals of those nodes
+    Kv: sp.csr_matrix = None    # coupled velocity block solved (D form or free slip), (u_0, u_1, u_2) order
+    Kv_node: np.ndarray = None  # (n_u, 3, 3) diagonal node blocks of Kv
+
+    @property
+    def coupled(self) -> bool:
+        return self.Kv is not None
 
     @property
     def n_u(self) -> int:
@@ -59,17 +82,27 @@ class StokesLevel:
         return 3 * self.n_u + self.n_p
 
     # --- the operator K and the residual (Sec. 3) --------------------------
+    def proj(self, v: np.ndarray) -> np.ndarray:
+        """Pi v for v of shape (3, n_u): the normal part removed at slip nodes."""
+        v = np.array(v, dtype=float, copy=True)
+        if self.slip is not None and len(self.slip):
+            vs = v[:, self.slip]
+            v[:, self.slip] = vs - self.normals.T * np.sum(vs * self.normals.T, axis=0)
+        return v
+
     def apply_A(self, u: np.ndarray) -> np.ndarray:
-        """The velocity block: A u_d per component (Laplace form) or A2 u (D form)."""
-        if self.form == "D":
-            return (self.A2 @ np.asarray(u).ravel()).reshape(3, self.n_u)
+        """The velocity block: A u_d per component (Laplace form), or the
+        coupled block Kv (D form, free slip)."""
+        if self.coupled:
+            return (self.Kv @ np.asarray(u).ravel()).reshape(3, self.n_u)
         return np.stack([self.A @ u[d] for d in range(3)])
 
     def apply(self, u: np.ndarray, p: np.ndarray):
-        """K (u, p) = (A u + B^T p,  sum_d B_d u_d - C p)."""
+        """K (u, p) = (A u + Pi B^T p,  sum_d B_d (Pi u)_d - C p)."""
         au = self.apply_A(u)
-        ru = np.stack([au[d] + self.BT[d] @ p for d in range(3)])
-        rp = sum(self.B[d] @ u[d] for d in range(3)) - self.C @ p
+        ru = au + self.proj(np.stack([self.BT[d] @ p for d in range(3)]))
+        up = self.proj(u)
+        rp = sum(self.B[d] @ up[d] for d in range(3)) - self.C @ p
         return ru, rp
 
     def residual(self, u, p, f, g):
@@ -107,7 +140,7 @@ class StokesLevel:
                 g = g - self.ops.B[d][:, self.dir] @ vd
         if self.pure_dirichlet:
             g = g - g.mean()
-        return fu, g
+        return self.proj(fu), g
 
     def scatter(self, u: np.ndarray, u_dirichlet=None) -> np.ndarray:
         """Full nodal velocity (n, 3) from free values (3, n_u) and boundary data."""
@@ -131,9 +164,51 @@ def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, f
                             for a in range(3)], axis=1)
     elif form != "laplace":
         raise ValueError(form)
-    return StokesLevel(mesh=mesh, ops=ops, free=free, dir=dirn, A=A, A_diag=A.diagonal().copy(),
-                       B=B, BT=[b.T.tocsr() for b in B], C=ops.C, C_diag=ops.C.diagonal().copy(),
-                       m=ops.m, pure_dirichlet=not mesh.has_outflow, form=form, A2=A2, A2_node=A2_node)
+    L = StokesLevel(mesh=mesh, ops=ops, free=free, dir=dirn, A=A, A_diag=A.diagonal().copy(),
+                    B=B, BT=[b.T.tocsr() for b in B], C=ops.C, C_diag=ops.C.diagonal().copy(),
+                    m=ops.m, pure_dirichlet=not mesh.has_outflow, form=form, A2=A2, A2_node=A2_node)
+    on_slip = mesh.on_slip if mesh.on_slip is not None else np.zeros(mesh.n_nodes, bool)
+    L.slip = np.where(on_slip[free])[0]
+    if len(L.slip):
+        # <grad phi_i, 1> = -(B^T 1)_i, component by component (Sec. 6.1)
+        ones = np.ones(mesh.n_nodes)
+        gint = -np.stack([ops.B[d].T @ ones for d in range(3)], axis=1)[free[L.slip]]
+        # where free-slip faces meet back to back (obstacles touching along an
+        # edge or at a corner) the integral vanishes: no normal, no constraint
+        nrm = np.linalg.norm(gint, axis=1)
+        ok = nrm > 1e-12 * mesh.h ** 2
+        L.normals = np.zeros_like(gint)
+        L.normals[ok] = gint[ok] / nrm[ok][:, None]
+    else:
+        L.normals = np.zeros((0, 3))
+    couple(L)
+    return L
+
+
+def couple(L: StokesLevel) -> None:
+    """Set the coupled velocity block Kv and its node blocks from the form
+    and the slip normals: A2 (D form) or A per component (Laplace form),
+    constrained as Pi (.) Pi + (I - Pi) at slip nodes.  Nothing to do for the
+    Laplace form without slip nodes."""
+    if L.form == "D" or len(L.slip):
+        n = L.n_u
+        blocks = L.A2 if L.form == "D" else sp.block_diag([L.A, L.A, L.A], format="csr")
+        if len(L.slip):
+            # Pi (A) Pi + (I - Pi), with Pi = I - sum_slip n n^T as a 3 n x 3 n matrix
+            rows, cols, vals = [], [], []
+            for a in range(3):
+                for b in range(3):
+                    rows.append(a * n + L.slip)
+                    cols.append(b * n + L.slip)
+                    vals.append(L.normals[:, a] * L.normals[:, b])
+            Nn = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                               shape=(3 * n, 3 * n)).tocsr()
+            Pi = sp.identity(3 * n, format="csr") - Nn
+            blocks = (Pi @ blocks @ Pi + Nn).tocsr()
+            blocks.eliminate_zeros()
+        L.Kv = blocks
+        L.Kv_node = np.stack([np.stack([blocks[a * n:(a + 1) * n, b * n:(b + 1) * n].diagonal() for b in range(3)],
+                                       axis=1) for a in range(3)], axis=1)
 
 
 def build_from_macro(macro, level: int, nu: float = 1.0, delta: float = 1.0 / 12.0,
@@ -147,13 +222,21 @@ def full_matrix(L: StokesLevel) -> sp.csr_matrix:
     """K as one sparse matrix, unknown order (u_0, u_1, u_2, p)."""
     Z = [[None] * 4 for _ in range(4)]
     n = L.n_u
+    # Pi as 3 x 3 blocks of diagonal matrices over the free nodes
+    Pi = [[sp.identity(n, format="csr") if a == b else sp.csr_matrix((n, n)) for b in range(3)] for a in range(3)]
+    if len(L.slip):
+        for a in range(3):
+            for b in range(3):
+                dg = np.zeros(n)
+                dg[L.slip] = L.normals[:, a] * L.normals[:, b]
+                Pi[a][b] = Pi[a][b] - sp.diags(dg, format="csr")
     for d in range(3):
-        if L.form == "D":
+        if L.coupled:
             for e in range(3):
-                Z[d][e] = L.A2[d * n:(d + 1) * n, e * n:(e + 1) * n]
+                Z[d][e] = L.Kv[d * n:(d + 1) * n, e * n:(e + 1) * n]
         else:
             Z[d][d] = L.A
-        Z[d][3] = L.BT[d]
-        Z[3][d] = L.B[d]
+        Z[d][3] = sum(Pi[d][e] @ L.BT[e] for e in range(3))
+        Z[3][d] = sum(L.B[e] @ Pi[e][d] for e in range(3))
     Z[3][3] = -L.C
     return sp.bmat(Z, format="csr")

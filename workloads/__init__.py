@@ -21,6 +21,8 @@ Workloads (paper: Sec. 4 serial runs, Sec. 5 TME study, Sec. 6 application):
     removed as no-slip obstacles, inflow on x=0 and do-nothing outflow on
     x=16 -- a synthetic stand-in for the sphere bed of Sec. 6, whose NETGEN
     meshes are not available;
+  * free-slip variants (Sec. 6.1): the channel with free-slip obstacles and
+    the unit cube with free-slip faces x = 0 and x = 1;
   * the paper's random initial guess (Sec. 3.5): u0 ~ U[0,1],
     p0 ~ U[0, 1/h_min];
   * N(0,1) nodal body forces and random directions for the gradient check.
@@ -37,6 +39,7 @@ import numpy as np
 BC_AUTO = 0       # interior face, or a boundary face treated as Dirichlet
 BC_DIRICHLET = 1  # prescribed velocity
 BC_OUTFLOW = 2    # do-nothing (natural) boundary
+BC_SLIP = 3       # free slip: no flow through the face, no tangential stress (Sec. 6.1)
 
 # The 6 Kuhn tetrahedra of a unit cell: vertex path 0 -> e_a -> e_a+e_b -> 1.
 KUHN_PATHS = list(itertools.permutations(range(3)))
@@ -72,11 +75,15 @@ def _box_vertex_id(i, j, k, nx, ny):
     return i + (nx + 1) * (j + (ny + 1) * k)
 
 
-def box_of_cubes(nx: int, ny: int, nz: int, removed=(), outflow_x_max: bool = False) -> MacroMesh:
+def box_of_cubes(nx: int, ny: int, nz: int, removed=(), outflow_x_max: bool = False,
+                 slip_sides=(), slip_obstacles: bool = False) -> MacroMesh:
     """Union of nx*ny*nz unit cubes, each split into the 6 Kuhn tetrahedra.
 
     ``removed`` lists cells (i, j, k) left out (obstacles).  Every boundary
-    face is Dirichlet, except the faces on x = nx when ``outflow_x_max``.
+    face is Dirichlet, except the faces on x = nx when ``outflow_x_max``, the
+    faces on the box sides named in ``slip_sides`` ("x0", "x1", "y0", "y1",
+    "z0", "z1": the planes x = 0, x = nx, ...), which are free slip, and the
+    obstacle faces when ``slip_obstacles``.
     """
     removed = tuple(sorted(tuple(int(v) for v in c) for c in removed))
     rset = set(removed)
@@ -113,7 +120,13 @@ def box_of_cubes(nx: int, ny: int, nz: int, removed=(), outflow_x_max: bool = Fa
             fv = [int(v) for m, v in enumerate(tets[t]) if m != f]
             if faces[tuple(sorted(fv))] == 1:
                 on_out = outflow_x_max and all(verts[v, 0] == nx for v in fv)
-                flags[t, f] = BC_OUTFLOW if on_out else BC_DIRICHLET
+                side = None
+                for a, ext in enumerate((nx, ny, nz)):
+                    for end, val in ((0, 0), (1, ext)):
+                        if all(verts[v, a] == val for v in fv):
+                            side = "xyz"[a] + str(end)
+                slip = (side in slip_sides) if side is not None else slip_obstacles
+                flags[t, f] = BC_OUTFLOW if on_out else (BC_SLIP if slip else BC_DIRICHLET)
     return MacroMesh(vertices=verts, tets=tets, bc_flags=flags, cells=(nx, ny, nz),
                      spacing=1.0, origin=np.zeros(3), removed=removed)
 
@@ -148,6 +161,20 @@ def channel_obstacles(seed: int = 0, nx: int = 16, ny: int = 4, nz: int = 4, fra
 def obstacle_channel(seed: int = 0, nx: int = 16, ny: int = 4, nz: int = 4, fraction: float = 0.1) -> MacroMesh:
     """16x4x4 channel of unit cubes with seeded obstacles, do-nothing outflow on x = nx."""
     return box_of_cubes(nx, ny, nz, removed=channel_obstacles(seed, nx, ny, nz, fraction), outflow_x_max=True)
+
+
+def slip_channel(seed: int = 0, nx: int = 16, ny: int = 4, nz: int = 4, fraction: float = 0.1) -> MacroMesh:
+    """The obstacle channel with free-slip obstacle faces and no-slip walls:
+    the synthetic stand-in for the sphere bed with free-slip spheres of
+    Sec. 6 (inflow on x = 0, do-nothing outflow on x = nx)."""
+    return box_of_cubes(nx, ny, nz, removed=channel_obstacles(seed, nx, ny, nz, fraction), outflow_x_max=True,
+                        slip_obstacles=True)
+
+
+def slip_cube() -> MacroMesh:
+    """The unit cube with free-slip faces x = 0 and x = 1 and Dirichlet faces
+    elsewhere (the Dirichlet faces own the shared edges)."""
+    return box_of_cubes(1, 1, 1, slip_sides=("x0", "x1"))
 
 
 # --- manufactured solution of the TME study (Sec. 5) -----------------------
