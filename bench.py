@@ -1,7 +1,7 @@
 """Benchmark: Stokes DoF solved per second to a 1e-8 relative residual.
 
 Workload (default): unit cube of 6 Kuhn tetrahedra refined to level 9
-(513^3 nodes, 535,291,902 free DoFs), manufactured smooth solution (Sec. 5),
+(513^3 nodes, 535,304,190 free DoFs), manufactured smooth solution (Sec. 5),
 viscosity 1, Dirichlet velocity, zero-mean pressure; all-at-once Uzawa
 multigrid V_var(3,3) from a zero initial guess.  One step = set the
 right-hand side from device-resident nodal inputs + solve to 1e-8 in the
@@ -9,7 +9,8 @@ FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
 the level-7 cube (8,291,838 free DoFs) under "level7".  "fmg" times full
 multigrid (Sec. 5) on the headline level, with its error ratio gamma;
-"channel_level6" times the obstacle channel (2.7e8 free DoFs) FP32+IR solve;
+"channel_level6" times the obstacle channel (2.6e8 free DoFs) FP32+IR solve
+and "slip_channel_level6" the same channel with free-slip obstacles (Sec. 6.1);
 "dform_level7" the D-operator formulation beside the Laplace form.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU oracle on a
@@ -331,6 +332,7 @@ def run_gpu(args):
     head.close()
     del head
     channel = channel_solve(pkg, args.channel_level, stream) if args.channel_level else None
+    slip_channel = channel_solve(pkg, args.channel_level, stream, slip=True) if args.channel_level else None
     dform = dform_solve(pkg, args.dform_level, stream) if args.dform_level else None
     extra = None
     if args.extra_level and args.extra_level != args.level:
@@ -360,6 +362,7 @@ def run_gpu(args):
         out[f"level{args.extra_level}"] = extra
     if channel:
         out[f"channel_level{args.channel_level}"] = channel
+        out[f"slip_channel_level{args.channel_level}"] = slip_channel
     if dform:
         out[f"dform_level{args.dform_level}"] = dform
     if rank == 0:
@@ -371,16 +374,17 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def channel_solve(pkg, level, stream, reps=3):
+def channel_solve(pkg, level, stream, reps=3, slip=False):
     """Obstacle channel (16 x 4 x 4 unit cubes, 6 seeded obstacles, inflow of
     peak 1, do-nothing outflow; the stand-in for the sphere bed of Sec. 6) at
     `level`, FP32+IR to 1e-8 from zero; coarsest level 1 with the
     tolerance-driven coarse MINRES (relative 5e-3, at most 300 iterations,
-    Sec. 3.7).  Best of `reps` device-timed set_rhs + solve steps."""
+    Sec. 3.7).  slip: free-slip obstacle faces (Sec. 6.1) instead of no-slip.
+    Best of `reps` device-timed set_rhs + solve steps."""
     import torch
 
     import workloads as W
-    ch = W.obstacle_channel()
+    ch = W.slip_channel() if slip else W.obstacle_channel()
     mesh = pkg.Mesh(ch.vertices, ch.tets, ch.bc_flags, level, coarsest_level=1, coarse_minres_max=300,
                     coarse_minres_rtol=5e-3, stream=stream.cuda_stream)
     x = mesh.node_coords()
@@ -401,7 +405,8 @@ def channel_solve(pkg, level, stream, reps=3):
     mesh.close()
     return {"free_dofs": dofs, "ms_per_step": best, "value": dofs / (best / 1e3), "unit": "DoF/s",
             "cycles": st.cycles, "rel_residual": st.rel_residual, "status": st.status,
-            "config": "16x4x4 channel, 6 obstacle cubes, coarsest level 1, coarse MINRES 5e-3 / 300"}
+            "config": "16x4x4 channel, 6 " + ("free-slip" if slip else "no-slip") +
+                      " obstacle cubes, coarsest level 1, coarse MINRES 5e-3 / 300"}
 
 
 def dform_solve(pkg, level, stream, reps=3):

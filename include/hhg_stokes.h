@@ -61,6 +61,11 @@ extern "C" {
 #define HHG_BC_AUTO 0       /* boundary face: Dirichlet */
 #define HHG_BC_DIRICHLET 1  /* prescribed velocity (Sec. 2) */
 #define HHG_BC_OUTFLOW 2    /* do-nothing boundary nu du/dn - p n = 0 (natural, Sec. 6.1) */
+#define HHG_BC_SLIP 3       /* free slip (Sec. 6.1): u . n_i = 0 with the mass-conservative normal
+                               n_i = <grad phi_i, 1> / |<grad phi_i, 1>|, and no tangential stress
+                               (the momentum rows are tested in the tangent plane only).  A node
+                               on a Dirichlet face is Dirichlet; a node whose integral vanishes
+                               (slip faces back to back) has no normal and no constraint */
 
 /* Node flag bits returned by hhg_node_flags. */
 #define HHG_NODE_ACTIVE 1   /* carries a pressure unknown */
@@ -69,6 +74,7 @@ extern "C" {
                                mesh is an affine lattice: every active node) */
 #define HHG_NODE_DIRICHLET 8
 #define HHG_NODE_OUTFLOW 16
+#define HHG_NODE_SLIP 32    /* velocity node on a free-slip face (carries HHG_NODE_IRREG) */
 
 /* Solver parameters; hhg_default_options gives the paper's UMG set-up
  * (Tab. "settings" of Sec. 3.7 and the text of Sec. 2.1, 3.5, 4.1). */
@@ -218,7 +224,8 @@ int hhg_device_bytes(const hhg_mesh* mesh, int64_t* bytes);
 int hhg_set_rhs(hhg_mesh* mesh, const double* f_nodal, const double* u_dirichlet);
 
 /* Initial iterate: u (n, 3) on velocity nodes and p (n,) on pressure nodes;
- * either may be NULL (= 0).  Call after hhg_set_rhs. */
+ * either may be NULL (= 0).  The velocity of a free-slip node is kept
+ * tangential (its normal part is dropped).  Call after hhg_set_rhs. */
 int hhg_set_initial(hhg_mesh* mesh, const double* u, const double* p);
 
 /* `count` FP64 V_var cycles on the current iterate, each followed by the

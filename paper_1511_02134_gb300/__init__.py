@@ -25,7 +25,7 @@ _LIB_PATH = os.path.join(_HERE, "_lib", "libhhg_stokes.so")
 MODE_FP64 = 0
 MODE_FP32_IR = 1
 
-NODE_ACTIVE, NODE_VFREE, NODE_IRREG, NODE_DIRICHLET, NODE_OUTFLOW = 1, 2, 4, 8, 16
+NODE_ACTIVE, NODE_VFREE, NODE_IRREG, NODE_DIRICHLET, NODE_OUTFLOW, NODE_SLIP = 1, 2, 4, 8, 16, 32
 FIELD = {"U": 0, "P": 1, "F": 2, "G": 3, "RU": 4, "RP": 5}
 OP = {"uzawa_step": 0, "vel_forward": 1, "vel_backward": 2, "vel_rhs": 3, "pres_rhs": 4,
       "pres_sweep": 5, "residual": 6, "restrict": 7, "prolong_add": 8, "coarse_solve": 9,

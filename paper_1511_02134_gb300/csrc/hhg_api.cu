@@ -471,6 +471,20 @@ void enq_ir_residual(hhg_mesh* M, bool from_update) {
   }
 }
 
+// Free slip (Sec. 6.1): after a refinement update the slip velocities of the
+// iterate are made tangential again in FP64 (the FP32 correction is
+// tangential only to FP32 rounding); fixed_point: on the finest level's
+// fixed-point iterate.
+void enq_slip_fix(hhg_mesh* M, int level, bool fixed_point) {
+  if (!M->macro.has_slip) return;
+  LevelHost& H = M->lv[level];
+  if (fixed_point)
+    launch_slip_fix_fx(M->fx, H.d64, fx_state(M), M->stream);
+  else
+    launch_slip_fix(H.d64, H.d_irr, H.nirr, M->stream);
+  M->launches += 1;
+}
+
 // FP32+IR cycle body: correction V-cycle in FP32 from zero on the FP32
 // residual, x += e (in fixed point: Q += round(e 2^s)), FP64 residual ->
 // FP32 right-hand side.  On a
@@ -484,11 +498,13 @@ void enq_cycle32(hhg_mesh* M, bool fp64_update = false) {
   if (M->opt.ir_fixed_point && !fp64_update) {
     launch_fx_update(M->fx, H.d32, fx_state(M), H.nalloc, M->stream);
     M->launches += 1;
+    enq_slip_fix(M, M->finest, true);
     enq_ir_residual(M, true);
   } else {
     // FP64 update; in fixed point the iterate is then quantized afresh
     launch_ir_update(H.d64, H.d32, M->stream);
     M->launches += 1;
+    enq_slip_fix(M, M->finest, false);
     enq_ir_residual(M, false);
   }
 }
@@ -523,6 +539,7 @@ int fx_recover_if_flagged(hhg_mesh* M) {
   LevelHost& H = M->lv[M->finest];
   const FxState st = fx_state(M);
   launch_fx_to_fp64(H.d64, M->fx, H.d32, st, true, M->stream);
+  enq_slip_fix(M, M->finest, false);
   enq_ir_residual(M, false);  // clears the flag
   M->launches += 1;
   CK(cudaGetLastError());
@@ -1222,6 +1239,7 @@ int hhg_set_initial(hhg_mesh* M, const double* u, const double* p) {
     int rc = stage_in(M, u, 3 * n);
     if (rc) return rc;
     launch_scatter(L, M->d_stage, 3, L.u, F_VFREE, M->stream);
+    enq_slip_fix(M, M->finest, false);  // a free-slip node's velocity is tangential
   }
   if (p) {
     int rc = stage_in(M, p, n);
@@ -1341,6 +1359,7 @@ int hhg_fmg_solve(hhg_mesh* M, const double* f_nodal, const double* u_dirichlet,
         enq_vcycle<float>(M, l);
         launch_ir_update(H.d64, H.d32, M->stream);
         M->launches += 3;
+        enq_slip_fix(M, l, false);
       }
       if (!M->macro.has_outflow) enq_project<double>(M, l);
     }
@@ -1708,6 +1727,7 @@ static int enqueue_op(hhg_mesh* M, int32_t level, int32_t precision, int32_t op)
         else
           launch_ir_update(M->lv[level].d64, M->lv[level].d32, M->stream);
         M->launches += 1;
+        enq_slip_fix(M, level, M->opt.ir_fixed_point != 0);
         enq_ir_residual(M, M->opt.ir_fixed_point != 0);
         break;
       case HHG_OP_CYCLE:

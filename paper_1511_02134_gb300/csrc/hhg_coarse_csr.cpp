@@ -99,6 +99,35 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
     val.push_back(v);
     ++nnz;
   };
+  // Free slip (Sec. 6.1): the unit normal of a slip node (from its class
+  // row), or null; the velocity block is then Pi (.) Pi + n n^T at slip
+  // nodes (Pi = I - n n^T) and the coupling blocks Pi B^T and B Pi, which
+  // couples the components, so the system is assembled in coupled form.
+  bool slip = false;
+  for (int32_t r = 0; r < nv && !slip; ++r) slip = (flags[lat_of[out.vidx[r]]] & F_SLIP) != 0;
+  auto normal_of = [&](int64_t pc) -> const double* {
+    const int64_t q = lat_of[pc];
+    if (!(flags[q] & F_SLIP)) return nullptr;
+    return table + (size_t)cls[q] * W_STRIDE + W_NRM;
+  };
+  auto pi = [](const double* n, int a, int b) { return (a == b ? 1.0 : 0.0) - (n ? n[a] * n[b] : 0.0); };
+  const bool coupled = table2 != nullptr || slip;
+  // 3 x 3 velocity block of row node r and its neighbour along offset o
+  auto vblock = [&](int32_t r, const Rows& w, const double* w2, int o, int64_t nb, double V[3][3]) {
+    double base[3][3];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b)
+        base[a][b] = w2 ? nuh * w2[15 * (3 * a + b) + o] : (a == b ? nuh * w.lap[o] : 0.0);
+    const double* nr = normal_of(out.vidx[r]);
+    const double* nn = normal_of(nb);
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        double s = 0.0;
+        for (int x = 0; x < 3; ++x)
+          for (int y = 0; y < 3; ++y) s += pi(nr, a, x) * base[x][y] * pi(nn, y, b);
+        V[a][b] = s + (o == 0 && nr ? nr[a] * nr[b] : 0.0);
+      }
+  };
   // velocity rows, component by component
   out.kptr.push_back(0);
   for (int d = 0; d < 3; ++d)
@@ -106,12 +135,16 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
       const int64_t pc = out.vidx[r];
       const uint16_t cl = cls[lat_of[pc]];
       const Rows w = rows_of(cl, table);
-      if (table2) {
-        const double* w2 = table2 + (size_t)cl * W2_STRIDE;
+      const double* w2 = table2 ? table2 + (size_t)cl * W2_STRIDE : nullptr;
+      const double* nr = normal_of(pc);
+      if (coupled) {
         for (int b = 0; b < 3; ++b)
           for (int o = 0; o < 15; ++o) {
             const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
-            if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)b * nv + iv[nb], nuh * w2[15 * (3 * d + b) + o]);
+            if (iv[nb] < 0) continue;
+            double V[3][3];
+            vblock(r, w, w2, o, nb, V);
+            push(out.kcol, out.kval, (int64_t)b * nv + iv[nb], V[d][b]);
           }
       } else {
         for (int o = 0; o < 15; ++o) {
@@ -121,7 +154,10 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
       }
       for (int o = 0; o < 15; ++o) {
         const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
-        if (ip[nb] >= 0) push(out.kcol, out.kval, 3 * (int64_t)nv + ip[nb], h2 * w.bt[d][o]);
+        if (ip[nb] < 0) continue;
+        double v = 0.0;
+        for (int e = 0; e < 3; ++e) v += pi(nr, d, e) * h2 * w.bt[e][o];
+        push(out.kcol, out.kval, 3 * (int64_t)nv + ip[nb], v);
       }
       if (nnz > std::numeric_limits<int32_t>::max() / 2) {
         err = "coarsest level too large for the assembled coarse solver";
@@ -129,14 +165,18 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
       }
       out.kptr.push_back((int32_t)nnz);
     }
-  // pressure rows: B u - C p
+  // pressure rows: B Pi u - C p
   for (int32_t r = 0; r < np; ++r) {
     const int64_t pc = out.pidx[r];
     const Rows w = rows_of(cls[lat_of[pc]], table);
     for (int d = 0; d < 3; ++d)
       for (int o = 0; o < 15; ++o) {
         const int64_t nb = nbr(qi[r], qj[r], qk[r], o);
-        if (iv[nb] >= 0) push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], h2 * w.b[d][o]);
+        if (iv[nb] < 0) continue;
+        const double* nn = normal_of(nb);
+        double v = 0.0;
+        for (int e = 0; e < 3; ++e) v += h2 * w.b[e][o] * pi(nn, e, d);
+        push(out.kcol, out.kval, (int64_t)d * nv + iv[nb], v);
       }
     for (int o = 0; o < 15; ++o) {
       const int64_t nb = nbr(qi[r], qj[r], qk[r], o);
@@ -149,18 +189,23 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
     out.kptr.push_back((int32_t)nnz);
     out.mass.push_back(h3 * w.lump);
   }
-  // A: the coupled D-form block (3 nv rows), or the scalar Laplacian
+  // A: the coupled block (3 nv rows: D form, free slip), or the scalar Laplacian
   nnz = 0;
   out.aptr.push_back(0);
-  if (table2) {
+  if (coupled) {
     out.coupled = 1;
     for (int d = 0; d < 3; ++d)
       for (int32_t r = 0; r < nv; ++r) {
-        const double* w2 = table2 + (size_t)cls[lat_of[out.vidx[r]]] * W2_STRIDE;
+        const uint16_t cl = cls[lat_of[out.vidx[r]]];
+        const Rows w = rows_of(cl, table);
+        const double* w2 = table2 ? table2 + (size_t)cl * W2_STRIDE : nullptr;
         for (int b = 0; b < 3; ++b)
           for (int o = 0; o < 15; ++o) {
             const int64_t nb = nbr(vi[r], vj[r], vk[r], o);
-            if (iv[nb] >= 0) push(out.acol, out.aval, (int64_t)b * nv + iv[nb], nuh * w2[15 * (3 * d + b) + o]);
+            if (iv[nb] < 0) continue;
+            double V[3][3];
+            vblock(r, w, w2, o, nb, V);
+            push(out.acol, out.aval, (int64_t)b * nv + iv[nb], V[d][b]);
           }
         out.aptr.push_back((int32_t)nnz);
       }

@@ -74,20 +74,21 @@ __global__ void k_vel_rhs(LevelDev<T> L) {
 
 // Gauss-Seidel update of the velocity nodes of one colour.  SPEC: the
 // speculative node form of small levels (hhg_node_ops.cuh).
-template <class T, bool SPEC>
+// DF: the velocity block's form (1 D form, 0 Laplace form; hhg_node_ops.cuh).
+template <class T, bool SPEC, int DF>
 __global__ void __launch_bounds__(CB * 4) k_vel_colour(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_vel_gs<SPEC>(L, node_at(L.px, L.pxy, i, j, k), inv6nuh);
+  node_vel_gs<SPEC, T, DF>(L, node_at(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
-template <class T, bool SPEC>
+template <class T, bool SPEC, int DF>
 __global__ void __launch_bounds__(CB * 4) k_vel_colour_rhs(LevelDev<T> L, int colour, T inv6nuh) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, colour, i, j, k)) return;
-  node_vel_gs_rhs<SPEC>(L, node_at(L.px, L.pxy, i, j, k), inv6nuh);
+  node_vel_gs_rhs<SPEC, T, DF>(L, node_at(L.px, L.pxy, i, j, k), inv6nuh);
 }
 
 // The last velocity colour of a step (backward colour 0) and the first
@@ -99,16 +100,16 @@ __global__ void __launch_bounds__(CB * 4) k_vel_colour_rhs(LevelDev<T> L, int co
 // the node's own pressure update.  So the sequential order is kept.
 // RU: the velocity right-hand side is read from RU (FP64 path) instead of
 // being formed at the node.
-template <class T, bool RU, bool SPEC>
+template <class T, bool RU, bool SPEC, int DF>
 __global__ void __launch_bounds__(CB * 4) k_vel_pres_colour0(LevelDev<T> L, T inv6nuh, T omega_over_6c) {
   pdl_enter();
   int i, j, k;
   if (!colour_node(L, 0, i, j, k)) return;
   const Node n = node_at(L.px, L.pxy, i, j, k);
   if (RU)
-    node_vel_gs<SPEC>(L, n, inv6nuh);
+    node_vel_gs<SPEC, T, DF>(L, n, inv6nuh);
   else
-    node_vel_gs_rhs<SPEC>(L, n, inv6nuh);
+    node_vel_gs_rhs<SPEC, T, DF>(L, n, inv6nuh);
   node_pres_gs_rhs<SPEC>(L, n, omega_over_6c);
 }
 
@@ -255,12 +256,12 @@ __global__ void __launch_bounds__(CB * 4) k_pres_colour(LevelDev<T> L, int colou
   node_pres_gs(L, node_at(L.px, L.pxy, i, j, k), omega_over_6c);
 }
 
-template <class T>
+template <class T, int DF>
 __global__ void k_residual(LevelDev<T> L) {
   pdl_enter();
   int i, j, k;
   if (!full_node(L, i, j, k)) return;
-  node_residual(L, node_at(L.px, L.pxy, i, j, k));
+  node_residual<T, DF>(L, node_at(L.px, L.pxy, i, j, k));
 }
 
 template <class T>
@@ -447,11 +448,14 @@ __global__ void k_ir_residual(LevelDev<double> X, LevelDev<float> E, double* par
       double au[3], bt[3];
       row_A(X, uu, n, fl, au);
       row_BT(X, X.p, n, fl, bt);
+      double r[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) r[d] = X.f[d][c] - au[d] - bt[d];
+      if (fl & F_SLIP) slip_project(class_row(X, c), r);
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        const double r = X.f[d][c] - au[d] - bt[d];
-        E.f[d][c] = (float)r;
-        v[0] += r * r;
+        E.f[d][c] = (float)r[d];
+        v[0] += r[d] * r[d];
       }
     } else {
 #pragma unroll
@@ -942,6 +946,48 @@ __global__ void k_ir_update(LevelDev<double> X, LevelDev<float> E) {
   }
 }
 
+// Free slip (Sec. 6.1): after a refinement update the velocity of every
+// slip node of the boundary list is made tangential again in FP64 (the FP32
+// correction is tangential only to FP32 rounding, and a normal part would
+// reach the pressure rows through B).  FP64 iterate:
+__global__ void k_slip_fix(LevelDev<double> X, const int64_t* irr, int64_t nirr) {
+  pdl_enter();
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nirr; t += stride) {
+    const int64_t e = irr[t];
+    const int64_t c = pidx(X.px, X.pxy, (int)(e & 0x1fffff), (int)((e >> 21) & 0x1fffff), (int)(e >> 42));
+    if (!(X.flags[c] & F_SLIP)) continue;
+    double v[3] = {X.u[0][c], X.u[1][c], X.u[2][c]};
+    slip_project(class_row(X, c), v);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) X.u[d][c] = v[d];
+  }
+}
+
+// The same on the fixed-point iterate (the three velocity fields share one
+// shift, so the projection acts on Q directly); a value that leaves the
+// range the fixed-point checks allow raises FX_FLAG_RESCALE (the host then
+// rebuilds and requantizes the FP64 iterate).
+__global__ void k_slip_fix_fx(FxIterate Q, LevelDev<double> X, const int64_t* irr, int64_t nirr, unsigned* flag) {
+  pdl_enter();
+  bool big = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nirr; t += stride) {
+    const int64_t e = irr[t];
+    const int64_t c = pidx(X.px, X.pxy, (int)(e & 0x1fffff), (int)((e >> 21) & 0x1fffff), (int)(e >> 42));
+    if (!(X.flags[c] & F_SLIP)) continue;
+    double v[3] = {(double)Q.u[0][c], (double)Q.u[1][c], (double)Q.u[2][c]};
+    slip_project(class_row(X, c), v);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const long long q = llrint(v[d]);
+      big |= (q < 0 ? -q : q) >= (1ll << 55);
+      Q.u[d][c] = q;
+    }
+  }
+  if (big) atomicOr(flag, FX_FLAG_RESCALE);
+}
+
 // ---- layout conversion ---------------------------------------------------------------------
 
 __global__ void k_scatter(LevelDev<double> L, const double* src, int ncomp, double* d0, double* d1, double* d2,
@@ -1061,10 +1107,15 @@ void launch_vel_rhs(const LevelDev<T>& L, cudaStream_t s) {
 template <class T>
 void launch_vel_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
   const T inv = (T)(1.0 / (6.0 * (double)L.nuh));
-  if (spec_level(L))
-    launch_k(k_vel_colour<T, true>, colour_grid(L), colour_block(L), s, L, colour, inv);
+  const bool sp = spec_level(L), df = L.wt2 != nullptr;
+  if (sp && df)
+    launch_k(k_vel_colour<T, true, 1>, colour_grid(L), colour_block(L), s, L, colour, inv);
+  else if (sp)
+    launch_k(k_vel_colour<T, true, 0>, colour_grid(L), colour_block(L), s, L, colour, inv);
+  else if (df)
+    launch_k(k_vel_colour<T, false, 1>, colour_grid(L), colour_block(L), s, L, colour, inv);
   else
-    launch_k(k_vel_colour<T, false>, colour_grid(L), colour_block(L), s, L, colour, inv);
+    launch_k(k_vel_colour<T, false, 0>, colour_grid(L), colour_block(L), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
@@ -1075,10 +1126,15 @@ void launch_vel_colour_rhs(const LevelDev<T>& L, int colour, cudaStream_t s) {
       return;
     }
   }
-  if (spec_level(L))
-    launch_k(k_vel_colour_rhs<T, true>, colour_grid(L), colour_block(L), s, L, colour, inv);
+  const bool sp = spec_level(L), df = L.wt2 != nullptr;
+  if (sp && df)
+    launch_k(k_vel_colour_rhs<T, true, 1>, colour_grid(L), colour_block(L), s, L, colour, inv);
+  else if (sp)
+    launch_k(k_vel_colour_rhs<T, true, 0>, colour_grid(L), colour_block(L), s, L, colour, inv);
+  else if (df)
+    launch_k(k_vel_colour_rhs<T, false, 1>, colour_grid(L), colour_block(L), s, L, colour, inv);
   else
-    launch_k(k_vel_colour_rhs<T, false>, colour_grid(L), colour_block(L), s, L, colour, inv);
+    launch_k(k_vel_colour_rhs<T, false, 0>, colour_grid(L), colour_block(L), s, L, colour, inv);
 }
 template <class T>
 void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
@@ -1091,14 +1147,26 @@ void launch_vel_pres_colour0(const LevelDev<T>& L, bool ru, cudaStream_t s) {
       return;
     }
   }
-  if (ru && sp)
-    launch_k(k_vel_pres_colour0<T, true, true>, colour_grid(L), colour_block(L), s, L, inv, w);
-  else if (ru)
-    launch_k(k_vel_pres_colour0<T, true, false>, colour_grid(L), colour_block(L), s, L, inv, w);
-  else if (sp)
-    launch_k(k_vel_pres_colour0<T, false, true>, colour_grid(L), colour_block(L), s, L, inv, w);
-  else
-    launch_k(k_vel_pres_colour0<T, false, false>, colour_grid(L), colour_block(L), s, L, inv, w);
+  auto go = [&](auto kernel) { launch_k(kernel, colour_grid(L), colour_block(L), s, L, inv, w); };
+  if (L.wt2) {
+    if (ru && sp)
+      go(k_vel_pres_colour0<T, true, true, 1>);
+    else if (ru)
+      go(k_vel_pres_colour0<T, true, false, 1>);
+    else if (sp)
+      go(k_vel_pres_colour0<T, false, true, 1>);
+    else
+      go(k_vel_pres_colour0<T, false, false, 1>);
+  } else {
+    if (ru && sp)
+      go(k_vel_pres_colour0<T, true, true, 0>);
+    else if (ru)
+      go(k_vel_pres_colour0<T, true, false, 0>);
+    else if (sp)
+      go(k_vel_pres_colour0<T, false, true, 0>);
+    else
+      go(k_vel_pres_colour0<T, false, false, 0>);
+  }
 }
 
 template <class T>
@@ -1126,7 +1194,10 @@ void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
 }
 template <class T>
 void launch_residual(const LevelDev<T>& L, cudaStream_t s) {
-  launch_k(k_residual<T>, full_grid(L), dim3(FX, FY), s, L);
+  if (L.wt2)
+    launch_k(k_residual<T, 1>, full_grid(L), dim3(FX, FY), s, L);
+  else
+    launch_k(k_residual<T, 0>, full_grid(L), dim3(FX, FY), s, L);
 }
 template <class T>
 void launch_restrict(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s) {
@@ -1218,6 +1289,12 @@ void launch_fx_to_fp64(const LevelDev<double>& x, const FxIterate& q, const Leve
   launch_k(k_fx_to_fp64, flat_blocks(x.nalloc), 256, s, x, q, e, (const int*)st.exp, recover ? 1 : 0);
 }
 
+void launch_slip_fix(const LevelDev<double>& x, const int64_t* irr, int64_t nirr, cudaStream_t s) {
+  launch_k(k_slip_fix, flat_blocks(nirr), 256, s, x, irr, nirr);
+}
+void launch_slip_fix_fx(const FxIterate& q, const LevelDev<double>& x, const FxState& st, cudaStream_t s) {
+  launch_k(k_slip_fix_fx, flat_blocks(st.nirr), 256, s, q, x, st.irr, st.nirr, st.flag);
+}
 void launch_ir_update(const LevelDev<double>& x, const LevelDev<float>& e, cudaStream_t s) {
   launch_k(k_ir_update, flat_blocks(x.nalloc), 256, s, x, e);
 }

@@ -150,6 +150,12 @@ constexpr unsigned FX_FLAG_RESCALE = 2u;  // the residual found the iterate unfi
 // true: Q comes from launch_fx_update and is checked first.
 void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,
                            bool from_update, double* partial, double* out, cudaStream_t s);
+// Free slip: the velocity of the slip nodes among the listed boundary nodes
+// (irr: lattice coordinates as in FxState::irr) made tangential in FP64, on
+// the FP64 iterate or on the fixed-point one (FX_FLAG_RESCALE if a value
+// leaves the checked range).
+void launch_slip_fix(const LevelDev<double>& x, const int64_t* irr, int64_t nirr, cudaStream_t s);
+void launch_slip_fix_fx(const FxIterate& q, const LevelDev<double>& x, const FxState& st, cudaStream_t s);
 // Q += round(e 2^s) over the nalloc padded positions.
 void launch_fx_update(const FxIterate& q, const LevelDev<float>& e, const FxState& st, int64_t nalloc, cudaStream_t s);
 // x = Q 2^-s, or (recover) the iterate before the last update + e in FP64.

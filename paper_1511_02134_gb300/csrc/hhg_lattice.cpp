@@ -205,7 +205,7 @@ int build_macro_lattice(const double* V, int64_t nv, const int32_t* T, int64_t n
     const int64_t t = tf / 4;
     const int f = (int)(tf % 4);
     const uint8_t code = bc ? bc[tf] : (uint8_t)HHG_BC_AUTO;
-    if (code > HHG_BC_OUTFLOW) {
+    if (code > HHG_BC_SLIP) {
       err = "unknown boundary flag";
       return HHG_EINVAL;
     }
@@ -216,8 +216,9 @@ int build_macro_lattice(const double* V, int64_t nv, const int32_t* T, int64_t n
         for (int a = 0; a < 3; ++a) bf.v[k][a] = L[T[4 * t + m]][a];
         ++k;
       }
-    bf.flag = code == HHG_BC_OUTFLOW ? 2 : 1;
+    bf.flag = code == HHG_BC_OUTFLOW ? 2 : (code == HHG_BC_SLIP ? 3 : 1);
     if (bf.flag == 2) out.has_outflow = true;
+    if (bf.flag == 3) out.has_slip = true;
     // physical edge vectors of the face (H basis times the lattice differences)
     auto phys = [&](const int64_t* d, double* x) {
       for (int a = 0; a < 3; ++a) {
@@ -324,9 +325,10 @@ void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
     if (k0 < k1) th.emplace_back(work, k0, k1);
   }
   for (auto& x : th) x.join();
-  // boundary faces: Dirichlet first, then outflow
+  // boundary faces: Dirichlet, outflow, free slip; a Dirichlet face wins on
+  // shared edges and corners
   for (const BoundaryFace& bf : m.bfaces) {
-    const uint8_t bit = bf.flag == 1 ? F_DIR : F_OUT;
+    const uint8_t bit = bf.flag == 1 ? F_DIR : (bf.flag == 2 ? F_OUT : F_SLIP);
     for_face_nodes(bf, level, [&](int64_t x, int64_t y, int64_t z) {
       flags[x + sh.nx * y + nxy * z] |= bit;
     });
@@ -334,8 +336,9 @@ void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
   const int64_t n = sh.n();
   for (int64_t i = 0; i < n; ++i) {
     uint8_t f = flags[i];
-    if (f & F_DIR) f &= (uint8_t)~F_OUT;
+    if (f & F_DIR) f &= (uint8_t)~(F_OUT | F_SLIP);
     if ((f & F_ACT) && !(f & F_DIR)) f |= F_VFREE;
+    if (!(f & F_VFREE)) f &= (uint8_t)~F_SLIP;
     flags[i] = f;
   }
 }
@@ -409,6 +412,29 @@ void class_rows(const MacroLattice& mac, uint32_t pattern, double* w) {
       w[W_LUMP] += vol / 24.0;
     }
   }
+  if (pattern & SLIP_CLASS_BIT) {
+    // <grad phi, 1> = -(B^T 1): minus the sum of the B^T row weights
+    double n[3], nn = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      n[d] = 0.0;
+      for (int o = 0; o < 15; ++o) n[d] -= w[W_BT + 15 * d + o];
+      nn += n[d] * n[d];
+    }
+    nn = std::sqrt(nn);
+    // zero where free-slip faces meet back to back (the entries are O(1) at
+    // unit spacing, so the cancellation leaves rounding only)
+    for (int d = 0; d < 3; ++d) w[W_NRM + d] = nn > 1e-12 ? n[d] / nn : 0.0;
+    w[W_SLIP] = 1.0;
+  }
+}
+
+// Unit normal of a class from its pattern (the integral of the hat
+// function's gradient over the active incident tetrahedra); zero when it
+// vanishes.
+void class_normal(const MacroLattice& mac, uint32_t pattern, double n[3]) {
+  std::vector<double> w(W_STRIDE);
+  class_rows(mac, pattern | SLIP_CLASS_BIT, w.data());
+  for (int d = 0; d < 3; ++d) n[d] = w[W_NRM + d];
 }
 
 // D-operator rows of one class: per active tetrahedron, with the centre the
@@ -466,6 +492,42 @@ void class_rows_d(const MacroLattice& mac, uint32_t pattern, double* w) {
       const int r1 = (cb + 1) % 3, r2 = (cb + 2) % 3, c1 = (ra + 1) % 3, c2 = (ra + 2) % 3;
       w[W2_DINV + 3 * ra + cb] = (D[r1][c1] * D[r2][c2] - D[r1][c2] * D[r2][c1]) / det;
     }
+  if (!(pattern & SLIP_CLASS_BIT)) return;
+  double n[3];
+  class_normal(mac, pattern, n);
+  if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return;  // no normal: no constraint
+  // orthonormal tangent basis t1, t2: t1 from the axis least aligned with n
+  int e = 0;
+  for (int a = 1; a < 3; ++a)
+    if (std::fabs(n[a]) < std::fabs(n[e])) e = a;
+  double t1[3] = {0, 0, 0}, t2[3];
+  t1[e] = 1.0;
+  const double dn = n[e];
+  for (int a = 0; a < 3; ++a) t1[a] -= dn * n[a];
+  const double l1 = std::sqrt(t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]);
+  for (int a = 0; a < 3; ++a) t1[a] /= l1;
+  t2[0] = n[1] * t1[2] - n[2] * t1[1];
+  t2[1] = n[2] * t1[0] - n[0] * t1[2];
+  t2[2] = n[0] * t1[1] - n[1] * t1[0];
+  const double* T[2] = {t1, t2};
+  // M = T^T D T (2 x 2), Z = T M^-1 T^T
+  double M[2][2];
+  for (int x = 0; x < 2; ++x)
+    for (int y = 0; y < 2; ++y) {
+      double s = 0.0;
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) s += T[x][a] * D[a][b] * T[y][b];
+      M[x][y] = s;
+    }
+  const double dm = M[0][0] * M[1][1] - M[0][1] * M[1][0];
+  const double Mi[2][2] = {{M[1][1] / dm, -M[0][1] / dm}, {-M[1][0] / dm, M[0][0] / dm}};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) {
+      double s = 0.0;
+      for (int x = 0; x < 2; ++x)
+        for (int y = 0; y < 2; ++y) s += T[x][a] * Mi[x][y] * T[y][b];
+      w[W2_DINV + 3 * a + b] = s;
+    }
 }
 
 }  // namespace
@@ -488,7 +550,7 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
       for (int i = 0; i < sh.nx; ++i) {
         const int64_t q = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
         if (!(flags[q] & F_IRR)) continue;
-        uint32_t pattern = 0;
+        uint32_t pattern = (flags[q] & F_SLIP) ? SLIP_CLASS_BIT : 0u;
         int bit = 0;
         for (int c = 0; c < 8; ++c) {
           const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;

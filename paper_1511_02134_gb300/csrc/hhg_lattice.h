@@ -11,7 +11,7 @@ namespace hhg {
 
 struct BoundaryFace {
   int64_t v[3][3];   // macro lattice coordinates of the three vertices
-  uint8_t flag;      // 1 Dirichlet, 2 outflow
+  uint8_t flag;      // 1 Dirichlet, 2 outflow, 3 free slip
   double normal[3];  // outward unit normal
   double area;       // area in physical units
 };
@@ -31,6 +31,7 @@ struct MacroLattice {
   std::vector<uint8_t> mask;         // per macro cell: bit s = Kuhn path s present
   std::vector<BoundaryFace> bfaces;  // faces of the macro mesh boundary
   bool has_outflow = false;
+  bool has_slip = false;
 };
 
 // Validate and convert a macro mesh.  Returns 0 or a negative HHG_E* code
@@ -56,8 +57,9 @@ void outflow_weights(const MacroLattice& m, int level, double* w);
 int active_incident(const MacroLattice& m, int level, int i, int j, int k);
 
 // Stencil classes of the nodes flagged F_IRR.  A node's class is the set of
-// its active incident tetrahedra (a 24-bit pattern); all nodes of a class
-// have the same assembled rows.  For every class the table holds, in
+// its active incident tetrahedra (a 24-bit pattern) and, in bit 24, whether
+// it is a free-slip node (F_SLIP); all nodes of a class have the same
+// assembled rows.  For every class the table holds, in
 // doubles and at unit lattice spacing, the 15-point row weights (offset
 // order of STENCIL_OFFSETS) of:
 //   [W_LAP, +15)   sum_T int grad phi_i . grad phi_j     (A = nu h *, C = delta h_T^2 h *)
@@ -65,15 +67,19 @@ int active_incident(const MacroLattice& m, int level, int i, int j, int k);
 //   [W_BT + 15 d)  B_d^T row                             (times h^2)
 //   [W_M, +15)     consistent mass row                   (times h^3)
 //   [W_LUMP]       lumped mass int phi_i                 (times h^3)
+//   [W_NRM, +3)    free-slip classes: unit normal <grad phi_i, 1> / |.|
+//   [W_SLIP]       1 for free-slip classes
 // cls receives the class of every lattice node (0 for nodes that are not
 // F_IRR; classes of F_IRR nodes start at 1), table receives
 // (n_classes + 1) * W_STRIDE doubles (class 0 unused).
 // Offsets of the 15-point pattern: 0 = centre, 1..7 = +o, 8..14 = -o over the
 // Kuhn directions o = e1, e2, e3, e1+e2, e2+e3, e1+e3, e1+e2+e3.
 extern const int STENCIL_OFFSETS[15][3];
-// patterns (optional) receives the set of active incident tetrahedra of each
-// class (bit per (cell corner, Kuhn path) pair; class 0: all 24).
+// patterns (optional) receives the key of each class: the set of active
+// incident tetrahedra (bit per (cell corner, Kuhn path) pair; class 0: all
+// 24) and SLIP_CLASS_BIT for free-slip classes.
 constexpr uint32_t FULL_STAR_PATTERN = (1u << 24) - 1;
+constexpr uint32_t SLIP_CLASS_BIT = 1u << 24;
 void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
                      std::vector<double>& table, int& n_classes, std::string& err,
                      std::vector<uint32_t>* patterns = nullptr);
@@ -96,7 +102,7 @@ namespace hhg {
 // Zero weights are not stored.
 struct CoarseMatrix {
   int32_t nv = 0, np = 0;
-  int32_t coupled = 0;  // D form: A is the coupled 3 nv x 3 nv velocity block (rows d nv + r)
+  int32_t coupled = 0;  // D form or free slip: A is the coupled 3 nv x 3 nv velocity block (rows d nv + r)
   std::vector<int32_t> vidx, pidx;  // padded lattice index of each velocity / pressure unknown
   std::vector<int32_t> kptr, kcol;
   std::vector<double> kval;
@@ -109,7 +115,9 @@ struct CoarseMatrix {
 // px, pxy the padded strides of the level's fields (ghost frame of one node).
 // Returns 0, or HHG_EINVAL when the matrix would not fit 32-bit indices.
 // table2 (D form, else null): the D-operator rows per class; the velocity
-// block of K and A are then the coupled a_2 rows.
+// block of K and A are then the coupled a_2 rows.  Free-slip nodes (F_SLIP)
+// take the velocity block Pi (.) Pi + n n^T and the coupling blocks Pi B^T,
+// B Pi (Pi = I - n n^T with the class normal), also in coupled form.
 int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t* flags, const uint16_t* cls,
                     const double* table, double nuh, double c, double h2, double h3, CoarseMatrix& out,
                     std::string& err, const double* table2 = nullptr);

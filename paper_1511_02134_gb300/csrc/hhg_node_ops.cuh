@@ -7,6 +7,26 @@
 
 namespace hhg {
 
+// Velocity block of the level: DF = 1 the D form (coupled 3 x 3 node blocks),
+// 0 the Laplace form, -1 read from the level (L.wt2 set in the D form).  The
+// grid kernels are instantiated per form, so that a kernel of one form does
+// not carry the other form's registers.
+template <int DF, class T>
+__device__ __forceinline__ bool d_form(const LevelDev<T>& L) {
+  return DF < 0 ? L.wt2 != nullptr : DF == 1;
+}
+
+// Free slip (Sec. 6.1): the tangential part v - n (n . v) of a velocity value
+// or residual at a node whose class row w is a free-slip class.
+template <class T>
+__device__ __forceinline__ void slip_project(const T* w, T v[3]) {
+  if (w[W_SLIP] != (T)0) {
+    const T s = (w[W_NRM] * v[0] + w[W_NRM + 1] * v[1]) + w[W_NRM + 2] * v[2];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v[d] -= s * w[W_NRM + d];
+  }
+}
+
 // RU = F - B^T P (velocity nodes).
 template <class T>
 __device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, const Node& n) {
@@ -31,9 +51,9 @@ __device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, const Node& n
 
 // u_d <- u_d + (RU_d - (A u_d)) / A_ii  (one node of the current colour);
 // in the D form the node's three components at once with its 3 x 3 block.
-template <bool SPEC, class T, class V>
+template <bool SPEC, class T, class V, int DF = -1>
 __device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, const V* u, T inv6nuh) {
-  if (L.wt2) {
+  if (d_form<DF>(L)) {
     if (!(L.flags[c] & F_VFREE)) return;
     const T r[3] = {L.r[0][c], L.r[1][c], L.r[2][c]};
     T out[3];
@@ -63,18 +83,22 @@ __device__ __forceinline__ void node_vel_gs_v(const LevelDev<T>& L, int64_t c, c
     return;
   }
   const T* w = class_row(L, c);
+  T out[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     T dg, of;
     irr_lap_parts_v<T>(u[d], w, dg, of);
-    L.u[d][c] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
+    out[d] = (L.r[d][c] - L.nuh * of) / (L.nuh * dg);
   }
+  slip_project(w, out);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) L.u[d][c] = out[d];
 }
 
-template <bool SPEC, class T>
+template <bool SPEC, class T, int DF = -1>
 __device__ __forceinline__ void node_vel_gs(const LevelDev<T>& L, const Node& n, T inv6nuh) {
   const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
-  node_vel_gs_v<SPEC>(L, n.c, u, inv6nuh);
+  node_vel_gs_v<SPEC, T, GNb<T>, DF>(L, n.c, u, inv6nuh);
 }
 
 // New velocity of a regular node from its right-hand side f (3 values) and
@@ -101,32 +125,47 @@ __device__ __forceinline__ void vel_irr_value(const LevelDev<T>& L, const T* w, 
     irr_lap_parts_v<T>(u[d], w, dg, of);
     out[d] = ((f[d] - bt[d]) - L.nuh * of) / (L.nuh * dg);
   }
+  slip_project(w, out);
 }
 
-// Regular-node velocity update with f - B^T p formed at the node.
+// Regular-node velocity update with f - B^T p formed at the node.  The same
+// arithmetic as vel_regular_value, with f read where it is used: loading it
+// ahead of the stencil keeps three more values live across the neighbour
+// loads and costs the grid kernels a resident block per SM.
 template <class T, class V>
 __device__ __forceinline__ void vel_rhs_regular(const LevelDev<T>& L, int64_t c, const V* u, const V& p, T inv6nuh,
                                                 T reg[3]) {
-  const T f[3] = {L.f[0][c], L.f[1][c], L.f[2][c]};
-  vel_regular_value(L, f, u, p, inv6nuh, reg);
+  T dv[3];
+  div12_all(diff7v<T>(p), dv);
+  const T s = -L.h2 * (T)(1.0 / 12.0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) reg[d] = ((L.f[d][c] - s * dv[d]) + L.nuh * nb6v(u[d])) * inv6nuh;
 }
 
-// Velocity update of a boundary node (class rows) with f - B^T p formed at the node.
+// Velocity update of a boundary node (class rows) with f - B^T p formed at
+// the node (the arithmetic of vel_irr_value).
 template <class T, class V>
 __device__ __forceinline__ void vel_rhs_irr(const LevelDev<T>& L, int64_t c, const V* u, const V& p) {
-  const T f[3] = {L.f[0][c], L.f[1][c], L.f[2][c]};
-  T out[3];
-  vel_irr_value(L, class_row(L, c), f, u, p, out);
+  const T* w = class_row(L, c);
+  T bt[3], out[3];
+  row_BT_v(L, p, w, F_IRR, bt);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    T dg, of;
+    irr_lap_parts_v<T>(u[d], w, dg, of);
+    out[d] = ((L.f[d][c] - bt[d]) - L.nuh * of) / (L.nuh * dg);
+  }
+  slip_project(w, out);
 #pragma unroll
   for (int d = 0; d < 3; ++d) L.u[d][c] = out[d];
 }
 
 // Same update with the right-hand side f - B^T p formed at the node (p does
 // not change during the velocity sweeps, Sec. 3.3), RU is not touched.
-template <bool SPEC, class T, class V>
+template <bool SPEC, class T, class V, int DF = -1>
 __device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t c, const V* u, const V& p,
                                                   T inv6nuh) {
-  if (L.wt2) {
+  if (d_form<DF>(L)) {
     const uint8_t fl = L.flags[c];
     if (!(fl & F_VFREE)) return;
     T bt[3];
@@ -157,10 +196,10 @@ __device__ __forceinline__ void node_vel_gs_rhs_v(const LevelDev<T>& L, int64_t 
   vel_rhs_irr(L, c, u, p);
 }
 
-template <bool SPEC, class T>
+template <bool SPEC, class T, int DF = -1>
 __device__ __forceinline__ void node_vel_gs_rhs(const LevelDev<T>& L, const Node& n, T inv6nuh) {
   const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
-  node_vel_gs_rhs_v<SPEC>(L, n.c, u, gnb(L.p, n, L.px, L.pxy), inv6nuh);
+  node_vel_gs_rhs_v<SPEC, T, GNb<T>, DF>(L, n.c, u, gnb(L.p, n, L.px, L.pxy), inv6nuh);
 }
 
 // RP = B U - G (pressure nodes).
@@ -260,19 +299,20 @@ __device__ __forceinline__ void node_pres_gs_rhs(const LevelDev<T>& L, const Nod
 
 // (RU, RP) = (F, G) - K (U, P) at one node, returned in r[0..3]; zero for
 // unknowns the node does not carry.
-template <class T, class V>
+template <class T, class V, int DF = -1>
 __device__ __forceinline__ void node_residual_v(const LevelDev<T>& L, int64_t c, uint8_t fl, const V* u, const V& p,
                                                 T r[4]) {
   const T* w = row_of(L, c, fl);
   if (fl & F_VFREE) {
     T au[3], bt[3];
-    if (L.wt2)
+    if (d_form<DF>(L))
       row_A2_v(L, u, d_row(L, c), au);
     else
       row_A_v(L, u, w, fl, au);
     row_BT_v(L, p, w, fl, bt);
 #pragma unroll
     for (int d = 0; d < 3; ++d) r[d] = L.f[d][c] - au[d] - bt[d];
+    if (fl & F_SLIP) slip_project(w, r);
   } else {
 #pragma unroll
     for (int d = 0; d < 3; ++d) r[d] = (T)0;
@@ -280,13 +320,13 @@ __device__ __forceinline__ void node_residual_v(const LevelDev<T>& L, int64_t c,
   r[3] = (fl & F_ACT) ? L.g[c] - row_B_v(L, u, w, fl) + row_C_v(L, p, w, fl) : (T)0;
 }
 
-template <class T>
+template <class T, int DF = -1>
 __device__ __forceinline__ void node_residual(const LevelDev<T>& L, const Node& n) {
   const int64_t c = n.c;
   const uint8_t fl = L.flags[c];
   const GNb<T> u[3] = {gnb(L.u[0], n, L.px, L.pxy), gnb(L.u[1], n, L.px, L.pxy), gnb(L.u[2], n, L.px, L.pxy)};
   T r[4];
-  node_residual_v(L, c, fl, u, gnb(L.p, n, L.px, L.pxy), r);
+  node_residual_v<T, GNb<T>, DF>(L, c, fl, u, gnb(L.p, n, L.px, L.pxy), r);
 #pragma unroll
   for (int d = 0; d < 3; ++d) L.r[d][c] = r[d];
   L.rp[c] = r[3];
@@ -318,6 +358,7 @@ __device__ __forceinline__ void node_restrict(const LevelDev<T>& Lf, const Level
     s[q] = x(0, 0, 0) + (T)0.5 * acc;
   }
   const bool vf = fl & F_VFREE, ac = fl & F_ACT;
+  if (fl & F_SLIP) slip_project(class_row(Lc, cc), s);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     Lc.f[d][cc] = vf ? s[d] : (T)0;
@@ -339,12 +380,15 @@ __device__ __forceinline__ void node_prolong_add(const LevelDev<T>& Lf, const Le
   const bool mid = (a | b | e) != 0;
   const int64_t c1 = pidx(Lc.px, Lc.pxy, I + a, J + b, K + e);
   if (fl & F_VFREE) {
+    T v[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const T* x = Lc.u[d];
-      const T v = mid ? (T)0.5 * (x[c0] + x[c1]) : x[c0];
-      Lf.u[d][cf] += v;
+      v[d] = mid ? (T)0.5 * (x[c0] + x[c1]) : x[c0];
     }
+    if (fl & F_SLIP) slip_project(class_row(Lf, cf), v);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) Lf.u[d][cf] += v[d];
   }
   const T v = mid ? (T)0.5 * (Lc.p[c0] + Lc.p[c1]) : Lc.p[c0];
   Lf.p[cf] += v;

@@ -426,6 +426,7 @@ __device__ void r_restrict(const Res<T>& R, int q) {
     }
     const uint8_t fl = C.flags[cc];
     const bool vf = fl & F_VFREE, ac = fl & F_ACT;
+    if (fl & F_SLIP) slip_project(class_row(C, cc), s);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       C.f[d][cc] = vf ? s[d] : (T)0;
@@ -482,11 +483,12 @@ __device__ void r_prolong(const Res<T>& R, int q) {
       c1 = pidx(Lc.px, Lc.pxy, I + a, J + b, K + e);
     }
     if (fl & F_VFREE) {
+      T v[3];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const T v = mid ? (T)0.5 * (cu0[d][c0] + cu1[d][c1]) : cu0[d][c0];
-        F.u[d][cf] += v;
-      }
+      for (int d = 0; d < 3; ++d) v[d] = mid ? (T)0.5 * (cu0[d][c0] + cu1[d][c1]) : cu0[d][c0];
+      if (fl & F_SLIP) slip_project(class_row(F, cf), v);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) F.u[d][cf] += v[d];
     }
     const T v = mid ? (T)0.5 * (cu0[3][c0] + cu1[3][c1]) : cu0[3][c0];
     F.p[cf] += v;

@@ -54,6 +54,10 @@ def macro_by_name(name):
         return W.obstacle_channel()
     if name == "sheared":
         return W.sheared_cube()
+    if name == "slip_channel":
+        return W.slip_channel()
+    if name == "slip_cube":
+        return W.slip_cube()
     if name == "partial":
         # two unit cubes with two Kuhn tetrahedra removed and one listed along
         # its reversed path: partially filled macro cells, irregular rows inside

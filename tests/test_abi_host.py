@@ -33,7 +33,8 @@ def test_exports_every_declared_symbol(pkg):
 
 
 @pytest.mark.parametrize("name,levels", [("cube", (0, 1, 2, 3)), ("channel", (0, 1, 2)), ("partial", (1, 2, 3)),
-                                         ("sheared", (1, 2, 3))])
+                                         ("sheared", (1, 2, 3)), ("slip_channel", (0, 1, 2)),
+                                         ("slip_cube", (1, 2, 3))])
 def test_classification_matches_oracle(pkg, name, levels):
     macro = macro_by_name(name)
     affine = macro.basis is not None
@@ -50,6 +51,10 @@ def test_classification_matches_oracle(pkg, name, levels):
         irr[lat[(cnt < 24) | affine]] = True   # affine lattices: every active node takes class rows
         out = np.zeros(len(fl), bool)
         out[lat[r.on_outflow]] = True
+        slip = np.zeros(len(fl), bool)
+        slip[lat[r.on_slip & r.free_velocity]] = True
+        assert np.array_equal(slip, (fl & pkg.NODE_SLIP) > 0)
+        assert np.all((fl[slip] & pkg.NODE_IRREG) > 0)
         assert np.array_equal(act, (fl & pkg.NODE_ACTIVE) > 0)
         assert np.array_equal(vf, (fl & pkg.NODE_VFREE) > 0)
         assert np.array_equal(irr, (fl & pkg.NODE_IRREG) > 0)

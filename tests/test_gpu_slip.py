@@ -1,0 +1,186 @@
+"""GPU free-slip boundaries (Sec. 6.1) against the oracle, element by element
+through the C ABI, in the Laplace and the D form: the operator with the
+tangential momentum rows, the right-hand side, Uzawa steps (FP64 1e-11,
+FP32 1e-5), residual, transfers with the coarse and fine normals, the coupled
+coarse solve, V-cycle iterates (launched and cluster-resident levels), and
+whole FP64 and FP32+IR solves with tangential slip velocities and the exact
+flux balance of the mass-conservative normals."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint, multigrid as MG
+from tests.helpers import lattice_index, macro_by_name, rel_err, u_from_lattice, u_to_lattice, p_to_lattice, p_from_lattice
+from tests.test_gpu_parity import TOL32, TOL64, _load, _p_err, _read_up
+
+pytestmark = pytest.mark.gpu
+
+FORMS = {"laplace": 0, "D": 1}
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    import __graft_entry__ as g
+    g.build()
+    import paper_1511_02134_gb300 as p
+    return p
+
+
+def _pair(pkg, name, form, finest, coarsest, mx=5):
+    macro = macro_by_name(name)
+    mesh = pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, finest, coarsest_level=coarsest,
+                    coarse_minres_max=mx, operator_form=FORMS[form])
+    H = MG.build_hierarchy(macro, finest, coarsest=coarsest, opt=MG.Options(coarse_minres_max=mx), form=form)
+    return macro, mesh, H
+
+
+def _state(H, l, seed):
+    """Random iterate and velocity right-hand side, both tangential at slip
+    nodes (the oracle's system takes f in the range of Pi, as its rhs and
+    restriction produce it; the kernels test the momentum rows in the tangent
+    plane whatever f holds), and g made consistent on meshes without outflow."""
+    L = H.levels[l]
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal(L.n_p)
+    if L.pure_dirichlet:
+        g -= g.mean()
+    return (L.proj(rng.standard_normal((3, L.n_u))), rng.standard_normal(L.n_p),
+            L.proj(rng.standard_normal((3, L.n_u))), g)
+
+
+def _data(name, x):
+    if name == "slip_channel":
+        return np.zeros_like(x), W.channel_inflow(x)
+    return W.manufactured_forcing(x), W.manufactured_velocity(x)
+
+
+def _normal_part(L, u):
+    return float(np.abs(np.sum(u[:, L.slip].T * L.normals, axis=1)).max()) if len(L.slip) else 0.0
+
+
+@pytest.mark.parametrize("form", ["laplace", "D"])
+@pytest.mark.parametrize("name,level", [("slip_channel", 2), ("slip_cube", 3)])
+def test_operator_rhs_smoother_residual(pkg, name, level, form):
+    macro, mesh, H = _pair(pkg, name, form, level, level - 1)
+    L = H.levels[level]
+    assert len(L.slip) > 0
+    dims = mesh.dims()
+    lat = lattice_index(L, dims)
+    fl = mesh.node_flags()
+    slip = np.zeros(len(fl), bool)
+    slip[lat[L.free[L.slip]]] = True
+    assert np.array_equal(slip, (fl & pkg.NODE_SLIP) > 0)
+    u, p, _, _ = _state(H, level, 51)
+    ku, kp = mesh.apply_operator(u_to_lattice(L, dims, u), p_to_lattice(L, dims, p))
+    ou, op = L.apply(u, p)
+    assert rel_err(u_from_lattice(L, dims, ku), ou) < TOL64
+    assert rel_err(p_from_lattice(L, dims, kp), op) < TOL64
+    x = mesh.node_coords()
+    fn, ud = _data(name, x)
+    mesh.set_rhs(fn, ud)
+    f, g = L.rhs(fn[lat], ud[lat])
+    # the stored f is the unprojected load; its tangential part is the oracle's
+    assert rel_err(L.proj(u_from_lattice(L, dims, mesh.level_field(level, "F"))), f) < TOL64
+    assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "G")), g) < TOL64
+    st = _state(H, level, 53)
+    for prec, tol in ((0, 1e-11), (1, TOL32)):
+        _load(mesh, H, level, st, precision=prec)
+        mesh.level_op(level, "uzawa_step", precision=prec, count=3)
+        uu, pp, ff, gg = (a.copy() for a in st)
+        for _ in range(3):
+            MG.uzawa_step(H, level, uu, pp, ff, gg)
+        gu, gp = _read_up(mesh, H, level, precision=prec)
+        assert rel_err(gu, uu) < tol and rel_err(gp, pp) < tol, prec
+        assert _normal_part(L, gu) <= (1e-14 if prec == 0 else 1e-6) * np.abs(gu).max()
+        mesh.level_op(level, "residual", precision=prec)
+        ru, rp = L.residual(uu, pp, ff, gg)
+        assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU", prec)), ru) < 10 * tol
+        assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP", prec)), rp) < 10 * tol
+    mesh.close()
+
+
+@pytest.mark.parametrize("form", ["laplace", "D"])
+@pytest.mark.parametrize("name,level,coarsest,mx", [("slip_cube", 4, 2, 5), ("slip_channel", 2, 1, 30)])
+def test_transfers_coarse_solve_and_vcycle_iterates(pkg, name, level, coarsest, mx, form):
+    macro, mesh, H = _pair(pkg, name, form, level, coarsest, mx)
+    # restriction and prolongation between the two finest levels
+    Lf, Lc = H.levels[level], H.levels[level - 1]
+    st = _state(H, level, 55)
+    _load(mesh, H, level, st)
+    mesh.level_op(level, "residual")
+    mesh.level_op(level, "restrict")
+    ru, rp = Lf.residual(*st)
+    fc = Lc.proj(np.stack([H.Pu[level].T @ ru[d] for d in range(3)]))
+    gc = H.P[level].T @ rp
+    dc = mesh.dims(level - 1)
+    assert rel_err(u_from_lattice(Lc, dc, mesh.level_field(level - 1, "F")), fc) < TOL64
+    assert rel_err(p_from_lattice(Lc, dc, mesh.level_field(level - 1, "G")), gc) < TOL64
+    stc = _state(H, level - 1, 57)
+    mesh.level_field(level - 1, "U", 0, u_to_lattice(Lc, dc, stc[0]))
+    mesh.level_field(level - 1, "P", 0, p_to_lattice(Lc, dc, stc[1]))
+    _load(mesh, H, level, st)
+    mesh.level_op(level, "prolong_add")
+    u = st[0] + Lf.proj(np.stack([H.Pu[level] @ stc[0][d] for d in range(3)]))
+    gu, gp = _read_up(mesh, H, level)
+    assert rel_err(gu, u) < TOL64 and rel_err(gp, st[1] + H.P[level] @ stc[1]) < TOL64
+    # coarse solve
+    Lcc = H.levels[coarsest]
+    stc = _state(H, coarsest, 59)
+    _load(mesh, H, coarsest, stc)
+    mesh.level_op(coarsest, "coarse_solve")
+    u, p, f, g = (a.copy() for a in stc)
+    MG.vcycle(H, coarsest, u, p, f, g)
+    gu, gp = _read_up(mesh, H, coarsest)
+    assert rel_err(gu, u) < 1e-9 and _p_err(Lcc, gp, p) < 1e-9
+    # V-cycle iterates
+    st = _state(H, level, 61)
+    _load(mesh, H, level, st)
+    u, p, f, g = (a.copy() for a in st)
+    tol = TOL64 if mx <= 5 else 1e-9
+    for cyc in range(2):
+        mesh.level_op(level, "vcycle")
+        MG.vcycle(H, level, u, p, f, g)
+        gu, gp = _read_up(mesh, H, level)
+        assert rel_err(gu, u) < tol and _p_err(Lf, gp, p) < tol, cyc
+    mesh.close()
+
+
+@pytest.mark.parametrize("form", ["laplace", "D"])
+@pytest.mark.parametrize("name,level,coarsest,mx", [("slip_cube", 5, 2, 5), ("slip_channel", 3, 1, 200)])
+def test_slip_solves_match_oracle(pkg, name, level, coarsest, mx, form):
+    macro, mesh, H = _pair(pkg, name, form, level, coarsest, mx)
+    L = H.levels[level]
+    dims = mesh.dims()
+    lat = lattice_index(L, dims)
+    x = mesh.node_coords()
+    fn, ud = _data(name, x)
+    f, g = L.rhs(fn[lat], ud[lat])
+    tight = MG.solve(H, f, g, tol=1e-12, max_cycles=60)
+    loose = MG.solve(H, f, g, tol=1e-8, max_cycles=40)
+    mesh.set_rhs(fn, ud)
+    u, p, st = mesh.solve(tol=1e-12, max_cycles=60, mode=pkg.MODE_FP64)
+    assert st.status == 0 and st.cycles == tight.cycles
+    np.testing.assert_allclose(st.history, tight.history, rtol=1e-6, atol=1e-13)
+    ut = L.scatter(tight.u, ud[lat])
+    assert rel_err(u[lat], ut) < 1e-9 and rel_err(p[lat], tight.p) < 1e-8
+    uf = u[lat][L.free].T
+    assert _normal_part(L, uf) <= 1e-13 * np.abs(uf).max()
+    eu64 = rel_err(L.scatter(loose.u, ud[lat]), ut)
+    ep64 = rel_err(loose.p, tight.p)
+    mesh.set_rhs(fn, ud)
+    u32, p32, s32 = mesh.solve(tol=1e-8, max_cycles=40, mode=pkg.MODE_FP32_IR)
+    assert s32.status == 0 and s32.rel_residual <= 1e-8
+    assert rel_err(u32[lat], ut) <= 10 * eu64 + 1e-9
+    assert rel_err(p32[lat], tight.p) <= 10 * ep64 + 1e-7
+    uf32 = u32[lat][L.free].T
+    # the refinement keeps the slip velocities tangential to FP64 rounding
+    assert _normal_part(L, uf32) <= 1e-13 * np.abs(uf32).max()
+    if name == "slip_channel":
+        # exact flux balance through the channel (mass-conservative normals)
+        full = np.zeros(L.mesh.n_nodes)
+        full[L.dir] = ud[lat][L.dir, 0]
+        flux_in = float(np.sum(L.ops.B[0] @ full))
+        for uu in (u, u32):
+            flux_out = adjoint.functional(L, uu[lat][L.free].T, ud[lat])
+            assert flux_out == pytest.approx(flux_in, rel=1e-7)
+    mesh.close()
