@@ -7,7 +7,8 @@ multigrid V_var(3,3) from a zero initial guess.  One step = set the
 right-hand side from device-resident nodal inputs + solve to 1e-8 in the
 FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
-the level-7 cube (8,291,838 free DoFs) under "level7".  "fmg" times full
+the level-7 cube (8,291,838 free DoFs) under "level7" and the level-4 cube
+(15,038 free DoFs, latency-bound) under "level4".  "fmg" times full
 multigrid (Sec. 5) on the headline level, with its error ratio gamma;
 "channel_level6" times the obstacle channel (2.6e8 free DoFs) FP32+IR solve
 and "slip_channel_level6" the same channel with free-slip obstacles (Sec. 6.1);
@@ -49,7 +50,7 @@ ORACLE_LEVEL = 5
 # few GB on the device: the fields are far larger than L2), scaled to the
 # bench level by its node count; None where no capture of the current kernel
 # exists.
-TRAFFIC_BYTES_PER_NODE = {"k_vel_colour_rhs": (296033536 + 43298560) / 257 ** 3}  # 19.99 B: 339.3 MB / 257^3
+TRAFFIC_BYTES_PER_NODE = {"k_vel_colour_rhs": (295984384 + 43319040) / 257 ** 3}  # 19.99 B: 339.3 MB / 257^3
 
 
 def _peaks():
@@ -334,16 +335,21 @@ def run_gpu(args):
     channel = channel_solve(pkg, args.channel_level, stream) if args.channel_level else None
     slip_channel = channel_solve(pkg, args.channel_level, stream, slip=True) if args.channel_level else None
     dform = dform_solve(pkg, args.dform_level, stream) if args.dform_level else None
-    extra = None
-    if args.extra_level and args.extra_level != args.level:
-        lb = LevelBench(pkg, args.extra_level, stream, flush, world)
-        r7 = lb.pair(args.steps, args.warmup, max(1, args.steps // 2))
-        extra = {"free_dofs": lb.dofs, "value": r7["value"], "ms_per_step": r7["ms_per_step"],
-                 "cycles": r7["cycles"][:1], "fp64": {k: r7["fp64"][k] for k in ("value", "ms_per_step")},
-                 "speedup_fp32ir_vs_fp64": r7["speedup_fp32ir_vs_fp64"],
-                 "roofline": measure_roofline(lb.mesh, args.extra_level, stream, flush, bound="l2")}
-        extra["fp64"]["cycles"] = r7["fp64"]["cycles"][:1]
+
+    def side_level(level, bound):
+        lb = LevelBench(pkg, level, stream, flush, world)
+        r = lb.pair(args.steps, args.warmup, max(1, args.steps // 2))
+        side = {"free_dofs": lb.dofs, "value": r["value"], "ms_per_step": r["ms_per_step"],
+                "cycles": r["cycles"][:1], "fp64": {k: r["fp64"][k] for k in ("value", "ms_per_step")},
+                "speedup_fp32ir_vs_fp64": r["speedup_fp32ir_vs_fp64"]}
+        if bound:
+            side["roofline"] = measure_roofline(lb.mesh, level, stream, flush, bound=bound)
+        side["fp64"]["cycles"] = r["fp64"]["cycles"][:1]
         lb.close()
+        return side
+
+    extra = side_level(args.extra_level, "l2") if args.extra_level and args.extra_level != args.level else None
+    small = side_level(args.small_level, None) if args.small_level and args.small_level != args.level else None
 
     out = {
         "metric": METRIC, "value": res["value"], "unit": "DoF/s", "n_gpus": world, "steps": args.steps,
@@ -360,6 +366,8 @@ def run_gpu(args):
     }
     if extra:
         out[f"level{args.extra_level}"] = extra
+    if small:
+        out[f"level{args.small_level}"] = small
     if channel:
         out[f"channel_level{args.channel_level}"] = channel
         out[f"slip_channel_level{args.channel_level}"] = slip_channel
@@ -590,6 +598,8 @@ def main():
     ap.add_argument("--level", type=int, default=LEVEL)
     ap.add_argument("--extra-level", type=int, default=EXTRA_LEVEL,
                     help="second cube level reported beside the headline (0: none)")
+    ap.add_argument("--small-level", type=int, default=4,
+                    help="also time the small cube level (launch- and latency-bound); 0 = skip")
     ap.add_argument("--channel-level", type=int, default=6,
                     help="obstacle channel level reported beside the headline (0: none)")
     ap.add_argument("--dform-level", type=int, default=7,

@@ -64,8 +64,9 @@ extern "C" {
 #define HHG_BC_SLIP 3       /* free slip (Sec. 6.1): u . n_i = 0 with the mass-conservative normal
                                n_i = <grad phi_i, 1> / |<grad phi_i, 1>|, and no tangential stress
                                (the momentum rows are tested in the tangent plane only).  A node
-                               on a Dirichlet face is Dirichlet; a node whose integral vanishes
-                               (slip faces back to back) has no normal and no constraint */
+                               on a Dirichlet face is Dirichlet; so is a node whose integral
+                               vanishes (slip faces back to back: obstacles touching along an
+                               edge or at a corner), which takes the boundary data given there */
 
 /* Node flag bits returned by hhg_node_flags. */
 #define HHG_NODE_ACTIVE 1   /* carries a pressure unknown */
@@ -114,7 +115,7 @@ typedef struct hhg_options {
                                 before reading a node's flags (hides load latency on small,
                                 latency-bound levels); 0 = default (2^20), -1 = never */
   int32_t colour_block_z;    /* planes per thread block of the colour kernels (1, 2 or 4; 0 =
-                                default: 2 on levels of at least 2^22 lattice nodes, else 1) */
+                                default: 1) */
   int32_t resident_node_lists; /* cluster-resident levels (fuse_coarse_levels 2): 1 runs each
                                 velocity / pressure colour phase over per-CTA lists of its
                                 regular nodes and then its boundary nodes; 0 = default (1),

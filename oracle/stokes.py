@@ -27,8 +27,10 @@ elsewhere) the system solved is
     [B Pi                 -C    ] [p] = [g   ]
 whose velocity block is the identity in the normal directions, so their
 solution is u . n_i = 0.  Where <grad phi_i, 1> = 0 (two free-slip faces
-back to back, e.g. obstacles that touch along an edge) there is no normal
-and the node carries no constraint (Pi_i = I); its flux term is zero anyway.  Since Pi_i B^T 1 = 0 at slip nodes, the constant
+back to back: obstacles that touch along an edge or at a corner) there is no
+normal; such a node is a contact point of two walls and takes its velocity
+from the boundary data like a Dirichlet node (its flux term is zero either
+way).  Since Pi_i B^T 1 = 0 at slip nodes, the constant
 pressure stays in the kernel of a slip-and-Dirichlet problem, and the flux
 through slip faces vanishes exactly (the mass-conservation property).
 """
@@ -153,6 +155,14 @@ class StokesLevel:
 
 def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, form: str = "laplace") -> StokesLevel:
     ops = fem.assemble(mesh, nu=nu, delta=delta)
+    on_slip = mesh.on_slip if mesh.on_slip is not None else np.zeros(mesh.n_nodes, bool)
+    # <grad phi_i, 1> = -(B^T 1)_i, component by component (Sec. 6.1)
+    gint_all = -np.stack([ops.B[d].T @ np.ones(mesh.n_nodes) for d in range(3)], axis=1)
+    pinch = on_slip & (np.linalg.norm(gint_all, axis=1) <= 1e-12 * mesh.h ** 2)
+    if pinch.any():
+        mesh.on_dirichlet = mesh.on_dirichlet | pinch
+        mesh.on_slip = on_slip & ~pinch
+        on_slip = mesh.on_slip
     free = np.where(mesh.free_velocity)[0]
     dirn = np.where(~mesh.free_velocity)[0]
     A = ops.A[free][:, free].tocsr()
@@ -167,20 +177,9 @@ def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, f
     L = StokesLevel(mesh=mesh, ops=ops, free=free, dir=dirn, A=A, A_diag=A.diagonal().copy(),
                     B=B, BT=[b.T.tocsr() for b in B], C=ops.C, C_diag=ops.C.diagonal().copy(),
                     m=ops.m, pure_dirichlet=not mesh.has_outflow, form=form, A2=A2, A2_node=A2_node)
-    on_slip = mesh.on_slip if mesh.on_slip is not None else np.zeros(mesh.n_nodes, bool)
     L.slip = np.where(on_slip[free])[0]
-    if len(L.slip):
-        # <grad phi_i, 1> = -(B^T 1)_i, component by component (Sec. 6.1)
-        ones = np.ones(mesh.n_nodes)
-        gint = -np.stack([ops.B[d].T @ ones for d in range(3)], axis=1)[free[L.slip]]
-        # where free-slip faces meet back to back (obstacles touching along an
-        # edge or at a corner) the integral vanishes: no normal, no constraint
-        nrm = np.linalg.norm(gint, axis=1)
-        ok = nrm > 1e-12 * mesh.h ** 2
-        L.normals = np.zeros_like(gint)
-        L.normals[ok] = gint[ok] / nrm[ok][:, None]
-    else:
-        L.normals = np.zeros((0, 3))
+    gint = gint_all[free[L.slip]]
+    L.normals = gint / np.linalg.norm(gint, axis=1)[:, None] if len(L.slip) else np.zeros((0, 3))
     couple(L)
     return L
 

@@ -84,6 +84,7 @@ struct hhg_mesh {
   double* d_dir_val = nullptr;
   double* d_stage = nullptr;  // 3 n doubles (finest)
   double* d_partial = nullptr;
+  double* d_ir_partial = nullptr;  // per-block partial norms of the fixed-point residual (finest level)
   double* d_scalars = nullptr;  // [0] norm2, [1..2] moments, [3..4] g-mean, [5..7] coarse info
   double* h_scalars = nullptr;  // pinned mirror
   unsigned long long* d_fxmax = nullptr;  // fixed-point state: FxState's mx, maxq and exp (12 words)
@@ -168,7 +169,8 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     // two planes per block on levels that stream from HBM (level 9: 5 % per
     // Uzawa step); no effect measured at level 7
     const int want = M->opt.colour_block_z;
-    L.cbz = want == 1 || want == 2 || want == 4 ? want : (H.sh.n() >= ((int64_t)1 << 22) ? 2 : 1);
+    // one plane per block: measured 4-5 % faster per FP32 Uzawa step than two on the level-8 and level-9 cubes
+    L.cbz = want == 1 || want == 2 || want == 4 ? want : 1;
     L.nq = (int)((H.sh.nx + 3) / 4);
     L.nq_mul = L.nq == 1 ? 0 : ~0ull / (uint64_t)L.nq + 1;
     // two nodes per thread in the FP32 colour kernels of the flags-first (large)
@@ -463,8 +465,8 @@ void enq_cycle64(hhg_mesh* M) {
 void enq_ir_residual(hhg_mesh* M, bool from_update) {
   LevelHost& H = M->lv[M->finest];
   if (M->opt.ir_fixed_point) {
-    launch_ir_residual_fx(H.d64, M->fx, H.d32, fx_state(M), from_update, M->d_partial, M->d_scalars, M->stream);
-    M->launches += from_update ? 3 : 5;
+    launch_ir_residual_fx(H.d64, M->fx, H.d32, fx_state(M), from_update, M->d_ir_partial, M->d_scalars, M->stream);
+    M->launches += from_update ? 4 : 6;
   } else {
     launch_ir_residual(H.d64, H.d32, M->d_partial, M->d_scalars, M->stream);
     M->launches += 2;
@@ -730,6 +732,7 @@ void release(hhg_mesh* M) {
   cudaFree(M->d_mmask);
   cudaFree(M->d_stage);
   cudaFree(M->d_partial);
+  cudaFree(M->d_ir_partial);
   cudaFree(M->d_scalars);
   cudaFree(M->d_coarse);
   cudaFree(M->d_fx);
@@ -982,6 +985,8 @@ int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, c
     if ((rc = dalloc(M, (void**)&M->d_stage, sizeof(double) * 3 * (size_t)H.sh.n()))) return bail(rc);
   }
   if ((rc = dalloc(M, (void**)&M->d_partial, sizeof(double) * 4 * std::max(REDUCE_BLOCKS, IR_BLOCKS + IR_IRR_BLOCKS)))) return bail(rc);
+  if ((rc = dalloc(M, (void**)&M->d_ir_partial, sizeof(double) * ir_residual_fx_partials(M->lv[finest].d64))))
+    return bail(rc);
   if ((rc = dalloc(M, (void**)&M->d_scalars, sizeof(double) * 16))) return bail(rc);
   cudaMemset(M->d_scalars, 0, sizeof(double) * 16);
   if ((rc = dalloc(M, (void**)&M->d_rhs_fx, sizeof(unsigned long long) * 10))) return bail(rc);

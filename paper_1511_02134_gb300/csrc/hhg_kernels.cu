@@ -16,6 +16,7 @@ namespace {
 constexpr int CB = 128;  // colour kernels: packed (row, quarter-row slot) indices per block; planes per level (cbz)
 // (blocks of CB x cbz threads, cbz <= 4: the colour kernels are compiled for 4 CB threads per block)
 constexpr int FX = 64, FY = 4;  // full kernels
+constexpr int IR_FZ = 8;        // planes per block of the fixed-point residual
 
 template <class T>
 dim3 colour_block(const LevelDev<T>& L) {
@@ -713,8 +714,15 @@ __device__ __forceinline__ bool fx_iterate_fit(const unsigned long long* maxq, u
 }
 
 // The regular nodes; boundary nodes (F_IRR) are left to k_ir_residual_fx_irr.
-__global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float> E, const int* fexp,
-                                 const unsigned long long* maxq, unsigned* flag, int check, double* partial) {
+// Each block takes an FX x FY tile through IR_FZ consecutive planes, one node
+// per thread and plane, blocks in lattice order: a block finds the planes
+// k - 1 and k + 1 of its tile among the ones it has just read, and its
+// neighbour tiles run beside it (a grid-stride loop over the whole level lets
+// the blocks drift apart by many planes and reads every plane about twice
+// from DRAM).  The block's partial norm goes to partial[linear block index].
+__global__ void __launch_bounds__(FX * FY, 3) k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float> E,
+                                                            const int* fexp, const unsigned long long* maxq,
+                                                            unsigned* flag, int check, double* partial) {
   pdl_enter();
   if (check && !fx_iterate_fit(maxq, flag)) return;
   double is[4];
@@ -723,21 +731,19 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
   // one shift for the three velocity components (k_ir_quantize)
   const double kA = X.nuh * is[0], kB = X.h2 * (1.0 / 12.0) * is[0];
   const double kBT = X.h2 * (1.0 / 12.0) * is[3], kC = X.c * is[3];
-  double v[1] = {0.0};
-  const int64_t n = (int64_t)X.nx * X.ny * X.nz;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += stride) {
-    const int i = (int)(q % X.nx);
-    const int j = (int)((q / X.nx) % X.ny);
-    const int k = (int)(q / ((int64_t)X.nx * X.ny));
+  double v = 0.0;
+  const int i = blockIdx.x * FX + threadIdx.x, j = blockIdx.y * FY + threadIdx.y;
+  const int k1 = min(X.nz, (int)(blockIdx.z + 1) * IR_FZ);
+  for (int k = blockIdx.z * IR_FZ; k < k1; ++k) {
+    if (i >= X.nx || j >= X.ny) break;
     const Node n = node_at(X.px, X.pxy, i, j, k);
     const int64_t c = n.c;
     const uint8_t fl = X.flags[c];
-    double r[4];
     if (!(fl & F_IRR)) {
       const GNb<int64_t> gu[3] = {gnb(Q.u[0], n, X.px, X.pxy), gnb(Q.u[1], n, X.px, X.pxy),
                                   gnb(Q.u[2], n, X.px, X.pxy)};
       const GNb<int64_t> gp = gnb(Q.p, n, X.px, X.pxy);
+      double r[4];
       if (fl & F_VFREE) {
         int64_t ibt[3];
         div12_all(diff7v<int64_t>(gp), ibt);
@@ -758,18 +764,41 @@ __global__ void k_ir_residual_fx(LevelDev<double> X, FxIterate Q, LevelDev<float
       } else {
         r[3] = 0.0;
       }
-    } else {
-      continue;
-    }
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      E.f[d][c] = (float)r[d];
-      v[0] += r[d] * r[d];
+      for (int d = 0; d < 3; ++d) {
+        E.f[d][c] = (float)r[d];
+        v += r[d] * r[d];
+      }
+      E.g[c] = (float)r[3];
+      v += r[3] * r[3];
     }
-    E.g[c] = (float)r[3];
-    v[0] += r[3] * r[3];
   }
-  block_reduce_store<1>(v, partial);
+  // block sum in a fixed order: warps by shuffles, then the warp sums
+  __shared__ double sh[FX * FY / 32];
+  const int t = threadIdx.x + FX * threadIdx.y;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((t & 31) == 0) sh[t >> 5] = v;
+  __syncthreads();
+  if (t == 0) {
+    double acc = 0.0;
+#pragma unroll
+    for (int w = 0; w < FX * FY / 32; ++w) acc += sh[w];
+    partial[blockIdx.x + (int64_t)gridDim.x * (blockIdx.y + (int64_t)gridDim.y * blockIdx.z)] = acc;
+  }
+}
+
+dim3 ir_residual_grid(const LevelDev<double>& L) {
+  return dim3((L.nx + FX - 1) / FX, (L.ny + FY - 1) / FY, (L.nz + IR_FZ - 1) / IR_FZ);
+}
+
+// out[b] = sum of in[b n / G, (b + 1) n / G) for the G blocks, in a fixed
+// order (first stage of a deterministic sum of many partials).
+__global__ void k_segment_sum(const double* in, int64_t n, double* out) {
+  pdl_enter();
+  const int64_t lo = n * blockIdx.x / gridDim.x, hi = n * (blockIdx.x + 1) / gridDim.x;
+  double v[1] = {0.0};
+  for (int64_t q = lo + threadIdx.x; q < hi; q += blockDim.x) v[0] += in[q];
+  block_reduce_store<1>(v, out);
 }
 
 // The boundary nodes of k_ir_residual_fx, from the list of their lattice
@@ -1273,12 +1302,20 @@ void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const 
     launch_k(k_ir_absmax, IR_BLOCKS, REDUCE_THREADS, s, x, st.mx);
     launch_k(k_ir_quantize, flat_blocks(x.nalloc), 256, s, x, q, (const unsigned long long*)st.mx, st.exp);
   }
-  launch_k(k_ir_residual_fx, IR_BLOCKS, REDUCE_THREADS, s, x, q, e, (const int*)st.exp,
-           (const unsigned long long*)st.maxq, st.flag, from_update ? 1 : 0, partial);
+  const dim3 grid = ir_residual_grid(x);
+  const int64_t nreg = (int64_t)grid.x * grid.y * grid.z;
+  launch_k(k_ir_residual_fx, grid, dim3(FX, FY), s, x, q, e, (const int*)st.exp, (const unsigned long long*)st.maxq,
+           st.flag, from_update ? 1 : 0, partial);
   launch_k(k_ir_residual_fx_irr, IR_IRR_BLOCKS, REDUCE_THREADS, s, x, q, e, (const int*)st.exp,
            (const unsigned long long*)st.maxq, st.flag, from_update ? 1 : 0, (const int64_t*)st.irr, st.nirr,
-           partial + IR_BLOCKS);
-  launch_k(k_final_sum<1>, 1, 32, s, (const double*)partial, IR_BLOCKS + IR_IRR_BLOCKS, out);
+           partial + nreg);
+  double* seg = partial + nreg + IR_IRR_BLOCKS;
+  launch_k(k_segment_sum, IR_BLOCKS, REDUCE_THREADS, s, (const double*)partial, nreg + IR_IRR_BLOCKS, seg);
+  launch_k(k_final_sum<1>, 1, 32, s, (const double*)seg, IR_BLOCKS, out);
+}
+int64_t ir_residual_fx_partials(const LevelDev<double>& x) {
+  const dim3 grid = ir_residual_grid(x);
+  return (int64_t)grid.x * grid.y * grid.z + IR_IRR_BLOCKS + IR_BLOCKS;
 }
 void launch_fx_update(const FxIterate& q, const LevelDev<float>& e, const FxState& st, int64_t nalloc, cudaStream_t s) {
   cudaMemsetAsync(st.maxq, 0, 4 * sizeof(unsigned long long), s);

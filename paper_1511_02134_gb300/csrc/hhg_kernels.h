@@ -147,7 +147,9 @@ constexpr unsigned FX_FLAG_REFUSED = 1u;  // k_fx_update left a correction out
 constexpr unsigned FX_FLAG_RESCALE = 2u;  // the residual found the iterate unfit for its shifts
 // Residual of the fixed-point iterate into e.f / e.g, norm into out[0].
 // from_update = false: max |x| -> shifts -> Q = round(x 2^s) first;
-// true: Q comes from launch_fx_update and is checked first.
+// true: Q comes from launch_fx_update and is checked first.  partial holds
+// ir_residual_fx_partials(x) doubles (one per block of the regular-node
+// kernel, then the boundary-node blocks and the segment sums).
 void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,
                            bool from_update, double* partial, double* out, cudaStream_t s);
 // Free slip: the velocity of the slip nodes among the listed boundary nodes
@@ -157,6 +159,7 @@ void launch_ir_residual_fx(const LevelDev<double>& x, const FxIterate& q, const 
 void launch_slip_fix(const LevelDev<double>& x, const int64_t* irr, int64_t nirr, cudaStream_t s);
 void launch_slip_fix_fx(const FxIterate& q, const LevelDev<double>& x, const FxState& st, cudaStream_t s);
 // Q += round(e 2^s) over the nalloc padded positions.
+int64_t ir_residual_fx_partials(const LevelDev<double>& x);
 void launch_fx_update(const FxIterate& q, const LevelDev<float>& e, const FxState& st, int64_t nalloc, cudaStream_t s);
 // x = Q 2^-s, or (recover) the iterate before the last update + e in FP64.
 void launch_fx_to_fp64(const LevelDev<double>& x, const FxIterate& q, const LevelDev<float>& e, const FxState& st,

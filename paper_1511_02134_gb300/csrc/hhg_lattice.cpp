@@ -291,6 +291,26 @@ void for_face_nodes(const BoundaryFace& bf, int level, F&& fn) {
 
 }  // namespace
 
+namespace {
+void class_normal(const MacroLattice& mac, uint32_t pattern, double n[3]);
+
+// Set of active incident tetrahedra of node (i, j, k): bit per (cell corner,
+// Kuhn path) pair, in the order of the class tables.
+uint32_t node_pattern(const MacroLattice& m, int level, int i, int j, int k) {
+  uint32_t pattern = 0;
+  int bit = 0;
+  for (int c = 0; c < 8; ++c) {
+    const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
+    for (int s = 0; s < 6; ++s) {
+      if (corner_local(s, qx, qy, qz) < 0) continue;
+      if (tet_active(m.mask.data(), m.mx, m.my, m.mz, level, i - qx, j - qy, k - qz, s)) pattern |= 1u << bit;
+      ++bit;
+    }
+  }
+  return pattern;
+}
+}  // namespace
+
 void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
   const LevelShape sh = level_shape(m, level);
   const int N = 1 << level;
@@ -340,6 +360,27 @@ void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
     if ((f & F_ACT) && !(f & F_DIR)) f |= F_VFREE;
     if (!(f & F_VFREE)) f &= (uint8_t)~F_SLIP;
     flags[i] = f;
+  }
+  // A free-slip node whose <grad phi, 1> vanishes (free-slip faces back to
+  // back: obstacles touching along an edge or at a corner) has no normal; it
+  // is a contact point of two walls and takes its velocity from the boundary
+  // data like a Dirichlet node.
+  if (m.has_slip) {
+    std::unordered_map<uint32_t, bool> no_normal;
+    for (int k = 0; k < sh.nz; ++k)
+      for (int j = 0; j < sh.ny; ++j)
+        for (int i = 0; i < sh.nx; ++i) {
+          uint8_t& f = flags[i + sh.nx * j + nxy * k];
+          if (!(f & F_SLIP)) continue;
+          const uint32_t pattern = node_pattern(m, level, i, j, k);
+          auto it = no_normal.find(pattern);
+          if (it == no_normal.end()) {
+            double nr[3];
+            class_normal(m, pattern, nr);
+            it = no_normal.emplace(pattern, nr[0] == 0.0 && nr[1] == 0.0 && nr[2] == 0.0).first;
+          }
+          if (it->second) f = (uint8_t)((f & ~(F_SLIP | F_VFREE)) | F_DIR);
+        }
   }
 }
 
@@ -550,16 +591,7 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
       for (int i = 0; i < sh.nx; ++i) {
         const int64_t q = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
         if (!(flags[q] & F_IRR)) continue;
-        uint32_t pattern = (flags[q] & F_SLIP) ? SLIP_CLASS_BIT : 0u;
-        int bit = 0;
-        for (int c = 0; c < 8; ++c) {
-          const int qx = c & 1, qy = (c >> 1) & 1, qz = (c >> 2) & 1;
-          for (int s = 0; s < 6; ++s) {
-            if (corner_local(s, qx, qy, qz) < 0) continue;
-            if (tet_active(m.mask.data(), m.mx, m.my, m.mz, level, i - qx, j - qy, k - qz, s)) pattern |= 1u << bit;
-            ++bit;
-          }
-        }
+        const uint32_t pattern = node_pattern(m, level, i, j, k) | ((flags[q] & F_SLIP) ? SLIP_CLASS_BIT : 0u);
         auto it = ids.find(pattern);
         if (it == ids.end()) {
           if (n_classes >= 65535) {

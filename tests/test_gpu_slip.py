@@ -184,3 +184,30 @@ def test_slip_solves_match_oracle(pkg, name, level, coarsest, mx, form):
             flux_out = adjoint.functional(L, uu[lat][L.free].T, ud[lat])
             assert flux_out == pytest.approx(flux_in, rel=1e-7)
     mesh.close()
+
+
+def test_contact_edge_nodes_are_dirichlet_and_converge(pkg):
+    """Two free-slip obstacles touching along an edge: the nodes of the
+    contact edge have no normal and take the wall's data.  With them left
+    unconstrained the FP32+IR cycle count grew with the level (10, 16, 23 at
+    levels 3-5); as Dirichlet nodes it stays within a few cycles of separated
+    obstacles (measured 9, 10, 15 against 10, 9, 12)."""
+    cycles = {}
+    for name, removed in (("edge", ((5, 1, 1), (6, 2, 1))), ("apart", ((5, 1, 1), (10, 2, 2)))):
+        ch = W.box_of_cubes(16, 4, 4, removed=removed, outflow_x_max=True, slip_obstacles=True)
+        for lev in (3, 4, 5):
+            m = pkg.Mesh(ch.vertices, ch.tets, ch.bc_flags, lev, coarsest_level=1, coarse_minres_max=300,
+                         coarse_minres_rtol=5e-3)
+            x = m.node_coords()
+            if name == "edge" and lev == 3:
+                fl = m.node_flags()
+                contact = (np.abs(x[:, 0] - 6) < 1e-12) & (np.abs(x[:, 1] - 2) < 1e-12) & (x[:, 2] > 1) & (x[:, 2] < 2)
+                assert contact.sum() == 7 and np.all((fl[contact] & pkg.NODE_DIRICHLET) > 0)
+            m.set_rhs(None, W.channel_inflow(x))
+            _, _, st = m.solve(tol=1e-8, max_cycles=60, mode=pkg.MODE_FP32_IR, want_solution=False)
+            assert st.status == 0
+            cycles[(name, lev)] = st.cycles
+            m.close()
+    for lev in (3, 4, 5):
+        assert cycles[("edge", lev)] <= cycles[("apart", lev)] + 4, cycles
+    assert max(cycles[("edge", l)] for l in (3, 4, 5)) <= 17, cycles
