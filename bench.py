@@ -122,11 +122,14 @@ def _dist():
 
 
 def _max_over_ranks(x: float, world: int) -> float:
+    """The largest x over the ranks (the job's time is its slowest rank's);
+    the tensor lives where the process group's backend wants it."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
