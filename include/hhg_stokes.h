@@ -63,10 +63,13 @@ extern "C" {
 #define HHG_BC_OUTFLOW 2    /* do-nothing boundary nu du/dn - p n = 0 (natural, Sec. 6.1) */
 #define HHG_BC_SLIP 3       /* free slip (Sec. 6.1): u . n_i = 0 with the mass-conservative normal
                                n_i = <grad phi_i, 1> / |<grad phi_i, 1>|, and no tangential stress
-                               (the momentum rows are tested in the tangent plane only).  A node
-                               on a Dirichlet face is Dirichlet; so is a node whose integral
-                               vanishes (slip faces back to back: obstacles touching along an
-                               edge or at a corner), which takes the boundary data given there */
+                               (the momentum rows are tested in the admissible directions only).
+                               Where two non-parallel free-slip face planes meet (an obstacle
+                               edge) the velocity is along the edge.  A node on a Dirichlet face
+                               is Dirichlet; so are corners of three slip planes and nodes whose
+                               integral vanishes (slip faces back to back: obstacles touching
+                               along an edge or at a corner); they take the boundary data given
+                               there.  Nodes also on an outflow face keep the normal n_i */
 
 /* Node flag bits returned by hhg_node_flags. */
 #define HHG_NODE_ACTIVE 1   /* carries a pressure unknown */

@@ -26,11 +26,17 @@ elsewhere) the system solved is
     [Pi A Pi + (I - Pi)   Pi B^T] [u]   [Pi f]
     [B Pi                 -C    ] [p] = [g   ]
 whose velocity block is the identity in the normal directions, so their
-solution is u . n_i = 0.  Where <grad phi_i, 1> = 0 (two free-slip faces
-back to back: obstacles that touch along an edge or at a corner) there is no
-normal; such a node is a contact point of two walls and takes its velocity
-from the boundary data like a Dirichlet node (its flux term is zero either
-way).  Since Pi_i B^T 1 = 0 at slip nodes, the constant
+solution is u . n_i = 0.  Where the free-slip faces at a node are not
+coplanar the printed normal is their average; there the node is constrained
+by every incident face instead (Pi_i the projector onto the edge direction
+where two face planes meet; a corner of three is a Dirichlet node), which
+keeps u_i . <grad phi_i, 1> = 0, since that integral lies in the span of the
+face normals, and keeps the multigrid contraction independent of the level.
+Where <grad phi_i, 1> = 0 (two free-slip faces back to back: obstacles that
+touch along an edge or at a corner) there is no normal; such a node is a
+contact point of two walls and takes its velocity from the boundary data like
+a Dirichlet node (its flux term is zero either way).  Nodes that also lie on
+an outflow face keep the printed normal.  Since Pi_i B^T 1 = 0 at slip nodes, the constant
 pressure stays in the kernel of a slip-and-Dirichlet problem, and the flux
 through slip faces vanishes exactly (the mass-conservation property).
 """
@@ -64,6 +70,8 @@ class StokesLevel:
     A2_node: np.ndarray = None  # D form: (n_u, 3, 3) diagonal node blocks of A2
     slip: np.ndarray = None     # positions (within free) of the free-slip velocity nodes
     normals: np.ndarray = None  # (n_slip, 3) mass-conservative unit normals of those nodes
+    slip_P: np.ndarray = None   # (n_slip, 3, 3) projector onto each node's admissible velocities
+    slip_edge: np.ndarray = None  # (n_slip,) bool: constrained by two face planes (velocity along the edge)
     Kv: sp.csr_matrix = None    # coupled velocity block solved (D form or free slip), (u_0, u_1, u_2) order
     Kv_node: np.ndarray = None  # (n_u, 3, 3) diagonal node blocks of Kv
 
@@ -85,11 +93,11 @@ class StokesLevel:
 
     # --- the operator K and the residual (Sec. 3) --------------------------
     def proj(self, v: np.ndarray) -> np.ndarray:
-        """Pi v for v of shape (3, n_u): the normal part removed at slip nodes."""
+        """Pi v for v of shape (3, n_u): each slip node's velocity projected on
+        its admissible subspace (the tangent plane, or the edge direction)."""
         v = np.array(v, dtype=float, copy=True)
         if self.slip is not None and len(self.slip):
-            vs = v[:, self.slip]
-            v[:, self.slip] = vs - self.normals.T * np.sum(vs * self.normals.T, axis=0)
+            v[:, self.slip] = np.einsum("nab,bn->an", self.slip_P, v[:, self.slip])
         return v
 
     def apply_A(self, u: np.ndarray) -> np.ndarray:
@@ -153,16 +161,51 @@ class StokesLevel:
         return out
 
 
+def boundary_face_normal_sums(mesh: RefinedMesh) -> np.ndarray:
+    """(n, 3, 3): sum of n_f n_f^T over the boundary faces f of the fine mesh
+    incident to each node (n_f the outward unit normal)."""
+    loc = np.array([[1, 2, 3], [0, 2, 3], [0, 1, 3], [0, 1, 2]])
+    faces = mesh.tets[:, loc].reshape(-1, 3)
+    opp = mesh.tets.reshape(-1)
+    key = np.sort(faces, axis=1)
+    _, first, counts = np.unique(key, axis=0, return_index=True, return_counts=True)
+    bnd = first[counts == 1]
+    f, o = faces[bnd], opp[bnd]
+    X = mesh.xyz
+    nrm = np.cross(X[f[:, 1]] - X[f[:, 0]], X[f[:, 2]] - X[f[:, 0]])
+    flip = np.sum(nrm * (X[o] - X[f[:, 0]]), axis=1) > 0
+    nrm[flip] *= -1.0
+    nrm /= np.linalg.norm(nrm, axis=1)[:, None]
+    S = np.zeros((mesh.n_nodes, 3, 3))
+    outer = nrm[:, :, None] * nrm[:, None, :]
+    for c in range(3):
+        np.add.at(S, f[:, c], outer)
+    return S
+
+
 def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, form: str = "laplace") -> StokesLevel:
     ops = fem.assemble(mesh, nu=nu, delta=delta)
     on_slip = mesh.on_slip if mesh.on_slip is not None else np.zeros(mesh.n_nodes, bool)
     # <grad phi_i, 1> = -(B^T 1)_i, component by component (Sec. 6.1)
     gint_all = -np.stack([ops.B[d].T @ np.ones(mesh.n_nodes) for d in range(3)], axis=1)
-    pinch = on_slip & (np.linalg.norm(gint_all, axis=1) <= 1e-12 * mesh.h ** 2)
-    if pinch.any():
-        mesh.on_dirichlet = mesh.on_dirichlet | pinch
-        mesh.on_slip = on_slip & ~pinch
-        on_slip = mesh.on_slip
+    edge_t = np.zeros((mesh.n_nodes, 3))
+    is_edge = np.zeros(mesh.n_nodes, bool)
+    if on_slip.any():
+        pinch = on_slip & (np.linalg.norm(gint_all, axis=1) <= 1e-12 * mesh.h ** 2)
+        # rank of the incident face normals at pure slip nodes (not on an outflow face)
+        S = boundary_face_normal_sums(mesh)
+        cand = np.where(on_slip & ~pinch & ~mesh.on_outflow)[0]
+        w, V = np.linalg.eigh(S[cand])
+        rank = np.sum(w > 1e-9 * w[:, -1:], axis=1)
+        corner = np.zeros(mesh.n_nodes, bool)
+        corner[cand[rank >= 3]] = True
+        is_edge[cand[rank == 2]] = True
+        edge_t[cand[rank == 2]] = V[rank == 2][:, :, 0]   # the null direction of the two face normals
+        stop = pinch | corner
+        if stop.any():
+            mesh.on_dirichlet = mesh.on_dirichlet | stop
+            mesh.on_slip = on_slip & ~stop
+            on_slip = mesh.on_slip
     free = np.where(mesh.free_velocity)[0]
     dirn = np.where(~mesh.free_velocity)[0]
     A = ops.A[free][:, free].tocsr()
@@ -178,8 +221,14 @@ def build_level(mesh: RefinedMesh, nu: float = 1.0, delta: float = 1.0 / 12.0, f
                     B=B, BT=[b.T.tocsr() for b in B], C=ops.C, C_diag=ops.C.diagonal().copy(),
                     m=ops.m, pure_dirichlet=not mesh.has_outflow, form=form, A2=A2, A2_node=A2_node)
     L.slip = np.where(on_slip[free])[0]
-    gint = gint_all[free[L.slip]]
+    nodes = free[L.slip]
+    gint = gint_all[nodes]
     L.normals = gint / np.linalg.norm(gint, axis=1)[:, None] if len(L.slip) else np.zeros((0, 3))
+    L.slip_edge = is_edge[nodes]
+    t = edge_t[nodes]
+    plane = np.eye(3)[None] - L.normals[:, :, None] * L.normals[:, None, :]
+    line = t[:, :, None] * t[:, None, :]
+    L.slip_P = np.where(L.slip_edge[:, None, None], line, plane)
     couple(L)
     return L
 
@@ -193,13 +242,13 @@ def couple(L: StokesLevel) -> None:
         n = L.n_u
         blocks = L.A2 if L.form == "D" else sp.block_diag([L.A, L.A, L.A], format="csr")
         if len(L.slip):
-            # Pi (A) Pi + (I - Pi), with Pi = I - sum_slip n n^T as a 3 n x 3 n matrix
+            # Pi (A) Pi + (I - Pi), with Pi the slip nodes' projectors (identity elsewhere) as a 3 n x 3 n matrix
             rows, cols, vals = [], [], []
             for a in range(3):
                 for b in range(3):
                     rows.append(a * n + L.slip)
                     cols.append(b * n + L.slip)
-                    vals.append(L.normals[:, a] * L.normals[:, b])
+                    vals.append((1.0 if a == b else 0.0) - L.slip_P[:, a, b])
             Nn = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                                shape=(3 * n, 3 * n)).tocsr()
             Pi = sp.identity(3 * n, format="csr") - Nn
@@ -227,7 +276,7 @@ def full_matrix(L: StokesLevel) -> sp.csr_matrix:
         for a in range(3):
             for b in range(3):
                 dg = np.zeros(n)
-                dg[L.slip] = L.normals[:, a] * L.normals[:, b]
+                dg[L.slip] = (1.0 if a == b else 0.0) - L.slip_P[:, a, b]
                 Pi[a][b] = Pi[a][b] - sp.diags(dg, format="csr")
     for d in range(3):
         if L.coupled:

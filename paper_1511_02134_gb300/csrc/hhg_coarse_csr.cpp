@@ -99,18 +99,24 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
     val.push_back(v);
     ++nnz;
   };
-  // Free slip (Sec. 6.1): the unit normal of a slip node (from its class
-  // row), or null; the velocity block is then Pi (.) Pi + n n^T at slip
-  // nodes (Pi = I - n n^T) and the coupling blocks Pi B^T and B Pi, which
-  // couples the components, so the system is assembled in coupled form.
+  // Free slip (Sec. 6.1): the class row of a slip node (its constraint at
+  // W_NRM, W_SLIP), or null; the velocity block is then Pi (.) Pi + (I - Pi)
+  // at slip nodes, Pi = I - n n^T (tangent plane) or t t^T (edge direction),
+  // and the coupling blocks Pi B^T and B Pi, which couples the components,
+  // so the system is assembled in coupled form.
   bool slip = false;
   for (int32_t r = 0; r < nv && !slip; ++r) slip = (flags[lat_of[out.vidx[r]]] & F_SLIP) != 0;
   auto normal_of = [&](int64_t pc) -> const double* {
     const int64_t q = lat_of[pc];
     if (!(flags[q] & F_SLIP)) return nullptr;
-    return table + (size_t)cls[q] * W_STRIDE + W_NRM;
+    return table + (size_t)cls[q] * W_STRIDE;
   };
-  auto pi = [](const double* n, int a, int b) { return (a == b ? 1.0 : 0.0) - (n ? n[a] * n[b] : 0.0); };
+  auto pi = [](const double* w, int a, int b) {
+    const double id = a == b ? 1.0 : 0.0;
+    if (!w || w[W_SLIP] == 0.0) return id;
+    const double* v = w + W_NRM;
+    return w[W_SLIP] == 1.0 ? id - v[a] * v[b] : v[a] * v[b];
+  };
   const bool coupled = table2 != nullptr || slip;
   // 3 x 3 velocity block of row node r and its neighbour along offset o
   auto vblock = [&](int32_t r, const Rows& w, const double* w2, int o, int64_t nb, double V[3][3]) {
@@ -125,7 +131,7 @@ int assemble_coarse(const LevelShape& sh, int64_t px, int64_t pxy, const uint8_t
         double s = 0.0;
         for (int x = 0; x < 3; ++x)
           for (int y = 0; y < 3; ++y) s += pi(nr, a, x) * base[x][y] * pi(nn, y, b);
-        V[a][b] = s + (o == 0 && nr ? nr[a] * nr[b] : 0.0);
+        V[a][b] = s + (o == 0 && nr ? (a == b ? 1.0 : 0.0) - pi(nr, a, b) : 0.0);
       }
   };
   // velocity rows, component by component

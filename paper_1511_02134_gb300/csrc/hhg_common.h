@@ -48,16 +48,18 @@ HHG_HD int64_t row_step_plus(int64_t q, int64_t px) { return (q & 3) == 3 ? 1 - 
 // row, B_d rows, B_d^T rows, mass row (15 weights each, offset order:
 // centre, +o then -o over the Kuhn directions e1, e2, e3, e1+e2, e2+e3,
 // e1+e3, e1+e2+e3), lumped mass.
-// Classes of free-slip nodes (Sec. 6.1) also hold the mass-conservative unit
-// normal <grad phi, 1> / |<grad phi, 1>| at W_NRM (zero where the integral
-// vanishes) and 1 at W_SLIP (0 for every other class).
+// Classes of free-slip nodes (Sec. 6.1) also hold their constraint: W_SLIP = 1
+// with the mass-conservative unit normal <grad phi, 1> / |<grad phi, 1>| at
+// W_NRM (velocity in its tangent plane), or W_SLIP = 2 with a unit edge
+// direction at W_NRM (two non-parallel free-slip face planes meet at the
+// node: velocity along the edge); W_SLIP = 0 for every other class.
 constexpr int W_LAP = 0, W_B = 15, W_BT = 60, W_M = 105, W_LUMP = 120, W_NRM = 121, W_SLIP = 124, W_STRIDE = 128;
 // Rows of the D-operator velocity block (Sec. 2.1, a_2) of one class (unit
 // lattice spacing): block (a, b) = row component a, column component b at
 // [15 (3 a + b), +15) in the same offset order, then the inverse of the
 // 3 x 3 centre block (row-major) at W2_DINV (for a free-slip class instead
-// Z = T (T^T D T)^-1 T^T, T an orthonormal basis of the tangent plane: the
-// node-block update with u . n = 0 imposed).  Class 0 holds the rows of the
+// Z = T (T^T D T)^-1 T^T, T an orthonormal basis of the admissible velocities:
+// the node-block update with the slip constraint imposed).  Class 0 holds the rows of the
 // nodes with all 24 incident tetrahedra.
 constexpr int W2_DINV = 135, W2_STRIDE = 144;
 

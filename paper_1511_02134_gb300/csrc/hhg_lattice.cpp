@@ -292,7 +292,7 @@ void for_face_nodes(const BoundaryFace& bf, int level, F&& fn) {
 }  // namespace
 
 namespace {
-void class_normal(const MacroLattice& mac, uint32_t pattern, double n[3]);
+int class_slip_kind(const MacroLattice& mac, uint32_t pattern, double v[3]);
 
 // Set of active incident tetrahedra of node (i, j, k): bit per (cell corner,
 // Kuhn path) pair, in the order of the class tables.
@@ -363,21 +363,22 @@ void classify_nodes(const MacroLattice& m, int level, uint8_t* flags) {
   }
   // A free-slip node whose <grad phi, 1> vanishes (free-slip faces back to
   // back: obstacles touching along an edge or at a corner) has no normal; it
-  // is a contact point of two walls and takes its velocity from the boundary
-  // data like a Dirichlet node.
+  // is a contact point of two walls.  A node where three free-slip face
+  // planes meet (a corner) has no admissible velocity.  Both take their
+  // velocity from the boundary data like Dirichlet nodes.
   if (m.has_slip) {
-    std::unordered_map<uint32_t, bool> no_normal;
+    std::unordered_map<uint32_t, bool> stop;
     for (int k = 0; k < sh.nz; ++k)
       for (int j = 0; j < sh.ny; ++j)
         for (int i = 0; i < sh.nx; ++i) {
           uint8_t& f = flags[i + sh.nx * j + nxy * k];
           if (!(f & F_SLIP)) continue;
-          const uint32_t pattern = node_pattern(m, level, i, j, k);
-          auto it = no_normal.find(pattern);
-          if (it == no_normal.end()) {
-            double nr[3];
-            class_normal(m, pattern, nr);
-            it = no_normal.emplace(pattern, nr[0] == 0.0 && nr[1] == 0.0 && nr[2] == 0.0).first;
+          const uint32_t key = node_pattern(m, level, i, j, k) | ((f & F_OUT) ? OUTFLOW_CLASS_BIT : 0u);
+          auto it = stop.find(key);
+          if (it == stop.end()) {
+            double v[3];
+            const int kind = class_slip_kind(m, key, v);
+            it = stop.emplace(key, kind != 1 && kind != 2).first;
           }
           if (it->second) f = (uint8_t)((f & ~(F_SLIP | F_VFREE)) | F_DIR);
         }
@@ -407,6 +408,114 @@ void geo_grads(const MacroLattice& m, const double g[4][3], double gp[4][3]) {
   for (int n = 0; n < 4; ++n)
     for (int a = 0; a < 3; ++a)
       gp[n][a] = m.basis_inv_t[a][0] * g[n][0] + m.basis_inv_t[a][1] * g[n][1] + m.basis_inv_t[a][2] * g[n][2];
+}
+
+// The 24 tetrahedra around a lattice node, in the bit order of a class
+// pattern: vertex offsets from the node (lattice steps) along the Kuhn path,
+// the node's local index, and for each face containing the node (opposite
+// local vertex j != m) the other tetrahedron of the star sharing it.
+struct StarTet {
+  int v[4][3];
+  int m;
+  int partner[4];
+};
+
+const std::vector<StarTet>& star_tets() {
+  static const std::vector<StarTet> star = [] {
+    std::vector<StarTet> st;
+    for (int q = 0; q < 8; ++q) {
+      const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+      for (int s = 0; s < 6; ++s) {
+        const int m = corner_local(s, qx, qy, qz);
+        if (m < 0) continue;
+        StarTet t{};
+        t.m = m;
+        int p[3] = {0, 0, 0};
+        for (int n = 0; n < 4; ++n) {
+          if (n > 0) p[path_axis(s, n - 1)] += 1;
+          t.v[n][0] = p[0] - qx;
+          t.v[n][1] = p[1] - qy;
+          t.v[n][2] = p[2] - qz;
+        }
+        st.push_back(t);
+      }
+    }
+    auto has = [](const StarTet& t, const int* x) {
+      for (int n = 0; n < 4; ++n)
+        if (t.v[n][0] == x[0] && t.v[n][1] == x[1] && t.v[n][2] == x[2]) return true;
+      return false;
+    };
+    for (size_t a = 0; a < st.size(); ++a)
+      for (int j = 0; j < 4; ++j) {
+        st[a].partner[j] = -1;
+        if (j == st[a].m) continue;
+        for (size_t b = 0; b < st.size() && st[a].partner[j] < 0; ++b) {
+          if (b == a) continue;
+          bool all = true;
+          for (int n = 0; n < 4 && all; ++n)
+            if (n != j) all = has(st[b], st[a].v[n]);
+          if (all) st[a].partner[j] = (int)b;
+        }
+      }
+    return st;
+  }();
+  return star;
+}
+
+// Constraint of a free-slip node from its class key and <grad phi, 1>
+// (Sec. 6.1).  1: the unit mass-conservative normal in out (the free-slip
+// faces at the node are parallel planes, or the node also lies on an outflow
+// face); 2: the unit edge direction in out (the face planes meet in a line:
+// velocity along the edge, orthogonal to every face normal and so to
+// <grad phi, 1>, which lies in their span); 3: the planes meet in a point
+// (corner); 0: the integral vanishes (faces back to back).
+int slip_constraint(const MacroLattice& mac, uint32_t key, const double gint[3], double out[3]) {
+  const double gn = std::sqrt(gint[0] * gint[0] + gint[1] * gint[1] + gint[2] * gint[2]);
+  // the entries are O(1) at unit spacing: a cancellation leaves rounding only
+  if (gn <= 1e-12) return 0;
+  for (int d = 0; d < 3; ++d) out[d] = gint[d] / gn;
+  if (key & OUTFLOW_CLASS_BIT) return 1;
+  const std::vector<StarTet>& st = star_tets();
+  std::vector<std::array<double, 3>> dirs;
+  for (size_t t = 0; t < st.size(); ++t) {
+    if (!((key >> t) & 1u)) continue;
+    for (int j = 0; j < 4; ++j) {
+      if (j == st[t].m) continue;
+      const int p = st[t].partner[j];
+      if (p >= 0 && ((key >> p) & 1u)) continue;  // face shared with an active tetrahedron
+      double x[3][3];
+      int c = 0;
+      for (int n = 0; n < 4; ++n)
+        if (n != j) {
+          for (int a = 0; a < 3; ++a)
+            x[c][a] = mac.basis[a][0] * st[t].v[n][0] + mac.basis[a][1] * st[t].v[n][1] +
+                      mac.basis[a][2] * st[t].v[n][2];
+          ++c;
+        }
+      double e1[3], e2[3], nv[3];
+      for (int a = 0; a < 3; ++a) {
+        e1[a] = x[1][a] - x[0][a];
+        e2[a] = x[2][a] - x[0][a];
+      }
+      nv[0] = e1[1] * e2[2] - e1[2] * e2[1];
+      nv[1] = e1[2] * e2[0] - e1[0] * e2[2];
+      nv[2] = e1[0] * e2[1] - e1[1] * e2[0];
+      const double l = std::sqrt(nv[0] * nv[0] + nv[1] * nv[1] + nv[2] * nv[2]);
+      std::array<double, 3> u{nv[0] / l, nv[1] / l, nv[2] / l};
+      bool seen = false;
+      for (const auto& d : dirs) seen |= std::fabs(d[0] * u[0] + d[1] * u[1] + d[2] * u[2]) > 1.0 - 1e-9;
+      if (!seen) dirs.push_back(u);
+    }
+  }
+  if (dirs.size() <= 1) return 1;
+  double cvec[3] = {dirs[0][1] * dirs[1][2] - dirs[0][2] * dirs[1][1], dirs[0][2] * dirs[1][0] - dirs[0][0] * dirs[1][2],
+                    dirs[0][0] * dirs[1][1] - dirs[0][1] * dirs[1][0]};
+  const double cl = std::sqrt(cvec[0] * cvec[0] + cvec[1] * cvec[1] + cvec[2] * cvec[2]);
+  for (int a = 0; a < 3; ++a) cvec[a] /= cl;
+  for (const auto& d : dirs)
+    if (std::fabs(d[0] * cvec[0] + d[1] * cvec[1] + d[2] * cvec[2]) > 1e-9) return 3;
+  for (int a = 0; a < 3; ++a) out[a] = cvec[a];
+  return 2;
 }
 
 void class_rows(const MacroLattice& mac, uint32_t pattern, double* w) {
@@ -455,27 +564,32 @@ void class_rows(const MacroLattice& mac, uint32_t pattern, double* w) {
   }
   if (pattern & SLIP_CLASS_BIT) {
     // <grad phi, 1> = -(B^T 1): minus the sum of the B^T row weights
-    double n[3], nn = 0.0;
+    double n[3];
     for (int d = 0; d < 3; ++d) {
       n[d] = 0.0;
       for (int o = 0; o < 15; ++o) n[d] -= w[W_BT + 15 * d + o];
-      nn += n[d] * n[d];
     }
-    nn = std::sqrt(nn);
-    // zero where free-slip faces meet back to back (the entries are O(1) at
-    // unit spacing, so the cancellation leaves rounding only)
-    for (int d = 0; d < 3; ++d) w[W_NRM + d] = nn > 1e-12 ? n[d] / nn : 0.0;
-    w[W_SLIP] = 1.0;
+    double v[3];
+    const int kind = slip_constraint(mac, pattern, n, v);
+    for (int d = 0; d < 3; ++d) w[W_NRM + d] = kind == 1 || kind == 2 ? v[d] : 0.0;
+    w[W_SLIP] = kind == 1 || kind == 2 ? (double)kind : 0.0;
   }
 }
 
-// Unit normal of a class from its pattern (the integral of the hat
-// function's gradient over the active incident tetrahedra); zero when it
-// vanishes.
-void class_normal(const MacroLattice& mac, uint32_t pattern, double n[3]) {
+// Constraint kind of a free-slip class (slip_constraint) and its vector.
+int class_slip_kind(const MacroLattice& mac, uint32_t pattern, double v[3]) {
   std::vector<double> w(W_STRIDE);
   class_rows(mac, pattern | SLIP_CLASS_BIT, w.data());
-  for (int d = 0; d < 3; ++d) n[d] = w[W_NRM + d];
+  for (int d = 0; d < 3; ++d) v[d] = w[W_NRM + d];
+  if (w[W_SLIP] != 0.0) return (int)w[W_SLIP];
+  // no stored constraint: contact point (zero integral) or corner
+  double n[3];
+  for (int d = 0; d < 3; ++d) {
+    n[d] = 0.0;
+    for (int o = 0; o < 15; ++o) n[d] -= w[W_BT + 15 * d + o];
+  }
+  double u[3];
+  return slip_constraint(mac, pattern | SLIP_CLASS_BIT, n, u);
 }
 
 // D-operator rows of one class: per active tetrahedron, with the centre the
@@ -535,8 +649,17 @@ void class_rows_d(const MacroLattice& mac, uint32_t pattern, double* w) {
     }
   if (!(pattern & SLIP_CLASS_BIT)) return;
   double n[3];
-  class_normal(mac, pattern, n);
-  if (n[0] == 0.0 && n[1] == 0.0 && n[2] == 0.0) return;  // no normal: no constraint
+  const int kind = class_slip_kind(mac, pattern, n);
+  if (kind == 2) {
+    // along the edge direction t: Z = t t^T / (t^T D t)
+    double q = 0.0;
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) q += n[a] * D[a][b] * n[b];
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) w[W2_DINV + 3 * a + b] = n[a] * n[b] / q;
+    return;
+  }
+  if (kind != 1) return;  // contact points and corners are Dirichlet nodes
   // orthonormal tangent basis t1, t2: t1 from the axis least aligned with n
   int e = 0;
   for (int a = 1; a < 3; ++a)
@@ -591,7 +714,8 @@ void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std
       for (int i = 0; i < sh.nx; ++i) {
         const int64_t q = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
         if (!(flags[q] & F_IRR)) continue;
-        const uint32_t pattern = node_pattern(m, level, i, j, k) | ((flags[q] & F_SLIP) ? SLIP_CLASS_BIT : 0u);
+        const uint32_t pattern = node_pattern(m, level, i, j, k) | ((flags[q] & F_SLIP) ? SLIP_CLASS_BIT : 0u) |
+                                 ((flags[q] & F_SLIP) && (flags[q] & F_OUT) ? OUTFLOW_CLASS_BIT : 0u);
         auto it = ids.find(pattern);
         if (it == ids.end()) {
           if (n_classes >= 65535) {

@@ -67,8 +67,9 @@ int active_incident(const MacroLattice& m, int level, int i, int j, int k);
 //   [W_BT + 15 d)  B_d^T row                             (times h^2)
 //   [W_M, +15)     consistent mass row                   (times h^3)
 //   [W_LUMP]       lumped mass int phi_i                 (times h^3)
-//   [W_NRM, +3)    free-slip classes: unit normal <grad phi_i, 1> / |.|
-//   [W_SLIP]       1 for free-slip classes
+//   [W_NRM, +3)    free-slip classes: unit normal <grad phi_i, 1> / |.|, or
+//                  the unit edge direction where two face planes meet
+//   [W_SLIP]       1 (normal) or 2 (edge) for free-slip classes
 // cls receives the class of every lattice node (0 for nodes that are not
 // F_IRR; classes of F_IRR nodes start at 1), table receives
 // (n_classes + 1) * W_STRIDE doubles (class 0 unused).
@@ -77,9 +78,11 @@ int active_incident(const MacroLattice& m, int level, int i, int j, int k);
 extern const int STENCIL_OFFSETS[15][3];
 // patterns (optional) receives the key of each class: the set of active
 // incident tetrahedra (bit per (cell corner, Kuhn path) pair; class 0: all
-// 24) and SLIP_CLASS_BIT for free-slip classes.
+// 24), SLIP_CLASS_BIT for free-slip classes and OUTFLOW_CLASS_BIT for
+// free-slip nodes that also lie on an outflow face.
 constexpr uint32_t FULL_STAR_PATTERN = (1u << 24) - 1;
 constexpr uint32_t SLIP_CLASS_BIT = 1u << 24;
+constexpr uint32_t OUTFLOW_CLASS_BIT = 1u << 25;
 void stencil_classes(const MacroLattice& m, int level, const uint8_t* flags, std::vector<uint16_t>& cls,
                      std::vector<double>& table, int& n_classes, std::string& err,
                      std::vector<uint32_t>* patterns = nullptr);

@@ -186,20 +186,27 @@ def test_slip_solves_match_oracle(pkg, name, level, coarsest, mx, form):
     mesh.close()
 
 
-def test_contact_edge_nodes_are_dirichlet_and_converge(pkg):
-    """Two free-slip obstacles touching along an edge: the nodes of the
-    contact edge have no normal and take the wall's data.  With them left
-    unconstrained the FP32+IR cycle count grew with the level (10, 16, 23 at
-    levels 3-5); as Dirichlet nodes it stays within a few cycles of separated
-    obstacles (measured 9, 10, 15 against 10, 9, 12)."""
+def test_slip_convergence_is_level_independent(pkg):
+    """Free-slip obstacles with sharp edges, corners and a contact edge (Sec.
+    6.1: the convergence is robust with respect to the boundary conditions):
+    the FP32+IR cycle count stays that of the no-slip channel as the level
+    grows.  With the printed (averaged) normal at the obstacle edges it grew
+    with the level (10, 18, 29, 47 cycles at levels 3-6 for the obstacle
+    channel); with the edge directions and Dirichlet corners and contact
+    points it stays at 9-10."""
+    cases = {"edge": W.box_of_cubes(16, 4, 4, removed=((5, 1, 1), (6, 2, 1)), outflow_x_max=True,
+                                    slip_obstacles=True),
+             "apart": W.box_of_cubes(16, 4, 4, removed=((5, 1, 1), (10, 2, 2)), outflow_x_max=True,
+                                     slip_obstacles=True),
+             "channel": W.slip_channel()}
     cycles = {}
-    for name, removed in (("edge", ((5, 1, 1), (6, 2, 1))), ("apart", ((5, 1, 1), (10, 2, 2)))):
-        ch = W.box_of_cubes(16, 4, 4, removed=removed, outflow_x_max=True, slip_obstacles=True)
+    for name, ch in cases.items():
         for lev in (3, 4, 5):
             m = pkg.Mesh(ch.vertices, ch.tets, ch.bc_flags, lev, coarsest_level=1, coarse_minres_max=300,
                          coarse_minres_rtol=5e-3)
             x = m.node_coords()
             if name == "edge" and lev == 3:
+                # the contact edge x = 6, y = 2 of the two obstacles: Dirichlet nodes
                 fl = m.node_flags()
                 contact = (np.abs(x[:, 0] - 6) < 1e-12) & (np.abs(x[:, 1] - 2) < 1e-12) & (x[:, 2] > 1) & (x[:, 2] < 2)
                 assert contact.sum() == 7 and np.all((fl[contact] & pkg.NODE_DIRICHLET) > 0)
@@ -208,6 +215,6 @@ def test_contact_edge_nodes_are_dirichlet_and_converge(pkg):
             assert st.status == 0
             cycles[(name, lev)] = st.cycles
             m.close()
-    for lev in (3, 4, 5):
-        assert cycles[("edge", lev)] <= cycles[("apart", lev)] + 4, cycles
-    assert max(cycles[("edge", l)] for l in (3, 4, 5)) <= 17, cycles
+    for name in cases:
+        c = [cycles[(name, lev)] for lev in (3, 4, 5)]
+        assert max(c) <= 11 and max(c) - min(c) <= 2, cycles

@@ -11,10 +11,11 @@ B Pi (Pi = I - n n^T at slip nodes).  What fixes it independently:
     triangles (area / 3 per vertex times the outward unit normal), without
     B.  On a flat face it is the face normal;
   * mass conservation: sum_j (B u)_j = -sum_i <grad phi_i, 1> . u_i, and a
-    slip node's term vanishes exactly when n_i is the mass-conservative
-    normal, so the flux out of the channel equals the interpolated inflow
-    with free-slip obstacles; with the geometric (face-averaged) normals it
-    does not;
+    slip node's term vanishes exactly when its admissible velocities are
+    orthogonal to <grad phi_i, 1> (the tangent plane of the mass-conservative
+    normal; along an obstacle edge, the edge direction), so the flux out of
+    the channel equals the interpolated inflow with free-slip obstacles; with
+    one face's normal at the edge nodes it does not;
   * exact states on the cube with free-slip faces x = 0 and x = 1: a linear
     divergence-free flow tangential to them with no x-dependence of its
     tangential part satisfies both the Laplace and the D-form natural
@@ -138,13 +139,19 @@ def test_mass_conservation_with_free_slip_obstacles():
     u0, _ = direct.solve_direct(L0, f0, g0)
     assert np.abs(L0.scatter(u0, uD) - u_full).max() > 1e-2
 
-    # the same system with geometric normals (mean of the incident faces'
-    # unit normals) loses the flux balance: at obstacle corners whose faces
-    # carry different areas of the corner node's hat function the two differ
+    # edge nodes are constrained along the edge: orthogonal to both faces'
+    # normals and to the mass-conservative normal
+    assert L.slip_edge.any() and not L.slip_edge.all()
+    Pe = L.slip_P[L.slip_edge]
+    assert np.abs(np.einsum("nab,nb->na", Pe, L.normals[L.slip_edge])).max() <= 1e-13
+    assert np.allclose(np.einsum("naa->n", Pe), 1.0)
+    # the same system with one face's normal at the edge nodes loses the flux balance
     Lg = S.build_from_macro(ch, 1)
-    geo = _face_mean_normals(Lg)
-    assert np.abs(geo - Lg.normals).max() > 1e-3
-    Lg.normals = geo
+    ax = np.argmax(np.abs(Lg.normals), axis=1)
+    one = np.zeros_like(Lg.normals)
+    one[np.arange(len(ax)), ax] = np.sign(Lg.normals[np.arange(len(ax)), ax])
+    P1 = np.eye(3)[None] - one[:, :, None] * one[:, None, :]
+    Lg.slip_P = np.where(Lg.slip_edge[:, None, None], P1, Lg.slip_P)
     S.couple(Lg)
     ug, _ = direct.solve_direct(Lg, *Lg.rhs(None, uD))
     out_g, inn_g = _channel_flux_balance(Lg, ug, uD)
@@ -216,33 +223,38 @@ def test_exact_state_on_slip_cube(form, level):
 
 @pytest.mark.parametrize("form", ["laplace", "D"])
 def test_slip_node_update_is_tangential_part_of_free_update(form):
-    """Block Gauss-Seidel on Pi A Pi + (I - Pi) at a slip node, from a
-    tangential iterate, equals: Laplace form, the unconstrained
-    component-wise update projected; D form, Z (rhs - off-diagonal row)
-    with Z = T (T^T A_ii T)^-1 T^T on the tangent plane."""
+    """Block Gauss-Seidel on Pi A Pi + (I - Pi) at a slip node, from an
+    admissible iterate, equals: Laplace form, the unconstrained
+    component-wise update projected on the node's admissible subspace (the
+    tangent plane, or the edge direction at obstacle edges); D form,
+    Z (rhs - off-diagonal row) with Z = T (T^T A_ii T)^-1 T^T, T an
+    orthonormal basis of that subspace."""
     L = S.build_from_macro(W.slip_channel(), 1, form=form)
     rng = np.random.default_rng(3)
     u = L.proj(rng.standard_normal((3, L.n_u)))
     rhs = rng.standard_normal((3, L.n_u))
-    for q in (0, len(L.slip) // 3, len(L.slip) - 1):
+    edges = np.where(L.slip_edge)[0]
+    planes = np.where(~L.slip_edge)[0]
+    for q in (planes[0], planes[-1], edges[0], edges[-1]):
         i = L.slip[q]
+        P = L.slip_P[q]
         r = L.proj(rhs)[:, i] - L.apply_A(u)[:, i]
         new_block = u[:, i] + np.linalg.solve(L.Kv_node[i], r)
-        nrm = L.normals[q]
         # unconstrained row without the node itself
         if form == "D":
             full = L.A2 @ u.ravel()
             Aii = L.A2_node[i]
             off = full.reshape(3, L.n_u)[:, i] - Aii @ u[:, i]
-            T = np.linalg.svd(np.eye(3) - np.outer(nrm, nrm))[0][:, :2]
+            w, V = np.linalg.eigh(P)
+            T = V[:, w > 0.5]
             Z = T @ np.linalg.solve(T.T @ Aii @ T, T.T)
             new_gpu = Z @ (rhs[:, i] - off)
         else:
             off = np.array([(L.A @ u[d])[i] for d in range(3)]) - L.A_diag[i] * u[:, i]
             free_upd = (rhs[:, i] - off) / L.A_diag[i]
-            new_gpu = free_upd - nrm * np.dot(nrm, free_upd)
+            new_gpu = P @ free_upd
         assert np.abs(new_block - new_gpu).max() <= 1e-12 * np.abs(new_gpu).max()
-        assert abs(np.dot(new_block, nrm)) <= 1e-13 * np.abs(new_block).max()
+        assert np.abs(new_block - P @ new_block).max() <= 1e-13 * np.abs(new_block).max()
 
 
 def test_shgs_symmetric_with_slip():
@@ -275,7 +287,7 @@ def test_laplace_smoother_matrix_unchanged_without_slip():
     assert np.abs(Msm - Msm.T).max() <= 1e-13 * np.abs(Msm).max()
 
 
-@pytest.mark.parametrize("name,form,level,coarsest", [("channel", "laplace", 1, 0), ("cube", "D", 3, 2),
+@pytest.mark.parametrize("name,form,level,coarsest", [("channel", "laplace", 2, 1), ("cube", "D", 3, 2),
                                                       ("cube", "laplace", 3, 2)])
 def test_multigrid_converges_to_direct_solution(name, form, level, coarsest):
     macro = W.slip_channel() if name == "channel" else W.slip_cube()
