@@ -58,6 +58,8 @@ def macro_by_name(name):
         return W.slip_channel()
     if name == "slip_cube":
         return W.slip_cube()
+    if name == "sheared_slip":
+        return W.sheared_slip_cube()
     if name == "partial":
         # two unit cubes with two Kuhn tetrahedra removed and one listed along
         # its reversed path: partially filled macro cells, irregular rows inside

@@ -59,7 +59,7 @@ def _normal_part(L, u):
 
 
 @pytest.mark.parametrize("form", ["laplace", "D"])
-@pytest.mark.parametrize("name,level", [("slip_channel", 2), ("slip_cube", 3)])
+@pytest.mark.parametrize("name,level", [("slip_channel", 2), ("slip_cube", 3), ("sheared_slip", 3)])
 def test_operator_rhs_smoother_residual(pkg, name, level, form):
     macro, mesh, H = _pair(pkg, name, form, level, level - 1)
     L = H.levels[level]
@@ -146,7 +146,8 @@ def test_transfers_coarse_solve_and_vcycle_iterates(pkg, name, level, coarsest, 
 
 
 @pytest.mark.parametrize("form", ["laplace", "D"])
-@pytest.mark.parametrize("name,level,coarsest,mx", [("slip_cube", 5, 2, 5), ("slip_channel", 3, 1, 200)])
+@pytest.mark.parametrize("name,level,coarsest,mx", [("slip_cube", 5, 2, 5), ("slip_channel", 3, 1, 200),
+                                                    ("sheared_slip", 4, 2, 5)])
 def test_slip_solves_match_oracle(pkg, name, level, coarsest, mx, form):
     macro, mesh, H = _pair(pkg, name, form, level, coarsest, mx)
     L = H.levels[level]

@@ -329,3 +329,26 @@ def test_fmg_exact_on_slip_cube():
     p_ref = phi - np.dot(L.m, phi) / L.m.sum()
     assert np.abs(res.u - u_ex[L.free].T).max() <= 1e-8 * np.abs(u_ex).max()
     assert np.abs(res.p - p_ref).max() <= 1e-7 * np.abs(p_ref).max()
+
+
+@pytest.mark.parametrize("form", ["laplace", "D"])
+def test_exact_state_on_sheared_slip_cube(form):
+    """Free-slip faces on the tilted planes x = y and x = y + 1 of the sheared
+    cube (affine lattice): their normals are (-1, 1, 0) / sqrt 2, and a
+    constant flow along the planes plus a hydrostatic pressure is an exact
+    discrete solution in both forms."""
+    L = S.build_from_macro(W.sheared_slip_cube(), 2, form=form)
+    assert len(L.slip) == 18 and not L.slip_edge.any()
+    exp = np.array([-1.0, 1.0, 0.0]) / np.sqrt(2.0)
+    assert np.abs(np.abs(L.normals @ exp) - 1.0).max() <= 1e-13
+    x = L.mesh.xyz
+    u_ex = np.broadcast_to(np.array([0.7, 0.7, -0.3]), x.shape).copy()
+    grad = np.array([0.4, -1.1, 0.6])
+    f, g = L.rhs(np.broadcast_to(grad, x.shape).copy(), u_ex)
+    phi = x @ grad
+    p_ref = phi - np.dot(L.m, phi) / L.m.sum()
+    ru, rp = L.residual(u_ex[L.free].T, p_ref, f, g)
+    scale = max(np.abs(f).max(), np.abs(g).max())
+    assert np.abs(ru).max() <= 1e-13 * scale and np.abs(rp).max() <= 1e-13 * scale
+    u, p = direct.solve_direct(L, f, g)
+    assert np.abs(u - u_ex[L.free].T).max() <= 1e-9 and np.abs(p - p_ref).max() <= 1e-9 * np.abs(p_ref).max()

@@ -177,6 +177,15 @@ def slip_cube() -> MacroMesh:
     return box_of_cubes(1, 1, 1, slip_sides=("x0", "x1"))
 
 
+def sheared_slip_cube() -> MacroMesh:
+    """The slip cube under the shear of sheared_cube: free-slip faces on the
+    two tilted planes x = y and x = y + 1."""
+    m = slip_cube()
+    m.vertices = m.vertices @ SHEAR.T
+    m.basis = SHEAR.copy()
+    return m
+
+
 # --- manufactured solution of the TME study (Sec. 5) -----------------------
 
 def manufactured_velocity(x: np.ndarray) -> np.ndarray:
