@@ -53,7 +53,7 @@ class Options(ctypes.Structure):
                 ("colour_block_z", ctypes.c_int32), ("resident_node_lists", ctypes.c_int32),
                 ("fused_tile_rows", ctypes.c_int32), ("wait_poll_limit", ctypes.c_int64),
                 ("operator_form", ctypes.c_int32), ("colour_pairs", ctypes.c_int32),
-                ("fused_wait_test", ctypes.c_int32)]
+                ("fused_wait_test", ctypes.c_int32), ("quad_min_nodes", ctypes.c_int32)]
 
 
 class _Stats(ctypes.Structure):

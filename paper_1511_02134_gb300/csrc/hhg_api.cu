@@ -7,6 +7,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <limits>
 #include <string>
 #include <vector>
 
@@ -166,8 +167,6 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     L.omega = (T)M->opt.omega;
     const int64_t lim = M->opt.spec_max_nodes != 0 ? M->opt.spec_max_nodes : SPEC_MAX_NODES;
     L.spec = lim > 0 && H.sh.n() < lim;
-    // two planes per block on levels that stream from HBM (level 9: 5 % per
-    // Uzawa step); no effect measured at level 7
     const int want = M->opt.colour_block_z;
     // one plane per block: measured 4-5 % faster per FP32 Uzawa step than two on the level-8 and level-9 cubes
     L.cbz = want == 1 || want == 2 || want == 4 ? want : 1;
@@ -180,6 +179,13 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
     // unaligned x-neighbour pairs of two residues in four cost more than the
     // halved load count saves)
     L.pairs = sizeof(T) == 4 && M->opt.colour_pairs > 0 && !L.spec;
+    {
+      const int32_t q = M->opt.quad_min_nodes;
+      // four nodes per thread pays on the largest levels only (measured: level 9
+      // 5.10 -> 4.30 ms, level 8 unchanged, level 7 0.100 -> 0.114 ms)
+      const int64_t lim = q == 0 ? ((int64_t)1 << 25) : (q < 0 ? std::numeric_limits<int64_t>::max() : (int64_t)q);
+      L.quad = H.sh.n() >= lim ? 1 : 0;
+    }
     L.nq2 = L.nq / 2 + 1;
     L.nq2_mul = L.nq2 == 1 ? 0 : ~0ull / (uint64_t)L.nq2 + 1;
   };

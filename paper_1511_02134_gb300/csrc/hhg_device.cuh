@@ -51,6 +51,7 @@ struct LevelDev {
   int nq;                // quarter-row slots per row, (nx + 3) / 4: the colour kernels' packed index
   uint64_t nq_mul;       // ceil(2^64 / nq) (0 when nq = 1): t / nq = umul64hi(t, nq_mul)
   int pairs;             // FP32 colour kernels update two nodes per thread (hhg_kernels.cu)
+  int quad;              // the residual four nodes per thread (k_residual_quad, Laplace form)
   int nq2;               // pair slots per row, nq / 2 + 1
   uint64_t nq2_mul;      // ceil(2^64 / nq2)
   T* u[3];

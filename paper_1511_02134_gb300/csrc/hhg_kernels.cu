@@ -265,6 +265,145 @@ __global__ void k_residual(LevelDev<T> L) {
   node_residual<T, DF>(L, node_at(L.px, L.pxy, i, j, k));
 }
 
+// The residual of the Laplace form on large levels, four nodes per thread:
+// the nodes at padded x = 4 pos .. 4 pos + 3 of one row, which sit at the
+// same position pos of the four residue groups (rows grouped by x mod 4).
+// Their 15-point stencils share most neighbours: per field the quad reads 36
+// values (6 in its own row, 5 in each of the rows y +- 1, z +- 1, (y, z) +-
+// (1, 1)) instead of 4 x 15, so each thread issues about half the loads of the
+// per-node kernel.  A quad with a node outside the lattice, without an
+// unknown or on the boundary (F_IRR) takes the per-node body for each of its
+// nodes.  The arithmetic is that of node_residual_v for regular nodes.
+struct QuadRows {
+  int64_t c;        // padded index of the quad's first node (padded x = 4 pos, residue 0)
+  int64_t g;        // entries per residue group, px / 4
+  int64_t py, pz;   // row steps +y, +z
+};
+
+// The 6 values of the quad's own row (padded x = 4 pos - 1 .. 4 pos + 4), the
+// 5 of a row above (x = 4 pos .. 4 pos + 4) or below (x = 4 pos - 1 .. 4 pos + 3).
+template <class T>
+__device__ __forceinline__ void quad_row6(const T* x, const QuadRows& q, int64_t r, T v[6]) {
+  const int64_t b = q.c + r;
+  v[0] = x[b + 3 * q.g - 1];
+  v[1] = x[b];
+  v[2] = x[b + q.g];
+  v[3] = x[b + 2 * q.g];
+  v[4] = x[b + 3 * q.g];
+  v[5] = x[b + 1];
+}
+template <class T>
+__device__ __forceinline__ void quad_row_up(const T* x, const QuadRows& q, int64_t r, T v[5]) {
+  const int64_t b = q.c + r;
+  v[0] = x[b];
+  v[1] = x[b + q.g];
+  v[2] = x[b + 2 * q.g];
+  v[3] = x[b + 3 * q.g];
+  v[4] = x[b + 1];
+}
+template <class T>
+__device__ __forceinline__ void quad_row_down(const T* x, const QuadRows& q, int64_t r, T v[5]) {
+  const int64_t b = q.c + r;
+  v[0] = x[b + 3 * q.g - 1];
+  v[1] = x[b];
+  v[2] = x[b + q.g];
+  v[3] = x[b + 2 * q.g];
+  v[4] = x[b + 3 * q.g];
+}
+
+// One field around the quad: centre, the six axis neighbours' sum and the
+// seven antisymmetric differences of each of the four nodes.
+template <class T>
+struct QuadField {
+  T ctr[4], nb6[4];
+  Diff7<T> d[4];
+};
+
+template <class T>
+__device__ __forceinline__ QuadField<T> quad_field(const T* x, const QuadRows& q) {
+  T o[6], ym[5], yp[5], zm[5], zp[5], wm[5], wp[5];
+  quad_row6(x, q, 0, o);
+  quad_row_up(x, q, q.py, yp);
+  quad_row_down(x, q, -q.py, ym);
+  quad_row_up(x, q, q.pz, zp);
+  quad_row_down(x, q, -q.pz, zm);
+  quad_row_up(x, q, q.py + q.pz, wp);
+  quad_row_down(x, q, -q.py - q.pz, wm);
+  QuadField<T> f;
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    f.ctr[n] = o[n + 1];
+    f.nb6[n] = ((o[n] + o[n + 2]) + (ym[n + 1] + yp[n])) + (zm[n + 1] + zp[n]);
+    f.d[n].e1 = o[n + 2] - o[n];
+    f.d[n].e2 = yp[n] - ym[n + 1];
+    f.d[n].e3 = zp[n] - zm[n + 1];
+    f.d[n].f12 = yp[n + 1] - ym[n];
+    f.d[n].f23 = wp[n] - wm[n + 1];
+    f.d[n].f13 = zp[n + 1] - zm[n];
+    f.d[n].b = wp[n + 1] - wm[n];
+  }
+  return f;
+}
+
+template <class T>
+__global__ void __launch_bounds__(FX * FY) k_residual_quad(LevelDev<T> L) {
+  pdl_enter();
+  const int pos = blockIdx.x * FX + threadIdx.x;
+  const int j = blockIdx.y * FY + threadIdx.y;
+  const int k = blockIdx.z;
+  const int i0 = 4 * pos - 1;  // lattice x of the quad's first node
+  if (j >= L.ny || i0 >= L.nx) return;
+  QuadRows q;
+  q.g = L.px >> 2;
+  q.c = (int64_t)pos + L.px * (j + 1) + L.pxy * (k + 1);
+  q.py = L.px;
+  q.pz = L.pxy;
+  bool fast = i0 >= 0 && i0 + 3 < L.nx;
+  uint8_t fl[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    fl[n] = fast ? L.flags[q.c + n * q.g] : (uint8_t)0;
+    fast = fast && (fl[n] & (F_ACT | F_VFREE | F_IRR)) == (F_ACT | F_VFREE);
+  }
+  if (!fast) {
+    for (int n = 0; n < 4; ++n) {
+      if (i0 + n < 0 || i0 + n >= L.nx) continue;
+      node_residual<T, 0>(L, node_at(L.px, L.pxy, i0 + n, j, k));
+    }
+    return;
+  }
+  T ru[3][4], rp[4];
+  {
+    const QuadField<T> p = quad_field(L.p, q);
+    const T s = -L.h2 * (T)(1.0 / 12.0);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      T dv[3];
+      div12_all(p.d[n], dv);
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ru[d][n] = L.f[d][q.c + n * q.g] - s * dv[d];
+      rp[n] = L.g[q.c + n * q.g] + L.c * ((T)6 * p.ctr[n] - p.nb6[n]);
+    }
+  }
+  T dsum[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const QuadField<T> u = quad_field(L.u[d], q);
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+      ru[d][n] -= L.nuh * ((T)6 * u.ctr[n] - u.nb6[n]);
+      dsum[n] += div12(u.d[n], d);
+    }
+  }
+#pragma unroll
+  for (int n = 0; n < 4; ++n) {
+    const int64_t c = q.c + n * q.g;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) L.r[d][c] = ru[d][n];
+    L.rp[c] = rp[n] - L.h2 * (T)(1.0 / 12.0) * dsum[n];
+  }
+}
+
 template <class T>
 __global__ void k_restrict(LevelDev<T> Lf, LevelDev<T> Lc) {
   pdl_enter();
@@ -1223,10 +1362,14 @@ void launch_pres_colour(const LevelDev<T>& L, int colour, cudaStream_t s) {
 }
 template <class T>
 void launch_residual(const LevelDev<T>& L, cudaStream_t s) {
-  if (L.wt2)
+  if (L.wt2) {
     launch_k(k_residual<T, 1>, full_grid(L), dim3(FX, FY), s, L);
-  else
+  } else if (L.quad) {
+    const int npos = L.nx / 4 + 1;  // quads cover padded x = 0 .. 4 npos - 1 >= nx
+    launch_k(k_residual_quad<T>, dim3((npos + FX - 1) / FX, (L.ny + FY - 1) / FY, L.nz), dim3(FX, FY), s, L);
+  } else {
     launch_k(k_residual<T, 0>, full_grid(L), dim3(FX, FY), s, L);
+  }
 }
 template <class T>
 void launch_restrict(const LevelDev<T>& fine, const LevelDev<T>& coarse, cudaStream_t s) {

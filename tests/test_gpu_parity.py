@@ -261,11 +261,12 @@ def test_fp32_steps_match_oracle(pkg, name, level, cbz, fused, pairs):
 
 
 def test_level6_large_level_kernels_match_oracle(pkg):
-    """The colour kernels in the form the bench uses on levels of 2^22 nodes
-    and more (flags-first node form, two planes per colour block), on a
-    level large enough to span many blocks with ragged edges (65^3 nodes):
-    FP64 Uzawa steps and a V-cycle against the oracle, and FP32 Uzawa steps."""
-    macro, mesh, H = _pair(pkg, "cube", 6, coarsest=2, spec_max_nodes=-1, colour_block_z=2)
+    """The kernels in the forms the bench uses on its largest levels
+    (flags-first node form, two planes per colour block, the residual four
+    nodes per thread), on a level large enough to span many blocks with
+    ragged edges (65^3 nodes): FP64 Uzawa steps and a V-cycle against the
+    oracle, and FP32 Uzawa steps."""
+    macro, mesh, H = _pair(pkg, "cube", 6, coarsest=2, spec_max_nodes=-1, colour_block_z=2, quad_min_nodes=1)
     L = H.levels[6]
     st = _random_state(H, 6, 23)
     _load(mesh, H, 6, st)
@@ -286,6 +287,34 @@ def test_level6_large_level_kernels_match_oracle(pkg):
         MG.uzawa_step(H, 6, u, p, f, g)
     gu, gp = _read_up(mesh, H, 6, precision=1)
     assert rel_err(gu, u) < TOL32 and rel_err(gp, p) < TOL32
+    mesh.close()
+
+
+@pytest.mark.parametrize("name,level", [("cube", 4), ("cube", 5), ("channel", 2), ("partial", 3), ("sheared", 3)])
+def test_quad_residual_matches_oracle(pkg, name, level):
+    """The residual four nodes per thread (quad_min_nodes = 1 forces it on
+    every level): quads of regular nodes take the shared-load path, quads
+    with a boundary, Dirichlet or outside node the per-node body (the
+    partially filled and sheared meshes exercise the fallback), in FP64 and
+    FP32 against the oracle, and V-cycle iterates with it."""
+    macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level - 1), quad_min_nodes=1)
+    L = H.levels[level]
+    dims = mesh.dims()
+    st = _random_state(H, level, 29)
+    ru, rp = L.residual(*st)
+    for prec, tol in ((0, TOL64), (1, 10 * TOL32)):
+        _load(mesh, H, level, st, precision=prec)
+        mesh.level_op(level, "residual", precision=prec)
+        assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU", prec)), ru) < tol, prec
+        assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP", prec)), rp) < tol, prec
+    if name == "cube":
+        _load(mesh, H, level, st)
+        u, p, f, g = (a.copy() for a in st)
+        for _ in range(2):
+            mesh.level_op(level, "vcycle")
+            MG.vcycle(H, level, u, p, f, g)
+            gu, gp = _read_up(mesh, H, level)
+            assert rel_err(gu, u) < TOL64 and _p_err(L, gp, p) < TOL64
     mesh.close()
 
 
