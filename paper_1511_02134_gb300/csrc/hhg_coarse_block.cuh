@@ -276,7 +276,15 @@ __device__ inline void minres_team(const Team& tm, const CoarseSys& S, const Lev
       const int d = q / nv;
       const int c = S.vidx[q - d * nv];
       up = (double)L.u[d][c];
-      fg = (double)L.f[d][c];
+      if (L.flags[c] & F_SLIP) {
+        // the admissible part of f at a free-slip node: the assembled rows
+        // carry the identity in the constrained directions (Sec. 6.1)
+        T fv[3] = {L.f[0][c], L.f[1][c], L.f[2][c]};
+        slip_project(class_row(L, c), fv);
+        fg = (double)fv[d];
+      } else {
+        fg = (double)L.f[d][c];
+      }
     } else {
       const int c = S.pidx[q - 3 * nv];
       up = (double)L.p[c];

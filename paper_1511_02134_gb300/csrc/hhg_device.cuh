@@ -339,6 +339,24 @@ __device__ __forceinline__ T row_C(const LevelDev<T>& L, const T* p, const Node&
   return row_C_v(L, gnb(p, n, L.px, L.pxy), row_of(L, n.c, fl), fl);
 }
 
+// Free slip (Sec. 6.1): the admissible part of a velocity value or residual
+// at a node whose class row w is a free-slip class: v - n (n . v) in the
+// tangent plane of the normal n, or t (t . v) along the edge direction t.
+template <class T>
+__device__ __forceinline__ void slip_project(const T* w, T v[3]) {
+  const T kind = w[W_SLIP];
+  if (kind != (T)0) {
+    const T s = (w[W_NRM] * v[0] + w[W_NRM + 1] * v[1]) + w[W_NRM + 2] * v[2];
+    if (kind == (T)1) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] -= s * w[W_NRM + d];
+    } else {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) v[d] = s * w[W_NRM + d];
+    }
+  }
+}
+
 // Lumped pressure mass m_i = int phi_i.
 template <class T>
 __device__ __forceinline__ T lumped_mass(const LevelDev<T>& L, int64_t c, uint8_t fl) {

@@ -16,24 +16,6 @@ __device__ __forceinline__ bool d_form(const LevelDev<T>& L) {
   return DF < 0 ? L.wt2 != nullptr : DF == 1;
 }
 
-// Free slip (Sec. 6.1): the admissible part of a velocity value or residual
-// at a node whose class row w is a free-slip class: v - n (n . v) in the
-// tangent plane of the normal n, or t (t . v) along the edge direction t.
-template <class T>
-__device__ __forceinline__ void slip_project(const T* w, T v[3]) {
-  const T kind = w[W_SLIP];
-  if (kind != (T)0) {
-    const T s = (w[W_NRM] * v[0] + w[W_NRM + 1] * v[1]) + w[W_NRM + 2] * v[2];
-    if (kind == (T)1) {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) v[d] -= s * w[W_NRM + d];
-    } else {
-#pragma unroll
-      for (int d = 0; d < 3; ++d) v[d] = s * w[W_NRM + d];
-    }
-  }
-}
-
 // RU = F - B^T P (velocity nodes).
 template <class T>
 __device__ __forceinline__ void node_vel_rhs(const LevelDev<T>& L, const Node& n) {

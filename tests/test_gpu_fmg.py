@@ -37,14 +37,16 @@ def _oracle_rhs(H, force, vel):
 
 
 @pytest.mark.parametrize("cycles", [1, 2])
-@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 4, 2, 5), ("channel", 2, 1, 30), ("partial", 3, 1, 30)])
+@pytest.mark.parametrize("name,level,coarsest,mx", [("cube", 4, 2, 5), ("channel", 2, 1, 30), ("partial", 3, 1, 30),
+                                                    ("slip_cube", 4, 2, 5), ("slip_channel", 2, 1, 30),
+                                                    ("sheared", 4, 2, 5)])
 def test_fmg_matches_oracle(pkg, name, level, coarsest, mx, cycles):
     macro = macro_by_name(name)
     mesh = pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=coarsest, coarse_minres_max=mx)
     H = MG.build_hierarchy(macro, level, coarsest=coarsest, opt=MG.Options(coarse_minres_max=mx))
-    if name == "cube":
+    if name in ("cube", "slip_cube", "sheared"):
         force, vel = W.manufactured_forcing, W.manufactured_velocity
-    elif name == "channel":
+    elif name in ("channel", "slip_channel"):
         force, vel = (lambda x: np.zeros_like(x)), W.channel_inflow
     else:
         force, vel = (lambda x: np.cos(3 * x) + 0.5), (lambda x: np.zeros_like(x))
@@ -112,4 +114,24 @@ def test_fmg_fp32_cycles_match_fp64_fmg(pkg):
     assert s32.cycles == s64.cycles
     assert rel_err(u32, u64) < 1e-5 and rel_err(p32, p64) < 1e-4
     assert s32.rel_residual == pytest.approx(s64.rel_residual, rel=1e-3)
+    mesh.close()
+
+
+@pytest.mark.parametrize("name", ["cube", "slip_cube"])
+def test_fmg_d_form_matches_oracle(pkg, name):
+    """FMG in the D-operator formulation (Sec. 2.1, a_2) against the oracle's
+    D-form FMG, with and without free-slip faces."""
+    macro = macro_by_name(name)
+    level, coarsest = 4, 2
+    mesh = pkg.Mesh(macro.vertices, macro.tets, macro.bc_flags, level, coarsest_level=coarsest, operator_form=1)
+    H = MG.build_hierarchy(macro, level, coarsest=coarsest, form="D")
+    rhs, dird = _oracle_rhs(H, W.manufactured_forcing, W.manufactured_velocity)
+    ref = MG.fmg(H, rhs, dird, cycles=1, nu=2)
+    x = mesh.node_coords()
+    u, p, st = mesh.fmg_solve(W.manufactured_forcing(x), W.manufactured_velocity(x), cycles=1, nu=2)
+    L = H.levels[level]
+    lat = lattice_index(L, mesh.dims())
+    assert st.cycles == ref.cycles
+    assert rel_err(u[lat], L.scatter(ref.u, dird[level])) < 1e-12
+    assert rel_err(p[lat], ref.p) < 1e-12
     mesh.close()
