@@ -140,10 +140,10 @@ typedef struct hhg_options {
                                 first staged plane delivers, so that its first wait runs out (the
                                 pass then withdraws them, waits for its copies to land and reports
                                 HHG_ECUDA); 0 = off */
-  int32_t quad_min_nodes;    /* Laplace-form levels with at least this many lattice nodes compute
-                                the residual four nodes per thread, sharing their neighbours'
-                                loads; 0 = default (2^25: the level-9 cube, 5.10 -> 4.30 ms; no
-                                gain at level 8, a loss at level 7), -1 = never */
+  int32_t quad_min_nodes;    /* FP32 Laplace-form levels with at least this many lattice nodes
+                                compute the residual four nodes per thread, sharing their
+                                neighbours' loads; 0 = default (2^25: the level-9 cube, 5.10 ->
+                                4.30 ms; no gain at level 8, a loss at level 7), -1 = never */
 } hhg_options;
 
 /* Per-solve statistics. */

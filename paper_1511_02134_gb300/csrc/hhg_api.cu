@@ -184,7 +184,7 @@ void fill_coefs(hhg_mesh* M, LevelHost& H) {
       // four nodes per thread pays on the largest levels only (measured: level 9
       // 5.10 -> 4.30 ms, level 8 unchanged, level 7 0.100 -> 0.114 ms)
       const int64_t lim = q == 0 ? ((int64_t)1 << 25) : (q < 0 ? std::numeric_limits<int64_t>::max() : (int64_t)q);
-      L.quad = H.sh.n() >= lim ? 1 : 0;
+      L.quad = sizeof(T) == 4 && H.sh.n() >= lim ? 1 : 0;  // FP64: 176 registers, no gain
     }
     L.nq2 = L.nq / 2 + 1;
     L.nq2_mul = L.nq2 == 1 ? 0 : ~0ull / (uint64_t)L.nq2 + 1;

@@ -292,29 +292,28 @@ def test_level6_large_level_kernels_match_oracle(pkg):
 
 @pytest.mark.parametrize("name,level", [("cube", 4), ("cube", 5), ("channel", 2), ("partial", 3), ("sheared", 3)])
 def test_quad_residual_matches_oracle(pkg, name, level):
-    """The residual four nodes per thread (quad_min_nodes = 1 forces it on
-    every level): quads of regular nodes take the shared-load path, quads
+    """The FP32 residual four nodes per thread (quad_min_nodes = 1 forces it
+    on every level): quads of regular nodes take the shared-load path, quads
     with a boundary, Dirichlet or outside node the per-node body (the
-    partially filled and sheared meshes exercise the fallback), in FP64 and
-    FP32 against the oracle, and V-cycle iterates with it."""
+    partially filled and sheared meshes exercise the fallback), against the
+    oracle, and FP32 V-cycles with it; the FP64 residual keeps the per-node
+    kernel."""
     macro, mesh, H = _pair(pkg, name, level, coarsest=min(2, level - 1), quad_min_nodes=1)
     L = H.levels[level]
     dims = mesh.dims()
     st = _random_state(H, level, 29)
     ru, rp = L.residual(*st)
-    for prec, tol in ((0, TOL64), (1, 10 * TOL32)):
+    for prec, tol in ((0, TOL64), (1, TOL32)):
         _load(mesh, H, level, st, precision=prec)
         mesh.level_op(level, "residual", precision=prec)
         assert rel_err(u_from_lattice(L, dims, mesh.level_field(level, "RU", prec)), ru) < tol, prec
         assert rel_err(p_from_lattice(L, dims, mesh.level_field(level, "RP", prec)), rp) < tol, prec
-    if name == "cube":
-        _load(mesh, H, level, st)
-        u, p, f, g = (a.copy() for a in st)
-        for _ in range(2):
-            mesh.level_op(level, "vcycle")
-            MG.vcycle(H, level, u, p, f, g)
-            gu, gp = _read_up(mesh, H, level)
-            assert rel_err(gu, u) < TOL64 and _p_err(L, gp, p) < TOL64
+    _load(mesh, H, level, st, precision=1)
+    u, p, f, g = (a.copy() for a in st)
+    mesh.level_op(level, "vcycle", precision=1)
+    MG.vcycle(H, level, u, p, f, g)
+    gu, gp = _read_up(mesh, H, level, precision=1)
+    assert rel_err(gu, u) < TOL32 and _p_err(L, gp, p) < TOL32
     mesh.close()
 
 
