@@ -9,7 +9,8 @@ FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
 the level-7 cube (8,291,838 free DoFs) under "level7" and the level-4 cube
 (15,038 free DoFs, latency-bound) under "level4".  "fmg" times full
-multigrid (Sec. 5) on the headline level, with its error ratio gamma;
+multigrid (Sec. 5) on the headline level, with its error ratio gamma, and
+the 1e-8 solve started from one FMG pass;
 "channel_level6" times the obstacle channel (2.6e8 free DoFs) FP32+IR solve
 and "slip_channel_level6" the same channel with free-slip obstacles (Sec. 6.1);
 "dform_level7" the D-operator formulation beside the Laplace form.
@@ -301,6 +302,27 @@ class LevelBench:
                 "ms": best, "value": self.world * self.dofs / (best / 1e3), "unit": "DoF/s",
                 "gamma": (hnorm2(u, p) / disc) ** 0.5, "rel_residual": st.rel_residual, "cycles": st.cycles}
             del u, p
+        # FMG as the start of the 1e-8 solve: one V_var(2,2) FMG pass with FP32
+        # corrections, then FP32+IR cycles from its iterate until the residual is
+        # 1e-8 of the zero start's (the bench criterion)
+        best, info = None, None
+        for _ in range(fmg_reps):
+            torch.cuda.synchronize()
+            e0.record(self.stream)
+            _, _, sf = self.mesh.fmg_solve(self.f_dev, self.ud_dev, cycles=1, nu=2, mode=pkg.MODE_FP32_IR,
+                                           want_solution=False)
+            _, _, ss = self.mesh.solve(tol=TOL / sf.rel_residual, max_cycles=50, mode=pkg.MODE_FP32_IR,
+                                       want_solution=False)
+            e1.record(self.stream)
+            e1.synchronize()
+            if ss.status != 0:
+                raise RuntimeError(f"solve from the FMG iterate did not converge: {ss}")
+            ms = e0.elapsed_time(e1)
+            if best is None or ms < best:
+                best, info = ms, (sf.rel_residual, ss.cycles, sf.rel_residual * ss.rel_residual)
+        fmg["fmg_start_to_1e-8_fp32ir"] = {
+            "ms": best, "value": self.world * self.dofs / (best / 1e3), "unit": "DoF/s",
+            "fmg_rel_residual": info[0], "cycles_after_fmg": info[1], "rel_residual": info[2]}
         out_fmg = fmg
         del u_ref, p_ref
         return out, out_fmg

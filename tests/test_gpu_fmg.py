@@ -135,3 +135,30 @@ def test_fmg_d_form_matches_oracle(pkg, name):
     assert rel_err(u[lat], L.scatter(ref.u, dird[level])) < 1e-12
     assert rel_err(p[lat], ref.p) < 1e-12
     mesh.close()
+
+
+def test_fp32ir_solve_continues_from_fmg(pkg):
+    """FP32+IR cycles continue from the FMG iterate (the fixed-point iterate
+    is quantised from it) to the same 1e-8 of the zero start's residual, in
+    fewer cycles, to the oracle's solution."""
+    cube = W.unit_cube()
+    level = 5
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, level)
+    x = mesh.node_coords()
+    fn, ud = W.manufactured_forcing(x), W.manufactured_velocity(x)
+    mesh.set_rhs(fn, ud)
+    _, _, st0 = mesh.solve(tol=1e-8, max_cycles=40, mode=pkg.MODE_FP32_IR, want_solution=False)
+    _, _, stf = mesh.fmg_solve(fn, ud, cycles=1, nu=2, mode=pkg.MODE_FP32_IR, want_solution=False)
+    u, p, st1 = mesh.solve(tol=1e-8 / stf.rel_residual, max_cycles=40, mode=pkg.MODE_FP32_IR)
+    assert st1.status == 0 and st1.cycles < st0.cycles, (st1.cycles, st0.cycles)
+    assert stf.rel_residual * st1.rel_residual <= 1e-8
+    H = MG.build_hierarchy(cube, level)
+    L = H.levels[level]
+    lat = lattice_index(L, mesh.dims())
+    f, g = L.rhs(fn[lat], ud[lat])
+    ref = MG.solve(H, f, g, tol=1e-12, max_cycles=60)
+    loose = MG.solve(H, f, g, tol=1e-8, max_cycles=40)
+    ut = L.scatter(ref.u, ud[lat])
+    assert rel_err(u[lat], ut) <= 10 * rel_err(L.scatter(loose.u, ud[lat]), ut) + 1e-9
+    assert rel_err(p[lat], ref.p) <= 10 * rel_err(loose.p, ref.p) + 1e-7
+    mesh.close()
