@@ -60,6 +60,9 @@ def macro_by_name(name):
         return W.slip_cube()
     if name == "sheared_slip":
         return W.sheared_slip_cube()
+    if name == "slip_obstacle":
+        # one free-slip obstacle cube inside a box of Dirichlet walls
+        return W.box_of_cubes(3, 3, 3, removed=((1, 1, 1),), slip_obstacles=True)
     if name == "partial":
         # two unit cubes with two Kuhn tetrahedra removed and one listed along
         # its reversed path: partially filled macro cells, irregular rows inside

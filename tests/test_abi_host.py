@@ -35,7 +35,8 @@ def test_exports_every_declared_symbol(pkg):
 
 @pytest.mark.parametrize("name,levels", [("cube", (0, 1, 2, 3)), ("channel", (0, 1, 2)), ("partial", (1, 2, 3)),
                                          ("sheared", (1, 2, 3)), ("slip_channel", (0, 1, 2)),
-                                         ("slip_cube", (1, 2, 3)), ("sheared_slip", (1, 2))])
+                                         ("slip_cube", (1, 2, 3)), ("sheared_slip", (1, 2)),
+                                         ("slip_obstacle", (1, 2))])
 def test_classification_matches_oracle(pkg, name, levels):
     macro = macro_by_name(name)
     affine = macro.basis is not None

@@ -352,3 +352,29 @@ def test_exact_state_on_sheared_slip_cube(form):
     assert np.abs(ru).max() <= 1e-13 * scale and np.abs(rp).max() <= 1e-13 * scale
     u, p = direct.solve_direct(L, f, g)
     assert np.abs(u - u_ex[L.free].T).max() <= 1e-9 and np.abs(p - p_ref).max() <= 1e-9 * np.abs(p_ref).max()
+
+
+def test_obstacle_edges_and_corners():
+    """One free-slip obstacle cube inside a box: at its 12 edges two face
+    planes meet and the node is constrained along the edge (projector t t^T,
+    t the edge's axis); at its 8 corners three meet and the node is
+    Dirichlet; its face nodes keep the mass-conservative normal, which there
+    is the face's axis."""
+    m = W.box_of_cubes(3, 3, 3, removed=((1, 1, 1),), slip_obstacles=True)
+    L = S.build_from_macro(m, 2)
+    x = L.mesh.xyz[L.free[L.slip]]
+    on_cube = lambda v: (np.abs(v - 1.0) < 1e-12) | (np.abs(v - 2.0) < 1e-12)   # noqa: E731
+    k = on_cube(x).sum(axis=1)   # coordinates on the cube's bounding planes
+    assert np.array_equal(L.slip_edge, k == 2) and len(x) == 6 * 3 * 3 + 12 * 3
+    diag = np.abs(np.einsum("naa->na", L.slip_P))
+    edge = np.where(L.slip_edge)[0]
+    t_axis = np.argmax(diag[edge], axis=1)
+    assert np.allclose(diag[edge].max(axis=1), 1.0)
+    assert not on_cube(x[edge, :])[np.arange(len(edge)), t_axis].any()   # t runs along the edge
+    face = np.where(~L.slip_edge)[0]
+    n_axis = np.argmax(np.abs(L.normals[face]), axis=1)
+    assert np.allclose(np.abs(L.normals[face]).max(axis=1), 1.0)
+    assert on_cube(x[face, :])[np.arange(len(face)), n_axis].all()   # the normal crosses the face
+    key = {tuple(np.rint(v).astype(int)) for v in L.mesh.xyz[L.dir]}
+    for c in np.ndindex(2, 2, 2):
+        assert (1 + c[0], 1 + c[1], 1 + c[2]) in key
