@@ -9,8 +9,9 @@ FP32-V-cycle-in-FP64-refinement mode (the headline); the plain FP64 solve is
 timed the same way and reported beside it, and the same pair is reported for
 the level-7 cube (8,291,838 free DoFs) under "level7" and the level-4 cube
 (15,038 free DoFs, latency-bound) under "level4".  "fmg" times full
-multigrid (Sec. 5) on the headline level, with its error ratio gamma, and
-the 1e-8 solve started from one FMG pass;
+multigrid (Sec. 5) on the headline level, with its error ratio gamma, its
+parallel textbook efficiency E_parTME (with and without the coarse-grid
+solves), and the 1e-8 solve started from one FMG pass;
 "channel_level6" times the obstacle channel (2.6e8 free DoFs) FP32+IR solve
 and "slip_channel_level6" the same channel with free-slip obstacles (Sec. 6.1);
 "dform_level7" the D-operator formulation beside the Laplace form.
@@ -323,9 +324,34 @@ class LevelBench:
         fmg["fmg_start_to_1e-8_fp32ir"] = {
             "ms": best, "value": self.world * self.dofs / (best / 1e3), "unit": "DoF/s",
             "fmg_rel_residual": info[0], "cycles_after_fmg": info[1], "rel_residual": info[2]}
+        fmg["parTME"] = self.partme(fmg)
         out_fmg = fmg
         del u_ref, p_ref
         return out, out_fmg
+
+    def partme(self, fmg, reps=10):
+        """Parallel textbook multigrid efficiency of the FMG runs (Sec. 5):
+        E_parTME = t n_c mu_sm / n = t / t_WU, the FMG time in work units.  One
+        work unit is one application of K to all n unknowns; with n_c = 1 GPU
+        its time t_WU is that of the finest-level residual kernel ((f, g) - K
+        (u, p)) in the precision of the FMG's V-cycles, so mu_sm = n / t_WU.
+        "wcg" leaves out the coarse-grid solves: one before the first level and
+        one per cycle, each timed alone on the coarsest level (the cycles run
+        it inside the cluster-resident kernel of the coarse levels)."""
+        lc, lf = self.mesh.coarsest, self.level
+        t_wu = {m: self.mesh.time_op(lf, "residual", precision=pr, reps=reps) for m, pr in (("fp64", 0), ("fp32ir", 1))}
+        t_cg = {m: self.mesh.time_op(lc, "coarse_solve", precision=pr, reps=reps)
+                for m, pr in (("fp64", 0), ("fp32ir", 1))}
+        out = {"work_unit": "one application of K on the finest level (the residual kernel), n_c = 1 GPU",
+               "t_WU_ms": t_wu, "mu_sm_lups": {m: self.dofs / (t / 1e3) for m, t in t_wu.items()},
+               "coarse_solve_ms": t_cg}
+        for key in ("V22_fp64", "2V22_fp64", "V22_fp32ir", "2V22_fp32ir"):
+            m = "fp64" if key.endswith("fp64") else "fp32ir"
+            cycles = 2 if key.startswith("2") else 1
+            t = fmg[key]["ms"]
+            t_coarse = t_cg["fp64"] + cycles * (lf - lc) * t_cg[m]
+            out[key] = {"E_parTME": t / t_wu[m], "E_parTME_wcg": (t - t_coarse) / t_wu[m]}
+        return out
 
     def close(self):
         self.mesh.close()

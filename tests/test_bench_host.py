@@ -69,3 +69,30 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("LOCAL_RANK", "1")
     bench.run_reference(argparse.Namespace(steps=1, warmup=0, level=9))
     assert capsys.readouterr().out == ""
+
+
+def test_partme_counts_work_units_and_coarse_solves():
+    """E_parTME = t n_c mu_sm / n (Sec. 5) with mu_sm = n / t_WU: the FMG time
+    in work units; without the coarse grid it leaves out one coarse solve
+    before the first level and one per cycle on each finer level."""
+    import bench
+
+    class FakeMesh:
+        coarsest = 2
+
+        def time_op(self, level, op, precision=0, reps=10):
+            return {("residual", 0): 4.0, ("residual", 1): 2.0,
+                    ("coarse_solve", 0): 1.0, ("coarse_solve", 1): 0.5}[(op, precision)]
+
+    lb = bench.LevelBench.__new__(bench.LevelBench)
+    lb.mesh, lb.level, lb.dofs = FakeMesh(), 9, 1000
+    fmg = {"V22_fp64": {"ms": 400.0}, "2V22_fp64": {"ms": 800.0},
+           "V22_fp32ir": {"ms": 200.0}, "2V22_fp32ir": {"ms": 300.0}}
+    r = lb.partme(fmg)
+    assert r["mu_sm_lups"]["fp64"] == pytest.approx(1000 / 4e-3)
+    assert r["V22_fp64"]["E_parTME"] == pytest.approx(100.0)
+    assert r["V22_fp64"]["E_parTME_wcg"] == pytest.approx((400.0 - 1.0 - 7 * 1.0) / 4.0)
+    assert r["2V22_fp64"]["E_parTME_wcg"] == pytest.approx((800.0 - 1.0 - 14 * 1.0) / 4.0)
+    # FP32 corrections: the first coarse solve is FP64, the cycles' are FP32
+    assert r["V22_fp32ir"]["E_parTME"] == pytest.approx(100.0)
+    assert r["2V22_fp32ir"]["E_parTME_wcg"] == pytest.approx((300.0 - 1.0 - 14 * 0.5) / 2.0)
