@@ -136,6 +136,10 @@ def _ptr(a):
     return a.data_ptr()  # torch.Tensor (host or device)
 
 
+def _is_tensor(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
 def _as_f64(a, shape=None):
     if a is None:
         return None
@@ -342,15 +346,24 @@ class Mesh:
         return out, _stats(st)
 
     # -- step-level hooks (parity tests) --
-    def level_field(self, level, field, precision=0, value=None):
-        """Read (value None) or write a field of one level; returns the read array."""
+    def level_field(self, level, field, precision=0, value=None, out=None):
+        """Read (value None) or write a field of one level, in lattice order.
+        value and out: float64 numpy arrays or contiguous float64 torch tensors
+        (host or device); a read goes into `out` if given, else into a new
+        numpy array, and returns it."""
         n = self.num_nodes(level)
         nc = 3 if field in ("U", "F", "RU") else 1
+        shape = (n, nc) if nc == 3 else (n,)
         if value is None:
-            buf = np.zeros((n, nc) if nc == 3 else n)
+            if out is None:
+                buf = np.zeros(shape)
+            else:
+                buf = _as_f64(out, shape)
+                if buf is not out:
+                    raise ValueError("out must be a contiguous float64 array")
             self._check(self._lib.hhg_level_field(self._h, level, precision, FIELD[field], 0, _ptr(buf)))
             return buf
-        buf = _as_f64(np.asarray(value), (n, nc) if nc == 3 else (n,))
+        buf = _as_f64(value if _is_tensor(value) else np.asarray(value), shape)
         self._check(self._lib.hhg_level_field(self._h, level, precision, FIELD[field], 1, _ptr(buf)))
         return None
 

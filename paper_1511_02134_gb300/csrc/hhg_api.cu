@@ -1547,6 +1547,9 @@ int hhg_level_field(hhg_mesh* M, int32_t level, int32_t precision, int32_t field
     } else {
       if ((rc = dalloc(M, (void**)&tmp, sizeof(double) * 3 * (size_t)H.nalloc))) return done(rc);
       M->device_bytes -= (int64_t)(sizeof(double) * 3 * (size_t)H.nalloc);
+      // the scatter writes lattice nodes only: the frame and row padding must
+      // reach the FP32 field as zeros, not as what the allocation held
+      cudaMemsetAsync(tmp, 0, sizeof(double) * 3 * (size_t)H.nalloc, M->stream);
       double* dst[3] = {tmp, tmp + H.nalloc, tmp + 2 * H.nalloc};
       launch_scatter(H.d64, stage, ncomp, dst, mask, M->stream);
       float* d32[3];
