@@ -18,7 +18,8 @@ cube, at one face and inside:
     residual in the windows;
   * the bench's solve: FP32+IR to 1e-8 from zero in 8 cycles.
 Tolerances as in test_gpu_parity.py: FP64 1e-12, FP32 steps 1e-5, the FP64
-residual stored in FP32 1e-6, relative to the window's maximum."""
+residual stored in FP32 1e-6, relative to the field's maximum over the
+sampled nodes (the window's, for the random states of the kernel tests)."""
 import numpy as np
 import pytest
 
@@ -112,16 +113,23 @@ def test_level9_rhs_and_bench_solve(pkg, torch, mesh, windows):
     del x
     F, G = _read(torch, mesh, LEVEL, "F", 0), _read(torch, mesh, LEVEL, "G", 0)
     assert abs(float(G.mean())) <= TOL64 * float(G.abs().max())
+    outs = []
     for w in windows[0]:
         fn = W.manufactured_forcing(w.coords)
         ud = np.where(w.on_cube_boundary[:, None], W.manufactured_velocity(w.coords), 0.0)
         fu, g = w.L.rhs(fn, ud)
-        gf, gg = _at(torch, w, F, G)
-        assert rel_err(gf[w.free], fu.T) < TOL64
+        outs.append((w, fu, g, *_at(torch, w, F, G)))
+    del F, G
+    # relative to the fields' maxima over the sampled nodes: the Dirichlet
+    # lift makes them largest next to the boundary, which the corner windows
+    # hold (inside the cube g is about 1e-9 of its maximum)
+    sf = max(np.abs(fu).max() for _, fu, _, _, _ in outs)
+    sg = max(np.abs(g[w.held_distance >= 1]).max() for w, _, g, _, _ in outs)
+    for w, fu, g, gf, gg in outs:
+        assert np.abs(gf[w.free] - fu.T).max() < TOL64 * sf
         rows = w.held_distance >= 1
         d = gg[rows] - g[rows]
-        assert np.abs(d - d.mean()).max() < TOL64 * np.abs(g[rows]).max()
-    del F, G
+        assert np.abs(d - d.mean()).max() < TOL64 * sg
     _, _, st = mesh.solve(tol=1e-8, max_cycles=50, mode=pkg.MODE_FP32_IR, want_solution=False)
     assert st.status == 0 and st.cycles == 8 and st.rel_residual <= 1e-8
 
