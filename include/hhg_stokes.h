@@ -24,8 +24,10 @@
  *     pointer.  Outputs are written to caller buffers of the documented size.
  *     All device memory is owned by the mesh and released by hhg_destroy.
  *   Streams: all device work of a mesh is ordered on the stream given to
- *     hhg_create_mesh (NULL = a stream the library creates).  Functions that
- *     return host data synchronise that stream.
+ *     hhg_create_mesh (NULL = a non-blocking stream the library creates,
+ *     which does not wait on the legacy default stream).  Device inputs must
+ *     be complete with respect to that stream when a call is made.
+ *     Functions that return host data synchronise that stream.
  *   Node order: nodal arrays cover the bounding-box lattice of a level,
  *     (n_x, n_y, n_z) nodes with n_a = cells_a * 2^level + 1, node (i,j,k)
  *     at flat index i + n_x (j + n_y k) (x fastest).  Vector fields are
