@@ -77,43 +77,79 @@ def macro_by_name(name):
 
 
 class LatticeWindow:
-    """A block of (2^wl + 1)^3 nodes of the unit cube's Kuhn lattice at
-    `level`, from lattice coordinates `origin`, assembled by the oracle: its
-    refinement of the unit cube at level wl (the same Kuhn lattice, which
-    is invariant under lattice translations), scaled to the spacing
-    2^-level and moved to the origin.  Every row of an interior node of the
-    window is the row of the whole cube at that node, so the oracle can
-    produce sampled outputs of levels it cannot assemble.
+    """A block of (2^wl + 1)^3 nodes of the Kuhn lattice at `level` of a box
+    of unit cubes (`domain`, a workloads.box_of_cubes mesh, default the unit
+    cube: obstacle cells removed, no-slip walls, optionally do-nothing
+    outflow on x = max), from lattice coordinates `origin`, assembled by
+    the oracle.  With the origin on multiples of 2^(wl-1) the block is
+    2 x 2 x 2 sub-cells, each inside one unit cube, and sub-cells inside an
+    obstacle are left out; otherwise it is one cell and must meet no
+    obstacle.  The oracle refines this small box of cubes (the same Kuhn
+    lattice, which is invariant under lattice translations) and scales and
+    moves it onto the block.  Every row of a
+    node off the block's faces is the row of the whole domain there, so the
+    oracle can produce sampled outputs of levels it cannot assemble.
 
-    The window's boundary nodes are Dirichlet nodes of its oracle level.
-    Where they lie on the cube's boundary they are Dirichlet nodes of the
-    cube too; elsewhere (the "held" faces) they stand for nodes whose rows
-    reach outside the window and keep the values they are given."""
+    The block's faces are Dirichlet faces of its oracle level, except an
+    outflow face of the domain.  Where they lie on the domain's walls or
+    obstacles they are Dirichlet faces of the domain too; elsewhere (the
+    "held" faces) they stand for nodes whose rows reach outside the block and
+    keep the values they are given."""
 
-    def __init__(self, level, origin, wl):
+    def __init__(self, level, origin, wl, domain=None):
+        import itertools
+
         from oracle import mesh as OM
         from oracle import stokes as S
-        cube = W.unit_cube()
-        m = OM.refine(cube.vertices, cube.tets, cube.bc_flags, wl)
-        scale = 2.0 ** (wl - level)
-        m.xyz = m.xyz * scale + np.asarray(origin, float) / (1 << level)
+        dom = W.unit_cube() if domain is None else domain
+        if np.any(dom.bc_flags == W.BC_SLIP):
+            raise NotImplementedError("windows of free-slip domains")
+        out_faces = dom.bc_flags == W.BC_OUTFLOW
+        has_outflow = bool(out_faces.any())
+        n_cell, width = 1 << level, 1 << wl
+        origin = np.asarray(origin, np.int64)
+        box = np.asarray(dom.cells, np.int64) * n_cell
+        end = origin + width
+        assert np.all(origin >= 0) and np.all(end <= box)
+        rset = set(tuple(c) for c in dom.removed)
+        if np.all(origin % (width // 2) == 0) and width // 2 <= n_cell:
+            k = 2   # 2 x 2 x 2 sub-cells, each inside one unit cube
+        else:
+            k = 1   # one cell: the block must meet no obstacle
+            lo, hi = origin // n_cell, (end - 1) // n_cell
+            assert not any(c in rset for c in itertools.product(*(range(a, b + 1) for a, b in zip(lo, hi))))
+        sub = width // k
+        removed = [c for c in itertools.product(range(k), repeat=3)
+                   if tuple(int(v) for v in (origin + sub * np.asarray(c)) // n_cell) in rset]
+        macro = W.box_of_cubes(k, k, k, removed=removed, outflow_x_max=has_outflow and end[0] == box[0])
+        m = OM.refine(macro.vertices, macro.tets, macro.bc_flags, wl - (k - 1))
+        m.ijk = m.key.copy()   # local lattice coordinates 0 .. 2^wl
+        scale = sub / float(n_cell)
+        m.xyz = m.xyz * scale + origin / float(n_cell)
         m.h = m.h * scale
-        self.level, self.wl = level, wl
-        self.origin = np.asarray(origin, np.int64)
+        self.level, self.wl, self.origin = level, wl, origin
         self.L = S.build_level(m)
         self.ijk = m.ijk
-        self.glob = m.ijk + self.origin
-        d = (1 << level) + 1
-        self.index = self.glob[:, 0] + d * (self.glob[:, 1] + d * self.glob[:, 2])
-        self.on_cube_boundary = ((self.glob == 0) | (self.glob == (1 << level))).any(axis=1)
-        self.coords = self.glob / float(1 << level)
-        n = 1 << wl
-        held = np.full(len(self.glob), np.iinfo(np.int64).max)
+        self.glob = m.ijk + origin
+        dims = box + 1
+        self.index = self.glob[:, 0] + dims[0] * (self.glob[:, 1] + dims[1] * self.glob[:, 2])
+        self.coords = self.glob / float(n_cell)
+        # velocity Dirichlet nodes of the domain: walls (and x = max without
+        # outflow) and the closed boxes of the obstacle cells
+        g = self.glob
+        wall = (g[:, 0] == 0) | (g[:, 1] == 0) | (g[:, 2] == 0) | (g[:, 1] == box[1]) | (g[:, 2] == box[2])
+        if not has_outflow:
+            wall |= g[:, 0] == box[0]
+        for c in rset:
+            lo = np.asarray(c) * n_cell
+            wall |= np.all((g >= lo) & (g <= lo + n_cell), axis=1)
+        self.dirichlet = wall
+        held = np.full(len(g), np.iinfo(np.int64).max)
         for a in range(3):
-            if self.origin[a] > 0:
+            if origin[a] > 0:
                 held = np.minimum(held, self.ijk[:, a])
-            if self.origin[a] + n < (1 << level):
-                held = np.minimum(held, n - self.ijk[:, a])
+            if end[a] < box[a]:
+                held = np.minimum(held, width - self.ijk[:, a])
         self.held_distance = held
 
     @property
