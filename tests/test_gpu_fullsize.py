@@ -78,8 +78,9 @@ def case(request, pkg):
 
 def _masks(torch, macro, level):
     """Velocity Dirichlet nodes (walls, x = max without outflow, obstacle
-    surfaces) and nodes inside obstacles (no unknowns), on the device, in
-    lattice order."""
+    surfaces) and inactive nodes (in no remaining cell: inside an obstacle,
+    or on a face or edge shared by obstacles only), on the device, in lattice
+    order."""
     n_cell = 1 << level
     dims = macro.lattice_dims(level)
     idx = torch.arange(int(np.prod(dims)), device="cuda")
@@ -90,21 +91,29 @@ def _masks(torch, macro, level):
     dirichlet = (g[0] == 0) | (g[1] == 0) | (g[2] == 0) | (g[1] == box[1]) | (g[2] == box[2])
     if not outflow:
         dirichlet |= g[0] == box[0]
-    inside = torch.zeros_like(dirichlet)
     for c in macro.removed:
         lo = [v * n_cell for v in c]
-        closed = (g[0] >= lo[0]) & (g[0] <= lo[0] + n_cell) & (g[1] >= lo[1]) & (g[1] <= lo[1] + n_cell) & \
-                 (g[2] >= lo[2]) & (g[2] <= lo[2] + n_cell)
-        dirichlet |= closed
-        inside |= (g[0] > lo[0]) & (g[0] < lo[0] + n_cell) & (g[1] > lo[1]) & (g[1] < lo[1] + n_cell) & \
-                  (g[2] > lo[2]) & (g[2] < lo[2] + n_cell)
-    return dirichlet, inside
+        dirichlet |= (g[0] >= lo[0]) & (g[0] <= lo[0] + n_cell) & (g[1] >= lo[1]) & (g[1] <= lo[1] + n_cell) & \
+                     (g[2] >= lo[2]) & (g[2] <= lo[2] + n_cell)
+    # a node is active when one of the (up to 8) cells whose closed box holds it is present
+    present = torch.zeros([c + 2 for c in macro.cells], dtype=torch.bool, device="cuda")
+    present[1:-1, 1:-1, 1:-1] = True
+    for c in macro.removed:
+        present[c[0] + 1, c[1] + 1, c[2] + 1] = False
+    cand = [((a - 1).clamp(min=0) // n_cell + 1, torch.minimum(a // n_cell, torch.full_like(a, e)) + 1)
+            for a, e in zip(g, macro.cells)]
+    active = torch.zeros_like(dirichlet)
+    for cx in cand[0]:
+        for cy in cand[1]:
+            for cz in cand[2]:
+                active |= present[cx, cy, cz]
+    return dirichlet, ~active
 
 
 def _state(torch, case, seed, fp32):
     """Seeded u, p, f, g of the finest level in lattice order (device,
     float64, rounded to FP32 values if fp32); u and f are zero on Dirichlet
-    nodes, all four inside obstacles."""
+    nodes, all four at inactive nodes."""
     n = case.mesh.num_nodes(case.level)
     gen = torch.Generator(device="cuda")
     gen.manual_seed(seed)
@@ -112,11 +121,11 @@ def _state(torch, case, seed, fp32):
     for shape in ((n, 3), (n,), (n, 3), (n,)):
         x = torch.randn(shape, generator=gen, device="cuda", dtype=torch.float64)
         out.append(x.float().double() if fp32 else x)
-    dirichlet, inside = _masks(torch, case.macro, case.level)
+    dirichlet, inactive = _masks(torch, case.macro, case.level)
     out[0][dirichlet] = 0.0
     out[2][dirichlet] = 0.0
-    out[1][inside] = 0.0
-    out[3][inside] = 0.0
+    out[1][inactive] = 0.0
+    out[3][inactive] = 0.0
     return out
 
 
@@ -128,9 +137,9 @@ def _coarse_state(torch, case, seed):
     gen.manual_seed(seed)
     u = torch.randn((n, 3), generator=gen, device="cuda", dtype=torch.float64).float().double()
     p = torch.randn((n,), generator=gen, device="cuda", dtype=torch.float64).float().double()
-    dirichlet, inside = _masks(torch, case.macro, level)
+    dirichlet, inactive = _masks(torch, case.macro, level)
     u[dirichlet] = 0.0
-    p[inside] = 0.0
+    p[inactive] = 0.0
     return u, p
 
 
