@@ -60,7 +60,9 @@ def pkg():
 
 @pytest.fixture(scope="module")
 def torch():
-    return pytest.importorskip("torch")
+    t = pytest.importorskip("torch")
+    yield t
+    t.cuda.empty_cache()   # the full-size states held tens of GB in torch's cache
 
 
 @pytest.fixture(scope="module", params=sorted(CASES))
