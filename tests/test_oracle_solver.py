@@ -215,3 +215,63 @@ def test_adjoint_gradient_matches_finite_differences():
         jm = adjoint.functional_direct(L, f0 - eps * d, uD, psi)
         fd = (jp - jm) / (2 * eps)
         assert fd == pytest.approx(float(np.sum(grad * d)), rel=1e-8)
+
+
+@pytest.mark.parametrize("macro_name,level", [("cube", 2), ("channel", 1)])
+def test_uzawa_step_equals_node_by_node_definition(macro_name, level):
+    """One Uzawa step (Sec. 3.3) against a node-by-node transcription of its
+    definition: the velocity takes a forward then a backward Gauss-Seidel
+    sweep on A (colours ascending, then descending; nodes of one colour by
+    index) with the right-hand side f - B^T p of the old pressure, then the
+    pressure one forward SOR sweep (omega = 0.3, colours ascending, as the
+    velocity's forward sweep) on C p = B u - g with the new velocity."""
+    macro = W.unit_cube() if macro_name == "cube" else W.obstacle_channel()
+    H = MG.build_hierarchy(macro, level, coarsest=level)
+    L = H.levels[level]
+    rng = np.random.default_rng(12)
+    u0, p0 = rng.standard_normal((3, L.n_u)), rng.standard_normal(L.n_p)
+    f, g = rng.standard_normal((3, L.n_u)), rng.standard_normal(L.n_p)
+    u, p = u0.copy(), p0.copy()
+    MG.uzawa_step(H, level, u, p, f, g)
+    A, C = L.A.toarray(), L.C.toarray()
+    B = [b.toarray() for b in L.B]
+    col = MG.colour_of(L)
+    cu = col[L.free]
+    ub, pb = u0.copy(), p0.copy()
+    for d in range(3):
+        rhs = f[d] - B[d].T @ p0
+        for order in ((0, 1, 2, 3), (3, 2, 1, 0)):
+            for c in order:
+                for i in np.where(cu == c)[0]:
+                    ub[d, i] += (rhs[i] - A[i] @ ub[d]) / A[i, i]
+    rhs_p = sum(B[d] @ ub[d] for d in range(3)) - g
+    for c in (0, 1, 2, 3):
+        for i in np.where(col == c)[0]:
+            pb[i] += 0.3 * (rhs_p[i] - C[i] @ pb) / C[i, i]
+    np.testing.assert_allclose(u, ub, rtol=0, atol=1e-13 * np.abs(ub).max())
+    np.testing.assert_allclose(p, pb, rtol=0, atol=1e-13 * np.abs(pb).max())
+
+
+def test_pure_dirichlet_rhs_is_made_consistent():
+    """With Dirichlet data of nonzero net flux (u_D = (x, 0, 0) on the cube's
+    boundary: the flux out is the integral of div u_D = 1) the raw pressure
+    right-hand side is not orthogonal to the null vector (0, 1) of the
+    symmetric K, so K x = b has no solution.  The right-hand side removes
+    that component: sum g = 0 (orthogonality in the Euclidean inner product,
+    the one in which range(K) is the complement of the kernel), the direct
+    solution then leaves a zero residual, and the multigrid converges."""
+    H = MG.build_hierarchy(W.unit_cube(), 3)
+    L = H.levels[3]
+    x = L.mesh.xyz
+    ud = np.zeros_like(x)
+    ud[:, 0] = x[:, 0]
+    f, g = L.rhs(None, ud)
+    assert abs(g.sum()) <= 1e-14 * np.abs(g).sum()
+    # the data's flux is not zero: the raw g had a mean of order h^2
+    raw = sum(L.ops.B[d][:, L.dir] @ ud[L.dir, d] for d in range(3))
+    assert abs(raw.sum()) > 1e-3 * np.abs(raw).sum()
+    u, p = direct.solve_direct(L, f, g)
+    ru, rp = L.residual(u, p, f, g)
+    assert L.norm(ru, rp) <= 1e-12 * L.norm(f, g)
+    res = MG.solve(H, f, g, tol=1e-10, max_cycles=40)
+    assert res.history[-1] <= 1e-10
