@@ -36,6 +36,10 @@ be reproduced without its source):
     restricted residual is projected with the coarse normals and the
     prolongated correction with the fine normals, so every level's iterate
     stays tangential at its own slip nodes.
+
+Parity unpinned: h_norm restates the mesh-dependent norm printed in Sec. 5
+and serves the reported gamma_l only; no pin distinguishes its weight h^2
+on the pressure from another power of h.
 """
 from __future__ import annotations
 
@@ -263,6 +267,25 @@ def coarse_solve(H: Hierarchy, f, g, history=None):
     return split(x)
 
 
+# --- transfers ------------------------------------------------------------------
+
+def restrict(H: Hierarchy, l: int, ru, rp):
+    """Right-hand side of the coarse correction equation from the residual of
+    level l: R = P^T for velocity and pressure (Sec. 3.5), the velocity
+    projected on the admissible subspace at the coarse free-slip nodes
+    (Sec. 6.1: the coarse correction is a constrained coarse velocity)."""
+    Lc = H.levels[l - 1]
+    return Lc.proj(np.stack([H.Pu[l].T @ ru[d] for d in range(3)])), H.P[l].T @ rp
+
+
+def prolong(H: Hierarchy, l: int, uc, pc):
+    """The coarse correction interpolated to level l by P, the velocity
+    projected on the admissible subspace at the fine free-slip nodes (where
+    the fine normals differ from the coarse ones, P uc is not tangential)."""
+    L = H.levels[l]
+    return L.proj(np.stack([H.Pu[l] @ uc[d] for d in range(3)])), H.P[l] @ pc
+
+
 # --- cycle and solve ----------------------------------------------------------
 
 def vcycle(H: Hierarchy, l: int, u, p, f, g, root: int | None = None, nu: int | None = None):
@@ -282,15 +305,14 @@ def vcycle(H: Hierarchy, l: int, u, p, f, g, root: int | None = None, nu: int | 
     H.count(l, "A", 1)
     H.count(l, "B", 2)
     H.count(l, "C", 1)
-    Pu, P = H.Pu[l], H.P[l]
     Lc = H.levels[l - 1]
-    fc = Lc.proj(np.stack([Pu.T @ ru[d] for d in range(3)]))
-    gc = P.T @ rp
+    fc, gc = restrict(H, l, ru, rp)
     uc = np.zeros((3, Lc.n_u))
     pc = np.zeros(Lc.n_p)
     vcycle(H, l - 1, uc, pc, fc, gc, root, nu)
-    u += L.proj(np.stack([Pu @ uc[d] for d in range(3)]))
-    p += P @ pc
+    du, dp = prolong(H, l, uc, pc)
+    u += du
+    p += dp
     for _ in range(smoothing_steps(H, l, False, root, nu)):
         uzawa_step(H, l, u, p, f, g)
     return u, p

@@ -378,3 +378,38 @@ def test_obstacle_edges_and_corners():
     key = {tuple(np.rint(v).astype(int)) for v in L.mesh.xyz[L.dir]}
     for c in np.ndindex(2, 2, 2):
         assert (1 + c[0], 1 + c[1], 1 + c[2]) in key
+
+
+@pytest.mark.parametrize("name,level", [("obstacle", 2), ("sheared", 2), ("channel", 2)])
+def test_transfers_keep_corrections_admissible(name, level):
+    """The transfer pair of the constrained problem: the restriction lands in
+    the coarse admissible space (tangent planes, edge directions at the
+    coarse free-slip nodes), the prolongation in the fine one, and on those
+    spaces each is the other's Euclidean adjoint, <prolong(e), r> =
+    <e, restrict(r)> for admissible e and r -- the coarse correction is a
+    constrained coarse velocity seen through P.  On the obstacle cube
+    (edges), the sheared cube (tilted faces) and the channel."""
+    macro = {"obstacle": lambda: W.box_of_cubes(3, 3, 3, removed=((1, 1, 1),), slip_obstacles=True),
+             "sheared": W.sheared_slip_cube, "channel": W.slip_channel}[name]()
+    H = MG.build_hierarchy(macro, level, coarsest=level - 1)
+    L, Lc = H.levels[level], H.levels[level - 1]
+    assert len(L.slip) and len(Lc.slip)
+    rng = np.random.default_rng(21)
+    r_any = rng.standard_normal((3, L.n_u))
+    rp = rng.standard_normal(L.n_p)
+    fc, gc = MG.restrict(H, level, r_any, rp)
+    np.testing.assert_allclose(Lc.proj(fc), fc, rtol=0, atol=1e-13 * np.abs(fc).max())
+    e = Lc.proj(rng.standard_normal((3, Lc.n_u)))
+    pc = rng.standard_normal(Lc.n_p)
+    du, dp = MG.prolong(H, level, e, pc)
+    np.testing.assert_allclose(L.proj(du), du, rtol=0, atol=1e-13 * np.abs(du).max())
+    r = L.proj(r_any)
+    fr, gr = MG.restrict(H, level, r, rp)
+    assert np.sum(du * r) == pytest.approx(np.sum(e * fr), rel=1e-12)
+    assert np.dot(dp, rp) == pytest.approx(np.dot(pc, gr), rel=1e-12)
+    # the coarse projection is not idle: P^T r of an admissible fine residual
+    # has normal parts at coarse slip nodes (from the free nodes next to
+    # them).  The fine one is on these polyhedral faces (fine and coarse
+    # normals agree, so P e is already admissible); it acts where they differ.
+    raw_c = np.stack([H.Pu[level].T @ r[d] for d in range(3)])
+    assert np.abs(Lc.proj(raw_c) - raw_c).max() > 1e-3 * np.abs(raw_c).max()

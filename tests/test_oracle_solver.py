@@ -275,3 +275,46 @@ def test_pure_dirichlet_rhs_is_made_consistent():
     assert L.norm(ru, rp) <= 1e-12 * L.norm(f, g)
     res = MG.solve(H, f, g, tol=1e-10, max_cycles=40)
     assert res.history[-1] <= 1e-10
+
+
+def test_cg_stops_at_the_relative_residual():
+    """The inner CG of the coarse solver stops at its first iterate with
+    ||b - A x|| <= rtol ||b|| (the relative residual tolerance of Sec. 3.7,
+    on the norm, not on its square)."""
+    L = S.build_from_macro(W.unit_cube(), 3)
+    b = np.random.default_rng(3).standard_normal(L.n_u)
+    nb = np.linalg.norm(b)
+
+    def run(k, rtol):
+        return krylov.cg(lambda v: L.A @ v, b, k, rtol)
+
+    for rtol in (1e-1, 1e-3):
+        x = run(500, rtol)
+        assert np.linalg.norm(b - L.A @ x) <= rtol * nb
+        first = next(k for k in range(1, 500) if np.linalg.norm(b - L.A @ run(k, 0.0)) <= rtol * nb)
+        np.testing.assert_allclose(x, run(first, 0.0), rtol=0, atol=1e-14 * np.abs(x).max())
+
+
+def test_coarse_solver_preconditioner():
+    """The coarse MINRES (Sec. 3.7) is preconditioned by diag(A^-1, M_l^-1):
+    the velocity block solved by the inner CG (per component in the Laplace
+    form), the pressure block the lumped mass.  With the inner CG run to
+    1e-14 its iterates are those of scipy's MINRES with that exact
+    preconditioner (the channel, whose outflow makes K non-singular)."""
+    H = MG.build_hierarchy(W.obstacle_channel(), 1, coarsest=1)
+    L = H.levels[1]
+    H.opt = MG.Options(coarse_minres_max=6, coarse_minres_rtol=0.0, coarse_cg_max=5000, coarse_cg_rtol=1e-14)
+    rng = np.random.default_rng(17)
+    f, g = rng.standard_normal((3, L.n_u)), rng.standard_normal(L.n_p)
+    u, p = MG.coarse_solve(H, f, g)
+    K = S.full_matrix(L)
+    lu = sla.splu(L.A.tocsc())
+    n = L.n_u
+
+    def minv(x):
+        return np.concatenate([lu.solve(x[d * n:(d + 1) * n]) for d in range(3)] + [x[3 * n:] / L.m])
+
+    M = sla.LinearOperator(K.shape, matvec=minv)
+    xs, _ = sla.minres(K, np.concatenate([f.ravel(), g]), M=M, maxiter=6, rtol=0.0)
+    x = np.concatenate([u.ravel(), p])
+    np.testing.assert_allclose(x, xs, rtol=0, atol=1e-9 * np.abs(xs).max())
