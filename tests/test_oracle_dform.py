@@ -146,3 +146,34 @@ def test_operator_count_ratio_matches_paper(golden):
     lap = 3 * oc["A"] + 3 * oc["B"] + oc["C"]
     dform = 3 * mu_d * oc["A"] + 3 * oc["B"] + oc["C"]
     assert dform / lap == pytest.approx(2.00, abs=0.005)
+
+
+@pytest.mark.parametrize("macro_name,level", [("cube", 2), ("channel", 1)])
+@pytest.mark.parametrize("form", ["laplace", "D"])
+def test_dirichlet_lift_from_the_bilinear_form(form, macro_name, level):
+    """The lift of the right-hand side (Sec. 2.1) is f_{i,a} = -a(w, phi_i e_a)
+    with w the interpolant of the Dirichlet data.  Computed here element by
+    element from the gradient of w, not from the assembled blocks:
+    a_1(w, phi_i e_a) = nu sum_T |T| (grad w grad phi_i)_a and
+    a_2(w, phi_i e_a) = 2 nu sum_T |T| (D(w) grad phi_i)_a, D(w) the
+    symmetric part of grad w (D(phi_i e_a) : D(w) = (D(w) grad phi_i)_a).
+    A_2 and its block transpose differ by a null Lagrangian, int (grad v :
+    grad w^T - div v div w), which vanishes for test functions that vanish on
+    the boundary: only rows of free boundary nodes (the channel's outflow
+    face) tell them apart, so the channel is checked beside the cube."""
+    macro = W.unit_cube() if macro_name == "cube" else W.obstacle_channel()
+    L = S.build_from_macro(macro, level, form=form)
+    x = L.mesh.xyz
+    ud = np.stack([np.sin(3 * x[:, 1]) + x[:, 0] ** 2, x[:, 2] * x[:, 0], np.cos(2 * x[:, 0] + x[:, 1])], axis=1)
+    w = np.zeros_like(ud)
+    w[L.dir] = ud[L.dir]
+    fu, _ = L.rhs(None, ud)
+    vol, grads = fem.element_geometry(x, L.mesh.tets)
+    gw = np.einsum("tmi,tmj->tij", w[L.mesh.tets], grads)   # (grad w)_ij = d_j w_i per element
+    Mt = 0.5 * (gw + np.transpose(gw, (0, 2, 1))) if form == "D" else gw
+    fac = 2.0 if form == "D" else 1.0
+    contrib = -fac * vol[:, None, None] * np.einsum("tij,tmj->tmi", Mt, grads)   # (nT, 4, 3)
+    ref = np.zeros_like(ud)
+    for m in range(4):
+        np.add.at(ref, L.mesh.tets[:, m], contrib[:, m])
+    np.testing.assert_allclose(fu.T, ref[L.free], rtol=0, atol=1e-13 * np.abs(ref[L.free]).max())

@@ -81,3 +81,27 @@ def test_fmg_reaches_discretisation_error():
     assert 0.95 <= g2 <= 1.05, g2
     assert g1 <= 1.25, g1
     assert r2.history[-1] < r1.history[-1] < 0.1
+
+
+@pytest.mark.parametrize("cycles", [1, 2])
+def test_fmg_work_is_the_tme_sum(cycles):
+    """The operator applications FMG makes (instrumented) against the terms
+    of the E_TME sum of Sec. 5: the stage rooted at level r smooths
+    nu + 2 (r - l) times before and after on level l and computes one
+    residual there, i.e. costs 2 (nu + 2 (r - l)) 13/10 + 1 work units of
+    level l, 8^(l - L) work units of the finest level L (one WU = 10 blocks:
+    3 for A, 3 for each of B and B^T, 1 for C; the coarse solves, the
+    transfers and FMG's interpolation are not counted, as in Sec. 5)."""
+    L, c, nu = 4, 1, 2
+    H = MG.build_hierarchy(W.unit_cube(), L, coarsest=c)
+    H.counts = {}
+    rhs, dird = {}, {}
+    for l, Lv in H.levels.items():
+        x = Lv.mesh.xyz
+        dird[l] = W.manufactured_velocity(x)
+        rhs[l] = Lv.rhs(W.manufactured_forcing(x), dird[l])
+    MG.fmg(H, rhs, dird, cycles=cycles, nu=nu)
+    counted = sum(8.0 ** (l - L) * (3 * k["A"] + 3 * k["B"] + k["C"]) / 10.0 for l, k in H.counts.items())
+    expected = cycles * sum(8.0 ** (l - L) * (2 * (nu + 2 * (r - l)) * 13.0 / 10.0 + 1.0)
+                            for r in range(c + 1, L + 1) for l in range(c + 1, r + 1))
+    assert counted == pytest.approx(expected, rel=1e-14)

@@ -116,3 +116,12 @@ def test_channel_obstacles():
     assert np.array_equal(m.on_outflow, on_x16 & ~rim)
     assert np.all(m.on_dirichlet[rim])
     assert m.on_outflow.sum() == 15 * 15
+
+
+def test_flag_zero_boundary_faces_are_dirichlet():
+    """Flag 0 (no condition given) on a boundary face means Dirichlet: the
+    cube with all flags 0 has the Dirichlet nodes of the cube with flags 1."""
+    cube = W.unit_cube()
+    a = M.refine(cube.vertices, cube.tets, np.zeros_like(cube.bc_flags), 2)
+    b = M.refine(cube.vertices, cube.tets, np.ones_like(cube.bc_flags), 2)
+    assert np.array_equal(a.on_dirichlet, b.on_dirichlet) and a.on_dirichlet.sum() == 5 ** 3 - 3 ** 3
