@@ -386,6 +386,24 @@ int hhg_lattice_classify(const double* macro_vertices, int64_t nv, const int32_t
                          int64_t nt, const uint8_t* bc_flags, int32_t level, int64_t dims[3],
                          uint8_t* flags);
 
+/* The saddle-point matrix K of `level` (the forms of Sec. 2.1: a_1 or, with
+ * opt->operator_form = 1, a_2; b; the PSPG term c_l; free-slip nodes
+ * constrained as in Sec. 6.1: Pi A Pi + (I - Pi), Pi B^T, B Pi), assembled on
+ * the host in CSR from the stencil classes and closed-form rows the kernels
+ * apply, with the level's scale factors (opt->nu, opt->delta; NULL =
+ * defaults).  No device is touched.  Unknowns: the free velocity nodes
+ * component by component, then the active pressure nodes, each in lattice
+ * order; rows in that order, the pressure rows being (B u - C p).
+ * sizes[0] receives the number of rows, sizes[1] of stored entries, sizes[2]
+ * of free velocity nodes; with kptr = NULL nothing else is written.  Else
+ * kptr (rows + 1), kcol and kval (entries), vnode (velocity nodes) and pnode
+ * (rows - 3 velocity nodes) receive the matrix and the lattice index of each
+ * unknown's node.  Errors: HHG_EINVAL, HHG_EMESH (hhg_last_error(NULL)). */
+int hhg_assemble_operator_host(const double* macro_vertices, int64_t nv, const int32_t* macro_tets,
+                               int64_t nt, const uint8_t* bc_flags, int32_t level, const hhg_options* opt,
+                               int64_t sizes[3], int32_t* kptr, int32_t* kcol, double* kval,
+                               int64_t* vnode, int64_t* pnode);
+
 #ifdef __cplusplus
 }
 #endif

@@ -807,6 +807,71 @@ int hhg_lattice_classify(const double* V, int64_t nv, const int32_t* T, int64_t 
   return HHG_OK;
 }
 
+int hhg_assemble_operator_host(const double* V, int64_t nv, const int32_t* T, int64_t nt, const uint8_t* bc,
+                               int32_t level, const hhg_options* opt, int64_t sizes[3], int32_t* kptr,
+                               int32_t* kcol, double* kval, int64_t* vnode, int64_t* pnode) {
+  if (!sizes || level < 0 || level > 12) {
+    g_create_error = "invalid level or sizes";
+    return HHG_EINVAL;
+  }
+  hhg_options o;
+  if (opt)
+    o = *opt;
+  else
+    hhg_default_options(&o);
+  if (o.nu <= 0 || o.delta <= 0 || (o.operator_form != 0 && o.operator_form != 1)) {
+    g_create_error = "invalid option";
+    return HHG_EINVAL;
+  }
+  MacroLattice m;
+  int rc = build_macro_lattice(V, nv, T, nt, bc, m, g_create_error);
+  if (rc) return rc;
+  const LevelShape sh = level_shape(m, level);
+  std::vector<uint8_t> flags(sh.n());
+  classify_nodes(m, level, flags.data());
+  std::vector<uint16_t> cls;
+  std::vector<double> table, table2;
+  std::vector<uint32_t> patterns;
+  std::string err;
+  int ncls = 0;
+  stencil_classes(m, level, flags.data(), cls, table, ncls, err, &patterns);
+  if (!err.empty()) {
+    g_create_error = err;
+    return HHG_EMESH;
+  }
+  if (o.operator_form == 1) stencil_classes_d(m, patterns, table2);
+  // the scale factors of the level, as hhg_create_mesh sets them
+  const double h = m.H / (double)(1 << level);
+  const double hT2 = std::pow(m.det * h * h * h / 6.0, 2.0 / 3.0);
+  const int64_t px = ((sh.nx + 2 + 15) / 16) * 16, pxy = px * (sh.ny + 2);
+  CoarseMatrix cm;
+  if ((rc = assemble_coarse(sh, px, pxy, flags.data(), cls.data(), table.data(), o.nu * h, o.delta * hT2 * h, h * h,
+                            h * h * h, cm, err, o.operator_form == 1 ? table2.data() : nullptr))) {
+    g_create_error = err;
+    return rc;
+  }
+  sizes[0] = (int64_t)cm.kptr.size() - 1;
+  sizes[1] = (int64_t)cm.kcol.size();
+  sizes[2] = cm.nv;
+  if (!kptr) return HHG_OK;
+  if (!kcol || !kval || !vnode || !pnode) {
+    g_create_error = "null output array";
+    return HHG_EINVAL;
+  }
+  std::copy(cm.kptr.begin(), cm.kptr.end(), kptr);
+  std::copy(cm.kcol.begin(), cm.kcol.end(), kcol);
+  std::copy(cm.kval.begin(), cm.kval.end(), kval);
+  // padded positions back to lattice indices
+  std::vector<int64_t> lat_of((size_t)pxy * (sh.nz + 2), -1);
+  for (int k = 0; k < sh.nz; ++k)
+    for (int j = 0; j < sh.ny; ++j)
+      for (int i = 0; i < sh.nx; ++i)
+        lat_of[pad_index(px, pxy, i, j, k)] = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
+  for (int32_t r = 0; r < cm.nv; ++r) vnode[r] = lat_of[cm.vidx[r]];
+  for (int32_t r = 0; r < cm.np; ++r) pnode[r] = lat_of[cm.pidx[r]];
+  return HHG_OK;
+}
+
 int hhg_create_mesh(const double* V, int64_t nv, const int32_t* T, int64_t nt, const uint8_t* bc,
                     int32_t finest, const hhg_options* opt, void* stream, hhg_mesh** out) {
   if (!out) return HHG_EINVAL;

@@ -1,7 +1,9 @@
 """C ABI checks that need no GPU: the library builds, loads and exports every
 function declared in include/hhg_stokes.h; the host-side lattice
-classification agrees with the oracle's refined mesh; bad macro meshes are
-rejected with error codes."""
+classification agrees with the oracle's refined mesh; the operator the
+kernels apply, assembled on the host from the same stencil classes and
+closed-form rows, equals the oracle's assembled K entry by entry; bad macro
+meshes are rejected with error codes."""
 import os
 import re
 
@@ -143,3 +145,39 @@ def test_binding_mirrors_header(pkg, tmp_path):
         assert int(got[cname]) == ctypes.sizeof(py), cname
         for pn, _ in py._fields_:
             assert int(got["%s.%s" % (cname, pn)]) == getattr(py, pn).offset, (cname, pn)
+
+
+@pytest.mark.parametrize("form", [0, 1])
+@pytest.mark.parametrize("name,level", [("cube", 2), ("channel", 1), ("partial", 2), ("sheared", 2),
+                                        ("slip_channel", 1), ("slip_cube", 2), ("sheared_slip", 2),
+                                        ("slip_obstacle", 2)])
+def test_host_operator_equals_oracle_matrix(pkg, name, level, form):
+    """K of a level from the stencil classes (boundary rows), the closed-form
+    rows (full-star nodes) and the scale factors the kernels use, against the
+    oracle's K assembled from element integrals (Sec. 2.1 forms; free slip
+    constrained as in Sec. 6.1), after matching the unknowns by their nodes:
+    each of the four blocks (A, B^T, B, -C) to 1e-12 of its largest entry."""
+    import scipy.sparse as sp
+    macro = macro_by_name(name)
+    kptr, kcol, kval, vnode, pnode = pkg.assemble_operator_host(macro.vertices, macro.tets, macro.bc_flags, level,
+                                                                operator_form=form)
+    L = S.build_from_macro(macro, level, form="D" if form else "laplace")
+    dims = macro.lattice_dims(level)
+    lat = L.mesh.ijk[:, 0] + dims[0] * (L.mesh.ijk[:, 1] + dims[1] * L.mesh.ijk[:, 2])
+    node_of = np.full(int(np.prod(dims)), -1)
+    node_of[lat] = np.arange(len(lat))
+    free_pos = np.full(L.n_p, -1)
+    free_pos[L.free] = np.arange(L.n_u)
+    nv, nu_ = len(vnode), L.n_u
+    assert nv == nu_ and len(pnode) == L.n_p
+    q = free_pos[node_of[vnode]]
+    assert np.all(q >= 0) and len(np.unique(q)) == nv
+    perm = np.concatenate([d * nu_ + q for d in range(3)] + [3 * nu_ + node_of[pnode]])
+    n = len(perm)
+    Kh = sp.csr_matrix((kval, kcol, kptr), shape=(n, n))
+    Ko = S.full_matrix(L).tocsr()[perm][:, perm]
+    for rs in (slice(0, 3 * nv), slice(3 * nv, n)):
+        for cs in (slice(0, 3 * nv), slice(3 * nv, n)):
+            ref = Ko[rs, cs]
+            diff = abs(Kh[rs, cs] - ref).max()
+            assert diff <= 1e-12 * abs(ref).max(), (name, form, rs, cs, diff, abs(ref).max())
