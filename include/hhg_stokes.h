@@ -398,11 +398,14 @@ int hhg_lattice_classify(const double* macro_vertices, int64_t nv, const int32_t
  * of free velocity nodes; with kptr = NULL nothing else is written.  Else
  * kptr (rows + 1), kcol and kval (entries), vnode (velocity nodes) and pnode
  * (rows - 3 velocity nodes) receive the matrix and the lattice index of each
- * unknown's node.  Errors: HHG_EINVAL, HHG_EMESH (hhg_last_error(NULL)). */
+ * unknown's node, and pmass (pressure nodes; NULL = not wanted) the lumped
+ * mass of each pressure unknown (the coarse solver's preconditioner and the
+ * weights of the pressure mean).  Errors: HHG_EINVAL, HHG_EMESH
+ * (hhg_last_error(NULL)). */
 int hhg_assemble_operator_host(const double* macro_vertices, int64_t nv, const int32_t* macro_tets,
                                int64_t nt, const uint8_t* bc_flags, int32_t level, const hhg_options* opt,
                                int64_t sizes[3], int32_t* kptr, int32_t* kcol, double* kval,
-                               int64_t* vnode, int64_t* pnode);
+                               int64_t* vnode, int64_t* pnode, double* pmass);
 
 #ifdef __cplusplus
 }

@@ -114,7 +114,7 @@ def load_library():
         "hhg_level_field": (I32, [P, I32, I32, I32, I32, P]),
         "hhg_level_op": (I32, [P, I32, I32, I32, I32]),
         "hhg_lattice_classify": (I32, [P, I64, P, I64, P, I32, P, P]),
-        "hhg_assemble_operator_host": (I32, [P, I64, P, I64, P, I32, P, P, P, P, P, P, P]),
+        "hhg_assemble_operator_host": (I32, [P, I64, P, I64, P, I32, P, P, P, P, P, P, P, P]),
         "hhg_time_op": (I32, [P, I32, I32, I32, I32, P]),
         "hhg_kernel_launches": (I32, [P, P]),
         "hhg_allocations": (I32, [P, P]),
@@ -187,9 +187,10 @@ def lattice_classify(vertices, tets, bc_flags, level: int):
 
 def assemble_operator_host(vertices, tets, bc_flags, level: int, options: Options | None = None, **opts):
     """Host-only CSR of the saddle-point matrix of a level as the kernels apply
-    it (hhg_assemble_operator_host): (kptr, kcol, kval, vnode, pnode), the
-    unknowns being the free velocity nodes (component by component), then the
-    active pressure nodes, with the lattice index of each unknown's node."""
+    it (hhg_assemble_operator_host): (kptr, kcol, kval, vnode, pnode, pmass),
+    the unknowns being the free velocity nodes (component by component), then
+    the active pressure nodes, with the lattice index of each unknown's node
+    and the lumped mass of each pressure unknown."""
     L = load_library()
     V, T, B = _macro_arrays(vertices, tets, bc_flags)
     o = default_options() if options is None else options
@@ -197,17 +198,19 @@ def assemble_operator_host(vertices, tets, bc_flags, level: int, options: Option
         setattr(o, k, v)
     sizes = np.zeros(3, np.int64)
     args = (_ptr(V), len(V), _ptr(T), len(T), _ptr(B), level, ctypes.byref(o), _ptr(sizes))
-    rc = L.hhg_assemble_operator_host(*args, None, None, None, None, None)
+    rc = L.hhg_assemble_operator_host(*args, None, None, None, None, None, None)
     if rc:
         raise HHGError(rc, L.hhg_last_error(None).decode())
     rows, nnz, nvel = (int(v) for v in sizes)
     kptr, kcol = np.zeros(rows + 1, np.int32), np.zeros(nnz, np.int32)
     kval = np.zeros(nnz)
     vnode, pnode = np.zeros(nvel, np.int64), np.zeros(rows - 3 * nvel, np.int64)
-    rc = L.hhg_assemble_operator_host(*args, _ptr(kptr), _ptr(kcol), _ptr(kval), _ptr(vnode), _ptr(pnode))
+    pmass = np.zeros(rows - 3 * nvel)
+    rc = L.hhg_assemble_operator_host(*args, _ptr(kptr), _ptr(kcol), _ptr(kval), _ptr(vnode), _ptr(pnode),
+                                      _ptr(pmass))
     if rc:
         raise HHGError(rc, L.hhg_last_error(None).decode())
-    return kptr, kcol, kval, vnode, pnode
+    return kptr, kcol, kval, vnode, pnode, pmass
 
 
 class Mesh:

@@ -809,7 +809,7 @@ int hhg_lattice_classify(const double* V, int64_t nv, const int32_t* T, int64_t 
 
 int hhg_assemble_operator_host(const double* V, int64_t nv, const int32_t* T, int64_t nt, const uint8_t* bc,
                                int32_t level, const hhg_options* opt, int64_t sizes[3], int32_t* kptr,
-                               int32_t* kcol, double* kval, int64_t* vnode, int64_t* pnode) {
+                               int32_t* kcol, double* kval, int64_t* vnode, int64_t* pnode, double* pmass) {
   if (!sizes || level < 0 || level > 12) {
     g_create_error = "invalid level or sizes";
     return HHG_EINVAL;
@@ -869,6 +869,7 @@ int hhg_assemble_operator_host(const double* V, int64_t nv, const int32_t* T, in
         lat_of[pad_index(px, pxy, i, j, k)] = i + (int64_t)sh.nx * (j + (int64_t)sh.ny * k);
   for (int32_t r = 0; r < cm.nv; ++r) vnode[r] = lat_of[cm.vidx[r]];
   for (int32_t r = 0; r < cm.np; ++r) pnode[r] = lat_of[cm.pidx[r]];
+  if (pmass) std::copy(cm.mass.begin(), cm.mass.end(), pmass);
   return HHG_OK;
 }
 

@@ -156,11 +156,12 @@ def test_host_operator_equals_oracle_matrix(pkg, name, level, form):
     rows (full-star nodes) and the scale factors the kernels use, against the
     oracle's K assembled from element integrals (Sec. 2.1 forms; free slip
     constrained as in Sec. 6.1), after matching the unknowns by their nodes:
-    each of the four blocks (A, B^T, B, -C) to 1e-12 of its largest entry."""
+    each of the four blocks (A, B^T, B, -C) to 1e-12 of its largest entry;
+    and the lumped pressure mass of the class tables against the oracle's."""
     import scipy.sparse as sp
     macro = macro_by_name(name)
-    kptr, kcol, kval, vnode, pnode = pkg.assemble_operator_host(macro.vertices, macro.tets, macro.bc_flags, level,
-                                                                operator_form=form)
+    kptr, kcol, kval, vnode, pnode, pmass = pkg.assemble_operator_host(macro.vertices, macro.tets, macro.bc_flags,
+                                                                       level, operator_form=form)
     L = S.build_from_macro(macro, level, form="D" if form else "laplace")
     dims = macro.lattice_dims(level)
     lat = L.mesh.ijk[:, 0] + dims[0] * (L.mesh.ijk[:, 1] + dims[1] * L.mesh.ijk[:, 2])
@@ -181,3 +182,4 @@ def test_host_operator_equals_oracle_matrix(pkg, name, level, form):
             ref = Ko[rs, cs]
             diff = abs(Kh[rs, cs] - ref).max()
             assert diff <= 1e-12 * abs(ref).max(), (name, form, rs, cs, diff, abs(ref).max())
+    np.testing.assert_allclose(pmass, L.m[node_of[pnode]], rtol=1e-13)
