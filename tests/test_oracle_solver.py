@@ -318,3 +318,28 @@ def test_coarse_solver_preconditioner():
     xs, _ = sla.minres(K, np.concatenate([f.ravel(), g]), M=M, maxiter=6, rtol=0.0)
     x = np.concatenate([u.ravel(), p])
     np.testing.assert_allclose(x, xs, rtol=0, atol=1e-9 * np.abs(xs).max())
+
+
+def test_minres_stops_at_the_relative_preconditioned_residual():
+    """The coarse MINRES stops at its first iterate whose residual, measured
+    in the preconditioner's inverse norm ||r||_{P^-1} = (r . P^-1 r)^(1/2)
+    (the norm MINRES minimises), is at most rtol times that of b (the
+    tolerance-driven coarse solve of Sec. 3.7)."""
+    rng = np.random.default_rng(4)
+    L = S.build_from_macro(W.unit_cube(), 2)
+    K = S.full_matrix(L)
+    K = K - sp.diags(np.r_[np.zeros(3 * L.n_u), 1e-3 * L.m])
+    dvec = np.r_[np.tile(L.A_diag, 3), L.m]
+    b = rng.standard_normal(K.shape[0])
+
+    def pnorm(r):
+        return float(np.sqrt(np.dot(r, r / dvec)))
+
+    def run(k, rtol):
+        return krylov.pminres(lambda v: K @ v, b, lambda v: v / dvec, k, rtol)
+
+    for rtol in (1e-1, 1e-3):
+        x = run(2000, rtol)
+        assert pnorm(b - K @ x) <= rtol * pnorm(b) * (1 + 1e-8)
+        first = next(k for k in range(1, 2000) if pnorm(b - K @ run(k, 0.0)) <= rtol * pnorm(b))
+        np.testing.assert_allclose(x, run(first, 0.0), rtol=0, atol=1e-12 * np.abs(x).max())
