@@ -552,6 +552,28 @@ def roofline_only(args):
     mesh.close()
 
 
+def fused_pass_only(args):
+    """Set up the cube of --level with the colour-fused FP32 passes on (levels
+    of at least 2^20 nodes), set the manufactured right-hand side, run fused
+    pass --fused-pass once and print its warm device time (the command the
+    fused-pass profile is taken with)."""
+    import torch
+    import paper_1511_02134_gb300 as pkg
+    import workloads as W
+    torch.cuda.set_device(0)
+    cube = W.unit_cube()
+    mesh = pkg.Mesh(cube.vertices, cube.tets, cube.bc_flags, args.level, fused_min_nodes=1 << 20)
+    x = mesh.node_coords()
+    mesh.set_rhs(W.manufactured_forcing(x), W.manufactured_velocity(x))
+    del x
+    op = "fused_pass%d" % args.fused_pass
+    mesh.level_op(args.level, op, precision=1)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernel": "k_uzawa_pass<%d>" % args.fused_pass, "level": args.level,
+                      "ms": mesh.time_op(args.level, op, precision=1, reps=3)}))
+    mesh.close()
+
+
 # ---- CPU oracle -----------------------------------------------------------------------------------
 
 def _cpu_model() -> str:
@@ -659,12 +681,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--roofline-only", action="store_true",
                     help="print only the roofline measurement of the dominant kernel")
+    ap.add_argument("--fused-pass", type=int, choices=[0, 1, 2], default=None,
+                    help="run and time one colour-fused FP32 pass on the cube of --level and exit")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     import __graft_entry__ as g
     g.build()
+    if args.fused_pass is not None:
+        fused_pass_only(args)
+        return
     if args.roofline_only:
         roofline_only(args)
         return
